@@ -1,0 +1,327 @@
+"""Benchmark of the belief-tensor propagation (Alg. 1 + the Eq. 9 normaliser) on one GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload office512] [--impl ours]
+
+One step = one propagation of the whole belief tensor (per-channel odometry shift, map mask,
+3-D Gaussian blur, map mask, edge normalisation, FP64 normaliser) driven by the workload's
+odometry stream.  The default workload is the 512 x 512 cell, 64-bin office plan in FP32
+(16.8 M cells).  Timing: W untimed warm-up steps, then exactly K steps, each bracketed by CUDA
+events on the session's stream, with L2 flushed (a 512 MiB device write) before every timed
+step; max over ranks.  N > 1 runs one independent session per rank (weak scaling, no data-path
+collective).  Rank 0 prints one JSON line.
+
+--impl reference times the FP64 CPU oracle on the host cores instead (each step a bounded
+sample of the same workload: a band of map rows, all bins), printing the same metric.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from synth import workloads  # noqa: E402
+
+METRIC = "belief cell-updates/s and p99 step latency, served BF16 vs plain FP32, 1 GB300"
+UNIT = "cell-updates/s"
+ELEM = {"f32": 4, "bf16": 2, "f16": 2}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--workload", default="office512")
+    ap.add_argument("--storage", default=None, help="override the workload's storage type")
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------- distributed
+
+def dist_init(n):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, ws: int) -> float:
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ----------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while the timed region runs."""
+
+    FIELDS = ("uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid: str | None):
+        self.uuid = uuid
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+            time.sleep(0.3)
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            time.sleep(0.1)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            if self.uuid and self.uuid not in f[0] and f[0] not in self.uuid:
+                continue
+            try:
+                rows.append((float(f[1]), float(f[2]), f[5:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i, v in enumerate(r) if v == "Active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ----------------------------------------------------------------------------- CPU oracle
+
+def oracle_band_rate(wl, occ, odom, budget_s: float, steps: int | None = None):
+    """Time the FP64 oracle's whole step (Filter.step) on a band of map rows (all bins).
+    Returns (cell-updates/s, seconds per step, rows, steps run)."""
+    from oracle import filter as F
+    H, W, K = wl["H"], wl["W"], wl["K"]
+    # cost model from a 16-row probe, then size the band to fit the budget
+    probe_rows = min(H, 16)
+    j0 = (H - probe_rows) // 2
+    f = F.Filter(occ[j0:j0 + probe_rows], K, wl["cell"], wl["sigma_xy_cells"], wl["sigma_theta_bins"])
+    t = time.perf_counter()
+    f.step(*odom[0])
+    per_row = (time.perf_counter() - t) / probe_rows
+    n_steps = steps if steps is not None else 2
+    rows = int(max(4, min(H, budget_s / max(n_steps, 1) / max(per_row, 1e-9))))
+    j0 = (H - rows) // 2
+    f = F.Filter(occ[j0:j0 + rows], K, wl["cell"], wl["sigma_xy_cells"], wl["sigma_theta_bins"])
+    times = []
+    for s in range(n_steps):
+        t = time.perf_counter()
+        f.step(*odom[s % len(odom)])
+        times.append(time.perf_counter() - t)
+    per_step = statistics.mean(times)
+    return rows * W * K / per_step, per_step, rows, n_steps, times
+
+
+# ----------------------------------------------------------------------------- arms
+
+def run_reference(args, wl, occ, walk, ws, rank):
+    if rank != 0:
+        return
+    K_, W_ = args.steps, args.warmup
+    budget = 150.0
+    rate, per_step, rows, n, times = oracle_band_rate(wl, occ, walk.odom, budget, steps=K_ + W_)
+    timed = times[W_:] if len(times) > W_ else times
+    sec = statistics.mean(timed)
+    cells = rows * wl["W"] * wl["K"]
+    value = cells / sec
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": K_, "warmup": W_, "ms_per_step": sec * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": config_of(wl, args, extra={"sample": f"oracle step on a {rows}-row band"}),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"FP64 oracle Filter.step on rows {rows} x {wl['W']} x "
+                                   f"{wl['K']} bins of the same map, {len(timed)} timed steps"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def config_of(wl, args, extra=None):
+    c = {"workload": wl["name"], "H": wl["H"], "W": wl["W"], "K": wl["K"], "cell_m": wl["cell"],
+         "storage": wl["storage"], "sigma_xy_cells": wl["sigma_xy_cells"],
+         "sigma_theta_bins": wl["sigma_theta_bins"], "global_batch": 1,
+         "parallelism": f"replicas{args.gpus}" if args.gpus > 1 else "single",
+         "l2": "flushed (512 MiB device write) before every timed step"}
+    if extra:
+        c.update(extra)
+    return c
+
+
+def run_ours(args, wl, occ, walk, ws, rank, local):
+    import torch
+
+    import paper_1910_00572_gb300 as loc
+    from paper_1910_00572_gb300 import build
+    build.build()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    storage = wl["storage"]
+    p = loc.loc_params_default(H=wl["H"], W=wl["W"], K=wl["K"], cell_m=wl["cell"],
+                               sigma_xy_cells=wl["sigma_xy_cells"],
+                               sigma_theta_bins=wl["sigma_theta_bins"], storage=storage,
+                               stream=loc.torch_stream())
+    h = loc.loc_create(occ, p)
+    odom = walk.odom
+    n_cells = wl["H"] * wl["W"] * wl["K"]
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    try:
+        for s in range(args.warmup):
+            loc.loc_step(h, *odom[s % len(odom)])
+        torch.cuda.synchronize()
+        barrier(ws)
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        uuid = None
+        try:
+            uuid = str(torch.cuda.get_device_properties(dev).uuid)
+        except Exception:
+            pass
+        with ClockSampler(uuid) as clk:
+            torch.cuda.synchronize()
+            for s in range(args.steps):
+                flush.zero_()
+                starts[s].record()
+                loc.loc_step(h, *odom[(args.warmup + s) % len(odom)])
+                ends[s].record()
+            torch.cuda.synchronize()
+        loc.loc_sync(h)
+        barrier(ws)
+        ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
+        total_s = max_over_ranks(sum(ms) / 1e3, ws)
+        per_step_s = total_s / args.steps
+        value = n_cells * ws / per_step_s
+        p50, p99 = float(np.percentile(ms, 50)), float(np.percentile(ms, 99))
+
+        # end to end through the C-ABI: odometry in, pose estimate (argmax) out, every step
+        n_e2e = min(args.steps, 1000)
+        e2e_t = 0.0
+        for s in range(n_e2e):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            loc.loc_step(h, *odom[s % len(odom)])
+            loc.loc_argmax(h)
+            e2e_t += time.perf_counter() - t
+        e2e_t = max_over_ranks(e2e_t, ws)
+        e2e_value = n_cells * ws * n_e2e / e2e_t
+        stats = loc.loc_stats(h)
+    finally:
+        loc.loc_destroy(h)
+
+    if rank != 0:
+        return
+    elem = ELEM[storage]
+    alg_bytes = n_cells * 2 * elem + wl["H"] * wl["W"] * (1 + 4)
+    achieved = alg_bytes / (statistics.mean(ms) / 1e3) / 1e9
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
+    peak = peaks.get("hbm_gbs", 6800.0)
+    cpu = None
+    if ws == 1 and not args.no_cpu_baseline:
+        rate, per_step, rows, n, _ = oracle_band_rate(wl, occ, odom, budget_s=15.0, steps=2)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"FP64 oracle Filter.step on a {rows}-row band ({rows} x {wl['W']} x "
+                         f"{wl['K']} cells) of the same map, mean of {n} steps, "
+                         f"{per_step:.2f} s/step"}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": per_step_s * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": storage, "data": "synthetic",
+        "config": config_of(wl, args),
+        "p50_step_ms": p50, "p99_step_ms": p99,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "kernel": "step (fused propagation + normaliser)",
+                     "algorithmic_bytes_per_launch": alg_bytes,
+                     "peak_source": "MEASURED_PEAKS.json hbm_gbs" if "hbm_gbs" in peaks else "fallback"},
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 16 * wl["K"],
+                "d2h_bytes_per_step": 12, "steps": n_e2e,
+                "path": "loc_step (odometry -> per-bin shift table in the launch parameters) + "
+                        "loc_argmax (pose estimate read back), host wall clock"},
+        "gpu_launches": args.steps,
+        "clocks": clk.summary(),
+        "last_Z": stats["last_Z"],
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_init(args.gpus)
+    wl = workloads.get(args.workload)
+    if args.storage:
+        wl["storage"] = args.storage
+    occ = workloads.make_map(wl)
+    walk = workloads.make_walk(wl, occ, seed_offset=rank)
+    if args.impl == "reference":
+        run_reference(args, wl, occ, walk, ws, rank)
+    else:
+        run_ours(args, wl, occ, walk, ws, rank, local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

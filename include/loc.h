@@ -1,0 +1,135 @@
+/* loc.h -- C-ABI of the GB300 belief-tensor localizer.
+ *
+ * Method: "Map as The Hidden Sensor: Fast Odometry-Based Global Localization"
+ * (Peng & Weikersdorfer, arXiv 1910.00572).  A dense belief tensor B[k][j][i] over the
+ * cells (j, i) of an occupancy map and K orientation bins is propagated by odometry
+ * (Section III-A, Algorithm 1), corrected by the map (Section III-A.3, Eq. 8), normalised
+ * (Eq. 9), and optionally reweighted by LIDAR on Floyd-Steinberg-selected samples
+ * (Section III-B).
+ *
+ * Conventions used by every entry point
+ *   - cell (j, i): row j (+y), column i (+x); the cell centre is ((i + 1/2) c, (j + 1/2) c) m.
+ *   - bin k: heading k * 2 pi / K + theta_t, where theta_t is the running sum of the w of
+ *     every odometry message (Section III-A).
+ *   - belief layout: [K][H][W] row-major (channel planes).
+ *   - occupancy map: uint8 [H][W] row-major, nonzero = occupied, 0 = free.
+ *   - odometry (u, v, w): relative pose between consecutive robot poses, (u, v) metres in
+ *     the robot frame at the earlier pose, w radians.
+ *
+ * Ownership and threading
+ *   - The caller owns every host array passed in; the library copies what it keeps
+ *     (the map at loc_create).  Readbacks copy into caller buffers and block until done.
+ *   - Device memory belongs to the handle.  It comes from the allocator registered with
+ *     loc_set_allocator (e.g. a framework's caching allocator), else cudaMalloc.
+ *   - All GPU work of a handle runs on the stream given in loc_params.stream (NULL: the
+ *     legacy default stream).  Calls that only enqueue work return before it finishes.
+ *   - A handle is not thread-safe; distinct handles are independent.
+ *
+ * Errors
+ *   - Every entry point returns a loc_status.  Arguments are validated before any state
+ *     changes (a call that fails with LOC_ERR_INVALID_ARG changed nothing).
+ *   - A CUDA error or a device-side failure makes the handle sticky-failed: every later call
+ *     returns LOC_ERR_STATE until loc_destroy.  loc_last_error(h) describes the failure.
+ */
+#ifndef LOC_H_
+#define LOC_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct loc_session* loc_handle;
+
+typedef enum {
+    LOC_OK = 0,
+    LOC_OK_DEFERRED = 1,       /* loc_step: the Alg. 1 gate was not reached; only theta_t
+                                  and the accumulated translation changed */
+    LOC_ERR_INVALID_ARG = -1,  /* bad pointer, size, non-finite value, or n mismatch */
+    LOC_ERR_OOM = -2,          /* device allocation failed */
+    LOC_ERR_CUDA = -3,         /* a CUDA runtime call failed */
+    LOC_ERR_TIMEOUT = -4,      /* a bounded device-side wait gave up */
+    LOC_ERR_STATE = -5         /* handle is sticky-failed or destroyed */
+} loc_status;
+
+enum { LOC_F32 = 0, LOC_BF16 = 1, LOC_F16 = 2 };   /* belief storage type */
+enum { LOC_MAP_SUM = 0, LOC_MAP_MAX = 1 };         /* loc_marginal modes */
+
+#define LOC_MAX_K 256          /* orientation bins per session */
+#define LOC_MAX_R_XY 4         /* x/y kernel radius */
+#define LOC_MAX_R_THETA 4      /* theta kernel radius */
+
+typedef struct {
+    int H, W, K;               /* grid rows, columns, orientation bins (K <= LOC_MAX_K) */
+    double cell_m;             /* cell size in metres */
+    double sigma_xy_cells;     /* motion-noise std-dev in x and y (cells), Eq. 5-6 */
+    double sigma_theta_bins;   /* motion-noise std-dev in theta (bins), Eq. 5-6 */
+    int r_xy, r_theta;         /* kernel radii; < 0 selects ceil(3 sigma) */
+    double min_shift_cells;    /* Alg. 1 gate |u_{t,k}| >= min_shift (cells); 0: always */
+    int storage;               /* LOC_F32 / LOC_BF16 / LOC_F16 */
+    int n_samples;             /* Floyd-Steinberg target sample count N_s (Section III-B.1) */
+    void* stream;              /* cudaStream_t for all work of the handle, or NULL */
+} loc_params;
+
+/* Fill *p with the defaults: sigma_xy 0.5 cells, sigma_theta 1 bin, radii ceil(3 sigma),
+ * min_shift 0, LOC_F32, n_samples 4096, NULL stream.  H, W, K, cell_m are set to 0. */
+void loc_params_default(loc_params* p);
+
+/* Optional device allocator for every later loc_create.  alloc(bytes, stream, ctx) returns
+ * a device pointer or NULL; release(ptr, stream, ctx) frees it.  Pass NULLs to go back to
+ * cudaMalloc/cudaFree.  Not thread-safe with concurrent loc_create/loc_destroy. */
+typedef void* (*loc_alloc_fn)(size_t bytes, void* stream, void* ctx);
+typedef void (*loc_free_fn)(void* ptr, void* stream, void* ctx);
+void loc_set_allocator(loc_alloc_fn alloc, loc_free_fn release, void* ctx);
+
+/* Create a session on the current CUDA device.  occ: host uint8 [H][W] (copied).
+ * The initial belief is uniform over free cells (Section III-A: the initial state is
+ * unknown).  Precomputes G(B_0)^-1 of Alg. 1 line 7 / Eq. 8 on the device.
+ * Errors: INVALID_ARG (sizes <= 0, K > LOC_MAX_K, radii above the maxima, cell_m <= 0,
+ * no free cell), OOM, CUDA.  On error *out is NULL. */
+loc_status loc_create(const uint8_t* occ, const loc_params* p, loc_handle* out);
+
+/* One odometry message (Section III-A, Eq. 2, Algorithm 1).  theta_t += w and the
+ * translation accumulates; when |accumulated| / cell >= min_shift the whole tensor is
+ * propagated on the device: per-channel bilinear shift (Eq. 3), map mask, 3-D Gaussian
+ * blur (Eq. 5-7), map mask, edge normalisation (Eq. 8), then the normaliser Z = sum B
+ * (Eq. 9) is reduced in FP64 and applied lazily.  If Z == 0 the belief restarts uniform
+ * over free cells (counted in loc_stats).  Returns LOC_OK (work enqueued, asynchronous) or
+ * LOC_OK_DEFERRED.  Errors: INVALID_ARG (non-finite input), STATE, CUDA. */
+loc_status loc_step(loc_handle h, double u, double v, double w);
+
+/* Readbacks (synchronous).  n must equal the element count exactly.
+ *   loc_belief:   normalised belief, host float[K][H][W].
+ *   loc_marginal: host float[H][W]: LOC_MAP_MAX = max over channels (the paper's belief
+ *                 map, Section III-A.3), LOC_MAP_SUM = sum over channels (marginal).
+ *   loc_argmax:   the most probable state (k, j, i) and its probability; ties go to the
+ *                 lowest linear index in [K][H][W] order. */
+loc_status loc_belief(loc_handle h, float* out, size_t n);
+loc_status loc_marginal(loc_handle h, float* out, size_t n, int mode);
+loc_status loc_argmax(loc_handle h, int* k, int* j, int* i, float* p);
+
+/* Replace the belief by host float[K][H][W] (non-negative, finite, positive sum); it is
+ * normalised on the device.  Synchronous.  Values on occupied cells are kept as given. */
+loc_status loc_set_belief(loc_handle h, const float* b, size_t n);
+
+/* Session scalars (synchronous): theta_t, the last normaliser Z, the running log-scale
+ * sum(log Z), the number of propagations and of restarts after Z == 0. */
+loc_status loc_stats(loc_handle h, double* theta_t, double* last_Z, double* logscale,
+                     long long* n_propagations, long long* n_reinit);
+
+/* Wait for all enqueued work of the handle; returns the first device-side error if any. */
+loc_status loc_sync(loc_handle h);
+
+/* Free the session (waits for its work).  h may be NULL. */
+loc_status loc_destroy(loc_handle h);
+
+/* Human-readable description of the last failure of h (or of the calling thread when h is
+ * NULL).  Valid until the next call on the same handle / thread. */
+const char* loc_last_error(loc_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LOC_H_ */

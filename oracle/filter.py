@@ -114,6 +114,51 @@ def propagate(B: np.ndarray, M: np.ndarray, corr: np.ndarray, shifts: np.ndarray
     return T * corr
 
 
+def propagate_at(B: np.ndarray, M: np.ndarray, shifts: np.ndarray, g: np.ndarray,
+                 idx) -> np.ndarray:
+    """Alg. 1 lines 3-7 (no normalisation) evaluated at the requested states only, each one
+    from the definitions: for output (k, j, i) on a free cell,
+        T = sum_{dk,dj,di} g[dk][dj][di] * M(j+dj, i+di) * AF(B, s)[(k+dk) mod K](j+dj, i+di)
+        G = sum_{dk,dj,di} g[dk][dj][di] * M(j+dj, i+di)           (G(B_0, k), Eq. 8)
+    and the result is T / G (0 on occupied cells).  AF is the bilinear pull of Eq. 3."""
+    K, H, W = B.shape
+    rk, r = g.shape[0] // 2, g.shape[1] // 2
+
+    def af(kk, jj, ii):
+        sx, sy = shifts[kk]
+        x, y = ii - sx, jj - sy
+        x0, y0 = math.floor(x), math.floor(y)
+        fx, fy = x - x0, y - y0
+        v = 0.0
+        for (dy, wy) in ((0, 1 - fy), (1, fy)):
+            for (dx, wx) in ((0, 1 - fx), (1, fx)):
+                yy, xx = y0 + dy, x0 + dx
+                if 0 <= yy < H and 0 <= xx < W:
+                    v += wy * wx * B[kk, yy, xx]
+        return v
+
+    out = np.zeros(len(idx))
+    for n, (k, j, i) in enumerate(idx):
+        if M[j, i] == 0:
+            continue
+        T = G = 0.0
+        for a in range(-rk, rk + 1):
+            kk = (k + a) % K
+            for b in range(-r, r + 1):
+                jj = j + b
+                if not 0 <= jj < H:
+                    continue
+                for c in range(-r, r + 1):
+                    ii = i + c
+                    if not 0 <= ii < W or M[jj, ii] == 0:
+                        continue
+                    w = g[a + rk, b + r, c + r]
+                    G += w
+                    T += w * af(kk, jj, ii)
+        out[n] = T / G
+    return out
+
+
 def normalise(B: np.ndarray, M: np.ndarray):
     """Eq. 9's eta: divide by Z = sum B.  Returns (B / Z, Z, reinit); Z == 0 restarts from
     the uniform belief over free cells."""

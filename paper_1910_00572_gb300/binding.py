@@ -1,0 +1,239 @@
+"""ctypes binding of the C-ABI in include/loc.h (argument marshalling only).
+
+Host arrays are numpy arrays; every step of the filter runs in the CUDA library.  Errors
+(negative loc_status) raise ``LocError`` with the library's message.  PyTorch is optional
+plumbing: ``torch_stream()`` passes torch's current CUDA stream to ``loc_create`` and
+``use_torch_allocator()`` makes the library take its device memory from torch's caching
+allocator.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+__all__ = [
+    "LOC_OK", "LOC_OK_DEFERRED", "LOC_ERR_INVALID_ARG", "LOC_ERR_OOM", "LOC_ERR_CUDA",
+    "LOC_ERR_TIMEOUT", "LOC_ERR_STATE", "LOC_F32", "LOC_BF16", "LOC_F16", "LOC_MAP_SUM",
+    "LOC_MAP_MAX", "LocError", "loc_params", "Handle", "library_path", "lib",
+    "loc_params_default", "loc_set_allocator", "loc_create", "loc_step", "loc_lidar_update",
+    "loc_lidar_update_cells", "loc_belief", "loc_marginal", "loc_argmax", "loc_set_belief",
+    "loc_stats", "loc_sync", "loc_destroy", "loc_last_error", "torch_stream",
+    "use_torch_allocator",
+]
+
+LOC_OK, LOC_OK_DEFERRED = 0, 1
+LOC_ERR_INVALID_ARG, LOC_ERR_OOM, LOC_ERR_CUDA, LOC_ERR_TIMEOUT, LOC_ERR_STATE = -1, -2, -3, -4, -5
+LOC_F32, LOC_BF16, LOC_F16 = 0, 1, 2
+LOC_MAP_SUM, LOC_MAP_MAX = 0, 1
+_STORAGE = {"f32": LOC_F32, "bf16": LOC_BF16, "f16": LOC_F16}
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def library_path() -> str:
+    return os.environ.get("LOC_LIBRARY", os.path.join(_HERE, "libloc.so"))
+
+
+class LocError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"loc status {status}: {msg}")
+        self.status = status
+
+
+class loc_params(ctypes.Structure):
+    _fields_ = [("H", ctypes.c_int), ("W", ctypes.c_int), ("K", ctypes.c_int),
+                ("cell_m", ctypes.c_double), ("sigma_xy_cells", ctypes.c_double),
+                ("sigma_theta_bins", ctypes.c_double), ("r_xy", ctypes.c_int),
+                ("r_theta", ctypes.c_int), ("min_shift_cells", ctypes.c_double),
+                ("storage", ctypes.c_int), ("n_samples", ctypes.c_int),
+                ("stream", ctypes.c_void_p)]
+
+
+_lib = None
+_P = ctypes.c_void_p
+_ALLOC = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+_FREE = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
+
+_SIGS = {
+    "loc_params_default": (None, [ctypes.POINTER(loc_params)]),
+    "loc_set_allocator": (None, [_ALLOC, _FREE, _P]),
+    "loc_create": (ctypes.c_int, [_P, ctypes.POINTER(loc_params), ctypes.POINTER(_P)]),
+    "loc_step": (ctypes.c_int, [_P, ctypes.c_double, ctypes.c_double, ctypes.c_double]),
+    "loc_lidar_update": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                        ctypes.c_double, ctypes.c_int, ctypes.c_double]),
+    "loc_lidar_update_cells": (ctypes.c_int, [_P, _P, ctypes.c_int, _P, ctypes.c_int,
+                                              ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                              ctypes.c_int, ctypes.c_double]),
+    "loc_belief": (ctypes.c_int, [_P, _P, ctypes.c_size_t]),
+    "loc_marginal": (ctypes.c_int, [_P, _P, ctypes.c_size_t, ctypes.c_int]),
+    "loc_argmax": (ctypes.c_int, [_P] + [ctypes.POINTER(ctypes.c_int)] * 3
+                   + [ctypes.POINTER(ctypes.c_float)]),
+    "loc_set_belief": (ctypes.c_int, [_P, _P, ctypes.c_size_t]),
+    "loc_stats": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double),
+                                 ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                 ctypes.POINTER(ctypes.c_longlong),
+                                 ctypes.POINTER(ctypes.c_longlong)]),
+    "loc_sync": (ctypes.c_int, [_P]),
+    "loc_destroy": (ctypes.c_int, [_P]),
+    "loc_last_error": (ctypes.c_char_p, [_P]),
+}
+
+
+def lib():
+    """The loaded CUDA library; raises if it was not built (no fallback exists)."""
+    global _lib
+    if _lib is None:
+        path = library_path()
+        if not os.path.exists(path):
+            raise RuntimeError(f"CUDA library {path} is missing: build it with "
+                               "`python -c 'import __graft_entry__ as g; g.build()'`")
+        L = ctypes.CDLL(path)
+        for name, (res, args) in _SIGS.items():
+            if hasattr(L, name):
+                f = getattr(L, name)
+                f.restype, f.argtypes = res, args
+        _lib = L
+    return _lib
+
+
+class Handle:
+    """A session handle plus the shape needed to size readback buffers."""
+
+    def __init__(self, ptr: int, H: int, W: int, K: int):
+        self.ptr, self.H, self.W, self.K = ptr, H, W, K
+
+    @property
+    def _as_parameter_(self):
+        return ctypes.c_void_p(self.ptr)
+
+
+def _check(h, status: int) -> int:
+    if status < 0:
+        ptr = h.ptr if isinstance(h, Handle) else None
+        msg = lib().loc_last_error(ptr)
+        raise LocError(status, msg.decode() if msg else "")
+    return status
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def loc_params_default(**kw) -> loc_params:
+    p = loc_params()
+    lib().loc_params_default(ctypes.byref(p))
+    for k, v in kw.items():
+        if k == "storage" and isinstance(v, str):
+            v = _STORAGE[v]
+        setattr(p, k, v)
+    return p
+
+
+_alloc_refs = []
+
+
+def loc_set_allocator(alloc, free, ctx=None) -> None:
+    """Register Python callables alloc(nbytes, stream) -> int and free(ptr, stream)."""
+    if alloc is None:
+        lib().loc_set_allocator(_ALLOC(0), _FREE(0), None)
+        _alloc_refs.clear()
+        return
+    a = _ALLOC(lambda n, s, c: alloc(int(n), s or 0))
+    f = _FREE(lambda p, s, c: free(p, s or 0))
+    _alloc_refs[:] = [a, f]
+    lib().loc_set_allocator(a, f, ctx)
+
+
+def use_torch_allocator() -> None:
+    """Take device memory from torch's caching allocator."""
+    import torch
+    loc_set_allocator(lambda n, s: torch.cuda.caching_allocator_alloc(n, stream=int(s)),
+                      lambda p, s: torch.cuda.caching_allocator_delete(p))
+
+
+def torch_stream() -> int:
+    import torch
+    return int(torch.cuda.current_stream().cuda_stream)
+
+
+def loc_create(occ: np.ndarray, params: loc_params) -> Handle:
+    occ = np.ascontiguousarray(occ, dtype=np.uint8)
+    if occ.shape != (params.H, params.W):
+        raise ValueError(f"map shape {occ.shape} != ({params.H}, {params.W})")
+    out = ctypes.c_void_p()
+    _check(None, lib().loc_create(_ptr(occ), ctypes.byref(params), ctypes.byref(out)))
+    return Handle(out.value, params.H, params.W, params.K)
+
+
+def loc_step(h: Handle, u: float, v: float, w: float) -> int:
+    return _check(h, lib().loc_step(h, float(u), float(v), float(w)))
+
+
+def loc_lidar_update(h: Handle, ranges: np.ndarray, angle_min: float, angle_inc: float,
+                     r_max: float, beam_stride: int, sigma_r: float) -> int:
+    z = np.ascontiguousarray(ranges, dtype=np.float32)
+    return _check(h, lib().loc_lidar_update(h, _ptr(z), int(z.size), float(angle_min),
+                                            float(angle_inc), float(r_max), int(beam_stride),
+                                            float(sigma_r)))
+
+
+def loc_lidar_update_cells(h: Handle, cells: np.ndarray, ranges: np.ndarray, angle_min: float,
+                           angle_inc: float, r_max: float, beam_stride: int,
+                           sigma_r: float) -> int:
+    c = np.ascontiguousarray(cells, dtype=np.int32)
+    z = np.ascontiguousarray(ranges, dtype=np.float32)
+    return _check(h, lib().loc_lidar_update_cells(h, _ptr(c), int(c.size), _ptr(z), int(z.size),
+                                                  float(angle_min), float(angle_inc),
+                                                  float(r_max), int(beam_stride), float(sigma_r)))
+
+
+def loc_belief(h: Handle, out: np.ndarray | None = None) -> np.ndarray:
+    if out is None:
+        out = np.empty((h.K, h.H, h.W), np.float32)
+    _check(h, lib().loc_belief(h, _ptr(out), out.size))
+    return out
+
+
+def loc_marginal(h: Handle, mode: int = LOC_MAP_MAX, out: np.ndarray | None = None) -> np.ndarray:
+    if out is None:
+        out = np.empty((h.H, h.W), np.float32)
+    _check(h, lib().loc_marginal(h, _ptr(out), out.size, int(mode)))
+    return out
+
+
+def loc_argmax(h: Handle):
+    k, j, i, p = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_float()
+    _check(h, lib().loc_argmax(h, ctypes.byref(k), ctypes.byref(j), ctypes.byref(i),
+                               ctypes.byref(p)))
+    return k.value, j.value, i.value, p.value
+
+
+def loc_set_belief(h: Handle, b: np.ndarray) -> None:
+    b = np.ascontiguousarray(b, dtype=np.float32)
+    _check(h, lib().loc_set_belief(h, _ptr(b), b.size))
+
+
+def loc_stats(h: Handle) -> dict:
+    th, z, ls = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    npro, nre = ctypes.c_longlong(), ctypes.c_longlong()
+    _check(h, lib().loc_stats(h, ctypes.byref(th), ctypes.byref(z), ctypes.byref(ls),
+                              ctypes.byref(npro), ctypes.byref(nre)))
+    return dict(theta=th.value, last_Z=z.value, logscale=ls.value, n_propagations=npro.value,
+                n_reinit=nre.value)
+
+
+def loc_sync(h: Handle) -> None:
+    _check(h, lib().loc_sync(h))
+
+
+def loc_destroy(h: Handle) -> None:
+    if h is not None and h.ptr:
+        lib().loc_destroy(h)
+        h.ptr = None
+
+
+def loc_last_error(h: Handle | None = None) -> str:
+    m = lib().loc_last_error(h.ptr if h is not None else None)
+    return m.decode() if m else ""

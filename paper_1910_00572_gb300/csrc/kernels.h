@@ -1,0 +1,47 @@
+// Host-side launchers of the localizer's kernels (internal to the library).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "loc_dev.cuh"
+
+namespace loc {
+
+// Tile of the generic step kernel (output cells per CTA).
+constexpr int kGenTH = 16, kGenTW = 32;
+
+// One propagation of Alg. 1 + the Eq. 9 sum.  `storage` is LOC_F32/LOC_BF16/LOC_F16.
+// `partials` must hold step_num_blocks(H, W) doubles.
+cudaError_t launch_step(const StepArgs& a, int storage, cudaStream_t st);
+unsigned int step_num_blocks(int H, int W);
+
+// corr[j][i] = trav ? 1 / G(M)(j, i) : 0 with G(M) the x/y blur of M by gx (Eq. 8).
+cudaError_t launch_edge_correction(const uint8_t* trav, float* corr, int H, int W,
+                                   const float* gx, int r, cudaStream_t st);
+
+// Normalised belief as FP32 [K][H][W].
+cudaError_t launch_read_belief(const void* B, int storage, const uint8_t* trav,
+                               const SessionDev* sd, float inv_uniform, int H, int W, int K,
+                               float* out, cudaStream_t st);
+
+// Belief map over channels: mode LOC_MAP_SUM or LOC_MAP_MAX, FP32 [H][W].
+cudaError_t launch_read_marginal(const void* B, int storage, const uint8_t* trav,
+                                 const SessionDev* sd, float inv_uniform, int H, int W, int K,
+                                 int mode, float* out, cudaStream_t st);
+
+// Argmax of the stored tensor: per-CTA (value, index) pairs then a final pass writing
+// out_idx[0] (linear index) and out_val[0] (normalised value).  `scratch` holds
+// argmax_scratch_len(n) float + int pairs.
+size_t argmax_scratch_bytes(size_t n);
+cudaError_t launch_argmax(const void* B, int storage, const uint8_t* trav,
+                          const SessionDev* sd, float inv_uniform, int H, int W, int K,
+                          void* scratch, long long* out_idx, float* out_val, cudaStream_t st);
+
+// Convert FP32 [K][H][W] to the storage type and set Z = sum of the stored values
+// (reinit cleared, logscale unchanged).
+cudaError_t launch_set_belief(const float* src, void* B, int storage, size_t n,
+                              SessionDev* sd, double* partials, unsigned int nparts,
+                              cudaStream_t st);
+
+}  // namespace loc

@@ -1,0 +1,221 @@
+// Create-time and readback kernels: the edge-normalisation field of Eq. 8, the normalised
+// belief, the belief map (max or sum over channels, Section III-A.3), the argmax estimate,
+// and loading a caller-given belief.
+#include <cfloat>
+#include <climits>
+
+#include "kernels.h"
+
+namespace loc {
+namespace {
+
+constexpr int NT = 256;
+
+// Eq. 8: G(B_0, k) for the binary free-space tensor is the x/y blur of M (the theta taps of
+// a theta-constant tensor sum to 1); corr = 1 / G on free cells, 0 on occupied cells.
+__global__ void edge_correction_kernel(const uint8_t* __restrict__ trav, float* __restrict__ corr,
+                                       int H, int W, const __grid_constant__ StepArgs g) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y;
+    if (i >= W) return;
+    const int r = g.r_xy;
+    float G = 0.0f;
+    for (int dj = -r; dj <= r; ++dj) {
+        const int jj = j + dj;
+        if (jj < 0 || jj >= H) continue;
+        float row = 0.0f;
+        for (int di = -r; di <= r; ++di) {
+            const int ii = i + di;
+            if (ii >= 0 && ii < W) row += g.gx[di + r] * (float)trav[(size_t)jj * W + ii];
+        }
+        G += g.gx[dj + r] * row;
+    }
+    const size_t o = (size_t)j * W + i;
+    corr[o] = (trav[o] && G > 0.0f) ? 1.0f / G : 0.0f;
+}
+
+template <typename T>
+__device__ __forceinline__ float belief_at(const T* B, const uint8_t* trav, size_t hw, size_t q,
+                                           int reinit, float inv_uniform, float scale) {
+    return reinit ? (float)trav[q % hw] * inv_uniform : Store<T>::ld(B + q) * scale;
+}
+
+template <typename T>
+__global__ void read_belief_kernel(const T* __restrict__ B, const uint8_t* __restrict__ trav,
+                                   const SessionDev* sd, float inv_uniform, size_t hw, size_t n,
+                                   float* __restrict__ out) {
+    const int reinit = sd->reinit;
+    const float scale = (float)(1.0 / sd->Z);
+    for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < n;
+         q += (size_t)gridDim.x * blockDim.x)
+        out[q] = belief_at(B, trav, hw, q, reinit, inv_uniform, scale);
+}
+
+template <typename T>
+__global__ void read_marginal_kernel(const T* __restrict__ B, const uint8_t* __restrict__ trav,
+                                     const SessionDev* sd, float inv_uniform, size_t hw, int K,
+                                     int mode, float* __restrict__ out) {
+    const int reinit = sd->reinit;
+    const float scale = (float)(1.0 / sd->Z);
+    for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < hw;
+         q += (size_t)gridDim.x * blockDim.x) {
+        float acc = 0.0f;                       // beliefs are non-negative
+        for (int k = 0; k < K; ++k) {
+            const float v = belief_at(B, trav, hw, (size_t)k * hw + q, reinit, inv_uniform, scale);
+            acc = mode == LOC_MAP_MAX ? fmaxf(acc, v) : acc + v;
+        }
+        out[q] = acc;
+    }
+}
+
+// (value, index) order: larger value first, then lower index.
+__device__ __forceinline__ bool better(float v, long long i, float bv, long long bi) {
+    return v > bv || (v == bv && i < bi);
+}
+
+template <typename T>
+__global__ void argmax_partial_kernel(const T* __restrict__ B, const uint8_t* __restrict__ trav,
+                                      const SessionDev* sd, float inv_uniform, size_t hw, size_t n,
+                                      float* __restrict__ pv, long long* __restrict__ pi) {
+    __shared__ float sv[NT];
+    __shared__ long long si[NT];
+    const int reinit = sd->reinit;
+    float bv = -FLT_MAX;
+    long long bi = (long long)n;
+    for (size_t q = (size_t)blockIdx.x * NT + threadIdx.x; q < n; q += (size_t)gridDim.x * NT) {
+        const float v = belief_at(B, trav, hw, q, reinit, inv_uniform, 1.0f);
+        if (better(v, (long long)q, bv, bi)) { bv = v; bi = (long long)q; }
+    }
+    sv[threadIdx.x] = bv;
+    si[threadIdx.x] = bi;
+    __syncthreads();
+    for (int s = NT / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s && better(sv[threadIdx.x + s], si[threadIdx.x + s], sv[threadIdx.x], si[threadIdx.x])) {
+            sv[threadIdx.x] = sv[threadIdx.x + s];
+            si[threadIdx.x] = si[threadIdx.x + s];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        pv[blockIdx.x] = sv[0];
+        pi[blockIdx.x] = si[0];
+    }
+}
+
+__global__ void argmax_final_kernel(const float* __restrict__ pv, const long long* __restrict__ pi,
+                                    int nb, const SessionDev* sd, long long* out_idx,
+                                    float* out_val) {
+    __shared__ float sv[NT];
+    __shared__ long long si[NT];
+    float bv = -FLT_MAX;
+    long long bi = LLONG_MAX;
+    for (int b = threadIdx.x; b < nb; b += NT)
+        if (better(pv[b], pi[b], bv, bi)) { bv = pv[b]; bi = pi[b]; }
+    sv[threadIdx.x] = bv;
+    si[threadIdx.x] = bi;
+    __syncthreads();
+    for (int s = NT / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s && better(sv[threadIdx.x + s], si[threadIdx.x + s], sv[threadIdx.x], si[threadIdx.x])) {
+            sv[threadIdx.x] = sv[threadIdx.x + s];
+            si[threadIdx.x] = si[threadIdx.x + s];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        *out_idx = si[0];
+        *out_val = sd->reinit ? sv[0] : (float)((double)sv[0] / sd->Z);
+    }
+}
+
+template <typename T>
+__global__ void set_belief_kernel(const float* __restrict__ src, T* __restrict__ B, size_t n,
+                                  SessionDev* sd, double* partials) {
+    __shared__ double red[NT / 32];
+    float part = 0.0f;
+    double acc = 0.0;
+    int cnt = 0;
+    for (size_t q = (size_t)blockIdx.x * NT + threadIdx.x; q < n; q += (size_t)gridDim.x * NT) {
+        part += Store<T>::st(B + q, src[q]);
+        if (++cnt == 64) { acc += (double)part; part = 0.0f; cnt = 0; }
+    }
+    acc += (double)part;
+    const double bt = block_sum<NT>(acc, red);
+    finish_sum<NT>(bt, partials, &sd->counter, gridDim.x, red, [sd](double Z) {
+        sd->Z = Z;
+        sd->reinit = 0;
+    });
+}
+
+constexpr int kArgmaxBlocks = 1024;
+
+}  // namespace
+
+cudaError_t launch_edge_correction(const uint8_t* trav, float* corr, int H, int W,
+                                   const float* gx, int r, cudaStream_t st) {
+    StepArgs g{};
+    g.r_xy = r;
+    for (int d = 0; d < 2 * r + 1; ++d) g.gx[d] = gx[d];
+    dim3 grid((W + NT - 1) / NT, H);
+    edge_correction_kernel<<<grid, NT, 0, st>>>(trav, corr, H, W, g);
+    return cudaGetLastError();
+}
+
+#define LOC_DISPATCH(storage, CALL)                                                   \
+    switch (storage) {                                                                \
+        case LOC_F32: { using T = float; CALL; } break;                               \
+        case LOC_BF16: { using T = __nv_bfloat16; CALL; } break;                      \
+        case LOC_F16: { using T = __half; CALL; } break;                              \
+        default: return cudaErrorInvalidValue;                                        \
+    }
+
+static unsigned int grid_for(size_t n) {
+    size_t b = (n + NT - 1) / NT;
+    return (unsigned int)(b < 4096 ? (b > 0 ? b : 1) : 4096);
+}
+
+cudaError_t launch_read_belief(const void* B, int storage, const uint8_t* trav,
+                               const SessionDev* sd, float inv_uniform, int H, int W, int K,
+                               float* out, cudaStream_t st) {
+    const size_t hw = (size_t)H * W, n = hw * K;
+    LOC_DISPATCH(storage, (read_belief_kernel<T><<<grid_for(n), NT, 0, st>>>(
+                              (const T*)B, trav, sd, inv_uniform, hw, n, out)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_read_marginal(const void* B, int storage, const uint8_t* trav,
+                                 const SessionDev* sd, float inv_uniform, int H, int W, int K,
+                                 int mode, float* out, cudaStream_t st) {
+    const size_t hw = (size_t)H * W;
+    LOC_DISPATCH(storage, (read_marginal_kernel<T><<<grid_for(hw), NT, 0, st>>>(
+                              (const T*)B, trav, sd, inv_uniform, hw, K, mode, out)));
+    return cudaGetLastError();
+}
+
+size_t argmax_scratch_bytes(size_t) {
+    return (size_t)kArgmaxBlocks * (sizeof(float) + sizeof(long long));
+}
+
+cudaError_t launch_argmax(const void* B, int storage, const uint8_t* trav,
+                          const SessionDev* sd, float inv_uniform, int H, int W, int K,
+                          void* scratch, long long* out_idx, float* out_val, cudaStream_t st) {
+    const size_t hw = (size_t)H * W, n = hw * K;
+    long long* pi = (long long*)scratch;
+    float* pv = (float*)(pi + kArgmaxBlocks);
+    unsigned int nb = grid_for(n);
+    if (nb > kArgmaxBlocks) nb = kArgmaxBlocks;
+    LOC_DISPATCH(storage, (argmax_partial_kernel<T><<<nb, NT, 0, st>>>(
+                              (const T*)B, trav, sd, inv_uniform, hw, n, pv, pi)));
+    argmax_final_kernel<<<1, NT, 0, st>>>(pv, pi, (int)nb, sd, out_idx, out_val);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_set_belief(const float* src, void* B, int storage, size_t n,
+                              SessionDev* sd, double* partials, unsigned int nparts,
+                              cudaStream_t st) {
+    unsigned int nb = grid_for(n);
+    if (nb > nparts) nb = nparts;
+    LOC_DISPATCH(storage, (set_belief_kernel<T><<<nb, NT, 0, st>>>(src, (T*)B, n, sd, partials)));
+    return cudaGetLastError();
+}
+
+}  // namespace loc

@@ -1,0 +1,57 @@
+"""The C-ABI library loads on a machine without a GPU and exports every function that the
+headers in include/ declare (no compute calls here)."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = open(h).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", "", src)
+        for m in re.finditer(r"^[A-Za-z_][\w \*]*?\b(loc_\w+)\s*\(", src, flags=re.M):
+            if "typedef" not in m.group(0) and "(*" not in m.group(0):
+                names.add(m.group(1))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def libloc():
+    from paper_1910_00572_gb300 import build
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def test_headers_declare_the_session_api():
+    names = declared_functions()
+    for n in ("loc_create", "loc_step", "loc_belief", "loc_marginal", "loc_destroy"):
+        assert n in names
+
+
+def test_library_exports_every_declared_function(libloc):
+    missing = [n for n in declared_functions() if not hasattr(libloc, n)]
+    assert not missing, missing
+
+
+def test_invalid_arguments_fail_without_gpu_work(libloc):
+    import paper_1910_00572_gb300 as loc
+    import numpy as np
+    p = loc.loc_params_default(H=0, W=4, K=4, cell_m=0.1)
+    with pytest.raises(loc.LocError) as e:
+        loc.loc_create(np.zeros((0, 4), np.uint8), p)
+    assert e.value.status == loc.LOC_ERR_INVALID_ARG
+    p = loc.loc_params_default(H=4, W=4, K=4, cell_m=0.1)
+    with pytest.raises(loc.LocError) as e:
+        loc.loc_create(np.ones((4, 4), np.uint8), p)          # no free cell
+    assert e.value.status == loc.LOC_ERR_INVALID_ARG
+    assert "free" in loc.loc_last_error()
+    p = loc.loc_params_default(H=4, W=4, K=4, cell_m=0.1, sigma_xy_cells=5.0)
+    with pytest.raises(loc.LocError):
+        loc.loc_create(np.zeros((4, 4), np.uint8), p)          # radius 15 > LOC_MAX_R_XY

@@ -288,6 +288,10 @@ def test_e_brute_force_transition_matrix(seed):
     nb = T @ b0
     assert np.abs(flt.B.reshape(-1) - nb / nb.sum()).max() < 1e-15
     assert abs(flt.last_Z - nb.sum()) < 1e-14
+    # the pointwise evaluator agrees with the same matrix
+    idx = [(k, j, i) for k in range(K) for j in range(H) for i in range(W)]
+    pt = F.propagate_at(b0.reshape(K, H, W), flt.M, odo.shifts(), flt.g, idx)
+    assert np.abs(pt - nb).max() < 1e-15
 
 
 def test_all_mass_removed_restarts_uniform():
