@@ -119,6 +119,29 @@ loc_status loc_set_belief(loc_handle h, const float* b, size_t n);
 loc_status loc_stats(loc_handle h, double* theta_t, double* last_Z, double* logscale,
                      long long* n_propagations, long long* n_reinit);
 
+/* Allocation-free propagation (the paper has no counterpart: this is a deployment aid).
+ * For callers that must not allocate device memory while they run: real-time loops where a
+ * cudaMalloc could stall, certified or embedded stacks whose memory is fixed at start-up,
+ * and hosts whose allocator belongs to another runtime.  The caller owns every buffer:
+ *   occ_dev    device uint8 [H][W], nonzero = occupied;
+ *   b_in_dev   device float [K][H][W], the belief to propagate (used as given);
+ *   b_out_dev  device float [K][H][W], receives the propagated, unnormalised tensor
+ *              (Alg. 1 lines 3-7 with the edge correction of Eq. 8);
+ *   z_out_dev  device double, receives Z = sum of b_out (the Eq. 9 normaliser);
+ *   dx_m, dy_m translation in metres in the frame of bin 0 (bin k moves by R(2 pi k / K)).
+ * From p it uses H, W, K, cell_m, the sigmas and radii and stream; storage must be LOC_F32.
+ * The only other memory it touches is a 64 KiB + 256 B scratch array compiled into the
+ * library, which every GPU that loads the library keeps until the process exits.  That
+ * bounds the grid: ceil(W / 32) * ceil(H / 16) must be <= 8192 (e.g. 2048 x 2048 cells);
+ * larger grids are rejected with LOC_ERR_INVALID_ARG.  It never calls cudaMalloc, cudaFree
+ * or any allocating routine.  The first call on a device looks up that device's scratch
+ * address, so make it before any stream capture.  All calls on a device share the one
+ * scratch array: calls whose kernels overlap on the GPU race and give wrong results.
+ * Asynchronous on p->stream.  Errors: INVALID_ARG, CUDA; message in loc_last_error(NULL). */
+loc_status loc_propagate_noalloc(const loc_params* p, const uint8_t* occ_dev,
+                                 const float* b_in_dev, float* b_out_dev, double* z_out_dev,
+                                 double dx_m, double dy_m);
+
 /* Wait for all enqueued work of the handle; returns the first device-side error if any. */
 loc_status loc_sync(loc_handle h);
 

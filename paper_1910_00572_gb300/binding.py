@@ -20,7 +20,7 @@ __all__ = [
     "loc_params_default", "loc_set_allocator", "loc_create", "loc_step", "loc_lidar_update",
     "loc_lidar_update_cells", "loc_belief", "loc_marginal", "loc_argmax", "loc_set_belief",
     "loc_stats", "loc_sync", "loc_destroy", "loc_last_error", "torch_stream",
-    "use_torch_allocator",
+    "use_torch_allocator", "loc_propagate_noalloc",
 ]
 
 LOC_OK, LOC_OK_DEFERRED = 0, 1
@@ -78,6 +78,8 @@ _SIGS = {
     "loc_sync": (ctypes.c_int, [_P]),
     "loc_destroy": (ctypes.c_int, [_P]),
     "loc_last_error": (ctypes.c_char_p, [_P]),
+    "loc_propagate_noalloc": (ctypes.c_int, [ctypes.POINTER(loc_params), _P, _P, _P, _P,
+                                             ctypes.c_double, ctypes.c_double]),
 }
 
 
@@ -237,3 +239,11 @@ def loc_destroy(h: Handle) -> None:
 def loc_last_error(h: Handle | None = None) -> str:
     m = lib().loc_last_error(h.ptr if h is not None else None)
     return m.decode() if m else ""
+
+
+def loc_propagate_noalloc(params: loc_params, occ_dev: int, b_in_dev: int, b_out_dev: int,
+                          z_out_dev: int, dx_m: float, dy_m: float) -> None:
+    """Allocation-free propagation on caller-owned device buffers (raw device pointers)."""
+    _check(None, lib().loc_propagate_noalloc(ctypes.byref(params), ctypes.c_void_p(occ_dev),
+                                             ctypes.c_void_p(b_in_dev), ctypes.c_void_p(b_out_dev),
+                                             ctypes.c_void_p(z_out_dev), float(dx_m), float(dy_m)))

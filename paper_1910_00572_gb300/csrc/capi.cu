@@ -22,6 +22,8 @@ void* g_alloc_ctx = nullptr;
 
 }  // namespace
 
+void loc::set_thread_error(const char* msg) { g_thread_err = msg ? msg : ""; }
+
 struct loc_session {
     loc_params p{};
     int r_xy = 0, r_th = 0;

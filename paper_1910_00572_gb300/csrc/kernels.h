@@ -44,4 +44,7 @@ cudaError_t launch_set_belief(const float* src, void* B, int storage, size_t n,
                               SessionDev* sd, double* partials, unsigned int nparts,
                               cudaStream_t st);
 
+// Sets the calling thread's error message returned by loc_last_error(NULL).
+void set_thread_error(const char* msg);
+
 }  // namespace loc
