@@ -71,10 +71,17 @@ typedef struct {
     int storage;               /* LOC_F32 / LOC_BF16 / LOC_F16 */
     int n_samples;             /* Floyd-Steinberg target sample count N_s (Section III-B.1) */
     void* stream;              /* cudaStream_t for all work of the handle, or NULL */
+    int kernel;                /* LOC_KERNEL_AUTO, or force LOC_KERNEL_GENERIC / LOC_KERNEL_TILED */
 } loc_params;
 
+/* Propagation kernel selection: AUTO takes the TMA-tiled kernel when it applies (x/y radius
+ * 2, theta radius 3, K >= 8, W a multiple of 16 bytes of storage) and the generic one
+ * otherwise; forcing TILED where it does not apply fails loc_create with INVALID_ARG. */
+enum { LOC_KERNEL_AUTO = 0, LOC_KERNEL_GENERIC = 1, LOC_KERNEL_TILED = 2 };
+
 /* Fill *p with the defaults: sigma_xy 0.5 cells, sigma_theta 1 bin, radii ceil(3 sigma),
- * min_shift 0, LOC_F32, n_samples 4096, NULL stream.  H, W, K, cell_m are set to 0. */
+ * min_shift 0, LOC_F32, n_samples 4096, NULL stream, LOC_KERNEL_AUTO.  H, W, K, cell_m are
+ * set to 0. */
 void loc_params_default(loc_params* p);
 
 /* Optional device allocator for every later loc_create.  alloc(bytes, stream, ctx) returns

@@ -16,7 +16,7 @@ import numpy as np
 __all__ = [
     "LOC_OK", "LOC_OK_DEFERRED", "LOC_ERR_INVALID_ARG", "LOC_ERR_OOM", "LOC_ERR_CUDA",
     "LOC_ERR_TIMEOUT", "LOC_ERR_STATE", "LOC_F32", "LOC_BF16", "LOC_F16", "LOC_MAP_SUM",
-    "LOC_MAP_MAX", "LocError", "loc_params", "Handle", "library_path", "lib",
+    "LOC_MAP_MAX", "LOC_KERNEL_AUTO", "LOC_KERNEL_GENERIC", "LOC_KERNEL_TILED", "LocError", "loc_params", "Handle", "library_path", "lib",
     "loc_params_default", "loc_set_allocator", "loc_create", "loc_step", "loc_lidar_update",
     "loc_lidar_update_cells", "loc_belief", "loc_marginal", "loc_argmax", "loc_set_belief",
     "loc_stats", "loc_sync", "loc_destroy", "loc_last_error", "torch_stream",
@@ -27,6 +27,7 @@ LOC_OK, LOC_OK_DEFERRED = 0, 1
 LOC_ERR_INVALID_ARG, LOC_ERR_OOM, LOC_ERR_CUDA, LOC_ERR_TIMEOUT, LOC_ERR_STATE = -1, -2, -3, -4, -5
 LOC_F32, LOC_BF16, LOC_F16 = 0, 1, 2
 LOC_MAP_SUM, LOC_MAP_MAX = 0, 1
+LOC_KERNEL_AUTO, LOC_KERNEL_GENERIC, LOC_KERNEL_TILED = 0, 1, 2
 _STORAGE = {"f32": LOC_F32, "bf16": LOC_BF16, "f16": LOC_F16}
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -48,7 +49,7 @@ class loc_params(ctypes.Structure):
                 ("sigma_theta_bins", ctypes.c_double), ("r_xy", ctypes.c_int),
                 ("r_theta", ctypes.c_int), ("min_shift_cells", ctypes.c_double),
                 ("storage", ctypes.c_int), ("n_samples", ctypes.c_int),
-                ("stream", ctypes.c_void_p)]
+                ("stream", ctypes.c_void_p), ("kernel", ctypes.c_int)]
 
 
 _lib = None

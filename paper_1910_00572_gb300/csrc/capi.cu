@@ -46,6 +46,8 @@ struct loc_session {
     void* argmax_scratch = nullptr;
     long long* argmax_idx = nullptr;
     float* argmax_val = nullptr;
+    bool tiled = false;            // use the TMA-tiled kernel
+    unsigned char tmap[2][128] __attribute__((aligned(128)));   // tensor maps of B[0], B[1]
     // host-side state (FP64)
     double theta = 0.0, px = 0.0, py = 0.0;
     long long n_prop = 0;
@@ -141,6 +143,7 @@ LOC_API void loc_params_default(loc_params* p) {
     p->storage = LOC_F32;
     p->n_samples = 4096;
     p->stream = nullptr;
+    p->kernel = LOC_KERNEL_AUTO;
 }
 
 LOC_API void loc_set_allocator(loc_alloc_fn alloc, loc_free_fn release, void* ctx) {
@@ -168,6 +171,11 @@ LOC_API loc_status loc_create(const uint8_t* occ, const loc_params* p, loc_handl
     if (rxy > LOC_MAX_R_XY || rth > LOC_MAX_R_THETA)
         return fail(nullptr, LOC_ERR_INVALID_ARG, "kernel radius above LOC_MAX_R_XY / LOC_MAX_R_THETA");
     if (p->n_samples < 0) return fail(nullptr, LOC_ERR_INVALID_ARG, "n_samples must be >= 0");
+    if (p->kernel < LOC_KERNEL_AUTO || p->kernel > LOC_KERNEL_TILED)
+        return fail(nullptr, LOC_ERR_INVALID_ARG, "unknown kernel selection");
+    const bool tiled_ok = step_fast_eligible(p->H, p->W, p->K, rxy, rth, p->storage);
+    if (p->kernel == LOC_KERNEL_TILED && !tiled_ok)
+        return fail(nullptr, LOC_ERR_INVALID_ARG, "the tiled kernel needs radii 2/3, K >= 8 and aligned W");
 
     const size_t hw = (size_t)p->H * p->W;
     std::vector<uint8_t> trav(hw);
@@ -210,6 +218,16 @@ LOC_API loc_status loc_create(const uint8_t* occ, const loc_params* p, loc_handl
         return fail(nullptr, LOC_ERR_OOM, "device allocation failed");
     }
     s->argmax_val = (float*)(s->argmax_idx + 1);
+    s->tiled = tiled_ok && p->kernel != LOC_KERNEL_GENERIC;
+    if (s->tiled) {
+        for (int b = 0; b < 2; ++b) {
+            if (make_step_tmap(s->tmap[b], s->B[b], p->storage, p->H, p->W, p->K) != cudaSuccess) {
+                release_all(s);
+                delete s;
+                return fail(nullptr, LOC_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+            }
+        }
+    }
 
     SessionDev init{};
     init.Z = 1.0;
@@ -277,7 +295,8 @@ LOC_API loc_status loc_step(loc_handle h, double u, double v, double w) {
         a.sh[k].fx = (float)fx;
         a.sh[k].fy = (float)fy;
     }
-    cudaError_t e = launch_step(a, h->p.storage, h->stream);
+    cudaError_t e = h->tiled ? launch_step_fast(a, h->tmap[h->cur], h->p.storage, h->stream)
+                             : launch_step(a, h->p.storage, h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "step launch");
     h->cur = 1 - h->cur;
     h->px = h->py = 0.0;

@@ -1,0 +1,512 @@
+// Fast fused propagation kernel for the default motion kernel (x/y radius 2, theta radius 3):
+// Algorithm 1 lines 3-7 for all K channels plus the Eq. 9 normaliser in one pass over HBM.
+//
+// One CTA (256 threads) owns a 32 x 64 output tile and streams the planes p = 0 .. K+5:
+//   * raw tile of X_{t-1}[p] around the tile, shifted by the plane's integer source offset,
+//     arrives by TMA (cp.async.bulk.tensor.3d, zero fill off the grid) three planes ahead
+//     into a 3-stage ring guarded by mbarriers;
+//   * S-pass: S = M * bilinear(raw) over the 36 x 68 halo region (Eq. 3, Alg. 1 line 4);
+//   * X-pass: X = x-blur(S) over 36 x 64 (Eq. 7, separable for the isotropic kernel);
+//   * P-pass: each thread owns 2 x 4 output cells, applies the y-blur and pushes the result
+//     into a 7-deep register ring over theta; once the ring holds planes p-6 .. p it writes
+//     channel p-3 = corr * (1/Z_{t-1}) * sum_d gt[d] P[p-3+d] (theta blur, Alg. 1 lines 6-7,
+//     Eq. 8) and adds the stored (rounded) values to its FP32 partial.
+// The circular theta blur needs planes 0..5 again at the end: the P-pass keeps them in
+// shared memory (planes p = K .. K+5 read them back), so every input plane is read from HBM
+// exactly once.  CTA partials are combined in FP64 by the last CTA (Z, log-scale).
+#include <cuda.h>
+
+#include "kernels.h"
+
+namespace loc {
+namespace {
+
+constexpr int R = 2, RT = 3;           // kernel radii this kernel is built for
+constexpr int TH = 32, TW = 64, NT = 256;
+constexpr int XR = TH + 2 * R;         // rows of S and X (36)
+constexpr int SW = 72;                 // S and mask row pitch (68 used: tile cols -2 .. 65)
+constexpr int RAW_H = XR + 1;          // 37 raw rows (bilinear needs one more)
+constexpr int BW = 80;                 // raw box width in elements (76 needed + alignment)
+constexpr int NSTAGE = 3;
+constexpr int RING = 2 * RT + 1;       // 7
+constexpr int NWRAP = 2 * RT;          // 6 planes kept for the circular wrap
+constexpr unsigned long long kWaitNs = 200ull * 1000 * 1000;   // bounded mbarrier wait
+
+struct FastArgs {
+    CUtensorMap tmap;                  // X_{t-1} as [K][H][W], box {BW, RAW_H, 1}
+    void* B_out;
+    const uint8_t* trav;
+    const float* corr;
+    SessionDev* sd;
+    double* partials;
+    float inv_uniform;
+    int H, W, K;
+    float g0, g1, g2;                  // x/y taps: centre, +-1, +-2
+    float gt[RING];                    // theta taps -3 .. +3
+    Shift sh[LOC_MAX_K];
+};
+
+template <typename T> __host__ __device__ constexpr int align_elems() { return 16 / (int)sizeof(T); }
+
+template <typename T>
+constexpr int raw_stride() {          // elements per raw stage, padded to 128 bytes
+    return (int)(((RAW_H * BW * sizeof(T) + 127) / 128) * 128 / sizeof(T));
+}
+
+template <typename T>
+struct Smem {
+    T raw[NSTAGE][raw_stride<T>()];    // each stage [RAW_H][BW], 128-byte aligned
+    float S[XR][SW];
+    float X[XR][TW];
+    float wrap[NWRAP][TH][TW];
+    uint8_t mk[XR][SW];                // 0xFF free, 0x00 occupied / off-grid
+    unsigned long long bar[NSTAGE];
+    double red[NT / 32];
+};
+
+__device__ __forceinline__ uint32_t su32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ unsigned long long gtimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ void bar_init(unsigned long long* b, uint32_t n) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b)), "r"(n) : "memory");
+}
+__device__ __forceinline__ void bar_expect(unsigned long long* b, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool bar_try(unsigned long long* b, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred q;\n mbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, q;\n}\n"
+        : "=r"(ok) : "r"(su32(b)), "r"(parity) : "memory");
+    return ok != 0;
+}
+// Wait for phase `parity` of barrier b; gives up after kWaitNs (returns false).
+__device__ __forceinline__ bool bar_wait(unsigned long long* b, uint32_t parity) {
+    if (bar_try(b, parity)) return true;
+    const unsigned long long t0 = gtimer();
+    for (uint32_t it = 0; it < (1u << 26); ++it) {
+        if (bar_try(b, parity)) return true;
+        if (gtimer() - t0 > kWaitNs) return false;
+    }
+    return false;
+}
+__device__ __forceinline__ void tma_load(void* dst, const CUtensorMap* map,
+                                         unsigned long long* b, int x, int y, int z) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(su32(dst)), "l"((unsigned long long)map),
+        "r"(su32(b)), "r"(x), "r"(y), "r"(z)
+        : "memory");
+}
+
+template <typename T> __device__ __forceinline__ float tof(T v);
+template <> __device__ __forceinline__ float tof<float>(float v) { return v; }
+template <> __device__ __forceinline__ float tof<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
+template <> __device__ __forceinline__ float tof<__half>(__half v) { return __half2float(v); }
+
+// Eight consecutive raw values starting at a 4-element boundary.
+template <typename T> __device__ __forceinline__ void load8(const T* p, float (&v)[8]);
+template <> __device__ __forceinline__ void load8<float>(const float* p, float (&v)[8]) {
+    const float4 a = reinterpret_cast<const float4*>(p)[0], b = reinterpret_cast<const float4*>(p)[1];
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+}
+__device__ __forceinline__ float2 tof2(__nv_bfloat162 h) { return __bfloat1622float2(h); }
+__device__ __forceinline__ float2 tof2(__half2 h) { return __half22float2(h); }
+template <typename H2, typename T>
+__device__ __forceinline__ void load8_16(const T* p, float (&v)[8]) {
+    const uint2 a = reinterpret_cast<const uint2*>(p)[0], b = reinterpret_cast<const uint2*>(p)[1];
+    const uint32_t w[4] = {a.x, a.y, b.x, b.y};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const H2 h = *reinterpret_cast<const H2*>(&w[k]);
+        const float2 f = tof2(h);
+        v[2 * k] = f.x;
+        v[2 * k + 1] = f.y;
+    }
+}
+template <> __device__ __forceinline__ void load8<__nv_bfloat16>(const __nv_bfloat16* p, float (&v)[8]) {
+    load8_16<__nv_bfloat162>(p, v);
+}
+template <> __device__ __forceinline__ void load8<__half>(const __half* p, float (&v)[8]) {
+    load8_16<__half2>(p, v);
+}
+
+// Source x of the raw box for a plane: aligned down to 16 bytes; xo = in-box offset of the
+// first needed column.
+template <typename T>
+__device__ __forceinline__ void box_x(int tx0, const Shift& s, int& x_al, int& xo) {
+    const int x = tx0 - R + s.ox;
+    x_al = x & ~(align_elems<T>() - 1);
+    xo = x - x_al;
+}
+
+// S-pass: S[y][c] for y in [0, 36), c in [0, 72) (tile col c - 2), items of 4 columns x 3
+// rows with the x-lerp of the shared raw row carried down.  XO is xo mod 4; the runtime
+// part xo - XO (0 or 4 for 16-bit types) moves the base address.
+template <typename T, int XO>
+__device__ __forceinline__ void s_pass(Smem<T>& sm, int stage, int xbase, float fx, float fy) {
+    constexpr int UNITS = SW / 4;              // 18
+    constexpr int ITEMS = UNITS * (XR / 3);    // 216
+    for (int q = threadIdx.x; q < ITEMS; q += NT) {
+        const int u = q % UNITS, y0 = (q / UNITS) * 3;
+        const int c0 = 4 * u;
+        float prev[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const T* row = &sm.raw[stage][(y0 + r) * BW + c0 + xbase];
+            float v[8];
+            load8<T>(row, v);
+            float xl[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) xl[k] = fmaf(fx, v[XO + k + 1] - v[XO + k], v[XO + k]);
+            if (r > 0) {
+                const uint32_t m = *reinterpret_cast<const uint32_t*>(&sm.mk[y0 + r - 1][c0]);
+                float4 o;
+                float* op = &o.x;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const float s = fmaf(fy, xl[k] - prev[k], prev[k]);
+                    const uint32_t mm = __byte_perm(m, 0u, 0x8888u + 0x1111u * k);
+                    op[k] = __uint_as_float(__float_as_uint(s) & mm);
+                }
+                *reinterpret_cast<float4*>(&sm.S[y0 + r - 1][c0]) = o;
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) prev[k] = xl[k];
+        }
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void x_pass(Smem<T>& sm, float g0, float g1, float g2) {
+    constexpr int UNITS = TW / 4;              // 16
+    for (int q = threadIdx.x; q < UNITS * XR; q += NT) {
+        const int u = q % UNITS, y = q / UNITS;
+        const float4 a = *reinterpret_cast<const float4*>(&sm.S[y][4 * u]);
+        const float4 b = *reinterpret_cast<const float4*>(&sm.S[y][4 * u + 4]);
+        const float s[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+        float4 o;
+        float* op = &o.x;
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            op[k] = fmaf(g2, s[k] + s[k + 4], fmaf(g1, s[k + 1] + s[k + 3], g0 * s[k + 2]));
+        *reinterpret_cast<float4*>(&sm.X[y][4 * u]) = o;
+    }
+}
+
+template <typename T> __device__ __forceinline__ void store2(T* p, float a, float b, float& sum);
+template <> __device__ __forceinline__ void store2<float>(float* p, float a, float b, float& sum) {
+    *reinterpret_cast<float2*>(p) = make_float2(a, b);
+    sum += a + b;
+}
+template <> __device__ __forceinline__ void store2<__nv_bfloat16>(__nv_bfloat16* p, float a, float b, float& sum) {
+    const __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
+    *reinterpret_cast<__nv_bfloat162*>(p) = v;
+    sum += __low2float(v) + __high2float(v);
+}
+template <> __device__ __forceinline__ void store2<__half>(__half* p, float a, float b, float& sum) {
+    const __half2 v = __floats2half2_rn(a, b);
+    *reinterpret_cast<__half2*>(p) = v;
+    sum += __low2float(v) + __high2float(v);
+}
+
+// P-pass for plane p with the newest ring slot PH = p mod 7.
+template <typename T, int PH>
+__device__ __forceinline__ void p_pass(Smem<T>& sm, const FastArgs& a, float (&ring)[RING][8],
+                                       const float (&cs)[8], int p, int rg, int cp, int ty0,
+                                       int tx0, double& acc) {
+    const int K = a.K;
+    if (p < K) {
+        float x[8][2];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const float2 v = *reinterpret_cast<const float2*>(&sm.X[4 * rg + q][2 * cp]);
+            x[q][0] = v.x;
+            x[q][1] = v.y;
+        }
+#pragma unroll
+        for (int rr = 0; rr < 4; ++rr)
+#pragma unroll
+            for (int cc = 0; cc < 2; ++cc)
+                ring[PH][rr * 2 + cc] = fmaf(a.g2, x[rr][cc] + x[rr + 4][cc],
+                                             fmaf(a.g1, x[rr + 1][cc] + x[rr + 3][cc], a.g0 * x[rr + 2][cc]));
+        if (p < NWRAP) {
+#pragma unroll
+            for (int rr = 0; rr < 4; ++rr)
+                *reinterpret_cast<float2*>(&sm.wrap[p][4 * rg + rr][2 * cp]) =
+                    make_float2(ring[PH][rr * 2], ring[PH][rr * 2 + 1]);
+        }
+    } else {
+#pragma unroll
+        for (int rr = 0; rr < 4; ++rr) {
+            const float2 v = *reinterpret_cast<const float2*>(&sm.wrap[p - K][4 * rg + rr][2 * cp]);
+            ring[PH][rr * 2] = v.x;
+            ring[PH][rr * 2 + 1] = v.y;
+        }
+    }
+    if (p >= 2 * RT) {
+        int o = p - RT;
+        if (o >= K) o -= K;
+        T* out = static_cast<T*>(a.B_out) + (size_t)o * a.H * a.W;
+        float part = 0.0f;
+        const int gx = tx0 + 2 * cp;
+#pragma unroll
+        for (int rr = 0; rr < 4; ++rr) {
+            float v[2];
+#pragma unroll
+            for (int cc = 0; cc < 2; ++cc) {
+                float t = 0.0f;
+#pragma unroll
+                for (int d = 0; d < RING; ++d) t = fmaf(a.gt[d], ring[(PH + 1 + d) % RING][rr * 2 + cc], t);
+                v[cc] = cs[rr * 2 + cc] * t;
+            }
+            const int gy = ty0 + 4 * rg + rr;
+            if (gy < a.H && gx < a.W) store2<T>(out + (size_t)gy * a.W + gx, v[0], v[1], part);
+        }
+        acc += (double)part;
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(NT, 2) step_fast_kernel(const __grid_constant__ FastArgs a) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    // the dynamic region is only guaranteed 16-byte aligned: round up to 128 bytes
+    const uint32_t base = su32(smem_raw);
+    Smem<T>& sm = *reinterpret_cast<Smem<T>*>(smem_raw + (((base + 127u) & ~127u) - base));
+    const int tid = threadIdx.x;
+    const int H = a.H, W = a.W, K = a.K;
+    const int ty0 = blockIdx.y * TH, tx0 = blockIdx.x * TW;
+    const int reinit = a.sd->reinit;
+    const float in_scale = reinit ? 1.0f : (float)(1.0 / a.sd->Z);
+    constexpr uint32_t kBoxBytes = RAW_H * BW * sizeof(T);
+
+    // map mask over the halo region: rows ty0-2 .., cols tx0-2 ..
+    for (int q = tid; q < XR * SW; q += NT) {
+        const int y = q / SW, c = q % SW;
+        const int gy = ty0 - R + y, gx = tx0 - R + c;
+        sm.mk[y][c] = (gy >= 0 && gy < H && gx >= 0 && gx < W && a.trav[(size_t)gy * W + gx]) ? 0xFF : 0x00;
+    }
+    if (tid == 0) {
+        for (int s = 0; s < NSTAGE; ++s) bar_init(&sm.bar[s], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    __syncthreads();
+    auto issue = [&](int q) {       // TMA of plane q into stage q % NSTAGE (thread 0 only)
+        const Shift s = a.sh[q];
+        int x_al, xo;
+        box_x<T>(tx0, s, x_al, xo);
+        unsigned long long* b = &sm.bar[q % NSTAGE];
+        bar_expect(b, kBoxBytes);
+        tma_load(&sm.raw[q % NSTAGE][0], &a.tmap, b, x_al, ty0 - R + s.oy, q);
+    };
+    int next_issue = 0;             // planes [p, next_issue) have a copy in flight
+    if (!reinit) {
+        next_issue = NSTAGE < K ? NSTAGE : K;
+        if (tid == 0)
+            for (int q = 0; q < next_issue; ++q) issue(q);
+    }
+
+    // this thread's output cells in the P-pass: rows 4rg..4rg+3, cols 2cp, 2cp+1
+    const int cp = tid % 32, rg = tid / 32;
+    float cs[8];
+#pragma unroll
+    for (int rr = 0; rr < 4; ++rr)
+#pragma unroll
+        for (int cc = 0; cc < 2; ++cc) {
+            const int gy = ty0 + 4 * rg + rr, gx = tx0 + 2 * cp + cc;
+            cs[rr * 2 + cc] = (gy < H && gx < W) ? a.corr[(size_t)gy * W + gx] * in_scale : 0.0f;
+        }
+    float ring[RING][8];
+#pragma unroll
+    for (int d = 0; d < RING; ++d)
+#pragma unroll
+        for (int k = 0; k < 8; ++k) ring[d][k] = 0.0f;
+    double acc = 0.0;
+    int failed = 0;
+
+    int p = 0;
+    for (; p < K + NWRAP; ++p) {
+        if (p < K) {
+            const int stage = p % NSTAGE;
+            const Shift s = a.sh[p];
+            int x_al, xo;
+            box_x<T>(tx0, s, x_al, xo);
+            if (reinit) {
+                // uniform belief over free cells, written where TMA would have put the tile
+                const int y0 = ty0 - R + s.oy;
+                for (int q = tid; q < RAW_H * BW; q += NT) {
+                    const int y = q / BW, c = q % BW;
+                    const int gy = y0 + y, gx = x_al + c;
+                    float v = 0.0f;
+                    if (gy >= 0 && gy < H && gx >= 0 && gx < W) v = (float)a.trav[(size_t)gy * W + gx] * a.inv_uniform;
+                    sm.raw[stage][y * BW + c] = T(v);
+                }
+                __syncthreads();
+            } else if (!bar_wait(&sm.bar[stage], (uint32_t)((p / NSTAGE) & 1))) {
+                failed = 1;
+            }
+            if (!failed) {
+                const int xb = xo & ~3;
+                switch (xo & 3) {
+                    case 0: s_pass<T, 0>(sm, stage, xb, s.fx, s.fy); break;
+                    case 1: s_pass<T, 1>(sm, stage, xb, s.fx, s.fy); break;
+                    case 2: s_pass<T, 2>(sm, stage, xb, s.fx, s.fy); break;
+                    default: s_pass<T, 3>(sm, stage, xb, s.fx, s.fy); break;
+                }
+            }
+            if (__syncthreads_or(failed)) {
+                failed = 1;
+                break;
+            }
+            if (!reinit && p + NSTAGE < K) {
+                if (tid == 0) {
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    issue(p + NSTAGE);
+                }
+                next_issue = p + NSTAGE + 1;
+            }
+            x_pass<T>(sm, a.g0, a.g1, a.g2);
+            __syncthreads();
+        }
+        switch (p % RING) {
+            case 0: p_pass<T, 0>(sm, a, ring, cs, p, rg, cp, ty0, tx0, acc); break;
+            case 1: p_pass<T, 1>(sm, a, ring, cs, p, rg, cp, ty0, tx0, acc); break;
+            case 2: p_pass<T, 2>(sm, a, ring, cs, p, rg, cp, ty0, tx0, acc); break;
+            case 3: p_pass<T, 3>(sm, a, ring, cs, p, rg, cp, ty0, tx0, acc); break;
+            case 4: p_pass<T, 4>(sm, a, ring, cs, p, rg, cp, ty0, tx0, acc); break;
+            case 5: p_pass<T, 5>(sm, a, ring, cs, p, rg, cp, ty0, tx0, acc); break;
+            default: p_pass<T, 6>(sm, a, ring, cs, p, rg, cp, ty0, tx0, acc); break;
+        }
+    }
+
+    if (failed) {
+        // a TMA wait gave up: report it, let the copies still in flight land (bounded), and
+        // leave without contributing a partial (the host sees the flag and fails the handle)
+        if (tid == 0) {
+            atomicOr(&a.sd->status, LOC_DEV_ERR_TIMEOUT);
+            for (int q = p; q < next_issue; ++q) bar_wait(&sm.bar[q % NSTAGE], (uint32_t)((q / NSTAGE) & 1));
+        }
+        __syncthreads();
+        return;
+    }
+
+    const double bt = block_sum<NT>(acc, sm.red);
+    SessionDev* sd = a.sd;
+    finish_sum<NT>(bt, a.partials, &sd->counter, gridDim.x * gridDim.y, sm.red, [sd](double Z) {
+        sd->n_prop += 1;
+        if (Z > 0.0 && isfinite(Z)) {
+            sd->Z = Z;
+            sd->logscale += log(Z);
+            sd->reinit = 0;
+        } else {
+            if (!isfinite(Z)) sd->status |= LOC_DEV_ERR_NONFINITE_Z;
+            sd->Z = 1.0;
+            sd->reinit = 1;
+            sd->n_reinit += 1;
+        }
+    });
+}
+
+using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                 const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                 const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                 CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiled encoder() {
+    static EncodeTiled fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiled>(p);
+    }
+    return fn;
+}
+
+template <typename T> size_t smem_bytes() { return sizeof(Smem<T>) + 128; }
+
+// Launch with the dynamic shared memory size; the attribute is set once per device.
+template <typename T>
+cudaError_t launch_typed(const FastArgs& a, dim3 grid, cudaStream_t st) {
+    static bool attr_set[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const size_t sb = smem_bytes<T>();
+    if (dev < 0 || dev >= 64 || !attr_set[dev]) {
+        cudaError_t e = cudaFuncSetAttribute(step_fast_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb);
+        if (e != cudaSuccess) return e;
+        if (dev >= 0 && dev < 64) attr_set[dev] = true;
+    }
+    step_fast_kernel<T><<<grid, NT, sb, st>>>(a);
+    return cudaSuccess;
+}
+
+}  // namespace
+
+bool step_fast_eligible(int H, int W, int K, int r_xy, int r_th, int storage) {
+    const int align = storage == LOC_F32 ? 4 : 8;
+    return r_xy == R && r_th == RT && K >= 8 && K <= LOC_MAX_K && W % align == 0 && W >= 8 && H >= 1;
+}
+
+cudaError_t make_step_tmap(void* tmap_out, const void* B, int storage, int H, int W, int K) {
+    EncodeTiled enc = encoder();
+    if (!enc) return cudaErrorNotSupported;
+    const size_t e = storage == LOC_F32 ? 4 : 2;
+    const CUtensorMapDataType dt = storage == LOC_F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                   : storage == LOC_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                                         : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+    const cuuint64_t dims[3] = {(cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)K};
+    const cuuint64_t strides[2] = {(cuuint64_t)W * e, (cuuint64_t)W * H * e};
+    const cuuint32_t box[3] = {(cuuint32_t)BW, (cuuint32_t)RAW_H, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = enc(static_cast<CUtensorMap*>(tmap_out), dt, 3, const_cast<void*>(B), dims, strides, box,
+                     estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+size_t step_tmap_bytes() { return sizeof(CUtensorMap); }
+
+unsigned int step_fast_num_blocks(int H, int W) {
+    return (unsigned int)(((W + TW - 1) / TW) * ((H + TH - 1) / TH));
+}
+
+cudaError_t launch_step_fast(const StepArgs& g, const void* tmap, int storage, cudaStream_t st) {
+    FastArgs a;
+    memcpy(&a.tmap, tmap, sizeof(CUtensorMap));
+    a.B_out = g.B_out;
+    a.trav = g.trav;
+    a.corr = g.corr;
+    a.sd = g.sd;
+    a.partials = g.partials;
+    a.inv_uniform = g.inv_uniform;
+    a.H = g.H;
+    a.W = g.W;
+    a.K = g.K;
+    a.g0 = g.gx[R];
+    a.g1 = g.gx[R + 1];
+    a.g2 = g.gx[R + 2];
+    for (int d = 0; d < RING; ++d) a.gt[d] = g.gt[d];
+    for (int k = 0; k < g.K; ++k) a.sh[k] = g.sh[k];
+    dim3 grid((g.W + TW - 1) / TW, (g.H + TH - 1) / TH);
+    cudaError_t e = cudaSuccess;
+    switch (storage) {
+        case LOC_F32: e = launch_typed<float>(a, grid, st); break;
+        case LOC_BF16: e = launch_typed<__nv_bfloat16>(a, grid, st); break;
+        case LOC_F16: e = launch_typed<__half>(a, grid, st); break;
+        default: return cudaErrorInvalidValue;
+    }
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
+}  // namespace loc

@@ -1,0 +1,147 @@
+"""GPU parity of the TMA-tiled propagation kernel (x/y radius 2, theta radius 3) against the
+FP64 oracle and against the generic kernel, on shapes that stress its tiling: ragged tile
+edges, widths that are not a multiple of the 64-cell tile, K not a multiple of the 7-deep
+theta ring, the smallest K it accepts, shifts larger than a tile, the uniform-restart input,
+and reduced-precision storage."""
+import numpy as np
+import pytest
+
+import paper_1910_00572_gb300 as loc
+from oracle import filter as F
+from oracle import readout as R
+from synth import fields, floorplan, workloads
+
+pytestmark = pytest.mark.gpu
+
+ABS_TOL = 1e-6
+REL_TOL = 2e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1910_00572_gb300 import build
+    build.build()
+    loc.lib()
+
+
+def make(occ, K, cell, kernel=loc.LOC_KERNEL_TILED, **kw):
+    p = loc.loc_params_default(H=occ.shape[0], W=occ.shape[1], K=K, cell_m=cell, kernel=kernel, **kw)
+    return loc.loc_create(occ, p)
+
+
+def close(gpu, ref, abs_tol=ABS_TOL, rel_tol=REL_TOL):
+    err = np.abs(gpu.astype(np.float64) - ref).max()
+    assert err <= abs_tol and err <= rel_tol * ref.max(), (err, ref.max())
+
+
+SHAPES = [
+    # (H, W, K, motion per step in cells (u, v) and w)
+    (64, 64, 16, (0.3, -0.7, 0.05)),
+    (70, 136, 9, (1.7, 0.4, -0.1)),
+    (33, 8, 8, (0.5, 0.25, 0.0)),
+    (100, 200, 13, (-2.6, 1.1, 0.2)),
+    (41, 72, 72, (0.9, 0.9, 0.03)),
+    (48, 96, 10, (37.5, -20.25, 0.0)),
+]
+
+
+@pytest.mark.parametrize("H,W,K,mot", SHAPES, ids=[f"{s[0]}x{s[1]}x{s[2]}" for s in SHAPES])
+def test_tiled_matches_oracle_and_generic(H, W, K, mot):
+    rng = np.random.default_rng(H * 7 + W * 3 + K)
+    occ = (rng.random((H, W)) < 0.2).astype(np.uint8)
+    occ[H // 2, W // 2] = 0
+    cell = 0.05
+    b = fields.belief_like(occ, K, seed=K, dtype=np.float32)
+    ht = make(occ, K, cell)
+    hg = make(occ, K, cell, kernel=loc.LOC_KERNEL_GENERIC)
+    ref = F.Filter(occ, K, cell)
+    ref.B = b.astype(np.float64) / b.astype(np.float64).sum()
+    try:
+        loc.loc_set_belief(ht, b)
+        loc.loc_set_belief(hg, b)
+        for _ in range(3):
+            u, v, w = mot[0] * cell, mot[1] * cell, mot[2]
+            for h in (ht, hg):
+                loc.loc_step(h, u, v, w)
+            ref.step(u, v, w)
+            if ref.last_Z == 0.0:
+                break
+            bt, bg = loc.loc_belief(ht), loc.loc_belief(hg)
+            close(bt, ref.B)
+            close(bt, bg.astype(np.float64))
+            assert abs(loc.loc_stats(ht)["last_Z"] - ref.last_Z) <= 1e-6 * max(ref.last_Z, 1e-30)
+    finally:
+        loc.loc_destroy(ht)
+        loc.loc_destroy(hg)
+
+
+def test_tiled_first_step_reads_uniform_and_walls_hold_no_mass():
+    occ = floorplan.rooms_map(9, size=64)
+    h = make(occ, 16, 0.1)
+    ref = F.Filter(occ, 16, 0.1)
+    try:
+        for (u, v, w) in [(0.04, 0.01, 0.1), (0.02, -0.05, -0.2)]:
+            loc.loc_step(h, u, v, w)
+            ref.step(u, v, w)
+            b = loc.loc_belief(h)
+            close(b, ref.B)
+            assert (b[:, occ != 0] == 0.0).all()
+    finally:
+        loc.loc_destroy(h)
+
+
+def test_tiled_restart_after_all_mass_removed():
+    occ = np.ones((40, 64), np.uint8)
+    occ[18:22, 30:34] = 0
+    h = make(occ, 8, 1.0)
+    try:
+        loc.loc_step(h, 12.0, 0.0, 0.0)                # everything walks into walls
+        st = loc.loc_stats(h)
+        b = loc.loc_belief(h)
+        assert st["n_reinit"] == 1 and st["last_Z"] == 0.0
+        M = (occ == 0).astype(np.float64)
+        assert np.abs(b - F.uniform_belief(M, 8)).max() <= 1e-9
+        loc.loc_step(h, 0.0, 0.0, 0.0)                 # the next step starts from uniform
+        ref = F.Filter(occ, 8, 1.0)
+        ref.step(0.0, 0.0, 0.0)
+        close(loc.loc_belief(h), ref.B)
+    finally:
+        loc.loc_destroy(h)
+
+
+def test_tiled_is_refused_where_it_does_not_apply():
+    occ = np.zeros((32, 30), np.uint8)                 # W * 4 bytes not a multiple of 16
+    with pytest.raises(loc.LocError):
+        make(occ, 16, 0.1)
+    with pytest.raises(loc.LocError):
+        make(np.zeros((32, 32), np.uint8), 6, 0.1)    # K below the tiled minimum
+    with pytest.raises(loc.LocError):
+        make(np.zeros((32, 32), np.uint8), 16, 0.1, sigma_xy_cells=1.0)
+
+
+@pytest.mark.parametrize("storage", ["bf16"])
+def test_reduced_precision_trajectory_l1_and_argmax(storage):
+    """Reduced-precision storage (FP32 arithmetic): L1 <= 1e-2 against the FP64 oracle and the
+    same argmax bin wherever the oracle's maximum is unambiguous."""
+    wl = workloads.get("rooms64")
+    occ = workloads.make_map(wl)
+    walk = workloads.make_walk(wl, occ)
+    h = make(occ, wl["K"], wl["cell"], storage=storage)
+    ref = F.Filter(occ, wl["K"], wl["cell"])
+    worst = 0.0
+    try:
+        for t, (u, v, w) in enumerate(walk.odom, start=1):
+            loc.loc_step(h, u, v, w)
+            ref.step(u, v, w)
+            if t % 25 == 0:
+                b = loc.loc_belief(h).astype(np.float64)
+                l1 = np.abs(b - ref.B).sum()
+                worst = max(worst, l1)
+                assert l1 <= 1e-2, (t, l1)
+                k, j, i, p = R.argmax_pose(ref.B)
+                top2 = np.sort(ref.B.reshape(-1))[-2:]
+                if top2[1] - top2[0] > 2 * 1e-2 * top2[1]:
+                    assert loc.loc_argmax(h)[:3] == (k, j, i), t
+    finally:
+        loc.loc_destroy(h)
+    print(f"{storage}: worst L1 over the trajectory {worst:.3e}")
