@@ -268,6 +268,9 @@ LOC_API loc_status loc_step(loc_handle h, double u, double v, double w) {
     a.sd = h->sd;
     a.partials = h->partials;
     a.inv_uniform = h->inv_uniform;
+    a.out_mult = storage_mult(h->p.storage);
+    a.log_out_mult = std::log((double)a.out_mult);
+    a.seed = pcg_hash((uint32_t)h->n_prop * 0x9E3779B9u + 0x632BE5ABu);
     a.H = h->p.H;
     a.W = h->p.W;
     a.K = h->p.K;
@@ -390,7 +393,7 @@ LOC_API loc_status loc_stats(loc_handle h, double* theta_t, double* last_Z, doub
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "loc_stats");
     if (theta_t) *theta_t = h->theta;
-    if (last_Z) *last_Z = d.reinit && d.n_reinit ? 0.0 : d.Z;
+    if (last_Z) *last_Z = d.reinit && d.n_reinit ? 0.0 : d.Z / (double)storage_mult(h->p.storage);
     if (logscale) *logscale = d.logscale;
     if (n_propagations) *n_propagations = h->n_prop;
     if (n_reinit) *n_reinit = (long long)d.n_reinit;

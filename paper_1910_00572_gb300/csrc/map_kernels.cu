@@ -129,13 +129,13 @@ __global__ void argmax_final_kernel(const float* __restrict__ pv, const long lon
 
 template <typename T>
 __global__ void set_belief_kernel(const float* __restrict__ src, T* __restrict__ B, size_t n,
-                                  SessionDev* sd, double* partials) {
+                                  float mult, SessionDev* sd, double* partials) {
     __shared__ double red[NT / 32];
     float part = 0.0f;
     double acc = 0.0;
     int cnt = 0;
     for (size_t q = (size_t)blockIdx.x * NT + threadIdx.x; q < n; q += (size_t)gridDim.x * NT) {
-        part += Store<T>::st(B + q, src[q]);
+        part += Store<T>::st(B + q, src[q] * mult);
         if (++cnt == 64) { acc += (double)part; part = 0.0f; cnt = 0; }
     }
     acc += (double)part;
@@ -214,7 +214,8 @@ cudaError_t launch_set_belief(const float* src, void* B, int storage, size_t n,
                               cudaStream_t st) {
     unsigned int nb = grid_for(n);
     if (nb > nparts) nb = nparts;
-    LOC_DISPATCH(storage, (set_belief_kernel<T><<<nb, NT, 0, st>>>(src, (T*)B, n, sd, partials)));
+    LOC_DISPATCH(storage, (set_belief_kernel<T><<<nb, NT, 0, st>>>(src, (T*)B, n, storage_mult(storage),
+                                                                    sd, partials)));
     return cudaGetLastError();
 }
 

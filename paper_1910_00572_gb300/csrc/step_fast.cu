@@ -40,6 +40,9 @@ struct FastArgs {
     SessionDev* sd;
     double* partials;
     float inv_uniform;
+    float out_mult;
+    double log_out_mult;
+    uint32_t seed;
     int H, W, K;
     float g0, g1, g2;                  // x/y taps: centre, +-1, +-2
     float gt[RING];                    // theta taps -3 .. +3
@@ -201,17 +204,21 @@ __device__ __forceinline__ void x_pass(Smem<T>& sm, float g0, float g1, float g2
     }
 }
 
-template <typename T> __device__ __forceinline__ void store2(T* p, float a, float b, float& sum);
-template <> __device__ __forceinline__ void store2<float>(float* p, float a, float b, float& sum) {
+// Store two neighbouring outputs (FP32 as is, BF16 stochastically rounded with the 32 random
+// bits h, FP16 round-to-nearest) and add the stored values to sum.
+template <typename T> __device__ __forceinline__ void store2(T* p, float a, float b, uint32_t h, float& sum);
+template <> __device__ __forceinline__ void store2<float>(float* p, float a, float b, uint32_t, float& sum) {
     *reinterpret_cast<float2*>(p) = make_float2(a, b);
     sum += a + b;
 }
-template <> __device__ __forceinline__ void store2<__nv_bfloat16>(__nv_bfloat16* p, float a, float b, float& sum) {
-    const __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
+template <> __device__ __forceinline__ void store2<__nv_bfloat16>(__nv_bfloat16* p, float a, float b, uint32_t h, float& sum) {
+    __nv_bfloat162 v;
+    v.x = bf16_sr(a, h);
+    v.y = bf16_sr(b, h >> 16);
     *reinterpret_cast<__nv_bfloat162*>(p) = v;
     sum += __low2float(v) + __high2float(v);
 }
-template <> __device__ __forceinline__ void store2<__half>(__half* p, float a, float b, float& sum) {
+template <> __device__ __forceinline__ void store2<__half>(__half* p, float a, float b, uint32_t, float& sum) {
     const __half2 v = __floats2half2_rn(a, b);
     *reinterpret_cast<__half2*>(p) = v;
     sum += __low2float(v) + __high2float(v);
@@ -268,7 +275,11 @@ __device__ __forceinline__ void p_pass(Smem<T>& sm, const FastArgs& a, float (&r
                 v[cc] = cs[rr * 2 + cc] * t;
             }
             const int gy = ty0 + 4 * rg + rr;
-            if (gy < a.H && gx < a.W) store2<T>(out + (size_t)gy * a.W + gx, v[0], v[1], part);
+            if (gy < a.H && gx < a.W) {
+                const size_t q_lin = ((size_t)o * a.H + gy) * a.W + gx;
+                const uint32_t h = sizeof(T) == 2 ? pcg_hash((uint32_t)q_lin ^ a.seed) : 0u;
+                store2<T>(out + (q_lin - (size_t)o * a.H * a.W), v[0], v[1], h, part);
+            }
         }
         acc += (double)part;
     }
@@ -284,7 +295,8 @@ __global__ void __launch_bounds__(NT, 2) step_fast_kernel(const __grid_constant_
     const int H = a.H, W = a.W, K = a.K;
     const int ty0 = blockIdx.y * TH, tx0 = blockIdx.x * TW;
     const int reinit = a.sd->reinit;
-    const float in_scale = reinit ? 1.0f : (float)(1.0 / a.sd->Z);
+    // restart: the input is M / (K n_free); read M and fold 1 / (K n_free) into the scale
+    const float in_scale = (reinit ? a.inv_uniform : (float)(1.0 / a.sd->Z)) * a.out_mult;
     constexpr uint32_t kBoxBytes = RAW_H * BW * sizeof(T);
 
     // map mask over the halo region: rows ty0-2 .., cols tx0-2 ..
@@ -346,7 +358,7 @@ __global__ void __launch_bounds__(NT, 2) step_fast_kernel(const __grid_constant_
                     const int y = q / BW, c = q % BW;
                     const int gy = y0 + y, gx = x_al + c;
                     float v = 0.0f;
-                    if (gy >= 0 && gy < H && gx >= 0 && gx < W) v = (float)a.trav[(size_t)gy * W + gx] * a.inv_uniform;
+                    if (gy >= 0 && gy < H && gx >= 0 && gx < W) v = (float)a.trav[(size_t)gy * W + gx];
                     sm.raw[stage][y * BW + c] = T(v);
                 }
                 __syncthreads();
@@ -400,11 +412,12 @@ __global__ void __launch_bounds__(NT, 2) step_fast_kernel(const __grid_constant_
 
     const double bt = block_sum<NT>(acc, sm.red);
     SessionDev* sd = a.sd;
-    finish_sum<NT>(bt, a.partials, &sd->counter, gridDim.x * gridDim.y, sm.red, [sd](double Z) {
+    const double log_mult = a.log_out_mult;
+    finish_sum<NT>(bt, a.partials, &sd->counter, gridDim.x * gridDim.y, sm.red, [sd, log_mult](double Z) {
         sd->n_prop += 1;
         if (Z > 0.0 && isfinite(Z)) {
             sd->Z = Z;
-            sd->logscale += log(Z);
+            sd->logscale += log(Z) - log_mult;
             sd->reinit = 0;
         } else {
             if (!isfinite(Z)) sd->status |= LOC_DEV_ERR_NONFINITE_Z;
@@ -489,6 +502,9 @@ cudaError_t launch_step_fast(const StepArgs& g, const void* tmap, int storage, c
     a.sd = g.sd;
     a.partials = g.partials;
     a.inv_uniform = g.inv_uniform;
+    a.out_mult = g.out_mult;
+    a.log_out_mult = g.log_out_mult;
+    a.seed = g.seed;
     a.H = g.H;
     a.W = g.W;
     a.K = g.K;

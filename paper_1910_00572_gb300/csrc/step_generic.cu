@@ -41,7 +41,8 @@ __global__ void __launch_bounds__(NT) step_generic_kernel(const __grid_constant_
     const int ring = 2 * rt + 1;
 
     const int reinit = a.sd->reinit;
-    const float in_scale = reinit ? 1.0f : (float)(1.0 / a.sd->Z);
+    // restart: the input is M / (K n_free); read M and fold 1 / (K n_free) into the scale
+    const float in_scale = (reinit ? a.inv_uniform : (float)(1.0 / a.sd->Z)) * a.out_mult;
     const T* Bin = static_cast<const T*>(a.B_in);
     T* Bout = static_cast<T*>(a.B_out);
 
@@ -64,7 +65,7 @@ __global__ void __launch_bounds__(NT) step_generic_kernel(const __grid_constant_
             float v = 0.0f;
             if (j >= 0 && j < H && i >= 0 && i < W) {
                 const size_t o = (size_t)j * W + i;
-                v = reinit ? (float)a.trav[o] * a.inv_uniform : Store<T>::ld(plane + o);
+                v = reinit ? (float)a.trav[o] : Store<T>::ld(plane + o);
             }
             raw[jj][ii] = v;
         }
@@ -104,7 +105,8 @@ __global__ void __launch_bounds__(NT) step_generic_kernel(const __grid_constant_
                 for (int d = -rt; d <= rt; ++d) v += a.gt[d + rt] * P[(o + d + rt) % ring][j][i];
                 const size_t off = (size_t)gj * W + gi;
                 v = a.corr[off] * in_scale * v;
-                part += Store<T>::st(oplane + off, v);
+                const uint32_t q_lin = (uint32_t)((size_t)o * H * W + off);
+                part += store_out<T>(oplane + off, v, pcg_hash(q_lin ^ a.seed));
             }
             acc += (double)part;
         }
@@ -116,11 +118,12 @@ __global__ void __launch_bounds__(NT) step_generic_kernel(const __grid_constant_
     const double bt = block_sum<NT>(acc, red);
     const unsigned int nblocks = gridDim.x * gridDim.y;
     SessionDev* sd = a.sd;
-    finish_sum<NT>(bt, a.partials, &sd->counter, nblocks, red, [sd](double Z) {
+    const double log_mult = a.log_out_mult;
+    finish_sum<NT>(bt, a.partials, &sd->counter, nblocks, red, [sd, log_mult](double Z) {
         sd->n_prop += 1;
         if (Z > 0.0 && isfinite(Z)) {
             sd->Z = Z;
-            sd->logscale += log(Z);
+            sd->logscale += log(Z) - log_mult;
             sd->reinit = 0;
         } else {
             if (!isfinite(Z)) sd->status |= LOC_DEV_ERR_NONFINITE_Z;

@@ -119,10 +119,11 @@ def test_tiled_is_refused_where_it_does_not_apply():
         make(np.zeros((32, 32), np.uint8), 16, 0.1, sigma_xy_cells=1.0)
 
 
-@pytest.mark.parametrize("storage", ["bf16"])
+@pytest.mark.parametrize("storage", ["bf16", "f16"])
 def test_reduced_precision_trajectory_l1_and_argmax(storage):
-    """Reduced-precision storage (FP32 arithmetic): L1 <= 1e-2 against the FP64 oracle and the
-    same argmax bin wherever the oracle's maximum is unambiguous."""
+    """Reduced-precision storage (FP32 arithmetic; BF16 stochastically rounded, FP16 scaled by
+    2^14): L1 <= 1e-2 against the FP64 oracle over the whole 200-step trajectory, and the same
+    argmax bin wherever the oracle's maximum is unambiguous."""
     wl = workloads.get("rooms64")
     occ = workloads.make_map(wl)
     walk = workloads.make_walk(wl, occ)
