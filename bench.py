@@ -46,6 +46,9 @@ def parse():
     ap.add_argument("--storage", default=None, help="override the workload's storage type")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tile", type=int, default=0, help="tiled-kernel configuration (0: auto)")
+    ap.add_argument("--kernel", type=int, default=0, help="0 auto, 1 generic, 2 tiled")
+    ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
 
 
@@ -216,7 +219,7 @@ def run_ours(args, wl, occ, walk, ws, rank, local):
     p = loc.loc_params_default(H=wl["H"], W=wl["W"], K=wl["K"], cell_m=wl["cell"],
                                sigma_xy_cells=wl["sigma_xy_cells"],
                                sigma_theta_bins=wl["sigma_theta_bins"], storage=storage,
-                               stream=loc.torch_stream())
+                               stream=loc.torch_stream(), tile=args.tile, kernel=args.kernel)
     h = loc.loc_create(occ, p)
     odom = walk.odom
     n_cells = wl["H"] * wl["W"] * wl["K"]
@@ -250,7 +253,7 @@ def run_ours(args, wl, occ, walk, ws, rank, local):
         p50, p99 = float(np.percentile(ms, 50)), float(np.percentile(ms, 99))
 
         # end to end through the C-ABI: odometry in, pose estimate (argmax) out, every step
-        n_e2e = min(args.steps, 1000)
+        n_e2e = 0 if args.no_e2e else min(args.steps, 1000)
         e2e_t = 0.0
         for s in range(n_e2e):
             flush.zero_()
@@ -260,7 +263,7 @@ def run_ours(args, wl, occ, walk, ws, rank, local):
             loc.loc_argmax(h)
             e2e_t += time.perf_counter() - t
         e2e_t = max_over_ranks(e2e_t, ws)
-        e2e_value = n_cells * ws * n_e2e / e2e_t
+        e2e_value = n_cells * ws * n_e2e / e2e_t if n_e2e else None
         stats = loc.loc_stats(h)
     finally:
         loc.loc_destroy(h)
@@ -287,7 +290,7 @@ def run_ours(args, wl, occ, walk, ws, rank, local):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": per_step_s * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": storage, "data": "synthetic",
-        "config": config_of(wl, args),
+        "config": config_of(wl, args, extra={"tile": args.tile, "kernel": args.kernel}),
         "p50_step_ms": p50, "p99_step_ms": p99,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": None,

@@ -72,7 +72,11 @@ typedef struct {
     int n_samples;             /* Floyd-Steinberg target sample count N_s (Section III-B.1) */
     void* stream;              /* cudaStream_t for all work of the handle, or NULL */
     int kernel;                /* LOC_KERNEL_AUTO, or force LOC_KERNEL_GENERIC / LOC_KERNEL_TILED */
+    int tile;                  /* tiled kernel: 0 picks a tile configuration for the grid,
+                                  1 .. LOC_TILE_CONFIGS forces one */
 } loc_params;
+
+#define LOC_TILE_CONFIGS 3     /* 1: 32x64 tiles, 2: 16x64 (256 threads), 3: 16x64 (128) */
 
 /* Propagation kernel selection: AUTO takes the TMA-tiled kernel when it applies (x/y radius
  * 2, theta radius 3, K >= 8, W a multiple of 16 bytes of storage) and the generic one
@@ -80,8 +84,8 @@ typedef struct {
 enum { LOC_KERNEL_AUTO = 0, LOC_KERNEL_GENERIC = 1, LOC_KERNEL_TILED = 2 };
 
 /* Fill *p with the defaults: sigma_xy 0.5 cells, sigma_theta 1 bin, radii ceil(3 sigma),
- * min_shift 0, LOC_F32, n_samples 4096, NULL stream, LOC_KERNEL_AUTO.  H, W, K, cell_m are
- * set to 0. */
+ * min_shift 0, LOC_F32, n_samples 4096, NULL stream, LOC_KERNEL_AUTO, tile 0.  H, W, K,
+ * cell_m are set to 0. */
 void loc_params_default(loc_params* p);
 
 /* Optional device allocator for every later loc_create.  alloc(bytes, stream, ctx) returns

@@ -49,7 +49,8 @@ class loc_params(ctypes.Structure):
                 ("sigma_theta_bins", ctypes.c_double), ("r_xy", ctypes.c_int),
                 ("r_theta", ctypes.c_int), ("min_shift_cells", ctypes.c_double),
                 ("storage", ctypes.c_int), ("n_samples", ctypes.c_int),
-                ("stream", ctypes.c_void_p), ("kernel", ctypes.c_int)]
+                ("stream", ctypes.c_void_p), ("kernel", ctypes.c_int),
+                ("tile", ctypes.c_int)]
 
 
 _lib = None

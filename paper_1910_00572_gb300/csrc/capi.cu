@@ -47,6 +47,7 @@ struct loc_session {
     long long* argmax_idx = nullptr;
     float* argmax_val = nullptr;
     bool tiled = false;            // use the TMA-tiled kernel
+    int tile_cfg = 0;              // its tile configuration
     unsigned char tmap[2][128] __attribute__((aligned(128)));   // tensor maps of B[0], B[1]
     // host-side state (FP64)
     double theta = 0.0, px = 0.0, py = 0.0;
@@ -144,6 +145,7 @@ LOC_API void loc_params_default(loc_params* p) {
     p->n_samples = 4096;
     p->stream = nullptr;
     p->kernel = LOC_KERNEL_AUTO;
+    p->tile = 0;
 }
 
 LOC_API void loc_set_allocator(loc_alloc_fn alloc, loc_free_fn release, void* ctx) {
@@ -173,7 +175,9 @@ LOC_API loc_status loc_create(const uint8_t* occ, const loc_params* p, loc_handl
     if (p->n_samples < 0) return fail(nullptr, LOC_ERR_INVALID_ARG, "n_samples must be >= 0");
     if (p->kernel < LOC_KERNEL_AUTO || p->kernel > LOC_KERNEL_TILED)
         return fail(nullptr, LOC_ERR_INVALID_ARG, "unknown kernel selection");
-    const bool tiled_ok = step_fast_eligible(p->H, p->W, p->K, rxy, rth, p->storage);
+    const bool tiled_ok = step_tiled_eligible(p->H, p->W, p->K, rxy, rth, p->storage);
+    if (p->tile < 0 || p->tile > step_tiled_num_cfgs())
+        return fail(nullptr, LOC_ERR_INVALID_ARG, "tile configuration out of range");
     if (p->kernel == LOC_KERNEL_TILED && !tiled_ok)
         return fail(nullptr, LOC_ERR_INVALID_ARG, "the tiled kernel needs radii 2/3, K >= 8 and aligned W");
 
@@ -220,8 +224,9 @@ LOC_API loc_status loc_create(const uint8_t* occ, const loc_params* p, loc_handl
     s->argmax_val = (float*)(s->argmax_idx + 1);
     s->tiled = tiled_ok && p->kernel != LOC_KERNEL_GENERIC;
     if (s->tiled) {
+        s->tile_cfg = p->tile > 0 ? p->tile : step_tiled_default_cfg(p->H, p->W, p->K, p->storage);
         for (int b = 0; b < 2; ++b) {
-            if (make_step_tmap(s->tmap[b], s->B[b], p->storage, p->H, p->W, p->K) != cudaSuccess) {
+            if (make_step_tmap(s->tmap[b], s->B[b], p->storage, p->H, p->W, p->K, s->tile_cfg) != cudaSuccess) {
                 release_all(s);
                 delete s;
                 return fail(nullptr, LOC_ERR_CUDA, "cuTensorMapEncodeTiled failed");
@@ -298,7 +303,7 @@ LOC_API loc_status loc_step(loc_handle h, double u, double v, double w) {
         a.sh[k].fx = (float)fx;
         a.sh[k].fy = (float)fy;
     }
-    cudaError_t e = h->tiled ? launch_step_fast(a, h->tmap[h->cur], h->p.storage, h->stream)
+    cudaError_t e = h->tiled ? launch_step_tiled(a, h->tmap[h->cur], h->p.storage, h->tile_cfg, h->stream)
                              : launch_step(a, h->p.storage, h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "step launch");
     h->cur = 1 - h->cur;

@@ -16,12 +16,14 @@ constexpr int kGenTH = 16, kGenTW = 32;
 cudaError_t launch_step(const StepArgs& a, int storage, cudaStream_t st);
 unsigned int step_num_blocks(int H, int W);
 
-// Fast TMA-pipelined propagation for the default kernel radii (x/y 2, theta 3).
-bool step_fast_eligible(int H, int W, int K, int r_xy, int r_th, int storage);
+// Tiled TMA-pipelined propagation for the default kernel radii (x/y 2, theta 3).  Tile
+// configurations are numbered 1 .. step_tiled_num_cfgs(); each needs its own tensor map.
+bool step_tiled_eligible(int H, int W, int K, int r_xy, int r_th, int storage);
+int step_tiled_num_cfgs();
+int step_tiled_default_cfg(int H, int W, int K, int storage);
 size_t step_tmap_bytes();
-cudaError_t make_step_tmap(void* tmap_out, const void* B, int storage, int H, int W, int K);
-unsigned int step_fast_num_blocks(int H, int W);
-cudaError_t launch_step_fast(const StepArgs& a, const void* tmap, int storage, cudaStream_t st);
+cudaError_t make_step_tmap(void* tmap_out, const void* B, int storage, int H, int W, int K, int cfg);
+cudaError_t launch_step_tiled(const StepArgs& a, const void* tmap, int storage, int cfg, cudaStream_t st);
 
 // corr[j][i] = trav ? 1 / G(M)(j, i) : 0 with G(M) the x/y blur of M by gx (Eq. 8).
 cudaError_t launch_edge_correction(const uint8_t* trav, float* corr, int H, int W,

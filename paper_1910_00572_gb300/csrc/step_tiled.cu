@@ -1,19 +1,22 @@
-// Fast fused propagation kernel for the default motion kernel (x/y radius 2, theta radius 3):
+// Tiled fused propagation kernel for the default motion kernel (x/y radius 2, theta radius 3):
 // Algorithm 1 lines 3-7 for all K channels plus the Eq. 9 normaliser in one pass over HBM.
 //
-// One CTA (256 threads) owns a 32 x 64 output tile and streams the planes p = 0 .. K+5:
+// One CTA owns a TH x 64 output tile and streams the planes p = 0 .. K+5:
 //   * raw tile of X_{t-1}[p] around the tile, shifted by the plane's integer source offset,
-//     arrives by TMA (cp.async.bulk.tensor.3d, zero fill off the grid) three planes ahead
-//     into a 3-stage ring guarded by mbarriers;
-//   * S-pass: S = M * bilinear(raw) over the 36 x 68 halo region (Eq. 3, Alg. 1 line 4);
-//   * X-pass: X = x-blur(S) over 36 x 64 (Eq. 7, separable for the isotropic kernel);
-//   * P-pass: each thread owns 2 x 4 output cells, applies the y-blur and pushes the result
+//     arrives by TMA (cp.async.bulk.tensor.3d, zero fill off the grid) NSTAGE-1 planes ahead
+//     into a ring of stages guarded by mbarriers;
+//   * S-pass: S = M * bilinear(raw) over the (TH+4) x 68 halo region (Eq. 3, Alg. 1 line 4);
+//   * X-pass: X = x-blur(S) over (TH+4) x 64 (Eq. 7, separable for the isotropic kernel);
+//   * P-pass: each thread owns 2 x MR output cells, applies the y-blur and pushes the result
 //     into a 7-deep register ring over theta; once the ring holds planes p-6 .. p it writes
-//     channel p-3 = corr * (1/Z_{t-1}) * sum_d gt[d] P[p-3+d] (theta blur, Alg. 1 lines 6-7,
+//     channel p-3 = corr * scale * sum_d gt[d] P[p-3+d] (theta blur, Alg. 1 lines 6-7,
 //     Eq. 8) and adds the stored (rounded) values to its FP32 partial.
 // The circular theta blur needs planes 0..5 again at the end: the P-pass keeps them in
 // shared memory (planes p = K .. K+5 read them back), so every input plane is read from HBM
-// exactly once.  CTA partials are combined in FP64 by the last CTA (Z, log-scale).
+// once.  CTA partials are combined in FP64 by the last CTA (Z, log-scale).
+//
+// Tile configurations (Cfg1..Cfg3) trade halo overhead against the number of resident CTAs;
+// the session picks one per grid shape.
 #include <cuda.h>
 
 #include "kernels.h"
@@ -22,15 +25,25 @@ namespace loc {
 namespace {
 
 constexpr int R = 2, RT = 3;           // kernel radii this kernel is built for
-constexpr int TH = 32, TW = 64, NT = 256;
-constexpr int XR = TH + 2 * R;         // rows of S and X (36)
+constexpr int TW = 64;                 // tile width (cells)
 constexpr int SW = 72;                 // S and mask row pitch (68 used: tile cols -2 .. 65)
-constexpr int RAW_H = XR + 1;          // 37 raw rows (bilinear needs one more)
 constexpr int BW = 80;                 // raw box width in elements (76 needed + alignment)
-constexpr int NSTAGE = 3;
 constexpr int RING = 2 * RT + 1;       // 7
 constexpr int NWRAP = 2 * RT;          // 6 planes kept for the circular wrap
 constexpr unsigned long long kWaitNs = 200ull * 1000 * 1000;   // bounded mbarrier wait
+
+// TH tile rows, MR rows per P-pass thread (2 columns each), SR S-pass rows per item, XW
+// X-pass columns per item, NSTAGE raw stages, MINB CTAs per SM asked of the compiler.
+template <int TH_, int MR_, int SR_, int XW_, int NSTAGE_, int MINB_>
+struct Cfg {
+    static constexpr int TH = TH_, MR = MR_, SR = SR_, XW = XW_, NSTAGE = NSTAGE_, MINB = MINB_;
+    static constexpr int NT = (TH / MR) * 32;
+    static constexpr int XR = TH + 2 * R;          // rows of S and X
+    static constexpr int RAW_H = XR + 1;           // raw rows (bilinear needs one more)
+    static_assert(XR % SR == 0, "S-pass row groups must tile the halo rows");
+    static_assert((SW / 4) * (XR / SR) <= NT, "one S-pass item per thread");
+    static_assert((TW / XW) * XR <= NT, "one X-pass item per thread");
+};
 
 struct FastArgs {
     CUtensorMap tmap;                  // X_{t-1} as [K][H][W], box {BW, RAW_H, 1}
@@ -51,20 +64,20 @@ struct FastArgs {
 
 template <typename T> __host__ __device__ constexpr int align_elems() { return 16 / (int)sizeof(T); }
 
-template <typename T>
+template <typename T, typename C>
 constexpr int raw_stride() {          // elements per raw stage, padded to 128 bytes
-    return (int)(((RAW_H * BW * sizeof(T) + 127) / 128) * 128 / sizeof(T));
+    return (int)(((C::RAW_H * BW * sizeof(T) + 127) / 128) * 128 / sizeof(T));
 }
 
-template <typename T>
+template <typename T, typename C>
 struct Smem {
-    T raw[NSTAGE][raw_stride<T>()];    // each stage [RAW_H][BW], 128-byte aligned
-    float S[XR][SW];
-    float X[XR][TW];
-    float wrap[NWRAP][TH][TW];
-    uint8_t mk[XR][SW];                // 0xFF free, 0x00 occupied / off-grid
-    unsigned long long bar[NSTAGE];
-    double red[NT / 32];
+    T raw[C::NSTAGE][raw_stride<T, C>()];   // each stage [RAW_H][BW], 128-byte aligned
+    float S[C::XR][SW];
+    float X[C::XR][TW];
+    float wrap[NWRAP][C::TH][TW];
+    uint8_t mk[C::XR][SW];                   // 0xFF free, 0x00 occupied / off-grid
+    unsigned long long bar[C::NSTAGE];
+    double red[C::NT / 32];
 };
 
 __device__ __forceinline__ uint32_t su32(const void* p) {
@@ -109,12 +122,7 @@ __device__ __forceinline__ void tma_load(void* dst, const CUtensorMap* map,
         : "memory");
 }
 
-template <typename T> __device__ __forceinline__ float tof(T v);
-template <> __device__ __forceinline__ float tof<float>(float v) { return v; }
-template <> __device__ __forceinline__ float tof<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
-template <> __device__ __forceinline__ float tof<__half>(__half v) { return __half2float(v); }
-
-// Eight consecutive raw values starting at a 4-element boundary.
+// Eight consecutive raw values starting at a 4-element boundary, as FP32.
 template <typename T> __device__ __forceinline__ void load8(const T* p, float (&v)[8]);
 template <> __device__ __forceinline__ void load8<float>(const float* p, float (&v)[8]) {
     const float4 a = reinterpret_cast<const float4*>(p)[0], b = reinterpret_cast<const float4*>(p)[1];
@@ -150,57 +158,64 @@ __device__ __forceinline__ void box_x(int tx0, const Shift& s, int& x_al, int& x
     xo = x - x_al;
 }
 
-// S-pass: S[y][c] for y in [0, 36), c in [0, 72) (tile col c - 2), items of 4 columns x 3
-// rows with the x-lerp of the shared raw row carried down.  XO is xo mod 4; the runtime
-// part xo - XO (0 or 4 for 16-bit types) moves the base address.
-template <typename T, int XO>
-__device__ __forceinline__ void s_pass(Smem<T>& sm, int stage, int xbase, float fx, float fy) {
+// S-pass: S[y][c] for y in [0, XR), c in [0, 72) (tile col c - 2); one item per thread: 4
+// columns x SR rows, the x-lerp of the shared raw row carried down.  XO is xo mod 4; the
+// runtime part xo - XO (0, or 4 for 16-bit types) moves the base address.
+template <typename T, typename C, int XO>
+__device__ __forceinline__ void s_pass(Smem<T, C>& sm, int stage, int xbase, float fx, float fy) {
     constexpr int UNITS = SW / 4;              // 18
-    constexpr int ITEMS = UNITS * (XR / 3);    // 216
-    for (int q = threadIdx.x; q < ITEMS; q += NT) {
-        const int u = q % UNITS, y0 = (q / UNITS) * 3;
-        const int c0 = 4 * u;
-        float prev[4];
+    constexpr int ITEMS = UNITS * (C::XR / C::SR);
+    const int q = threadIdx.x;
+    if (q >= ITEMS) return;
+    const int u = q % UNITS, y0 = (q / UNITS) * C::SR;
+    const int c0 = 4 * u;
+    float prev[4];
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            const T* row = &sm.raw[stage][(y0 + r) * BW + c0 + xbase];
-            float v[8];
-            load8<T>(row, v);
-            float xl[4];
+    for (int r = 0; r <= C::SR; ++r) {
+        float v[8];
+        load8<T>(&sm.raw[stage][(y0 + r) * BW + c0 + xbase], v);
+        float xl[4];
 #pragma unroll
-            for (int k = 0; k < 4; ++k) xl[k] = fmaf(fx, v[XO + k + 1] - v[XO + k], v[XO + k]);
-            if (r > 0) {
-                const uint32_t m = *reinterpret_cast<const uint32_t*>(&sm.mk[y0 + r - 1][c0]);
-                float4 o;
-                float* op = &o.x;
+        for (int k = 0; k < 4; ++k) xl[k] = fmaf(fx, v[XO + k + 1] - v[XO + k], v[XO + k]);
+        if (r > 0) {
+            const uint32_t m = *reinterpret_cast<const uint32_t*>(&sm.mk[y0 + r - 1][c0]);
+            float4 o;
+            float* op = &o.x;
 #pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    const float s = fmaf(fy, xl[k] - prev[k], prev[k]);
-                    const uint32_t mm = __byte_perm(m, 0u, 0x8888u + 0x1111u * k);
-                    op[k] = __uint_as_float(__float_as_uint(s) & mm);
-                }
-                *reinterpret_cast<float4*>(&sm.S[y0 + r - 1][c0]) = o;
+            for (int k = 0; k < 4; ++k) {
+                const float s = fmaf(fy, xl[k] - prev[k], prev[k]);
+                const uint32_t mm = __byte_perm(m, 0u, 0x8888u + 0x1111u * k);
+                op[k] = __uint_as_float(__float_as_uint(s) & mm);
             }
-#pragma unroll
-            for (int k = 0; k < 4; ++k) prev[k] = xl[k];
+            *reinterpret_cast<float4*>(&sm.S[y0 + r - 1][c0]) = o;
         }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) prev[k] = xl[k];
     }
 }
 
-template <typename T>
-__device__ __forceinline__ void x_pass(Smem<T>& sm, float g0, float g1, float g2) {
-    constexpr int UNITS = TW / 4;              // 16
-    for (int q = threadIdx.x; q < UNITS * XR; q += NT) {
-        const int u = q % UNITS, y = q / UNITS;
-        const float4 a = *reinterpret_cast<const float4*>(&sm.S[y][4 * u]);
-        const float4 b = *reinterpret_cast<const float4*>(&sm.S[y][4 * u + 4]);
-        const float s[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+// X-pass: X[y][c0..c0+XW) = x-blur of S, one item (XW columns of one row) per thread.
+template <typename T, typename C>
+__device__ __forceinline__ void x_pass(Smem<T, C>& sm, float g0, float g1, float g2) {
+    constexpr int UNITS = TW / C::XW;
+    const int q = threadIdx.x;
+    if (q >= UNITS * C::XR) return;
+    const int u = q % UNITS, y = q / UNITS;
+    const int c0 = C::XW * u;
+    float s[C::XW + 4];
+#pragma unroll
+    for (int k = 0; k < C::XW + 4; k += 4) {
+        const float4 a = *reinterpret_cast<const float4*>(&sm.S[y][c0 + k]);
+        s[k] = a.x; s[k + 1] = a.y; s[k + 2] = a.z; s[k + 3] = a.w;
+    }
+#pragma unroll
+    for (int k = 0; k < C::XW; k += 4) {
         float4 o;
         float* op = &o.x;
 #pragma unroll
-        for (int k = 0; k < 4; ++k)
-            op[k] = fmaf(g2, s[k] + s[k + 4], fmaf(g1, s[k + 1] + s[k + 3], g0 * s[k + 2]));
-        *reinterpret_cast<float4*>(&sm.X[y][4 * u]) = o;
+        for (int j = 0; j < 4; ++j)
+            op[j] = fmaf(g2, s[k + j] + s[k + j + 4], fmaf(g1, s[k + j + 1] + s[k + j + 3], g0 * s[k + j + 2]));
+        *reinterpret_cast<float4*>(&sm.X[y][c0 + k]) = o;
     }
 }
 
@@ -225,35 +240,37 @@ template <> __device__ __forceinline__ void store2<__half>(__half* p, float a, f
 }
 
 // P-pass for plane p with the newest ring slot PH = p mod 7.
-template <typename T, int PH>
-__device__ __forceinline__ void p_pass(Smem<T>& sm, const FastArgs& a, float (&ring)[RING][8],
-                                       const float (&cs)[8], int p, int rg, int cp, int ty0,
+template <typename T, typename C, int PH>
+__device__ __forceinline__ void p_pass(Smem<T, C>& sm, const FastArgs& a, float (&ring)[RING][2 * C::MR],
+                                       const float (&cs)[2 * C::MR], int p, int rg, int cp, int ty0,
                                        int tx0, double& acc) {
+    constexpr int MR = C::MR;
     const int K = a.K;
+    const int r0 = MR * rg;
     if (p < K) {
-        float x[8][2];
+        float x[MR + 4][2];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const float2 v = *reinterpret_cast<const float2*>(&sm.X[4 * rg + q][2 * cp]);
+        for (int q = 0; q < MR + 4; ++q) {
+            const float2 v = *reinterpret_cast<const float2*>(&sm.X[r0 + q][2 * cp]);
             x[q][0] = v.x;
             x[q][1] = v.y;
         }
 #pragma unroll
-        for (int rr = 0; rr < 4; ++rr)
+        for (int rr = 0; rr < MR; ++rr)
 #pragma unroll
             for (int cc = 0; cc < 2; ++cc)
                 ring[PH][rr * 2 + cc] = fmaf(a.g2, x[rr][cc] + x[rr + 4][cc],
                                              fmaf(a.g1, x[rr + 1][cc] + x[rr + 3][cc], a.g0 * x[rr + 2][cc]));
         if (p < NWRAP) {
 #pragma unroll
-            for (int rr = 0; rr < 4; ++rr)
-                *reinterpret_cast<float2*>(&sm.wrap[p][4 * rg + rr][2 * cp]) =
+            for (int rr = 0; rr < MR; ++rr)
+                *reinterpret_cast<float2*>(&sm.wrap[p][r0 + rr][2 * cp]) =
                     make_float2(ring[PH][rr * 2], ring[PH][rr * 2 + 1]);
         }
     } else {
 #pragma unroll
-        for (int rr = 0; rr < 4; ++rr) {
-            const float2 v = *reinterpret_cast<const float2*>(&sm.wrap[p - K][4 * rg + rr][2 * cp]);
+        for (int rr = 0; rr < MR; ++rr) {
+            const float2 v = *reinterpret_cast<const float2*>(&sm.wrap[p - K][r0 + rr][2 * cp]);
             ring[PH][rr * 2] = v.x;
             ring[PH][rr * 2 + 1] = v.y;
         }
@@ -261,11 +278,12 @@ __device__ __forceinline__ void p_pass(Smem<T>& sm, const FastArgs& a, float (&r
     if (p >= 2 * RT) {
         int o = p - RT;
         if (o >= K) o -= K;
-        T* out = static_cast<T*>(a.B_out) + (size_t)o * a.H * a.W;
+        const size_t plane = (size_t)o * a.H * a.W;
+        T* out = static_cast<T*>(a.B_out);
         float part = 0.0f;
         const int gx = tx0 + 2 * cp;
 #pragma unroll
-        for (int rr = 0; rr < 4; ++rr) {
+        for (int rr = 0; rr < MR; ++rr) {
             float v[2];
 #pragma unroll
             for (int cc = 0; cc < 2; ++cc) {
@@ -274,30 +292,31 @@ __device__ __forceinline__ void p_pass(Smem<T>& sm, const FastArgs& a, float (&r
                 for (int d = 0; d < RING; ++d) t = fmaf(a.gt[d], ring[(PH + 1 + d) % RING][rr * 2 + cc], t);
                 v[cc] = cs[rr * 2 + cc] * t;
             }
-            const int gy = ty0 + 4 * rg + rr;
+            const int gy = ty0 + r0 + rr;
             if (gy < a.H && gx < a.W) {
-                const size_t q_lin = ((size_t)o * a.H + gy) * a.W + gx;
+                const size_t q_lin = plane + (size_t)gy * a.W + gx;
                 const uint32_t h = sizeof(T) == 2 ? pcg_hash((uint32_t)q_lin ^ a.seed) : 0u;
-                store2<T>(out + (q_lin - (size_t)o * a.H * a.W), v[0], v[1], h, part);
+                store2<T>(out + q_lin, v[0], v[1], h, part);
             }
         }
         acc += (double)part;
     }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(NT, 2) step_fast_kernel(const __grid_constant__ FastArgs a) {
+template <typename T, typename C>
+__global__ void __launch_bounds__(C::NT, C::MINB) step_tiled_kernel(const __grid_constant__ FastArgs a) {
+    constexpr int NT = C::NT, TH = C::TH, MR = C::MR, NSTAGE = C::NSTAGE, XR = C::XR;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     // the dynamic region is only guaranteed 16-byte aligned: round up to 128 bytes
     const uint32_t base = su32(smem_raw);
-    Smem<T>& sm = *reinterpret_cast<Smem<T>*>(smem_raw + (((base + 127u) & ~127u) - base));
+    Smem<T, C>& sm = *reinterpret_cast<Smem<T, C>*>(smem_raw + (((base + 127u) & ~127u) - base));
     const int tid = threadIdx.x;
     const int H = a.H, W = a.W, K = a.K;
     const int ty0 = blockIdx.y * TH, tx0 = blockIdx.x * TW;
     const int reinit = a.sd->reinit;
     // restart: the input is M / (K n_free); read M and fold 1 / (K n_free) into the scale
     const float in_scale = (reinit ? a.inv_uniform : (float)(1.0 / a.sd->Z)) * a.out_mult;
-    constexpr uint32_t kBoxBytes = RAW_H * BW * sizeof(T);
+    constexpr uint32_t kBoxBytes = C::RAW_H * BW * sizeof(T);
 
     // map mask over the halo region: rows ty0-2 .., cols tx0-2 ..
     for (int q = tid; q < XR * SW; q += NT) {
@@ -326,21 +345,21 @@ __global__ void __launch_bounds__(NT, 2) step_fast_kernel(const __grid_constant_
             for (int q = 0; q < next_issue; ++q) issue(q);
     }
 
-    // this thread's output cells in the P-pass: rows 4rg..4rg+3, cols 2cp, 2cp+1
+    // this thread's output cells in the P-pass: rows MR*rg .. +MR-1, cols 2cp, 2cp+1
     const int cp = tid % 32, rg = tid / 32;
-    float cs[8];
+    float cs[2 * MR];
 #pragma unroll
-    for (int rr = 0; rr < 4; ++rr)
+    for (int rr = 0; rr < MR; ++rr)
 #pragma unroll
         for (int cc = 0; cc < 2; ++cc) {
-            const int gy = ty0 + 4 * rg + rr, gx = tx0 + 2 * cp + cc;
+            const int gy = ty0 + MR * rg + rr, gx = tx0 + 2 * cp + cc;
             cs[rr * 2 + cc] = (gy < H && gx < W) ? a.corr[(size_t)gy * W + gx] * in_scale : 0.0f;
         }
-    float ring[RING][8];
+    float ring[RING][2 * MR];
 #pragma unroll
     for (int d = 0; d < RING; ++d)
 #pragma unroll
-        for (int k = 0; k < 8; ++k) ring[d][k] = 0.0f;
+        for (int k = 0; k < 2 * MR; ++k) ring[d][k] = 0.0f;
     double acc = 0.0;
     int failed = 0;
 
@@ -352,9 +371,9 @@ __global__ void __launch_bounds__(NT, 2) step_fast_kernel(const __grid_constant_
             int x_al, xo;
             box_x<T>(tx0, s, x_al, xo);
             if (reinit) {
-                // uniform belief over free cells, written where TMA would have put the tile
+                // the uniform input, written where TMA would have put the tile (M as 0/1)
                 const int y0 = ty0 - R + s.oy;
-                for (int q = tid; q < RAW_H * BW; q += NT) {
+                for (int q = tid; q < C::RAW_H * BW; q += NT) {
                     const int y = q / BW, c = q % BW;
                     const int gy = y0 + y, gx = x_al + c;
                     float v = 0.0f;
@@ -368,10 +387,10 @@ __global__ void __launch_bounds__(NT, 2) step_fast_kernel(const __grid_constant_
             if (!failed) {
                 const int xb = xo & ~3;
                 switch (xo & 3) {
-                    case 0: s_pass<T, 0>(sm, stage, xb, s.fx, s.fy); break;
-                    case 1: s_pass<T, 1>(sm, stage, xb, s.fx, s.fy); break;
-                    case 2: s_pass<T, 2>(sm, stage, xb, s.fx, s.fy); break;
-                    default: s_pass<T, 3>(sm, stage, xb, s.fx, s.fy); break;
+                    case 0: s_pass<T, C, 0>(sm, stage, xb, s.fx, s.fy); break;
+                    case 1: s_pass<T, C, 1>(sm, stage, xb, s.fx, s.fy); break;
+                    case 2: s_pass<T, C, 2>(sm, stage, xb, s.fx, s.fy); break;
+                    default: s_pass<T, C, 3>(sm, stage, xb, s.fx, s.fy); break;
                 }
             }
             if (__syncthreads_or(failed)) {
@@ -385,17 +404,17 @@ __global__ void __launch_bounds__(NT, 2) step_fast_kernel(const __grid_constant_
                 }
                 next_issue = p + NSTAGE + 1;
             }
-            x_pass<T>(sm, a.g0, a.g1, a.g2);
+            x_pass<T, C>(sm, a.g0, a.g1, a.g2);
             __syncthreads();
         }
         switch (p % RING) {
-            case 0: p_pass<T, 0>(sm, a, ring, cs, p, rg, cp, ty0, tx0, acc); break;
-            case 1: p_pass<T, 1>(sm, a, ring, cs, p, rg, cp, ty0, tx0, acc); break;
-            case 2: p_pass<T, 2>(sm, a, ring, cs, p, rg, cp, ty0, tx0, acc); break;
-            case 3: p_pass<T, 3>(sm, a, ring, cs, p, rg, cp, ty0, tx0, acc); break;
-            case 4: p_pass<T, 4>(sm, a, ring, cs, p, rg, cp, ty0, tx0, acc); break;
-            case 5: p_pass<T, 5>(sm, a, ring, cs, p, rg, cp, ty0, tx0, acc); break;
-            default: p_pass<T, 6>(sm, a, ring, cs, p, rg, cp, ty0, tx0, acc); break;
+            case 0: p_pass<T, C, 0>(sm, a, ring, cs, p, rg, cp, ty0, tx0, acc); break;
+            case 1: p_pass<T, C, 1>(sm, a, ring, cs, p, rg, cp, ty0, tx0, acc); break;
+            case 2: p_pass<T, C, 2>(sm, a, ring, cs, p, rg, cp, ty0, tx0, acc); break;
+            case 3: p_pass<T, C, 3>(sm, a, ring, cs, p, rg, cp, ty0, tx0, acc); break;
+            case 4: p_pass<T, C, 4>(sm, a, ring, cs, p, rg, cp, ty0, tx0, acc); break;
+            case 5: p_pass<T, C, 5>(sm, a, ring, cs, p, rg, cp, ty0, tx0, acc); break;
+            default: p_pass<T, C, 6>(sm, a, ring, cs, p, rg, cp, ty0, tx0, acc); break;
         }
     }
 
@@ -428,6 +447,44 @@ __global__ void __launch_bounds__(NT, 2) step_fast_kernel(const __grid_constant_
     });
 }
 
+// The tile configurations.  1: 32-row tiles (large grids); 2: 16-row tiles with 2-row
+// P-pass items (256 threads); 3: 16-row tiles with 4-row P-pass items (128 threads).
+using Cfg1 = Cfg<32, 4, 3, 16, 3, 2>;
+using Cfg2 = Cfg<16, 2, 2, 8, 3, 3>;
+using Cfg3 = Cfg<16, 4, 4, 16, 3, 4>;
+
+template <typename T, typename C> size_t smem_bytes() { return sizeof(Smem<T, C>) + 128; }
+
+// Launch with the dynamic shared memory size; the attribute is set once per device.
+template <typename T, typename C>
+cudaError_t launch_typed(const FastArgs& a, dim3 grid, cudaStream_t st) {
+    static bool attr_set[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const size_t sb = smem_bytes<T, C>();
+    if (dev < 0 || dev >= 64 || !attr_set[dev]) {
+        cudaError_t e = cudaFuncSetAttribute(step_tiled_kernel<T, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb);
+        if (e != cudaSuccess) return e;
+        if (dev >= 0 && dev < 64) attr_set[dev] = true;
+    }
+    step_tiled_kernel<T, C><<<grid, C::NT, sb, st>>>(a);
+    return cudaSuccess;
+}
+
+template <typename T>
+cudaError_t launch_cfg(int cfg, const FastArgs& a, int W, int H, cudaStream_t st) {
+    switch (cfg) {
+        case 1: return launch_typed<T, Cfg1>(a, dim3((W + TW - 1) / TW, (H + Cfg1::TH - 1) / Cfg1::TH), st);
+        case 2: return launch_typed<T, Cfg2>(a, dim3((W + TW - 1) / TW, (H + Cfg2::TH - 1) / Cfg2::TH), st);
+        case 3: return launch_typed<T, Cfg3>(a, dim3((W + TW - 1) / TW, (H + Cfg3::TH - 1) / Cfg3::TH), st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+int cfg_tile_rows(int cfg) {
+    return cfg == 1 ? Cfg1::TH : cfg == 2 ? Cfg2::TH : Cfg3::TH;
+}
+
 using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
@@ -445,41 +502,34 @@ EncodeTiled encoder() {
     return fn;
 }
 
-template <typename T> size_t smem_bytes() { return sizeof(Smem<T>) + 128; }
-
-// Launch with the dynamic shared memory size; the attribute is set once per device.
-template <typename T>
-cudaError_t launch_typed(const FastArgs& a, dim3 grid, cudaStream_t st) {
-    static bool attr_set[64] = {};
-    int dev = 0;
-    cudaGetDevice(&dev);
-    const size_t sb = smem_bytes<T>();
-    if (dev < 0 || dev >= 64 || !attr_set[dev]) {
-        cudaError_t e = cudaFuncSetAttribute(step_fast_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb);
-        if (e != cudaSuccess) return e;
-        if (dev >= 0 && dev < 64) attr_set[dev] = true;
-    }
-    step_fast_kernel<T><<<grid, NT, sb, st>>>(a);
-    return cudaSuccess;
-}
-
 }  // namespace
 
-bool step_fast_eligible(int H, int W, int K, int r_xy, int r_th, int storage) {
+bool step_tiled_eligible(int H, int W, int K, int r_xy, int r_th, int storage) {
     const int align = storage == LOC_F32 ? 4 : 8;
     return r_xy == R && r_th == RT && K >= 8 && K <= LOC_MAX_K && W % align == 0 && W >= 8 && H >= 1;
 }
 
-cudaError_t make_step_tmap(void* tmap_out, const void* B, int storage, int H, int W, int K) {
+int step_tiled_num_cfgs() { return 3; }
+
+int step_tiled_default_cfg(int H, int W, int K, int storage) {
+    (void)K;
+    (void)storage;
+    // enough 32-row tiles to give every SM several: large grids; otherwise 16-row tiles
+    const long long tiles32 = (long long)((W + TW - 1) / TW) * ((H + 31) / 32);
+    return tiles32 >= 4 * 152 ? 1 : 2;
+}
+
+cudaError_t make_step_tmap(void* tmap_out, const void* B, int storage, int H, int W, int K, int cfg) {
     EncodeTiled enc = encoder();
     if (!enc) return cudaErrorNotSupported;
+    if (cfg < 1 || cfg > 3) return cudaErrorInvalidValue;
     const size_t e = storage == LOC_F32 ? 4 : 2;
     const CUtensorMapDataType dt = storage == LOC_F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
                                    : storage == LOC_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
                                                          : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
     const cuuint64_t dims[3] = {(cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)K};
     const cuuint64_t strides[2] = {(cuuint64_t)W * e, (cuuint64_t)W * H * e};
-    const cuuint32_t box[3] = {(cuuint32_t)BW, (cuuint32_t)RAW_H, 1};
+    const cuuint32_t box[3] = {(cuuint32_t)BW, (cuuint32_t)(cfg_tile_rows(cfg) + 2 * R + 1), 1};
     const cuuint32_t estr[3] = {1, 1, 1};
     CUresult r = enc(static_cast<CUtensorMap*>(tmap_out), dt, 3, const_cast<void*>(B), dims, strides, box,
                      estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -489,11 +539,7 @@ cudaError_t make_step_tmap(void* tmap_out, const void* B, int storage, int H, in
 
 size_t step_tmap_bytes() { return sizeof(CUtensorMap); }
 
-unsigned int step_fast_num_blocks(int H, int W) {
-    return (unsigned int)(((W + TW - 1) / TW) * ((H + TH - 1) / TH));
-}
-
-cudaError_t launch_step_fast(const StepArgs& g, const void* tmap, int storage, cudaStream_t st) {
+cudaError_t launch_step_tiled(const StepArgs& g, const void* tmap, int storage, int cfg, cudaStream_t st) {
     FastArgs a;
     memcpy(&a.tmap, tmap, sizeof(CUtensorMap));
     a.B_out = g.B_out;
@@ -513,12 +559,11 @@ cudaError_t launch_step_fast(const StepArgs& g, const void* tmap, int storage, c
     a.g2 = g.gx[R + 2];
     for (int d = 0; d < RING; ++d) a.gt[d] = g.gt[d];
     for (int k = 0; k < g.K; ++k) a.sh[k] = g.sh[k];
-    dim3 grid((g.W + TW - 1) / TW, (g.H + TH - 1) / TH);
-    cudaError_t e = cudaSuccess;
+    cudaError_t e;
     switch (storage) {
-        case LOC_F32: e = launch_typed<float>(a, grid, st); break;
-        case LOC_BF16: e = launch_typed<__nv_bfloat16>(a, grid, st); break;
-        case LOC_F16: e = launch_typed<__half>(a, grid, st); break;
+        case LOC_F32: e = launch_cfg<float>(cfg, a, g.W, g.H, st); break;
+        case LOC_BF16: e = launch_cfg<__nv_bfloat16>(cfg, a, g.W, g.H, st); break;
+        case LOC_F16: e = launch_cfg<__half>(cfg, a, g.W, g.H, st); break;
         default: return cudaErrorInvalidValue;
     }
     if (e != cudaSuccess) return e;

@@ -45,14 +45,15 @@ SHAPES = [
 ]
 
 
+@pytest.mark.parametrize("tile", [1, 2, 3])
 @pytest.mark.parametrize("H,W,K,mot", SHAPES, ids=[f"{s[0]}x{s[1]}x{s[2]}" for s in SHAPES])
-def test_tiled_matches_oracle_and_generic(H, W, K, mot):
+def test_tiled_matches_oracle_and_generic(H, W, K, mot, tile):
     rng = np.random.default_rng(H * 7 + W * 3 + K)
     occ = (rng.random((H, W)) < 0.2).astype(np.uint8)
     occ[H // 2, W // 2] = 0
     cell = 0.05
     b = fields.belief_like(occ, K, seed=K, dtype=np.float32)
-    ht = make(occ, K, cell)
+    ht = make(occ, K, cell, tile=tile)
     hg = make(occ, K, cell, kernel=loc.LOC_KERNEL_GENERIC)
     ref = F.Filter(occ, K, cell)
     ref.B = b.astype(np.float64) / b.astype(np.float64).sum()
@@ -117,6 +118,8 @@ def test_tiled_is_refused_where_it_does_not_apply():
         make(np.zeros((32, 32), np.uint8), 6, 0.1)    # K below the tiled minimum
     with pytest.raises(loc.LocError):
         make(np.zeros((32, 32), np.uint8), 16, 0.1, sigma_xy_cells=1.0)
+    with pytest.raises(loc.LocError):
+        make(np.zeros((32, 32), np.uint8), 16, 0.1, tile=9)
 
 
 @pytest.mark.parametrize("storage", ["bf16", "f16"])
