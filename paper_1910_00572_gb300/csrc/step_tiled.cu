@@ -122,6 +122,32 @@ __device__ __forceinline__ void tma_load(void* dst, const CUtensorMap* map,
         : "memory");
 }
 
+// Packed pairs of FP32 (Blackwell's 2-wide FP32 pipe): lo = first element, hi = second.
+typedef unsigned long long f2;
+__device__ __forceinline__ f2 pk(float a, float b) {
+    f2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void upk(f2 v, float& a, float& b) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ f2 fadd2(f2 a, f2 b) {
+    f2 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2 fmul2(f2 a, f2 b) {
+    f2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2 ffma2(f2 a, f2 b, f2 c) {
+    f2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
 // Eight consecutive raw values starting at a 4-element boundary, as FP32.
 template <typename T> __device__ __forceinline__ void load8(const T* p, float (&v)[8]);
 template <> __device__ __forceinline__ void load8<float>(const float* p, float (&v)[8]) {
@@ -169,6 +195,7 @@ __device__ __forceinline__ void s_pass(Smem<T, C>& sm, int stage, int xbase, flo
     if (q >= ITEMS) return;
     const int u = q % UNITS, y0 = (q / UNITS) * C::SR;
     const int c0 = 4 * u;
+    const f2 fy2 = pk(fy, fy), gy02 = pk(1.0f - fy, 1.0f - fy);
     float prev[4];
 #pragma unroll
     for (int r = 0; r <= C::SR; ++r) {
@@ -179,13 +206,18 @@ __device__ __forceinline__ void s_pass(Smem<T, C>& sm, int stage, int xbase, flo
         for (int k = 0; k < 4; ++k) xl[k] = fmaf(fx, v[XO + k + 1] - v[XO + k], v[XO + k]);
         if (r > 0) {
             const uint32_t m = *reinterpret_cast<const uint32_t*>(&sm.mk[y0 + r - 1][c0]);
+            // y-lerp on column pairs: (1 - fy) * upper + fy * lower
+            const f2 s01 = ffma2(fy2, pk(xl[0], xl[1]), fmul2(gy02, pk(prev[0], prev[1])));
+            const f2 s23 = ffma2(fy2, pk(xl[2], xl[3]), fmul2(gy02, pk(prev[2], prev[3])));
+            float sv[4];
+            upk(s01, sv[0], sv[1]);
+            upk(s23, sv[2], sv[3]);
             float4 o;
             float* op = &o.x;
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-                const float s = fmaf(fy, xl[k] - prev[k], prev[k]);
                 const uint32_t mm = __byte_perm(m, 0u, 0x8888u + 0x1111u * k);
-                op[k] = __uint_as_float(__float_as_uint(s) & mm);
+                op[k] = __uint_as_float(__float_as_uint(sv[k]) & mm);
             }
             *reinterpret_cast<float4*>(&sm.S[y0 + r - 1][c0]) = o;
         }
@@ -219,87 +251,82 @@ __device__ __forceinline__ void x_pass(Smem<T, C>& sm, float g0, float g1, float
     }
 }
 
-// Store two neighbouring outputs (FP32 as is, BF16 stochastically rounded with the 32 random
-// bits h, FP16 round-to-nearest) and add the stored values to sum.
-template <typename T> __device__ __forceinline__ void store2(T* p, float a, float b, uint32_t h, float& sum);
-template <> __device__ __forceinline__ void store2<float>(float* p, float a, float b, uint32_t, float& sum) {
-    *reinterpret_cast<float2*>(p) = make_float2(a, b);
-    sum += a + b;
+// Store two neighbouring outputs v = {a, b} (FP32 as is, BF16 stochastically rounded with the
+// 32 random bits h, FP16 round-to-nearest) and add the stored values to sum.
+template <typename T> __device__ __forceinline__ void store2(T* p, f2 v, uint32_t h, f2& sum);
+template <> __device__ __forceinline__ void store2<float>(float* p, f2 v, uint32_t, f2& sum) {
+    *reinterpret_cast<f2*>(p) = v;
+    sum = fadd2(sum, v);
 }
-template <> __device__ __forceinline__ void store2<__nv_bfloat16>(__nv_bfloat16* p, float a, float b, uint32_t h, float& sum) {
-    __nv_bfloat162 v;
-    v.x = bf16_sr(a, h);
-    v.y = bf16_sr(b, h >> 16);
-    *reinterpret_cast<__nv_bfloat162*>(p) = v;
-    sum += __low2float(v) + __high2float(v);
+template <> __device__ __forceinline__ void store2<__nv_bfloat16>(__nv_bfloat16* p, f2 v, uint32_t h, f2& sum) {
+    float a, b;
+    upk(v, a, b);
+    const uint32_t ua = __float_as_uint(a) + (h & 0xFFFFu);
+    const uint32_t ub = __float_as_uint(b) + (h >> 16);
+    const uint32_t packed = __byte_perm(ua, ub, 0x7632);         // high halves: {a, b} as bf16x2
+    *reinterpret_cast<uint32_t*>(p) = packed;
+    sum = fadd2(sum, pk(__uint_as_float(ua & 0xFFFF0000u), __uint_as_float(ub & 0xFFFF0000u)));
 }
-template <> __device__ __forceinline__ void store2<__half>(__half* p, float a, float b, uint32_t, float& sum) {
-    const __half2 v = __floats2half2_rn(a, b);
-    *reinterpret_cast<__half2*>(p) = v;
-    sum += __low2float(v) + __high2float(v);
+template <> __device__ __forceinline__ void store2<__half>(__half* p, f2 v, uint32_t, f2& sum) {
+    float a, b;
+    upk(v, a, b);
+    const __half2 hv = __floats2half2_rn(a, b);
+    *reinterpret_cast<__half2*>(p) = hv;
+    sum = fadd2(sum, pk(__low2float(hv), __high2float(hv)));
 }
 
-// P-pass for plane p with the newest ring slot PH = p mod 7.
+// Packed taps of the P-pass.
+struct Taps2 {
+    f2 g0, g1, g2;                     // y taps {g, g}
+    f2 gt[RING];                       // theta taps {g, g}
+};
+
+// P-pass for plane p with the newest ring slot PH = p mod 7.  The thread's cells are rows
+// r0 .. r0+MR-1 of the tile, columns 2cp and 2cp+1, handled as column pairs.
 template <typename T, typename C, int PH>
-__device__ __forceinline__ void p_pass(Smem<T, C>& sm, const FastArgs& a, float (&ring)[RING][2 * C::MR],
-                                       const float (&cs)[2 * C::MR], int p, int rg, int cp, int ty0,
-                                       int tx0, double& acc) {
+__device__ __forceinline__ void p_pass(Smem<T, C>& sm, const FastArgs& a, const Taps2& tp,
+                                       f2 (&ring)[RING][C::MR], const f2 (&cs)[C::MR], int p,
+                                       int r0, int cp, int ty0, int gx, double& acc) {
     constexpr int MR = C::MR;
     const int K = a.K;
-    const int r0 = MR * rg;
     if (p < K) {
-        float x[MR + 4][2];
+        f2 x[MR + 4];
 #pragma unroll
-        for (int q = 0; q < MR + 4; ++q) {
-            const float2 v = *reinterpret_cast<const float2*>(&sm.X[r0 + q][2 * cp]);
-            x[q][0] = v.x;
-            x[q][1] = v.y;
-        }
+        for (int q = 0; q < MR + 4; ++q) x[q] = *reinterpret_cast<const f2*>(&sm.X[r0 + q][2 * cp]);
 #pragma unroll
         for (int rr = 0; rr < MR; ++rr)
-#pragma unroll
-            for (int cc = 0; cc < 2; ++cc)
-                ring[PH][rr * 2 + cc] = fmaf(a.g2, x[rr][cc] + x[rr + 4][cc],
-                                             fmaf(a.g1, x[rr + 1][cc] + x[rr + 3][cc], a.g0 * x[rr + 2][cc]));
+            ring[PH][rr] = ffma2(tp.g2, fadd2(x[rr], x[rr + 4]),
+                                 ffma2(tp.g1, fadd2(x[rr + 1], x[rr + 3]), fmul2(tp.g0, x[rr + 2])));
         if (p < NWRAP) {
 #pragma unroll
-            for (int rr = 0; rr < MR; ++rr)
-                *reinterpret_cast<float2*>(&sm.wrap[p][r0 + rr][2 * cp]) =
-                    make_float2(ring[PH][rr * 2], ring[PH][rr * 2 + 1]);
+            for (int rr = 0; rr < MR; ++rr) *reinterpret_cast<f2*>(&sm.wrap[p][r0 + rr][2 * cp]) = ring[PH][rr];
         }
     } else {
 #pragma unroll
-        for (int rr = 0; rr < MR; ++rr) {
-            const float2 v = *reinterpret_cast<const float2*>(&sm.wrap[p - K][r0 + rr][2 * cp]);
-            ring[PH][rr * 2] = v.x;
-            ring[PH][rr * 2 + 1] = v.y;
-        }
+        for (int rr = 0; rr < MR; ++rr) ring[PH][rr] = *reinterpret_cast<const f2*>(&sm.wrap[p - K][r0 + rr][2 * cp]);
     }
     if (p >= 2 * RT) {
         int o = p - RT;
         if (o >= K) o -= K;
-        const size_t plane = (size_t)o * a.H * a.W;
-        T* out = static_cast<T*>(a.B_out);
-        float part = 0.0f;
-        const int gx = tx0 + 2 * cp;
+        const size_t base = ((size_t)o * a.H + (ty0 + r0)) * a.W + gx;
+        T* out = static_cast<T*>(a.B_out) + base;
+        uint32_t h = sizeof(T) == 2 ? pcg_hash((uint32_t)base ^ a.seed) : 0u;
+        f2 part = 0ull;
 #pragma unroll
         for (int rr = 0; rr < MR; ++rr) {
-            float v[2];
+            f2 t = fmul2(tp.gt[0], ring[(PH + 1) % RING][rr]);
 #pragma unroll
-            for (int cc = 0; cc < 2; ++cc) {
-                float t = 0.0f;
-#pragma unroll
-                for (int d = 0; d < RING; ++d) t = fmaf(a.gt[d], ring[(PH + 1 + d) % RING][rr * 2 + cc], t);
-                v[cc] = cs[rr * 2 + cc] * t;
-            }
-            const int gy = ty0 + r0 + rr;
-            if (gy < a.H && gx < a.W) {
-                const size_t q_lin = plane + (size_t)gy * a.W + gx;
-                const uint32_t h = sizeof(T) == 2 ? pcg_hash((uint32_t)q_lin ^ a.seed) : 0u;
-                store2<T>(out + q_lin, v[0], v[1], h, part);
+            for (int d = 1; d < RING; ++d) t = ffma2(tp.gt[d], ring[(PH + 1 + d) % RING][rr], t);
+            const f2 v = fmul2(cs[rr], t);
+            if (ty0 + r0 + rr < a.H && gx < a.W) store2<T>(out + (size_t)rr * a.W, v, h, part);
+            if (sizeof(T) == 2) {       // next 32 random bits: LCG step, high bits folded down
+                h = h * 0x9E3779B1u + 0x7F4A7C15u;
+                h ^= h >> 16;
             }
         }
-        acc += (double)part;
+        float p0, p1;
+        upk(part, p0, p1);
+        acc += (double)(p0 + p1);
     }
 }
 
@@ -347,19 +374,29 @@ __global__ void __launch_bounds__(C::NT, C::MINB) step_tiled_kernel(const __grid
 
     // this thread's output cells in the P-pass: rows MR*rg .. +MR-1, cols 2cp, 2cp+1
     const int cp = tid % 32, rg = tid / 32;
-    float cs[2 * MR];
+    const int r0 = MR * rg, gxp = tx0 + 2 * cp;
+    f2 cs[MR];
 #pragma unroll
-    for (int rr = 0; rr < MR; ++rr)
-#pragma unroll
-        for (int cc = 0; cc < 2; ++cc) {
-            const int gy = ty0 + MR * rg + rr, gx = tx0 + 2 * cp + cc;
-            cs[rr * 2 + cc] = (gy < H && gx < W) ? a.corr[(size_t)gy * W + gx] * in_scale : 0.0f;
+    for (int rr = 0; rr < MR; ++rr) {
+        const int gy = ty0 + r0 + rr;
+        float c0 = 0.0f, c1 = 0.0f;
+        if (gy < H && gxp < W) {
+            c0 = a.corr[(size_t)gy * W + gxp] * in_scale;
+            c1 = a.corr[(size_t)gy * W + gxp + 1] * in_scale;
         }
-    float ring[RING][2 * MR];
+        cs[rr] = pk(c0, c1);
+    }
+    Taps2 tp;
+    tp.g0 = pk(a.g0, a.g0);
+    tp.g1 = pk(a.g1, a.g1);
+    tp.g2 = pk(a.g2, a.g2);
+#pragma unroll
+    for (int d = 0; d < RING; ++d) tp.gt[d] = pk(a.gt[d], a.gt[d]);
+    f2 ring[RING][MR];
 #pragma unroll
     for (int d = 0; d < RING; ++d)
 #pragma unroll
-        for (int k = 0; k < 2 * MR; ++k) ring[d][k] = 0.0f;
+        for (int k = 0; k < MR; ++k) ring[d][k] = 0ull;
     double acc = 0.0;
     int failed = 0;
 
@@ -408,13 +445,13 @@ __global__ void __launch_bounds__(C::NT, C::MINB) step_tiled_kernel(const __grid
             __syncthreads();
         }
         switch (p % RING) {
-            case 0: p_pass<T, C, 0>(sm, a, ring, cs, p, rg, cp, ty0, tx0, acc); break;
-            case 1: p_pass<T, C, 1>(sm, a, ring, cs, p, rg, cp, ty0, tx0, acc); break;
-            case 2: p_pass<T, C, 2>(sm, a, ring, cs, p, rg, cp, ty0, tx0, acc); break;
-            case 3: p_pass<T, C, 3>(sm, a, ring, cs, p, rg, cp, ty0, tx0, acc); break;
-            case 4: p_pass<T, C, 4>(sm, a, ring, cs, p, rg, cp, ty0, tx0, acc); break;
-            case 5: p_pass<T, C, 5>(sm, a, ring, cs, p, rg, cp, ty0, tx0, acc); break;
-            default: p_pass<T, C, 6>(sm, a, ring, cs, p, rg, cp, ty0, tx0, acc); break;
+            case 0: p_pass<T, C, 0>(sm, a, tp, ring, cs, p, r0, cp, ty0, gxp, acc); break;
+            case 1: p_pass<T, C, 1>(sm, a, tp, ring, cs, p, r0, cp, ty0, gxp, acc); break;
+            case 2: p_pass<T, C, 2>(sm, a, tp, ring, cs, p, r0, cp, ty0, gxp, acc); break;
+            case 3: p_pass<T, C, 3>(sm, a, tp, ring, cs, p, r0, cp, ty0, gxp, acc); break;
+            case 4: p_pass<T, C, 4>(sm, a, tp, ring, cs, p, r0, cp, ty0, gxp, acc); break;
+            case 5: p_pass<T, C, 5>(sm, a, tp, ring, cs, p, r0, cp, ty0, gxp, acc); break;
+            default: p_pass<T, C, 6>(sm, a, tp, ring, cs, p, r0, cp, ty0, gxp, acc); break;
         }
     }
 
