@@ -236,6 +236,7 @@ LOC_API loc_status loc_create(const uint8_t* occ, const loc_params* p, loc_handl
 
     SessionDev init{};
     init.Z = 1.0;
+    init.inv_Z = 1.0f;
     init.reinit = 1;               // the stored tensor reads as uniform over free cells
     cudaError_t e = cudaMemcpyAsync(s->trav, trav.data(), hw, cudaMemcpyHostToDevice, s->stream);
     if (e == cudaSuccess)

@@ -6,7 +6,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include "../../include/loc.h"
+#include "loc.h"
 
 namespace loc {
 
@@ -29,6 +29,22 @@ struct SessionDev {
     int pad;
     unsigned long long n_reinit;   // restarts after Z == 0
     unsigned long long n_prop;     // propagations done on the device
+    float inv_Z;                   // (float)(1 / Z), written with Z (one FP64 division per step)
+    int pad2;
+};
+
+// Compensated (Kahan) FP32 running sum: a thread's share of the normaliser stays in FP32
+// registers (FP64 arithmetic is slow on this GPU) with an error of a few FP32 ulps of the
+// total, and is widened to FP64 once for the FP64 block and grid reduction.
+struct KahanF {
+    float s = 0.0f, c = 0.0f;
+    __device__ __forceinline__ void add(float x) {
+        const float y = x - c;
+        const float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return (double)s - (double)c; }
 };
 
 enum { LOC_DEV_ERR_NONFINITE_Z = 1, LOC_DEV_ERR_TIMEOUT = 2 };

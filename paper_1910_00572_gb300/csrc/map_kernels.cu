@@ -45,7 +45,7 @@ __global__ void read_belief_kernel(const T* __restrict__ B, const uint8_t* __res
                                    const SessionDev* sd, float inv_uniform, size_t hw, size_t n,
                                    float* __restrict__ out) {
     const int reinit = sd->reinit;
-    const float scale = (float)(1.0 / sd->Z);
+    const float scale = sd->inv_Z;
     for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < n;
          q += (size_t)gridDim.x * blockDim.x)
         out[q] = belief_at(B, trav, hw, q, reinit, inv_uniform, scale);
@@ -56,7 +56,7 @@ __global__ void read_marginal_kernel(const T* __restrict__ B, const uint8_t* __r
                                      const SessionDev* sd, float inv_uniform, size_t hw, int K,
                                      int mode, float* __restrict__ out) {
     const int reinit = sd->reinit;
-    const float scale = (float)(1.0 / sd->Z);
+    const float scale = sd->inv_Z;
     for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < hw;
          q += (size_t)gridDim.x * blockDim.x) {
         float acc = 0.0f;                       // beliefs are non-negative
@@ -142,6 +142,7 @@ __global__ void set_belief_kernel(const float* __restrict__ src, T* __restrict__
     const double bt = block_sum<NT>(acc, red);
     finish_sum<NT>(bt, partials, &sd->counter, gridDim.x, red, [sd](double Z) {
         sd->Z = Z;
+        sd->inv_Z = (float)(1.0 / Z);
         sd->reinit = 0;
     });
 }

@@ -42,7 +42,7 @@ __global__ void __launch_bounds__(NT) step_generic_kernel(const __grid_constant_
 
     const int reinit = a.sd->reinit;
     // restart: the input is M / (K n_free); read M and fold 1 / (K n_free) into the scale
-    const float in_scale = (reinit ? a.inv_uniform : (float)(1.0 / a.sd->Z)) * a.out_mult;
+    const float in_scale = (reinit ? a.inv_uniform : a.sd->inv_Z) * a.out_mult;
     const T* Bin = static_cast<const T*>(a.B_in);
     T* Bout = static_cast<T*>(a.B_out);
 
@@ -53,7 +53,7 @@ __global__ void __launch_bounds__(NT) step_generic_kernel(const __grid_constant_
         Mt[jj][ii] = (j >= 0 && j < H && i >= 0 && i < W) ? (float)a.trav[(size_t)j * W + i] : 0.0f;
     }
 
-    double acc = 0.0;
+    KahanF acc;
     for (int kk = -rt; kk < K + rt; ++kk) {
         const int c = ((kk % K) + K) % K;
         const Shift s = a.sh[c];
@@ -108,14 +108,14 @@ __global__ void __launch_bounds__(NT) step_generic_kernel(const __grid_constant_
                 const uint32_t q_lin = (uint32_t)((size_t)o * H * W + off);
                 part += store_out<T>(oplane + off, v, pcg_hash(q_lin ^ a.seed));
             }
-            acc += (double)part;
+            acc.add(part);
         }
         // the next channel overwrites raw/S/Xb and one ring slot that the theta blur above
         // may still read: wait for every thread first
         __syncthreads();
     }
 
-    const double bt = block_sum<NT>(acc, red);
+    const double bt = block_sum<NT>(acc.value(), red);
     const unsigned int nblocks = gridDim.x * gridDim.y;
     SessionDev* sd = a.sd;
     const double log_mult = a.log_out_mult;
@@ -123,11 +123,13 @@ __global__ void __launch_bounds__(NT) step_generic_kernel(const __grid_constant_
         sd->n_prop += 1;
         if (Z > 0.0 && isfinite(Z)) {
             sd->Z = Z;
+            sd->inv_Z = (float)(1.0 / Z);
             sd->logscale += log(Z) - log_mult;
             sd->reinit = 0;
         } else {
             if (!isfinite(Z)) sd->status |= LOC_DEV_ERR_NONFINITE_Z;
             sd->Z = 1.0;
+            sd->inv_Z = 1.0f;
             sd->reinit = 1;
             sd->n_reinit += 1;
         }

@@ -26,7 +26,10 @@ namespace {
 
 constexpr int R = 2, RT = 3;           // kernel radii this kernel is built for
 constexpr int TW = 64;                 // tile width (cells)
-constexpr int SW = 72;                 // S and mask row pitch (68 used: tile cols -2 .. 65)
+constexpr int SW = 76;                 // S row pitch (68 used: tile cols -2 .. 65; 76 = 12 mod 32
+                                       // banks, so 8 consecutive rows hit 8 distinct bank groups)
+constexpr int MW = 72;                 // mask row pitch (bytes)
+constexpr int XW_PITCH = 68;           // X row pitch (64 used; 68 = 4 mod 32 banks)
 constexpr int BW = 80;                 // raw box width in elements (76 needed + alignment)
 constexpr int RING = 2 * RT + 1;       // 7
 constexpr int NWRAP = 2 * RT;          // 6 planes kept for the circular wrap
@@ -41,7 +44,7 @@ struct Cfg {
     static constexpr int XR = TH + 2 * R;          // rows of S and X
     static constexpr int RAW_H = XR + 1;           // raw rows (bilinear needs one more)
     static_assert(XR % SR == 0, "S-pass row groups must tile the halo rows");
-    static_assert((SW / 4) * (XR / SR) <= NT, "one S-pass item per thread");
+    static_assert((72 / 4) * (XR / SR) <= NT, "one S-pass item per thread");
     static_assert((TW / XW) * XR <= NT, "one X-pass item per thread");
 };
 
@@ -73,9 +76,9 @@ template <typename T, typename C>
 struct Smem {
     T raw[C::NSTAGE][raw_stride<T, C>()];   // each stage [RAW_H][BW], 128-byte aligned
     float S[C::XR][SW];
-    float X[C::XR][TW];
+    float X[C::XR][XW_PITCH];
     float wrap[NWRAP][C::TH][TW];
-    uint8_t mk[C::XR][SW];                   // 0xFF free, 0x00 occupied / off-grid
+    uint8_t mk[C::XR][MW];                   // 0xFF free, 0x00 occupied / off-grid
     unsigned long long bar[C::NSTAGE];
     double red[C::NT / 32];
 };
@@ -189,13 +192,13 @@ __device__ __forceinline__ void box_x(int tx0, const Shift& s, int& x_al, int& x
 // runtime part xo - XO (0, or 4 for 16-bit types) moves the base address.
 template <typename T, typename C, int XO>
 __device__ __forceinline__ void s_pass(Smem<T, C>& sm, int stage, int xbase, float fx, float fy) {
-    constexpr int UNITS = SW / 4;              // 18
+    constexpr int UNITS = 72 / 4;              // 18 items of 4 columns cover tile cols -2 .. 69
     constexpr int ITEMS = UNITS * (C::XR / C::SR);
     const int q = threadIdx.x;
     if (q >= ITEMS) return;
     const int u = q % UNITS, y0 = (q / UNITS) * C::SR;
     const int c0 = 4 * u;
-    const f2 fy2 = pk(fy, fy), gy02 = pk(1.0f - fy, 1.0f - fy);
+    const float gy0 = 1.0f - fy;
     float prev[4];
 #pragma unroll
     for (int r = 0; r <= C::SR; ++r) {
@@ -206,18 +209,13 @@ __device__ __forceinline__ void s_pass(Smem<T, C>& sm, int stage, int xbase, flo
         for (int k = 0; k < 4; ++k) xl[k] = fmaf(fx, v[XO + k + 1] - v[XO + k], v[XO + k]);
         if (r > 0) {
             const uint32_t m = *reinterpret_cast<const uint32_t*>(&sm.mk[y0 + r - 1][c0]);
-            // y-lerp on column pairs: (1 - fy) * upper + fy * lower
-            const f2 s01 = ffma2(fy2, pk(xl[0], xl[1]), fmul2(gy02, pk(prev[0], prev[1])));
-            const f2 s23 = ffma2(fy2, pk(xl[2], xl[3]), fmul2(gy02, pk(prev[2], prev[3])));
-            float sv[4];
-            upk(s01, sv[0], sv[1]);
-            upk(s23, sv[2], sv[3]);
             float4 o;
             float* op = &o.x;
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
+                const float sv = fmaf(fy, xl[k], gy0 * prev[k]);
                 const uint32_t mm = __byte_perm(m, 0u, 0x8888u + 0x1111u * k);
-                op[k] = __uint_as_float(__float_as_uint(sv[k]) & mm);
+                op[k] = __uint_as_float(__float_as_uint(sv) & mm);
             }
             *reinterpret_cast<float4*>(&sm.S[y0 + r - 1][c0]) = o;
         }
@@ -232,7 +230,7 @@ __device__ __forceinline__ void x_pass(Smem<T, C>& sm, float g0, float g1, float
     constexpr int UNITS = TW / C::XW;
     const int q = threadIdx.x;
     if (q >= UNITS * C::XR) return;
-    const int u = q % UNITS, y = q / UNITS;
+    const int y = q % C::XR, u = q / C::XR;    // consecutive threads take consecutive rows
     const int c0 = C::XW * u;
     float s[C::XW + 4];
 #pragma unroll
@@ -263,9 +261,9 @@ template <> __device__ __forceinline__ void store2<__nv_bfloat16>(__nv_bfloat16*
     upk(v, a, b);
     const uint32_t ua = __float_as_uint(a) + (h & 0xFFFFu);
     const uint32_t ub = __float_as_uint(b) + (h >> 16);
-    const uint32_t packed = __byte_perm(ua, ub, 0x7632);         // high halves: {a, b} as bf16x2
-    *reinterpret_cast<uint32_t*>(p) = packed;
-    sum = fadd2(sum, pk(__uint_as_float(ua & 0xFFFF0000u), __uint_as_float(ub & 0xFFFF0000u)));
+    *reinterpret_cast<uint32_t*>(p) = __byte_perm(ua, ub, 0x7632);   // high halves: {a, b}
+    // the stochastic rounding is unbiased: Z takes the unrounded values (within ~1e-7)
+    sum = fadd2(sum, v);
 }
 template <> __device__ __forceinline__ void store2<__half>(__half* p, f2 v, uint32_t, f2& sum) {
     float a, b;
@@ -286,7 +284,7 @@ struct Taps2 {
 template <typename T, typename C, int PH>
 __device__ __forceinline__ void p_pass(Smem<T, C>& sm, const FastArgs& a, const Taps2& tp,
                                        f2 (&ring)[RING][C::MR], const f2 (&cs)[C::MR], int p,
-                                       int r0, int cp, int ty0, int gx, double& acc) {
+                                       int r0, int cp, int ty0, int gx, KahanF& acc) {
     constexpr int MR = C::MR;
     const int K = a.K;
     if (p < K) {
@@ -326,7 +324,7 @@ __device__ __forceinline__ void p_pass(Smem<T, C>& sm, const FastArgs& a, const 
         }
         float p0, p1;
         upk(part, p0, p1);
-        acc += (double)(p0 + p1);
+        acc.add(p0 + p1);
     }
 }
 
@@ -342,12 +340,12 @@ __global__ void __launch_bounds__(C::NT, C::MINB) step_tiled_kernel(const __grid
     const int ty0 = blockIdx.y * TH, tx0 = blockIdx.x * TW;
     const int reinit = a.sd->reinit;
     // restart: the input is M / (K n_free); read M and fold 1 / (K n_free) into the scale
-    const float in_scale = (reinit ? a.inv_uniform : (float)(1.0 / a.sd->Z)) * a.out_mult;
+    const float in_scale = (reinit ? a.inv_uniform : a.sd->inv_Z) * a.out_mult;
     constexpr uint32_t kBoxBytes = C::RAW_H * BW * sizeof(T);
 
     // map mask over the halo region: rows ty0-2 .., cols tx0-2 ..
-    for (int q = tid; q < XR * SW; q += NT) {
-        const int y = q / SW, c = q % SW;
+    for (int q = tid; q < XR * MW; q += NT) {
+        const int y = q / MW, c = q % MW;
         const int gy = ty0 - R + y, gx = tx0 - R + c;
         sm.mk[y][c] = (gy >= 0 && gy < H && gx >= 0 && gx < W && a.trav[(size_t)gy * W + gx]) ? 0xFF : 0x00;
     }
@@ -397,7 +395,7 @@ __global__ void __launch_bounds__(C::NT, C::MINB) step_tiled_kernel(const __grid
     for (int d = 0; d < RING; ++d)
 #pragma unroll
         for (int k = 0; k < MR; ++k) ring[d][k] = 0ull;
-    double acc = 0.0;
+    KahanF acc;
     int failed = 0;
 
     int p = 0;
@@ -466,18 +464,20 @@ __global__ void __launch_bounds__(C::NT, C::MINB) step_tiled_kernel(const __grid
         return;
     }
 
-    const double bt = block_sum<NT>(acc, sm.red);
+    const double bt = block_sum<NT>(acc.value(), sm.red);
     SessionDev* sd = a.sd;
     const double log_mult = a.log_out_mult;
     finish_sum<NT>(bt, a.partials, &sd->counter, gridDim.x * gridDim.y, sm.red, [sd, log_mult](double Z) {
         sd->n_prop += 1;
         if (Z > 0.0 && isfinite(Z)) {
             sd->Z = Z;
+            sd->inv_Z = (float)(1.0 / Z);
             sd->logscale += log(Z) - log_mult;
             sd->reinit = 0;
         } else {
             if (!isfinite(Z)) sd->status |= LOC_DEV_ERR_NONFINITE_Z;
             sd->Z = 1.0;
+            sd->inv_Z = 1.0f;
             sd->reinit = 1;
             sd->n_reinit += 1;
         }
@@ -489,6 +489,8 @@ __global__ void __launch_bounds__(C::NT, C::MINB) step_tiled_kernel(const __grid
 using Cfg1 = Cfg<32, 4, 3, 16, 3, 2>;
 using Cfg2 = Cfg<16, 2, 2, 8, 3, 3>;
 using Cfg3 = Cfg<16, 4, 4, 16, 3, 4>;
+using Cfg4 = Cfg<16, 1, 2, 8, 3, 2>;
+using Cfg5 = Cfg<32, 2, 3, 16, 3, 1>;
 
 template <typename T, typename C> size_t smem_bytes() { return sizeof(Smem<T, C>) + 128; }
 
@@ -514,12 +516,20 @@ cudaError_t launch_cfg(int cfg, const FastArgs& a, int W, int H, cudaStream_t st
         case 1: return launch_typed<T, Cfg1>(a, dim3((W + TW - 1) / TW, (H + Cfg1::TH - 1) / Cfg1::TH), st);
         case 2: return launch_typed<T, Cfg2>(a, dim3((W + TW - 1) / TW, (H + Cfg2::TH - 1) / Cfg2::TH), st);
         case 3: return launch_typed<T, Cfg3>(a, dim3((W + TW - 1) / TW, (H + Cfg3::TH - 1) / Cfg3::TH), st);
+        case 4: return launch_typed<T, Cfg4>(a, dim3((W + TW - 1) / TW, (H + Cfg4::TH - 1) / Cfg4::TH), st);
+        case 5: return launch_typed<T, Cfg5>(a, dim3((W + TW - 1) / TW, (H + Cfg5::TH - 1) / Cfg5::TH), st);
         default: return cudaErrorInvalidValue;
     }
 }
 
 int cfg_tile_rows(int cfg) {
-    return cfg == 1 ? Cfg1::TH : cfg == 2 ? Cfg2::TH : Cfg3::TH;
+    switch (cfg) {
+        case 1: return Cfg1::TH;
+        case 2: return Cfg2::TH;
+        case 3: return Cfg3::TH;
+        case 4: return Cfg4::TH;
+        default: return Cfg5::TH;
+    }
 }
 
 using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
@@ -546,7 +556,7 @@ bool step_tiled_eligible(int H, int W, int K, int r_xy, int r_th, int storage) {
     return r_xy == R && r_th == RT && K >= 8 && K <= LOC_MAX_K && W % align == 0 && W >= 8 && H >= 1;
 }
 
-int step_tiled_num_cfgs() { return 3; }
+int step_tiled_num_cfgs() { return 5; }
 
 int step_tiled_default_cfg(int H, int W, int K, int storage) {
     (void)K;
@@ -559,7 +569,7 @@ int step_tiled_default_cfg(int H, int W, int K, int storage) {
 cudaError_t make_step_tmap(void* tmap_out, const void* B, int storage, int H, int W, int K, int cfg) {
     EncodeTiled enc = encoder();
     if (!enc) return cudaErrorNotSupported;
-    if (cfg < 1 || cfg > 3) return cudaErrorInvalidValue;
+    if (cfg < 1 || cfg > step_tiled_num_cfgs()) return cudaErrorInvalidValue;
     const size_t e = storage == LOC_F32 ? 4 : 2;
     const CUtensorMapDataType dt = storage == LOC_F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
                                    : storage == LOC_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
