@@ -28,7 +28,7 @@ constexpr int R = 2, RT = 3;           // kernel radii this kernel is built for
 constexpr int TW = 64;                 // tile width (cells)
 constexpr int SW = 76;                 // S row pitch (68 used: tile cols -2 .. 65; 76 = 12 mod 32
                                        // banks, so 8 consecutive rows hit 8 distinct bank groups)
-constexpr int MW = 72;                 // mask row pitch (bytes)
+constexpr int MW = 76;                 // mask row pitch (floats, same bank spread as S)
 constexpr int XW_PITCH = 68;           // X row pitch (64 used; 68 = 4 mod 32 banks)
 constexpr int BW = 80;                 // raw box width in elements (76 needed + alignment)
 constexpr int RING = 2 * RT + 1;       // 7
@@ -78,7 +78,7 @@ struct Smem {
     float S[C::XR][SW];
     float X[C::XR][XW_PITCH];
     float wrap[NWRAP][C::TH][TW];
-    uint8_t mk[C::XR][MW];                   // 0xFF free, 0x00 occupied / off-grid
+    float mk[C::XR][MW];                     // 1 free, 0 occupied / off-grid
     unsigned long long bar[C::NSTAGE];
     double red[C::NT / 32];
 };
@@ -191,10 +191,11 @@ __device__ __forceinline__ void box_x(int tx0, const Shift& s, int& x_al, int& x
 // columns x SR rows, the x-lerp of the shared raw row carried down.  XO is xo mod 4; the
 // runtime part xo - XO (0, or 4 for 16-bit types) moves the base address.
 template <typename T, typename C, int XO>
-__device__ __forceinline__ void s_pass(Smem<T, C>& sm, int stage, int xbase, float fx, float fy) {
+__device__ __forceinline__ void s_pass(const T* raw, const float (*mk)[MW], float (*S)[SW], int t,
+                                       int xbase, float fx, float fy) {
     constexpr int UNITS = 72 / 4;              // 18 items of 4 columns cover tile cols -2 .. 69
     constexpr int ITEMS = UNITS * (C::XR / C::SR);
-    const int q = threadIdx.x;
+    const int q = t;
     if (q >= ITEMS) return;
     const int u = q % UNITS, y0 = (q / UNITS) * C::SR;
     const int c0 = 4 * u;
@@ -203,21 +204,18 @@ __device__ __forceinline__ void s_pass(Smem<T, C>& sm, int stage, int xbase, flo
 #pragma unroll
     for (int r = 0; r <= C::SR; ++r) {
         float v[8];
-        load8<T>(&sm.raw[stage][(y0 + r) * BW + c0 + xbase], v);
+        load8<T>(&raw[(y0 + r) * BW + c0 + xbase], v);
         float xl[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) xl[k] = fmaf(fx, v[XO + k + 1] - v[XO + k], v[XO + k]);
         if (r > 0) {
-            const uint32_t m = *reinterpret_cast<const uint32_t*>(&sm.mk[y0 + r - 1][c0]);
+            const float4 m = *reinterpret_cast<const float4*>(&mk[y0 + r - 1][c0]);
+            const float mm[4] = {m.x, m.y, m.z, m.w};
             float4 o;
             float* op = &o.x;
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const float sv = fmaf(fy, xl[k], gy0 * prev[k]);
-                const uint32_t mm = __byte_perm(m, 0u, 0x8888u + 0x1111u * k);
-                op[k] = __uint_as_float(__float_as_uint(sv) & mm);
-            }
-            *reinterpret_cast<float4*>(&sm.S[y0 + r - 1][c0]) = o;
+            for (int k = 0; k < 4; ++k) op[k] = mm[k] * fmaf(fy, xl[k], gy0 * prev[k]);
+            *reinterpret_cast<float4*>(&S[y0 + r - 1][c0]) = o;
         }
 #pragma unroll
         for (int k = 0; k < 4; ++k) prev[k] = xl[k];
@@ -225,17 +223,18 @@ __device__ __forceinline__ void s_pass(Smem<T, C>& sm, int stage, int xbase, flo
 }
 
 // X-pass: X[y][c0..c0+XW) = x-blur of S, one item (XW columns of one row) per thread.
-template <typename T, typename C>
-__device__ __forceinline__ void x_pass(Smem<T, C>& sm, float g0, float g1, float g2) {
+template <typename C>
+__device__ __forceinline__ void x_pass(const float (*S)[SW], float (*X)[XW_PITCH], int t, float g0,
+                                       float g1, float g2) {
     constexpr int UNITS = TW / C::XW;
-    const int q = threadIdx.x;
+    const int q = t;
     if (q >= UNITS * C::XR) return;
     const int y = q % C::XR, u = q / C::XR;    // consecutive threads take consecutive rows
     const int c0 = C::XW * u;
     float s[C::XW + 4];
 #pragma unroll
     for (int k = 0; k < C::XW + 4; k += 4) {
-        const float4 a = *reinterpret_cast<const float4*>(&sm.S[y][c0 + k]);
+        const float4 a = *reinterpret_cast<const float4*>(&S[y][c0 + k]);
         s[k] = a.x; s[k + 1] = a.y; s[k + 2] = a.z; s[k + 3] = a.w;
     }
 #pragma unroll
@@ -245,7 +244,7 @@ __device__ __forceinline__ void x_pass(Smem<T, C>& sm, float g0, float g1, float
 #pragma unroll
         for (int j = 0; j < 4; ++j)
             op[j] = fmaf(g2, s[k + j] + s[k + j + 4], fmaf(g1, s[k + j + 1] + s[k + j + 3], g0 * s[k + j + 2]));
-        *reinterpret_cast<float4*>(&sm.X[y][c0 + k]) = o;
+        *reinterpret_cast<float4*>(&X[y][c0 + k]) = o;
     }
 }
 
@@ -282,7 +281,8 @@ struct Taps2 {
 // P-pass for plane p with the newest ring slot PH = p mod 7.  The thread's cells are rows
 // r0 .. r0+MR-1 of the tile, columns 2cp and 2cp+1, handled as column pairs.
 template <typename T, typename C, int PH>
-__device__ __forceinline__ void p_pass(Smem<T, C>& sm, const FastArgs& a, const Taps2& tp,
+__device__ __forceinline__ void p_pass(const float (*X)[XW_PITCH], float (*wrap)[C::TH][TW],
+                                       const FastArgs& a, const Taps2& tp,
                                        f2 (&ring)[RING][C::MR], const f2 (&cs)[C::MR], int p,
                                        int r0, int cp, int ty0, int gx, KahanF& acc) {
     constexpr int MR = C::MR;
@@ -290,25 +290,27 @@ __device__ __forceinline__ void p_pass(Smem<T, C>& sm, const FastArgs& a, const 
     if (p < K) {
         f2 x[MR + 4];
 #pragma unroll
-        for (int q = 0; q < MR + 4; ++q) x[q] = *reinterpret_cast<const f2*>(&sm.X[r0 + q][2 * cp]);
+        for (int q = 0; q < MR + 4; ++q) x[q] = *reinterpret_cast<const f2*>(&X[r0 + q][2 * cp]);
 #pragma unroll
         for (int rr = 0; rr < MR; ++rr)
             ring[PH][rr] = ffma2(tp.g2, fadd2(x[rr], x[rr + 4]),
                                  ffma2(tp.g1, fadd2(x[rr + 1], x[rr + 3]), fmul2(tp.g0, x[rr + 2])));
         if (p < NWRAP) {
 #pragma unroll
-            for (int rr = 0; rr < MR; ++rr) *reinterpret_cast<f2*>(&sm.wrap[p][r0 + rr][2 * cp]) = ring[PH][rr];
+            for (int rr = 0; rr < MR; ++rr) *reinterpret_cast<f2*>(&wrap[p][r0 + rr][2 * cp]) = ring[PH][rr];
         }
     } else {
 #pragma unroll
-        for (int rr = 0; rr < MR; ++rr) ring[PH][rr] = *reinterpret_cast<const f2*>(&sm.wrap[p - K][r0 + rr][2 * cp]);
+        for (int rr = 0; rr < MR; ++rr) ring[PH][rr] = *reinterpret_cast<const f2*>(&wrap[p - K][r0 + rr][2 * cp]);
     }
     if (p >= 2 * RT) {
         int o = p - RT;
         if (o >= K) o -= K;
         const size_t base = ((size_t)o * a.H + (ty0 + r0)) * a.W + gx;
         T* out = static_cast<T*>(a.B_out) + base;
-        uint32_t h = sizeof(T) == 2 ? pcg_hash((uint32_t)base ^ a.seed) : 0u;
+        const uint32_t h = sizeof(T) == 2 ? pcg_hash((uint32_t)base ^ a.seed) : 0u;
+        const int rows = a.H - (ty0 + r0);             // rows of this thread inside the grid
+        const bool full = rows >= MR && gx < a.W;
         f2 part = 0ull;
 #pragma unroll
         for (int rr = 0; rr < MR; ++rr) {
@@ -316,11 +318,9 @@ __device__ __forceinline__ void p_pass(Smem<T, C>& sm, const FastArgs& a, const 
 #pragma unroll
             for (int d = 1; d < RING; ++d) t = ffma2(tp.gt[d], ring[(PH + 1 + d) % RING][rr], t);
             const f2 v = fmul2(cs[rr], t);
-            if (ty0 + r0 + rr < a.H && gx < a.W) store2<T>(out + (size_t)rr * a.W, v, h, part);
-            if (sizeof(T) == 2) {       // next 32 random bits: LCG step, high bits folded down
-                h = h * 0x9E3779B1u + 0x7F4A7C15u;
-                h ^= h >> 16;
-            }
+            // 32 random bits per row: the thread's hash with a per-row odd constant mixed in
+            const uint32_t hr = h ^ (0x9E3779B9u * (uint32_t)(2 * rr + 1));
+            if (full || (rr < rows && gx < a.W)) store2<T>(out + (size_t)rr * a.W, v, hr, part);
         }
         float p0, p1;
         upk(part, p0, p1);
@@ -347,7 +347,7 @@ __global__ void __launch_bounds__(C::NT, C::MINB) step_tiled_kernel(const __grid
     for (int q = tid; q < XR * MW; q += NT) {
         const int y = q / MW, c = q % MW;
         const int gy = ty0 - R + y, gx = tx0 - R + c;
-        sm.mk[y][c] = (gy >= 0 && gy < H && gx >= 0 && gx < W && a.trav[(size_t)gy * W + gx]) ? 0xFF : 0x00;
+        sm.mk[y][c] = (gy >= 0 && gy < H && gx >= 0 && gx < W && a.trav[(size_t)gy * W + gx]) ? 1.0f : 0.0f;
     }
     if (tid == 0) {
         for (int s = 0; s < NSTAGE; ++s) bar_init(&sm.bar[s], 1);
@@ -422,10 +422,10 @@ __global__ void __launch_bounds__(C::NT, C::MINB) step_tiled_kernel(const __grid
             if (!failed) {
                 const int xb = xo & ~3;
                 switch (xo & 3) {
-                    case 0: s_pass<T, C, 0>(sm, stage, xb, s.fx, s.fy); break;
-                    case 1: s_pass<T, C, 1>(sm, stage, xb, s.fx, s.fy); break;
-                    case 2: s_pass<T, C, 2>(sm, stage, xb, s.fx, s.fy); break;
-                    default: s_pass<T, C, 3>(sm, stage, xb, s.fx, s.fy); break;
+                    case 0: s_pass<T, C, 0>(sm.raw[stage], sm.mk, sm.S, tid, xb, s.fx, s.fy); break;
+                    case 1: s_pass<T, C, 1>(sm.raw[stage], sm.mk, sm.S, tid, xb, s.fx, s.fy); break;
+                    case 2: s_pass<T, C, 2>(sm.raw[stage], sm.mk, sm.S, tid, xb, s.fx, s.fy); break;
+                    default: s_pass<T, C, 3>(sm.raw[stage], sm.mk, sm.S, tid, xb, s.fx, s.fy); break;
                 }
             }
             if (__syncthreads_or(failed)) {
@@ -439,17 +439,17 @@ __global__ void __launch_bounds__(C::NT, C::MINB) step_tiled_kernel(const __grid
                 }
                 next_issue = p + NSTAGE + 1;
             }
-            x_pass<T, C>(sm, a.g0, a.g1, a.g2);
+            x_pass<C>(sm.S, sm.X, tid, a.g0, a.g1, a.g2);
             __syncthreads();
         }
         switch (p % RING) {
-            case 0: p_pass<T, C, 0>(sm, a, tp, ring, cs, p, r0, cp, ty0, gxp, acc); break;
-            case 1: p_pass<T, C, 1>(sm, a, tp, ring, cs, p, r0, cp, ty0, gxp, acc); break;
-            case 2: p_pass<T, C, 2>(sm, a, tp, ring, cs, p, r0, cp, ty0, gxp, acc); break;
-            case 3: p_pass<T, C, 3>(sm, a, tp, ring, cs, p, r0, cp, ty0, gxp, acc); break;
-            case 4: p_pass<T, C, 4>(sm, a, tp, ring, cs, p, r0, cp, ty0, gxp, acc); break;
-            case 5: p_pass<T, C, 5>(sm, a, tp, ring, cs, p, r0, cp, ty0, gxp, acc); break;
-            default: p_pass<T, C, 6>(sm, a, tp, ring, cs, p, r0, cp, ty0, gxp, acc); break;
+            case 0: p_pass<T, C, 0>(sm.X, sm.wrap, a, tp, ring, cs, p, r0, cp, ty0, gxp, acc); break;
+            case 1: p_pass<T, C, 1>(sm.X, sm.wrap, a, tp, ring, cs, p, r0, cp, ty0, gxp, acc); break;
+            case 2: p_pass<T, C, 2>(sm.X, sm.wrap, a, tp, ring, cs, p, r0, cp, ty0, gxp, acc); break;
+            case 3: p_pass<T, C, 3>(sm.X, sm.wrap, a, tp, ring, cs, p, r0, cp, ty0, gxp, acc); break;
+            case 4: p_pass<T, C, 4>(sm.X, sm.wrap, a, tp, ring, cs, p, r0, cp, ty0, gxp, acc); break;
+            case 5: p_pass<T, C, 5>(sm.X, sm.wrap, a, tp, ring, cs, p, r0, cp, ty0, gxp, acc); break;
+            default: p_pass<T, C, 6>(sm.X, sm.wrap, a, tp, ring, cs, p, r0, cp, ty0, gxp, acc); break;
         }
     }
 
@@ -484,6 +484,218 @@ __global__ void __launch_bounds__(C::NT, C::MINB) step_tiled_kernel(const __grid
     });
 }
 
+// ---------------------------------------------------------------------------------------------
+// Warp-specialised variant.  Four producer warps run the S-pass and X-pass of plane p+1 while
+// four consumer warps run the P-pass of plane p; the X plane is double-buffered between them.
+// Hand-offs use mbarriers with bounded waits (FULL[b]: producers arrive after writing X[b];
+// EMPTY[b]: consumers arrive after reading it); producers synchronise among themselves with a
+// 128-thread named barrier that every producer thread reaches on every plane.
+
+__device__ __forceinline__ void bar_arrive(unsigned long long* b) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(b)) : "memory");
+}
+__device__ __forceinline__ void producers_sync() {       // named barrier 1, producer threads only
+    asm volatile("bar.sync 1, 128;" ::: "memory");
+}
+
+// TH tile rows (consumers: TH/4 rows x 2 columns each), SR S-pass rows per item, XW X-pass
+// columns per item, NSTAGE raw stages, MINB CTAs per SM asked of the compiler.
+template <int TH_, int SR_, int XW_, int NSTAGE_, int MINB_>
+struct WsCfg {
+    static constexpr int TH = TH_, SR = SR_, XW = XW_, NSTAGE = NSTAGE_, MINB = MINB_;
+    static constexpr int NP = 128, NC = 128, NT = NP + NC;
+    static constexpr int MR = TH * TW / (2 * NC);          // consumer rows per thread
+    static constexpr int XR = TH + 2 * R;
+    static constexpr int RAW_H = XR + 1;
+    static_assert(XR % SR == 0, "S-pass row groups must tile the halo rows");
+    static_assert((72 / 4) * (XR / SR) <= NP, "one S-pass item per producer thread");
+    static_assert((TW / XW) * XR <= NP, "one X-pass item per producer thread");
+    static_assert(MR * 2 * NC == TH * TW && (TH / MR) * 32 == NC, "consumer tiling");
+};
+
+template <typename T, typename C>
+struct SmemWS {
+    T raw[C::NSTAGE][raw_stride<T, C>()];
+    float S[C::XR][SW];
+    float X[2][C::XR][XW_PITCH];
+    float wrap[NWRAP][C::TH][TW];
+    float mk[C::XR][MW];
+    unsigned long long tma[C::NSTAGE];
+    unsigned long long full[2], empty[2];
+    // failure flags.  Producers write fail_a only before their first named barrier of a plane
+    // and read it right after it, fail_b likewise for the second barrier, so every producer
+    // takes the same decision; consumers (no named barriers) use fail_c.
+    int fail_a, fail_b, fail_c;
+    double red[C::NT / 32];
+};
+
+template <typename T, typename C>
+__global__ void __launch_bounds__(C::NT, C::MINB) step_ws_kernel(const __grid_constant__ FastArgs a) {
+    constexpr int NT = C::NT, NP = C::NP, TH = C::TH, MR = C::MR, NSTAGE = C::NSTAGE, XR = C::XR;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const uint32_t base = su32(smem_raw);
+    SmemWS<T, C>& sm = *reinterpret_cast<SmemWS<T, C>*>(smem_raw + (((base + 127u) & ~127u) - base));
+    const int tid = threadIdx.x;
+    const int H = a.H, W = a.W, K = a.K;
+    const int ty0 = blockIdx.y * TH, tx0 = blockIdx.x * TW;
+    const int reinit = a.sd->reinit;
+    const float in_scale = (reinit ? a.inv_uniform : a.sd->inv_Z) * a.out_mult;
+    constexpr uint32_t kBoxBytes = C::RAW_H * BW * sizeof(T);
+
+    for (int q = tid; q < XR * MW; q += NT) {
+        const int y = q / MW, c = q % MW;
+        const int gy = ty0 - R + y, gx = tx0 - R + c;
+        sm.mk[y][c] = (gy >= 0 && gy < H && gx >= 0 && gx < W && a.trav[(size_t)gy * W + gx]) ? 1.0f : 0.0f;
+    }
+    if (tid == 0) {
+        for (int s = 0; s < NSTAGE; ++s) bar_init(&sm.tma[s], 1);
+        for (int b = 0; b < 2; ++b) {
+            bar_init(&sm.full[b], C::NP);
+            bar_init(&sm.empty[b], C::NC);
+        }
+        sm.fail_a = sm.fail_b = sm.fail_c = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    __syncthreads();
+
+    KahanF acc;
+    int p_done = 0, next_issue = 0;         // producer: planes [p_done, next_issue) in flight
+    if (tid < NP) {
+        // ------------------------------------------------------------------ producers
+        const int t = tid;
+        auto issue = [&](int q) {
+            const Shift s = a.sh[q];
+            int x_al, xo;
+            box_x<T>(tx0, s, x_al, xo);
+            bar_expect(&sm.tma[q % NSTAGE], kBoxBytes);
+            tma_load(&sm.raw[q % NSTAGE][0], &a.tmap, &sm.tma[q % NSTAGE], x_al, ty0 - R + s.oy, q);
+        };
+        if (!reinit) {
+            next_issue = NSTAGE < K ? NSTAGE : K;
+            if (t == 0)
+                for (int q = 0; q < next_issue; ++q) issue(q);
+        }
+        for (int p = 0; p < K; ++p) {
+            p_done = p;
+            const int stage = p % NSTAGE;
+            const Shift s = a.sh[p];
+            int x_al, xo;
+            box_x<T>(tx0, s, x_al, xo);
+            if (reinit) {
+                const int y0 = ty0 - R + s.oy;
+                for (int q = t; q < C::RAW_H * BW; q += NP) {
+                    const int y = q / BW, c = q % BW;
+                    const int gy = y0 + y, gx = x_al + c;
+                    float v = 0.0f;
+                    if (gy >= 0 && gy < H && gx >= 0 && gx < W) v = (float)a.trav[(size_t)gy * W + gx];
+                    sm.raw[stage][y * BW + c] = T(v);
+                }
+                producers_sync();
+            } else if (!bar_wait(&sm.tma[stage], (uint32_t)((p / NSTAGE) & 1))) {
+                sm.fail_a = 1;
+            }
+            if (!sm.fail_a) {
+                const int xb = xo & ~3;
+                switch (xo & 3) {
+                    case 0: s_pass<T, C, 0>(sm.raw[stage], sm.mk, sm.S, t, xb, s.fx, s.fy); break;
+                    case 1: s_pass<T, C, 1>(sm.raw[stage], sm.mk, sm.S, t, xb, s.fx, s.fy); break;
+                    case 2: s_pass<T, C, 2>(sm.raw[stage], sm.mk, sm.S, t, xb, s.fx, s.fy); break;
+                    default: s_pass<T, C, 3>(sm.raw[stage], sm.mk, sm.S, t, xb, s.fx, s.fy); break;
+                }
+            }
+            producers_sync();                        // S complete; raw stage free
+            if (sm.fail_a) break;                    // the same decision in every producer
+            if (!reinit && p + NSTAGE < K) {
+                if (t == 0) {
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    issue(p + NSTAGE);
+                }
+                next_issue = p + NSTAGE + 1;
+            }
+            const int b = p & 1;
+            if (p >= 2 && !bar_wait(&sm.empty[b], (uint32_t)(((p - 2) >> 1) & 1))) sm.fail_b = 1;
+            producers_sync();
+            if (sm.fail_b) break;
+            x_pass<C>(sm.S, sm.X[b], t, a.g0, a.g1, a.g2);
+            bar_arrive(&sm.full[b]);                 // X[b] of plane p is ready
+            producers_sync();                        // the X-pass has read S: S may be rewritten
+            p_done = p + 1;
+        }
+    } else {
+        // ------------------------------------------------------------------ consumers
+        const int t = tid - NP;
+        const int cp = t % 32, rg = t / 32;
+        const int r0 = MR * rg, gxp = tx0 + 2 * cp;
+        f2 cs[MR];
+#pragma unroll
+        for (int rr = 0; rr < MR; ++rr) {
+            const int gy = ty0 + r0 + rr;
+            float c0 = 0.0f, c1 = 0.0f;
+            if (gy < H && gxp < W) {
+                c0 = a.corr[(size_t)gy * W + gxp] * in_scale;
+                c1 = a.corr[(size_t)gy * W + gxp + 1] * in_scale;
+            }
+            cs[rr] = pk(c0, c1);
+        }
+        Taps2 tp;
+        tp.g0 = pk(a.g0, a.g0);
+        tp.g1 = pk(a.g1, a.g1);
+        tp.g2 = pk(a.g2, a.g2);
+#pragma unroll
+        for (int d = 0; d < RING; ++d) tp.gt[d] = pk(a.gt[d], a.gt[d]);
+        f2 ring[RING][MR];
+#pragma unroll
+        for (int d = 0; d < RING; ++d)
+#pragma unroll
+            for (int k = 0; k < MR; ++k) ring[d][k] = 0ull;
+        for (int p = 0; p < K + NWRAP; ++p) {
+            const int b = p & 1;
+            if (p < K && !bar_wait(&sm.full[b], (uint32_t)((p >> 1) & 1))) {
+                sm.fail_c = 1;
+                break;
+            }
+            switch (p % RING) {
+                case 0: p_pass<T, C, 0>(sm.X[b], sm.wrap, a, tp, ring, cs, p, r0, cp, ty0, gxp, acc); break;
+                case 1: p_pass<T, C, 1>(sm.X[b], sm.wrap, a, tp, ring, cs, p, r0, cp, ty0, gxp, acc); break;
+                case 2: p_pass<T, C, 2>(sm.X[b], sm.wrap, a, tp, ring, cs, p, r0, cp, ty0, gxp, acc); break;
+                case 3: p_pass<T, C, 3>(sm.X[b], sm.wrap, a, tp, ring, cs, p, r0, cp, ty0, gxp, acc); break;
+                case 4: p_pass<T, C, 4>(sm.X[b], sm.wrap, a, tp, ring, cs, p, r0, cp, ty0, gxp, acc); break;
+                case 5: p_pass<T, C, 5>(sm.X[b], sm.wrap, a, tp, ring, cs, p, r0, cp, ty0, gxp, acc); break;
+                default: p_pass<T, C, 6>(sm.X[b], sm.wrap, a, tp, ring, cs, p, r0, cp, ty0, gxp, acc); break;
+            }
+            if (p + 2 < K) bar_arrive(&sm.empty[b]);  // a producer waits for this release
+        }
+    }
+    __syncthreads();
+    if (sm.fail_a | sm.fail_b | sm.fail_c) {
+        if (tid == 0) {
+            atomicOr(&a.sd->status, LOC_DEV_ERR_TIMEOUT);
+            for (int q = p_done; q < next_issue; ++q) bar_wait(&sm.tma[q % NSTAGE], (uint32_t)((q / NSTAGE) & 1));
+        }
+        __syncthreads();
+        return;
+    }
+    const double bt = block_sum<NT>(acc.value(), sm.red);
+    SessionDev* sd = a.sd;
+    const double log_mult = a.log_out_mult;
+    finish_sum<NT>(bt, a.partials, &sd->counter, gridDim.x * gridDim.y, sm.red, [sd, log_mult](double Z) {
+        sd->n_prop += 1;
+        if (Z > 0.0 && isfinite(Z)) {
+            sd->Z = Z;
+            sd->inv_Z = (float)(1.0 / Z);
+            sd->logscale += log(Z) - log_mult;
+            sd->reinit = 0;
+        } else {
+            if (!isfinite(Z)) sd->status |= LOC_DEV_ERR_NONFINITE_Z;
+            sd->Z = 1.0;
+            sd->inv_Z = 1.0f;
+            sd->reinit = 1;
+            sd->n_reinit += 1;
+        }
+    });
+}
+
 // The tile configurations.  1: 32-row tiles (large grids); 2: 16-row tiles with 2-row
 // P-pass items (256 threads); 3: 16-row tiles with 4-row P-pass items (128 threads).
 using Cfg1 = Cfg<32, 4, 3, 16, 3, 2>;
@@ -491,6 +703,8 @@ using Cfg2 = Cfg<16, 2, 2, 8, 3, 3>;
 using Cfg3 = Cfg<16, 4, 4, 16, 3, 4>;
 using Cfg4 = Cfg<16, 1, 2, 8, 3, 2>;
 using Cfg5 = Cfg<32, 2, 3, 16, 3, 1>;
+using Cfg6 = WsCfg<16, 4, 16, 3, 2>;   // warp-specialised, 16-row tiles
+using Cfg7 = WsCfg<8, 2, 8, 3, 4>;     // warp-specialised, 8-row tiles
 
 template <typename T, typename C> size_t smem_bytes() { return sizeof(Smem<T, C>) + 128; }
 
@@ -510,6 +724,21 @@ cudaError_t launch_typed(const FastArgs& a, dim3 grid, cudaStream_t st) {
     return cudaSuccess;
 }
 
+template <typename T, typename C>
+cudaError_t launch_ws(const FastArgs& a, dim3 grid, cudaStream_t st) {
+    static bool attr_set[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const size_t sb = sizeof(SmemWS<T, C>) + 128;
+    if (dev < 0 || dev >= 64 || !attr_set[dev]) {
+        cudaError_t e = cudaFuncSetAttribute(step_ws_kernel<T, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb);
+        if (e != cudaSuccess) return e;
+        if (dev >= 0 && dev < 64) attr_set[dev] = true;
+    }
+    step_ws_kernel<T, C><<<grid, C::NT, sb, st>>>(a);
+    return cudaSuccess;
+}
+
 template <typename T>
 cudaError_t launch_cfg(int cfg, const FastArgs& a, int W, int H, cudaStream_t st) {
     switch (cfg) {
@@ -518,6 +747,8 @@ cudaError_t launch_cfg(int cfg, const FastArgs& a, int W, int H, cudaStream_t st
         case 3: return launch_typed<T, Cfg3>(a, dim3((W + TW - 1) / TW, (H + Cfg3::TH - 1) / Cfg3::TH), st);
         case 4: return launch_typed<T, Cfg4>(a, dim3((W + TW - 1) / TW, (H + Cfg4::TH - 1) / Cfg4::TH), st);
         case 5: return launch_typed<T, Cfg5>(a, dim3((W + TW - 1) / TW, (H + Cfg5::TH - 1) / Cfg5::TH), st);
+        case 6: return launch_ws<T, Cfg6>(a, dim3((W + TW - 1) / TW, (H + Cfg6::TH - 1) / Cfg6::TH), st);
+        case 7: return launch_ws<T, Cfg7>(a, dim3((W + TW - 1) / TW, (H + Cfg7::TH - 1) / Cfg7::TH), st);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -528,7 +759,9 @@ int cfg_tile_rows(int cfg) {
         case 2: return Cfg2::TH;
         case 3: return Cfg3::TH;
         case 4: return Cfg4::TH;
-        default: return Cfg5::TH;
+        case 5: return Cfg5::TH;
+        case 6: return Cfg6::TH;
+        default: return Cfg7::TH;
     }
 }
 
@@ -556,14 +789,15 @@ bool step_tiled_eligible(int H, int W, int K, int r_xy, int r_th, int storage) {
     return r_xy == R && r_th == RT && K >= 8 && K <= LOC_MAX_K && W % align == 0 && W >= 8 && H >= 1;
 }
 
-int step_tiled_num_cfgs() { return 5; }
+int step_tiled_num_cfgs() { return 7; }
 
 int step_tiled_default_cfg(int H, int W, int K, int storage) {
     (void)K;
     (void)storage;
-    // enough 32-row tiles to give every SM several: large grids; otherwise 16-row tiles
-    const long long tiles32 = (long long)((W + TW - 1) / TW) * ((H + 31) / 32);
-    return tiles32 >= 4 * 152 ? 1 : 2;
+    // measured on GB300 (office plans): with few tiles per SM the warp-specialised pipeline
+    // (6) is fastest; with many tiles the 128-thread synchronous configuration (3)
+    const long long tiles16 = (long long)((W + TW - 1) / TW) * ((H + 15) / 16);
+    return tiles16 >= 8 * 152 ? 3 : 6;
 }
 
 cudaError_t make_step_tmap(void* tmap_out, const void* B, int storage, int H, int W, int K, int cfg) {

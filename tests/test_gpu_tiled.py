@@ -45,7 +45,7 @@ SHAPES = [
 ]
 
 
-@pytest.mark.parametrize("tile", [1, 2, 3])
+@pytest.mark.parametrize("tile", [1, 2, 3, 4, 5, 6, 7])
 @pytest.mark.parametrize("H,W,K,mot", SHAPES, ids=[f"{s[0]}x{s[1]}x{s[2]}" for s in SHAPES])
 def test_tiled_matches_oracle_and_generic(H, W, K, mot, tile):
     rng = np.random.default_rng(H * 7 + W * 3 + K)
