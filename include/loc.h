@@ -113,6 +113,50 @@ loc_status loc_create(const uint8_t* occ, const loc_params* p, loc_handle* out);
  * LOC_OK_DEFERRED.  Errors: INVALID_ARG (non-finite input), STATE, CUDA. */
 loc_status loc_step(loc_handle h, double u, double v, double w);
 
+/* LIDAR sample update (Section III-B, Eq. 9).  ranges: host float[n_beams] in metres,
+ * beam b at angle_min + b * angle_inc relative to the robot heading.  Beams with
+ * b % beam_stride == 0 and range < r_max are scored with a Gaussian range likelihood of
+ * std-dev sigma_r against the expected range of every sampled state, found by walking the
+ * grid from the cell centre along the beam to the first occupied cell or the grid edge
+ * (capped at r_max).  Samples are the cells that Floyd-Steinberg dithering selects from the
+ * belief map (max over channels) scaled to about loc_params.n_samples selections
+ * (Section III-B.1); every channel of a sampled cell is a sampled state.  The sampled states
+ * are multiplied by their likelihood and renormalised so that the set keeps its total
+ * mass (Eq. 9's eta over the sampled set); other states are unchanged.  Enqueued on the
+ * handle's stream (asynchronous).  Errors: INVALID_ARG (sizes, non-finite values,
+ * sigma_r <= 0, r_max <= 0, beam_stride < 1), STATE, CUDA. */
+loc_status loc_lidar_update(loc_handle h, const float* ranges, int n_beams, double angle_min,
+                            double angle_inc, double r_max, int beam_stride, double sigma_r);
+
+/* Same as loc_lidar_update but with the sampled cells given by the caller: host int32
+ * linear indices j * W + i, no duplicates, at most H * W of them (e.g. from a previous
+ * loc_samples call, or from another sampler).  Synchronous for the host array. */
+loc_status loc_lidar_update_cells(loc_handle h, const int32_t* cells, int n_cells,
+                                  const float* ranges, int n_beams, double angle_min,
+                                  double angle_inc, double r_max, int beam_stride,
+                                  double sigma_r);
+
+/* The cells selected by the last loc_lidar_update (host int32 linear indices j * W + i in
+ * raster order; the paper's "samples from the belief map", Fig. 1c).  *n receives the count;
+ * at most cap indices are written.  Synchronous. */
+loc_status loc_samples(loc_handle h, int32_t* out, size_t cap, int* n);
+
+/* Floyd-Steinberg dithering of a caller map (Section III-B.1), as loc_lidar_update applies it
+ * to the belief map: value v = min(1, m[q] * fs) plus the diffused error, selected iff
+ * >= 0.5, errors 7/16 right, 3/16 down-left, 5/16 down, 1/16 down-right, raster order, all in
+ * FP32 with the operations in that order (no fused multiply-add).  m: host float[H][W] of
+ * the handle's grid; sel: host uint8[H][W] (1 = selected); *count receives the number of
+ * selected cells.  Synchronous. */
+loc_status loc_dither(loc_handle h, const float* m, float fs, uint8_t* sel, int* count);
+
+/* Expected ranges (metres) used by the LIDAR likelihood, for given cells and unit directions:
+ * out[c * n_dirs + d] = distance from the centre of cell cells[c] along dirs[2d], dirs[2d+1]
+ * (FP32 cos, sin in the map frame) to the first occupied cell or the grid edge, capped at
+ * r_max; a tie between the next x and y cell boundaries steps x first; FP32 arithmetic in
+ * a fixed order (no fused multiply-add).  Host arrays; synchronous. */
+loc_status loc_ray_ranges(loc_handle h, const int32_t* cells, int n_cells, const float* dirs,
+                          int n_dirs, double r_max, float* out);
+
 /* Readbacks (synchronous).  n must equal the element count exactly.
  *   loc_belief:   normalised belief, host float[K][H][W].
  *   loc_marginal: host float[H][W]: LOC_MAP_MAX = max over channels (the paper's belief

@@ -20,7 +20,7 @@ __all__ = [
     "loc_params_default", "loc_set_allocator", "loc_create", "loc_step", "loc_lidar_update",
     "loc_lidar_update_cells", "loc_belief", "loc_marginal", "loc_argmax", "loc_set_belief",
     "loc_stats", "loc_sync", "loc_destroy", "loc_last_error", "torch_stream",
-    "use_torch_allocator", "loc_propagate_noalloc",
+    "use_torch_allocator", "loc_propagate_noalloc", "loc_samples", "loc_dither", "loc_ray_ranges",
 ]
 
 LOC_OK, LOC_OK_DEFERRED = 0, 1
@@ -82,6 +82,9 @@ _SIGS = {
     "loc_last_error": (ctypes.c_char_p, [_P]),
     "loc_propagate_noalloc": (ctypes.c_int, [ctypes.POINTER(loc_params), _P, _P, _P, _P,
                                              ctypes.c_double, ctypes.c_double]),
+    "loc_samples": (ctypes.c_int, [_P, _P, ctypes.c_size_t, ctypes.POINTER(ctypes.c_int)]),
+    "loc_dither": (ctypes.c_int, [_P, _P, ctypes.c_float, _P, ctypes.POINTER(ctypes.c_int)]),
+    "loc_ray_ranges": (ctypes.c_int, [_P, _P, ctypes.c_int, _P, ctypes.c_int, ctypes.c_double, _P]),
 }
 
 
@@ -191,6 +194,36 @@ def loc_lidar_update_cells(h: Handle, cells: np.ndarray, ranges: np.ndarray, ang
     return _check(h, lib().loc_lidar_update_cells(h, _ptr(c), int(c.size), _ptr(z), int(z.size),
                                                   float(angle_min), float(angle_inc),
                                                   float(r_max), int(beam_stride), float(sigma_r)))
+
+
+def loc_samples(h: Handle) -> np.ndarray:
+    """Cells selected by the last loc_lidar_update (linear indices, raster order)."""
+    n = ctypes.c_int()
+    _check(h, lib().loc_samples(h, None, 0, ctypes.byref(n)))
+    out = np.empty(max(n.value, 1), np.int32)
+    _check(h, lib().loc_samples(h, _ptr(out), out.size, ctypes.byref(n)))
+    return out[:n.value]
+
+
+def loc_dither(h: Handle, m: np.ndarray, fs: float):
+    """Floyd-Steinberg selection of the handle-shaped map m scaled by fs: (mask, count)."""
+    m = np.ascontiguousarray(m, dtype=np.float32)
+    if m.shape != (h.H, h.W):
+        raise ValueError("map shape must match the handle")
+    sel = np.empty((h.H, h.W), np.uint8)
+    n = ctypes.c_int()
+    _check(h, lib().loc_dither(h, _ptr(m), ctypes.c_float(fs), _ptr(sel), ctypes.byref(n)))
+    return sel, n.value
+
+
+def loc_ray_ranges(h: Handle, cells: np.ndarray, dirs: np.ndarray, r_max: float) -> np.ndarray:
+    """Expected ranges (m) for each cell and FP32 unit direction: shape (n_cells, n_dirs)."""
+    c = np.ascontiguousarray(cells, dtype=np.int32)
+    d = np.ascontiguousarray(dirs, dtype=np.float32).reshape(-1, 2)
+    out = np.empty((c.size, d.shape[0]), np.float32)
+    _check(h, lib().loc_ray_ranges(h, _ptr(c), int(c.size), _ptr(d), int(d.shape[0]), float(r_max),
+                                   _ptr(out)))
+    return out
 
 
 def loc_belief(h: Handle, out: np.ndarray | None = None) -> np.ndarray:

@@ -1,10 +1,12 @@
 // C-ABI of the localizer: session state on the host, device buffers, odometry bookkeeping
 // (Section III-A, Eq. 2, the Alg. 1 gate) and the launches of the device kernels.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <new>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "kernels.h"
@@ -46,6 +48,24 @@ struct loc_session {
     void* argmax_scratch = nullptr;
     long long* argmax_idx = nullptr;
     float* argmax_val = nullptr;
+    // LIDAR sample update scratch (allocated on first use)
+    bool lidar_ready = false;
+    int cap = 0;                   // capacity of the sample list
+    float* m = nullptr;            // belief map [H][W]
+    uint8_t* sel = nullptr;        // selection mask [H][W]
+    int* rowcnt = nullptr;         // per-row selections [H]
+    int* rowoff = nullptr;         // exclusive prefix [H]
+    float* bnd = nullptr;          // row-block boundary rows for the dithering wavefront
+    int* prog = nullptr;           // their progress counters
+    int32_t* samples = nullptr;    // sampled cells [cap]
+    float* logL = nullptr;         // log-likelihood [cap][K]
+    int* dscal = nullptr;          // device scalars: count, maxL (as uint), fs (as float)
+    void* rs = nullptr;            // reweight scalars
+    float* dirs = nullptr;         // distinct beam directions (cos, sin) [cap_dirs][2]
+    int32_t* dir_of = nullptr;     // direction of (bin, used beam) [K][cap_beams]
+    float* z = nullptr;            // used ranges [cap_beams]
+    int cap_dirs = 0, cap_beams = 0, cap_dir_of = 0;
+    long long n_lidar = 0;
     bool tiled = false;            // use the TMA-tiled kernel
     int tile_cfg = 0;              // its tile configuration
     unsigned char tmap[2][128] __attribute__((aligned(128)));   // tensor maps of B[0], B[1]
@@ -311,6 +331,279 @@ LOC_API loc_status loc_step(loc_handle h, double u, double v, double w) {
     h->px = h->py = 0.0;
     h->n_prop += 1;
     return LOC_OK;
+}
+
+namespace {
+
+loc_status lidar_setup(loc_session* h) {
+    if (h->lidar_ready) return LOC_OK;
+    const int H = h->p.H, W = h->p.W, K = h->p.K;
+    const long long hw = (long long)H * W;
+    long long cap = 2LL * h->p.n_samples + 4LL * (H + W) + 1024;
+    if (cap > hw) cap = hw;
+    h->cap = (int)cap;
+    const int nrb = (H + 31) / 32;
+    h->m = (float*)dev_alloc(h, sizeof(float) * hw);
+    h->sel = (uint8_t*)dev_alloc(h, hw);
+    h->rowcnt = (int*)dev_alloc(h, sizeof(int) * H);
+    h->rowoff = (int*)dev_alloc(h, sizeof(int) * H);
+    h->bnd = (float*)dev_alloc(h, sizeof(float) * (size_t)(nrb + 1) * W);
+    h->prog = (int*)dev_alloc(h, sizeof(int) * (size_t)(nrb + 2));
+    h->samples = (int32_t*)dev_alloc(h, sizeof(int32_t) * (size_t)cap);
+    h->logL = (float*)dev_alloc(h, sizeof(float) * (size_t)cap * K);
+    h->dscal = (int*)dev_alloc(h, 64);
+    h->rs = dev_alloc(h, reweight_scalars_bytes());
+    if (!h->m || !h->sel || !h->rowcnt || !h->rowoff || !h->bnd || !h->prog || !h->samples || !h->logL ||
+        !h->dscal || !h->rs)
+        return fail(h, LOC_ERR_OOM, "LIDAR scratch allocation failed");
+    cudaError_t e = cudaMemsetAsync(h->dscal, 0, 64, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->rs, 0, reweight_scalars_bytes(), h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "LIDAR scratch init");
+    h->lidar_ready = true;
+    return LOC_OK;
+}
+
+void dev_release(loc_session* h, void* p) {
+    auto it = std::find(h->owned.begin(), h->owned.end(), p);
+    if (it == h->owned.end()) return;
+    h->owned.erase(it);
+    if (g_free) g_free(p, (void*)h->stream, g_alloc_ctx);
+    else cudaFree(p);
+}
+
+// Grow a device buffer to at least n elements of `elem` bytes (the old one is released).
+template <typename P>
+bool grow(loc_session* h, P*& ptr, int& capn, int n, size_t elem) {
+    if (n <= capn && ptr) return true;
+    void* q = dev_alloc(h, elem * (size_t)std::max(n, 1));
+    if (!q) return false;
+    if (ptr) dev_release(h, (void*)ptr);
+    ptr = (P*)q;
+    capn = std::max(n, 1);
+    return true;
+}
+
+// Scoring inputs for one scan: the used beams (b % stride == 0, range < r_max), their
+// ranges, the distinct FP32 map-frame directions of every (bin, used beam) pair and the
+// direction index of each pair.  The angle of bin k and beam b is
+// (2 pi / K) k + theta_t + (angle_min + angle_inc b), evaluated in FP64 in that order.
+loc_status upload_scan(loc_session* h, const float* ranges, int n_beams, double angle_min, double angle_inc,
+                       double r_max, int stride, int* n_used_out, int* n_dirs_out) {
+    const int K = h->p.K;
+    std::vector<int> used;
+    std::vector<float> zu;
+    for (int b = 0; b < n_beams; b += stride)
+        if (ranges[b] < r_max) {
+            used.push_back(b);
+            zu.push_back(ranges[b]);
+        }
+    const int nu = (int)used.size();
+    std::vector<float> dirs;
+    std::vector<int32_t> dir_of((size_t)K * std::max(nu, 1));
+    std::unordered_map<unsigned long long, int> uniq;
+    for (int k = 0; k < K; ++k)
+        for (int u = 0; u < nu; ++u) {
+            const double a = (2.0 * M_PI / K) * k + h->theta + (angle_min + angle_inc * used[u]);
+            const float c = (float)std::cos(a), sn = (float)std::sin(a);
+            unsigned int bc, bs;
+            std::memcpy(&bc, &c, 4);
+            std::memcpy(&bs, &sn, 4);
+            const unsigned long long key = ((unsigned long long)bc << 32) | bs;
+            auto it = uniq.find(key);
+            int id;
+            if (it == uniq.end()) {
+                id = (int)(dirs.size() / 2);
+                uniq.emplace(key, id);
+                dirs.push_back(c);
+                dirs.push_back(sn);
+            } else {
+                id = it->second;
+            }
+            dir_of[(size_t)k * nu + u] = id;
+        }
+    const int nd = (int)(dirs.size() / 2);
+    if (!grow(h, h->dirs, h->cap_dirs, nd, 2 * sizeof(float)) ||
+        !grow(h, h->z, h->cap_beams, nu, sizeof(float)) ||
+        !grow(h, h->dir_of, h->cap_dir_of, K * nu, sizeof(int32_t)))
+        return fail(h, LOC_ERR_OOM, "scan buffers");
+    cudaError_t e = cudaSuccess;
+    if (nd) e = cudaMemcpyAsync(h->dirs, dirs.data(), sizeof(float) * dirs.size(), cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess && nu)
+        e = cudaMemcpyAsync(h->z, zu.data(), sizeof(float) * nu, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess && nu)
+        e = cudaMemcpyAsync(h->dir_of, dir_of.data(), sizeof(int32_t) * (size_t)K * nu, cudaMemcpyHostToDevice,
+                            h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "scan upload");
+    *n_used_out = nu;
+    *n_dirs_out = nd;
+    return LOC_OK;
+}
+
+loc_status check_scan(loc_session* h, const float* ranges, int n_beams, double angle_min, double angle_inc,
+                      double r_max, int stride, double sigma_r) {
+    if (!ranges || n_beams <= 0) return fail(h, LOC_ERR_INVALID_ARG, "ranges null or n_beams <= 0");
+    if (!std::isfinite(angle_min) || !std::isfinite(angle_inc) || !(r_max > 0.0) || !std::isfinite(r_max) ||
+        !(sigma_r > 0.0) || !std::isfinite(sigma_r) || stride < 1)
+        return fail(h, LOC_ERR_INVALID_ARG, "scan parameters: finite angles, r_max > 0, sigma_r > 0, stride >= 1");
+    for (int b = 0; b < n_beams; ++b)
+        if (!std::isfinite(ranges[b]) || ranges[b] < 0.0f)
+            return fail(h, LOC_ERR_INVALID_ARG, "ranges must be finite and >= 0");
+    return LOC_OK;
+}
+
+// Scores the sample list on the device (h->samples, count in h->dscal[0]) and reweights.
+loc_status score_and_reweight(loc_session* h, int n_used, int n_dirs, double r_max, double sigma_r) {
+    if (n_used == 0 || n_dirs == 0) return LOC_OK;        // nothing to score
+    const double cell = h->p.cell_m;
+    const uint32_t seed = pcg_hash((uint32_t)h->n_lidar * 0x85EBCA6Bu + 0x27D4EB2Fu);
+    cudaError_t e = launch_score_reweight(
+        h->B[h->cur], h->p.storage, h->trav, h->p.H, h->p.W, h->p.K, h->samples, h->dscal, h->cap, h->dirs,
+        n_dirs, h->dir_of, h->z, n_used, (float)(r_max / cell), (float)cell, (float)(1.0 / (2.0 * sigma_r * sigma_r)),
+        h->logL, reinterpret_cast<unsigned int*>(h->dscal + 1), h->rs, h->partials, h->nparts, seed, h->sd,
+        h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "score/reweight launch");
+    h->n_lidar += 1;
+    return LOC_OK;
+}
+
+loc_status materialize(loc_session* h) {
+    cudaError_t e = launch_materialize(h->B[h->cur], h->p.storage, h->trav, h->sd,
+                                       h->inv_uniform * storage_mult(h->p.storage), h->hw, h->p.K, h->partials,
+                                       h->nparts, h->stream);
+    return e == cudaSuccess ? LOC_OK : cuda_fail(h, e, "materialize");
+}
+
+}  // namespace
+
+LOC_API loc_status loc_lidar_update(loc_handle h, const float* ranges, int n_beams, double angle_min,
+                                    double angle_inc, double r_max, int beam_stride, double sigma_r) {
+    loc_status st = check_live(h);
+    if (st != LOC_OK) return st;
+    st = check_scan(h, ranges, n_beams, angle_min, angle_inc, r_max, beam_stride, sigma_r);
+    if (st != LOC_OK) return st;
+    if ((st = lidar_setup(h)) != LOC_OK) return st;
+    int nu = 0, nd = 0;
+    if ((st = upload_scan(h, ranges, n_beams, angle_min, angle_inc, r_max, beam_stride, &nu, &nd)) != LOC_OK)
+        return st;
+    if ((st = materialize(h)) != LOC_OK) return st;
+    cudaError_t e = launch_belief_map(h->B[h->cur], h->p.storage, h->trav, h->sd, h->inv_uniform, h->p.H, h->p.W,
+                                      h->p.K, h->m, h->partials, h->nparts, &h->sd->counter, h->p.n_samples,
+                                      reinterpret_cast<float*>(h->dscal + 2), h->stream);
+    if (e == cudaSuccess)
+        e = launch_dither(h->m, reinterpret_cast<float*>(h->dscal + 2), h->p.H, h->p.W, h->sel, h->rowcnt,
+                          h->rowoff, h->dscal, h->bnd, h->prog, &h->sd->status, h->cap, h->samples, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "sample selection launch");
+    return score_and_reweight(h, nu, nd, r_max, sigma_r);
+}
+
+LOC_API loc_status loc_lidar_update_cells(loc_handle h, const int32_t* cells, int n_cells, const float* ranges,
+                                          int n_beams, double angle_min, double angle_inc, double r_max,
+                                          int beam_stride, double sigma_r) {
+    loc_status st = check_live(h);
+    if (st != LOC_OK) return st;
+    st = check_scan(h, ranges, n_beams, angle_min, angle_inc, r_max, beam_stride, sigma_r);
+    if (st != LOC_OK) return st;
+    if (n_cells < 0 || (n_cells > 0 && !cells) || (long long)n_cells > (long long)h->hw)
+        return fail(h, LOC_ERR_INVALID_ARG, "cells null or n_cells out of range");
+    std::vector<int32_t> sorted(cells, cells + n_cells);
+    std::sort(sorted.begin(), sorted.end());
+    for (int c = 0; c < n_cells; ++c) {
+        if (sorted[c] < 0 || (size_t)sorted[c] >= h->hw) return fail(h, LOC_ERR_INVALID_ARG, "cell index out of grid");
+        if (c > 0 && sorted[c] == sorted[c - 1]) return fail(h, LOC_ERR_INVALID_ARG, "duplicate cell index");
+    }
+    if ((st = lidar_setup(h)) != LOC_OK) return st;
+    if (n_cells > h->cap) {                 // a larger sample list than dithering would give
+        int32_t* s2 = (int32_t*)dev_alloc(h, sizeof(int32_t) * (size_t)n_cells);
+        float* l2 = (float*)dev_alloc(h, sizeof(float) * (size_t)n_cells * h->p.K);
+        if (!s2 || !l2) return fail(h, LOC_ERR_OOM, "sample buffers");
+        dev_release(h, h->samples);
+        dev_release(h, h->logL);
+        h->samples = s2;
+        h->logL = l2;
+        h->cap = n_cells;
+    }
+    int nu = 0, nd = 0;
+    if ((st = upload_scan(h, ranges, n_beams, angle_min, angle_inc, r_max, beam_stride, &nu, &nd)) != LOC_OK)
+        return st;
+    if ((st = materialize(h)) != LOC_OK) return st;
+    cudaError_t e = cudaSuccess;
+    if (n_cells)
+        e = cudaMemcpyAsync(h->samples, cells, sizeof(int32_t) * n_cells, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->dscal, &n_cells, sizeof(int), cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);      // n_cells lives on this stack frame
+    if (e != cudaSuccess) return cuda_fail(h, e, "sample upload");
+    return score_and_reweight(h, nu, nd, r_max, sigma_r);
+}
+
+LOC_API loc_status loc_samples(loc_handle h, int32_t* out, size_t cap, int* n) {
+    loc_status st = check_live(h);
+    if (st != LOC_OK) return st;
+    if (!n || (cap > 0 && !out)) return fail(h, LOC_ERR_INVALID_ARG, "null output");
+    *n = 0;
+    if (!h->lidar_ready) return LOC_OK;
+    int cnt = 0;
+    cudaError_t e = cudaMemcpyAsync(&cnt, h->dscal, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "loc_samples");
+    const int avail = std::min(cnt, h->cap);
+    const size_t nout = std::min((size_t)avail, cap);
+    if (nout) {
+        e = cudaMemcpyAsync(out, h->samples, sizeof(int32_t) * nout, cudaMemcpyDeviceToHost, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "loc_samples");
+    }
+    *n = cnt;
+    return sync_and_check(h);
+}
+
+LOC_API loc_status loc_dither(loc_handle h, const float* m, float fs, uint8_t* sel, int* count) {
+    loc_status st = check_live(h);
+    if (st != LOC_OK) return st;
+    if (!m || !sel || !count) return fail(h, LOC_ERR_INVALID_ARG, "null argument");
+    if (!std::isfinite(fs)) return fail(h, LOC_ERR_INVALID_ARG, "fs must be finite");
+    for (size_t q = 0; q < h->hw; ++q)
+        if (!std::isfinite(m[q])) return fail(h, LOC_ERR_INVALID_ARG, "map values must be finite");
+    if ((st = lidar_setup(h)) != LOC_OK) return st;
+    cudaError_t e = cudaMemcpyAsync(h->m, m, sizeof(float) * h->hw, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h->dscal + 2, &fs, sizeof(float), cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess)
+        e = launch_dither(h->m, reinterpret_cast<float*>(h->dscal + 2), h->p.H, h->p.W, h->sel, h->rowcnt, h->rowoff,
+                          h->dscal + 3, h->bnd, h->prog, &h->sd->status, 0, nullptr, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(sel, h->sel, h->hw, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(count, h->dscal + 3, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "loc_dither");
+    return sync_and_check(h);
+}
+
+LOC_API loc_status loc_ray_ranges(loc_handle h, const int32_t* cells, int n_cells, const float* dirs, int n_dirs,
+                                  double r_max, float* out) {
+    loc_status st = check_live(h);
+    if (st != LOC_OK) return st;
+    if (n_cells < 0 || n_dirs < 0 || (n_cells && !cells) || (n_dirs && !dirs) || (n_cells && n_dirs && !out))
+        return fail(h, LOC_ERR_INVALID_ARG, "null argument or negative count");
+    if (!(r_max > 0.0) || !std::isfinite(r_max)) return fail(h, LOC_ERR_INVALID_ARG, "r_max must be > 0");
+    for (int c = 0; c < n_cells; ++c)
+        if (cells[c] < 0 || (size_t)cells[c] >= h->hw) return fail(h, LOC_ERR_INVALID_ARG, "cell index out of grid");
+    for (int d = 0; d < 2 * n_dirs; ++d)
+        if (!std::isfinite(dirs[d])) return fail(h, LOC_ERR_INVALID_ARG, "directions must be finite");
+    if (!n_cells || !n_dirs) return LOC_OK;
+    const size_t n = (size_t)n_cells * n_dirs;
+    int32_t* dc = (int32_t*)dev_alloc(h, sizeof(int32_t) * n_cells);
+    float* dd = (float*)dev_alloc(h, sizeof(float) * 2 * n_dirs);
+    float* dout = (float*)dev_alloc(h, sizeof(float) * n);
+    if (!dc || !dd || !dout) return fail(h, LOC_ERR_OOM, "ray buffers");
+    cudaError_t e = cudaMemcpyAsync(dc, cells, sizeof(int32_t) * n_cells, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dd, dirs, sizeof(float) * 2 * n_dirs, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess)
+        e = launch_ray_ranges(h->trav, h->p.H, h->p.W, dc, n_cells, dd, n_dirs, (float)(r_max / h->p.cell_m),
+                              (float)h->p.cell_m, dout, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, dout, sizeof(float) * n, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    for (void* p : {(void*)dc, (void*)dd, (void*)dout}) dev_release(h, p);
+    if (e != cudaSuccess) return cuda_fail(h, e, "loc_ray_ranges");
+    return sync_and_check(h);
 }
 
 LOC_API loc_status loc_belief(loc_handle h, float* out, size_t n) {

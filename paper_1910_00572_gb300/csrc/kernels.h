@@ -53,6 +53,30 @@ cudaError_t launch_set_belief(const float* src, void* B, int storage, size_t n,
                               SessionDev* sd, double* partials, unsigned int nparts,
                               cudaStream_t st);
 
+// ---- LIDAR sample update (lidar.cu)
+// m = belief map (max over bins), fs = n_samples / sum(m) (device float).
+cudaError_t launch_belief_map(const void* B, int storage, const uint8_t* trav, SessionDev* sd, float inv_uniform,
+                              int H, int W, int K, float* m, double* partials, unsigned int nparts,
+                              unsigned int* counter, int n_samples, float* fs_out, cudaStream_t st);
+// Floyd-Steinberg selection of m * fs -> sel, per-row counts/offsets, total -> *count and (if
+// samples) the raster-ordered list of at most cap selected linear indices.  bnd holds
+// ((H+31)/32 + 1) * W floats, prog (H+31)/32 + 2 ints.
+cudaError_t launch_dither(const float* m, const float* fs, int H, int W, uint8_t* sel, int* rowcnt, int* rowoff,
+                          int* count, float* bnd, int* prog, int* status, int cap, int32_t* samples,
+                          cudaStream_t st);
+cudaError_t launch_ray_ranges(const uint8_t* trav, int H, int W, const int32_t* cells, int n_cells, const float* dirs,
+                              int n_dirs, float rmax_cells, float cell_m, float* out, cudaStream_t st);
+size_t reweight_scalars_bytes();
+// Score the samples against the scan and reweight them (Eq. 9 on the sampled set).
+cudaError_t launch_score_reweight(void* B, int storage, const uint8_t* trav, int H, int W, int K,
+                                  const int32_t* samples, const int* count, int cap, const float* dirs, int n_dirs,
+                                  const int32_t* dir_of, const float* z, int n_used, float rmax_cells, float cell_m,
+                                  float inv2s2, float* logL, unsigned int* maxL, void* rs, double* partials,
+                                  unsigned int nparts, uint32_t seed, SessionDev* sd, cudaStream_t st);
+// If the session reads as uniform (restart flag), write that belief into B and clear the flag.
+cudaError_t launch_materialize(void* B, int storage, const uint8_t* trav, SessionDev* sd, float value,
+                               size_t hw, int K, double* partials, unsigned int nparts, cudaStream_t st);
+
 // Sets the calling thread's error message returned by loc_last_error(NULL).
 void set_thread_error(const char* msg);
 

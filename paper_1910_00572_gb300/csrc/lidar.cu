@@ -1,0 +1,428 @@
+// LIDAR sample update of Section III-B: belief map -> Floyd-Steinberg sample selection
+// (III-B.1) -> expected ranges by grid ray casting -> Gaussian range likelihood -> Eq. 9 on
+// the sampled states (the sampled set keeps its mass).
+//
+// The two steps whose results are integers decided by floating point -- the dithering and
+// the ray walk -- use FP32 with every operation explicitly rounded (__fadd_rn / __fmul_rn /
+// __fdiv_rn, so nothing is contracted into an FMA) in a fixed order.
+#include <cfloat>
+
+#include "kernels.h"
+
+namespace loc {
+namespace {
+
+constexpr int NT = 256;
+constexpr unsigned long long kSpinNs = 200ull * 1000 * 1000;
+
+__device__ __forceinline__ unsigned long long gtime() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// ------------------------------------------------------------------ belief map and fs
+
+// m[q] = max_k belief(k, q) (normalised, FP32); the last CTA writes fs = n_samples / sum(m)
+// (FP64 sum, rounded to FP32), or 0 when the map is empty.
+template <typename T>
+__global__ void __launch_bounds__(NT) belief_map_kernel(const T* __restrict__ B, const uint8_t* __restrict__ trav,
+                                                        SessionDev* sd, float inv_uniform, size_t hw, int K,
+                                                        float* __restrict__ m, double* partials,
+                                                        unsigned int* counter, int n_samples, float* fs_out) {
+    __shared__ double red[NT / 32];
+    const int reinit = sd->reinit;
+    const float scale = sd->inv_Z;
+    KahanF acc;
+    for (size_t q = (size_t)blockIdx.x * NT + threadIdx.x; q < hw; q += (size_t)gridDim.x * NT) {
+        float v = 0.0f;
+        if (reinit) {
+            v = (float)trav[q] * inv_uniform;
+        } else {
+            for (int k = 0; k < K; ++k) v = fmaxf(v, Store<T>::ld(B + (size_t)k * hw + q) * scale);
+        }
+        m[q] = v;
+        acc.add(v);
+    }
+    const double bt = block_sum<NT>(acc.value(), red);
+    finish_sum<NT>(bt, partials, counter, gridDim.x, red, [fs_out, n_samples](double S) {
+        *fs_out = S > 0.0 ? (float)((double)n_samples / S) : 0.0f;
+    });
+}
+
+// ------------------------------------------------------------------ Floyd-Steinberg
+
+// One CTA of 32 warps.  Warp w takes the 32-row blocks rb = w, w + 32, ...; lane l owns row
+// 32 rb + l and handles column i = t - 2l at step t, so the three errors it needs from the
+// row above (columns i-1, i, i+1) were produced by lane l-1 at steps t-3, t-2, t-1 and arrive
+// by warp shuffle.  Lane 0 takes the row above from the previous block's last row, which that
+// block's lane 31 writes into bnd[rb][*] and publishes in prog[rb] (columns written);
+// every wait on prog is bounded.
+__global__ void __launch_bounds__(1024) fs_kernel(const float* __restrict__ m, const float* fs_ptr, int H, int W,
+                                                  uint8_t* __restrict__ sel, int* __restrict__ rowcnt,
+                                                  float* bnd, int* prog, int* status) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const float fs = *fs_ptr;
+    const int nrb = (H + 31) / 32;
+    const float w7 = 0.4375f, w3 = 0.1875f, w5 = 0.3125f, w1 = 0.0625f;
+    for (int rb = warp; rb < nrb; rb += 32) {
+        const int j = 32 * rb + lane;
+        const bool row_ok = j < H;
+        float up_old = 0.0f, up_mid = 0.0f, up_new = 0.0f;   // row above: columns i-1, i, i+1
+        float e_prev = 0.0f, last = 0.0f;                      // own error at i-1; newest error
+        float chunk = 0.0f;                                    // lane L: bnd[rb][t0 + 1 + L]
+        int cnt = 0;
+        bool failed = false;
+        const int steps = W + 62;
+        for (int t = 0; t < steps; ++t) {
+            if (rb > 0 && (t & 31) == 0) {
+                // the row above for columns t+1 .. t+32 must be published before lane 0 uses it
+                const int need = min(W, t + 33);
+                int ok = 1;
+                if (lane == 0) {
+                    const unsigned long long t0 = gtime();
+                    unsigned int it = 0;
+                    while (((volatile int*)prog)[rb] < need) {
+                        if (++it > (1u << 26) || gtime() - t0 > kSpinNs) {
+                            ok = 0;
+                            break;
+                        }
+                    }
+                }
+                ok = __shfl_sync(0xffffffffu, ok, 0);
+                if (!ok) {
+                    failed = true;
+                    if (lane == 0) atomicOr(status, LOC_DEV_ERR_TIMEOUT);
+                    break;
+                }
+                __threadfence_block();
+                const int c = t + 1 + lane;
+                chunk = c < W ? ((volatile float*)bnd)[(size_t)rb * W + c] : 0.0f;
+            }
+            const float from_above = __shfl_sync(0xffffffffu, chunk, t & 31);
+            const float from_left = __shfl_up_sync(0xffffffffu, last, 1);
+            const float incoming = lane == 0 ? (rb > 0 ? from_above : 0.0f) : from_left;
+            up_old = up_mid;
+            up_mid = up_new;
+            up_new = incoming;
+            const int i = t - 2 * lane;
+            if (i >= 0 && i < W && row_ok) {
+                float E = 0.0f;
+                if (j > 0) {
+                    if (i > 0) E = __fadd_rn(E, __fmul_rn(up_old, w1));
+                    E = __fadd_rn(E, __fmul_rn(up_mid, w5));
+                    if (i + 1 < W) E = __fadd_rn(E, __fmul_rn(up_new, w3));
+                }
+                if (i > 0) E = __fadd_rn(E, __fmul_rn(e_prev, w7));
+                float v = __fmul_rn(m[(size_t)j * W + i], fs);
+                if (v > 1.0f) v = 1.0f;
+                const float val = __fadd_rn(v, E);
+                const bool on = val >= 0.5f;
+                const float err = on ? __fsub_rn(val, 1.0f) : val;
+                sel[(size_t)j * W + i] = on ? 1 : 0;
+                cnt += on ? 1 : 0;
+                e_prev = err;
+                last = err;
+                if (lane == 31 && rb + 1 < nrb) {
+                    bnd[(size_t)(rb + 1) * W + i] = err;
+                    if (((i + 1) & 31) == 0 || i == W - 1) {
+                        __threadfence_block();
+                        ((volatile int*)prog)[rb + 1] = i + 1;
+                    }
+                }
+            }
+        }
+        if (failed) return;
+        if (row_ok) rowcnt[j] = cnt;
+    }
+}
+
+// Exclusive prefix of the per-row counts (one CTA); total -> *count.
+__global__ void __launch_bounds__(1024) row_scan_kernel(const int* __restrict__ rowcnt, int H,
+                                                        int* __restrict__ rowoff, int* count) {
+    __shared__ int part[1024];
+    const int per = (H + 1023) / 1024;
+    const int j0 = threadIdx.x * per;
+    int s = 0;
+    for (int j = j0; j < j0 + per && j < H; ++j) s += rowcnt[j];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {            // inclusive Hillis-Steele scan
+        const int v = threadIdx.x >= o ? part[threadIdx.x - o] : 0;
+        __syncthreads();
+        part[threadIdx.x] += v;
+        __syncthreads();
+    }
+    int run = threadIdx.x > 0 ? part[threadIdx.x - 1] : 0;
+    for (int j = j0; j < j0 + per && j < H; ++j) {
+        rowoff[j] = run;
+        run += rowcnt[j];
+    }
+    if (threadIdx.x == 1023) *count = part[1023];
+}
+
+// Linear indices of the selected cells in raster order (one warp per row), at most cap.
+__global__ void __launch_bounds__(NT) compact_kernel(const uint8_t* __restrict__ sel, const int* __restrict__ rowoff,
+                                                     int H, int W, int cap, int32_t* __restrict__ out) {
+    const int lane = threadIdx.x & 31;
+    for (int j = (blockIdx.x * NT + threadIdx.x) >> 5; j < H; j += (gridDim.x * NT) >> 5) {
+        int base = rowoff[j];
+        for (int i0 = 0; i0 < W; i0 += 32) {
+            const int i = i0 + lane;
+            const bool on = i < W && sel[(size_t)j * W + i];
+            const unsigned int ball = __ballot_sync(0xffffffffu, on);
+            const int pos = base + __popc(ball & ((1u << lane) - 1u));
+            if (on && pos < cap) out[pos] = j * W + i;
+            base += __popc(ball);
+        }
+    }
+}
+
+// ------------------------------------------------------------------ ray casting + scoring
+
+// Distance in cells from the centre of free cell (j, i) along (dx, dy) to the first occupied
+// cell or the grid edge, capped at rmax; ties step x first.  Same FP32 operations, in the
+// same order, as the reference walk.
+__device__ float dda_cells(const uint8_t* __restrict__ trav, int H, int W, int j, int i, float dx, float dy,
+                           float rmax) {
+    if (!trav[(size_t)j * W + i]) return 0.0f;
+    const int sx = dx > 0.0f ? 1 : -1, sy = dy > 0.0f ? 1 : -1;
+    const float tdx = dx != 0.0f ? __fdiv_rn(1.0f, fabsf(dx)) : INFINITY;
+    const float tdy = dy != 0.0f ? __fdiv_rn(1.0f, fabsf(dy)) : INFINITY;
+    int nx = 0, ny = 0;
+    // every step crosses one cell boundary and t grows by at least 1/2 cell per two steps
+    const int max_steps = 4 * (int)rmax + 16;
+    for (int s = 0; s < max_steps; ++s) {
+        const float tx = __fmul_rn(__fadd_rn((float)nx, 0.5f), tdx);
+        const float ty = __fmul_rn(__fadd_rn((float)ny, 0.5f), tdy);
+        float t;
+        if (tx <= ty) { i += sx; nx += 1; t = tx; }
+        else          { j += sy; ny += 1; t = ty; }
+        if (t >= rmax) return rmax;
+        if (i < 0 || i >= W || j < 0 || j >= H) return t;
+        if (!trav[(size_t)j * W + i]) return t;
+    }
+    return rmax;
+}
+
+// Ranges for given cells and directions (the loc_ray_ranges entry point).
+__global__ void __launch_bounds__(NT) ray_ranges_kernel(const uint8_t* __restrict__ trav, int H, int W,
+                                                        const int32_t* __restrict__ cells, int n_cells,
+                                                        const float* __restrict__ dirs, int n_dirs, float rmax,
+                                                        float cell_m, float* __restrict__ out) {
+    const size_t n = (size_t)n_cells * n_dirs;
+    for (size_t q = (size_t)blockIdx.x * NT + threadIdx.x; q < n; q += (size_t)gridDim.x * NT) {
+        const int c = (int)(q / n_dirs), d = (int)(q % n_dirs);
+        const int cell = cells[c];
+        const float t = dda_cells(trav, H, W, cell / W, cell % W, dirs[2 * d], dirs[2 * d + 1], rmax);
+        out[q] = __fmul_rn(t, cell_m);
+    }
+}
+
+// Order-preserving map of floats to unsigned ints (for atomicMax on floats).
+__device__ __forceinline__ unsigned int f2ord(float f) {
+    const unsigned int u = __float_as_uint(f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float ord2f(unsigned int u) {
+    return __uint_as_float((u & 0x80000000u) ? (u & 0x7FFFFFFFu) : ~u);
+}
+
+// One CTA per sampled cell (grid-stride): cast the n_dirs distinct rays once, then for every
+// bin k: logL[s][k] = -sum_b (z_b - r(dir_of[k][b]))^2 / (2 sigma^2) over the used beams.
+__global__ void __launch_bounds__(NT) score_kernel(const uint8_t* __restrict__ trav, int H, int W, int K,
+                                                   const int32_t* __restrict__ samples, const int* count_ptr, int cap,
+                                                   const float* __restrict__ dirs, int n_dirs,
+                                                   const int32_t* __restrict__ dir_of, const float* __restrict__ z,
+                                                   int n_used, float rmax, float cell_m, float inv2s2,
+                                                   float* __restrict__ logL, unsigned int* maxL) {
+    extern __shared__ float rh[];                 // n_dirs expected ranges (metres)
+    const int n = min(*count_ptr, cap);
+    float best = -FLT_MAX;
+    for (int s = blockIdx.x; s < n; s += gridDim.x) {
+        const int cell = samples[s];
+        const int j = cell / W, i = cell % W;
+        for (int d = threadIdx.x; d < n_dirs; d += NT)
+            rh[d] = __fmul_rn(dda_cells(trav, H, W, j, i, dirs[2 * d], dirs[2 * d + 1], rmax), cell_m);
+        __syncthreads();
+        for (int k = threadIdx.x; k < K; k += NT) {
+            float acc = 0.0f;
+            const int32_t* row = dir_of + (size_t)k * n_used;
+            for (int b = 0; b < n_used; ++b) {
+                const float e = z[b] - rh[row[b]];
+                acc = fmaf(e, e, acc);
+            }
+            const float l = -acc * inv2s2;
+            logL[(size_t)s * K + k] = l;
+            best = fmaxf(best, l);
+        }
+        __syncthreads();
+    }
+    for (int o = 16; o > 0; o >>= 1) best = fmaxf(best, __shfl_down_sync(0xffffffffu, best, o));
+    if ((threadIdx.x & 31) == 0 && best > -FLT_MAX) atomicMax(maxL, f2ord(best));
+}
+
+// ------------------------------------------------------------------ Eq. 9 on the sampled set
+
+struct ReweightScalars {
+    double mass, wmass, factor;                   // sum b, sum b w over the set; mass / wmass
+    unsigned int counter;
+    int pad;
+};
+
+// Sums over the sampled states (stored units): mass = sum b, wmass = sum b w,
+// w = exp(logL - max logL); the last CTA writes factor = mass / wmass (0: leave as is).
+template <typename T>
+__global__ void __launch_bounds__(NT) reweight_sums_kernel(const T* __restrict__ B, size_t hw, int K,
+                                                           const int32_t* __restrict__ samples, const int* count_ptr,
+                                                           int cap, const float* __restrict__ logL,
+                                                           const unsigned int* maxL, double* partials,
+                                                           ReweightScalars* rs) {
+    __shared__ double red[NT / 32];
+    __shared__ double red2[NT / 32];
+    const int n = min(*count_ptr, cap);
+    const float mx = ord2f(*maxL);
+    KahanF m, wm;
+    const size_t total = (size_t)n * K;
+    for (size_t q = (size_t)blockIdx.x * NT + threadIdx.x; q < total; q += (size_t)gridDim.x * NT) {
+        const int s = (int)(q / K), k = (int)(q % K);
+        const float b = Store<T>::ld(B + (size_t)k * hw + samples[s]);
+        const float w = expf(logL[q] - mx);
+        m.add(b);
+        wm.add(b * w);
+    }
+    const double bm = block_sum<NT>(m.value(), red);
+    const double bw = block_sum<NT>(wm.value(), red2);
+    __shared__ int s_last;
+    if (threadIdx.x == 0) {
+        partials[2 * blockIdx.x] = bm;
+        partials[2 * blockIdx.x + 1] = bw;
+        __threadfence();
+        s_last = atomicAdd(&rs->counter, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    double a = 0.0, c = 0.0;
+    for (unsigned int b = threadIdx.x; b < gridDim.x; b += NT) {
+        a += ((volatile double*)partials)[2 * b];
+        c += ((volatile double*)partials)[2 * b + 1];
+    }
+    const double A = block_sum<NT>(a, red), C = block_sum<NT>(c, red2);
+    if (threadIdx.x == 0) {
+        rs->counter = 0u;
+        rs->mass = A;
+        rs->wmass = C;
+        rs->factor = (C > 0.0 && isfinite(C) && A > 0.0) ? A / C : 0.0;
+    }
+}
+
+// b <- b w factor on the sampled states; the last CTA updates Z by the change of the set's sum.
+template <typename T>
+__global__ void __launch_bounds__(NT) reweight_apply_kernel(T* __restrict__ B, size_t hw, int K,
+                                                            const int32_t* __restrict__ samples, const int* count_ptr,
+                                                            int cap, const float* __restrict__ logL,
+                                                            const unsigned int* maxL, ReweightScalars* rs,
+                                                            uint32_t seed, double* partials, SessionDev* sd) {
+    __shared__ double red[NT / 32];
+    const double factor = rs->factor;
+    const int n = min(*count_ptr, cap);
+    const float mx = ord2f(*maxL);
+    const float f = (float)factor;
+    KahanF acc;
+    const size_t total = (size_t)n * K;
+    if (factor > 0.0) {
+        for (size_t q = (size_t)blockIdx.x * NT + threadIdx.x; q < total; q += (size_t)gridDim.x * NT) {
+            const int s = (int)(q / K), k = (int)(q % K);
+            const size_t at = (size_t)k * hw + samples[s];
+            const float b = Store<T>::ld(B + at);
+            const float v = b * expf(logL[q] - mx) * f;
+            acc.add(store_out<T>(B + at, v, pcg_hash((uint32_t)at ^ seed)));
+        }
+    }
+    const double bt = block_sum<NT>(acc.value(), red);
+    finish_sum<NT>(bt, partials, &sd->counter, gridDim.x, red, [sd, rs, factor](double S) {
+        if (factor > 0.0) {
+            const double Z = sd->Z - rs->mass + S;
+            if (Z > 0.0 && isfinite(Z)) {
+                sd->Z = Z;
+                sd->inv_Z = (float)(1.0 / Z);
+            }
+        }
+    });
+}
+
+unsigned int grid_for(size_t n, unsigned int cap) {
+    size_t b = (n + NT - 1) / NT;
+    if (b < 1) b = 1;
+    return (unsigned int)(b < cap ? b : cap);
+}
+
+}  // namespace
+
+size_t reweight_scalars_bytes() { return sizeof(ReweightScalars); }
+
+#define LOC_DISPATCH(storage, CALL)                                                   \
+    switch (storage) {                                                                \
+        case LOC_F32: { using T = float; CALL; } break;                               \
+        case LOC_BF16: { using T = __nv_bfloat16; CALL; } break;                      \
+        case LOC_F16: { using T = __half; CALL; } break;                              \
+        default: return cudaErrorInvalidValue;                                        \
+    }
+
+cudaError_t launch_belief_map(const void* B, int storage, const uint8_t* trav, SessionDev* sd, float inv_uniform,
+                              int H, int W, int K, float* m, double* partials, unsigned int nparts,
+                              unsigned int* counter, int n_samples, float* fs_out, cudaStream_t st) {
+    const size_t hw = (size_t)H * W;
+    const unsigned int nb = grid_for(hw, nparts < 2048 ? nparts : 2048);
+    LOC_DISPATCH(storage, (belief_map_kernel<T><<<nb, NT, 0, st>>>((const T*)B, trav, sd, inv_uniform, hw, K, m,
+                                                                      partials, counter, n_samples, fs_out)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dither(const float* m, const float* fs, int H, int W, uint8_t* sel, int* rowcnt, int* rowoff,
+                          int* count, float* bnd, int* prog, int* status, int cap, int32_t* samples,
+                          cudaStream_t st) {
+    const int nrb = (H + 31) / 32;
+    cudaError_t e = cudaMemsetAsync(prog, 0, sizeof(int) * (size_t)(nrb + 1), st);
+    if (e != cudaSuccess) return e;
+    fs_kernel<<<1, 1024, 0, st>>>(m, fs, H, W, sel, rowcnt, bnd, prog, status);
+    row_scan_kernel<<<1, 1024, 0, st>>>(rowcnt, H, rowoff, count);
+    if (samples) compact_kernel<<<grid_for((size_t)H * 32, 1024), NT, 0, st>>>(sel, rowoff, H, W, cap, samples);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ray_ranges(const uint8_t* trav, int H, int W, const int32_t* cells, int n_cells, const float* dirs,
+                              int n_dirs, float rmax_cells, float cell_m, float* out, cudaStream_t st) {
+    ray_ranges_kernel<<<grid_for((size_t)n_cells * n_dirs, 4096), NT, 0, st>>>(trav, H, W, cells, n_cells, dirs,
+                                                                              n_dirs, rmax_cells, cell_m, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_score_reweight(void* B, int storage, const uint8_t* trav, int H, int W, int K,
+                                  const int32_t* samples, const int* count, int cap, const float* dirs, int n_dirs,
+                                  const int32_t* dir_of, const float* z, int n_used, float rmax_cells, float cell_m,
+                                  float inv2s2, float* logL, unsigned int* maxL, void* rs, double* partials,
+                                  unsigned int nparts, uint32_t seed, SessionDev* sd, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(maxL, 0, sizeof(unsigned int), st);
+    if (e != cudaSuccess) return e;
+    const size_t smem = sizeof(float) * (size_t)n_dirs;
+    if (smem > 48 * 1024) {
+        e = cudaFuncSetAttribute(score_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    const unsigned int ns = (unsigned int)(cap < 8192 ? (cap > 0 ? cap : 1) : 8192);
+    score_kernel<<<ns, NT, smem, st>>>(trav, H, W, K, samples, count, cap, dirs, n_dirs, dir_of, z, n_used,
+                                       rmax_cells, cell_m, inv2s2, logL, maxL);
+    const size_t hw = (size_t)H * W;
+    const unsigned int half = nparts / 2 < 1024 ? nparts / 2 : 1024;
+    const unsigned int nb = grid_for((size_t)cap * K, half > 0 ? half : 1);
+    ReweightScalars* r = static_cast<ReweightScalars*>(rs);
+    LOC_DISPATCH(storage, (reweight_sums_kernel<T><<<nb, NT, 0, st>>>((const T*)B, hw, K, samples, count, cap, logL,
+                                                                        maxL, partials, r)));
+    LOC_DISPATCH(storage, (reweight_apply_kernel<T><<<nb, NT, 0, st>>>((T*)B, hw, K, samples, count, cap, logL, maxL,
+                                                                         r, seed, partials, sd)));
+    return cudaGetLastError();
+}
+
+}  // namespace loc

@@ -149,7 +149,40 @@ __global__ void set_belief_kernel(const float* __restrict__ src, T* __restrict__
 
 constexpr int kArgmaxBlocks = 1024;
 
+// Writes the uniform belief (trav * value) into B when the restart flag is set; the last CTA
+// sets Z to its sum and clears the flag.  Every CTA reads the flag before it arrives.
+template <typename T>
+__global__ void materialize_kernel(T* __restrict__ B, const uint8_t* __restrict__ trav, SessionDev* sd,
+                                   float value, size_t hw, int K, double* partials) {
+    __shared__ double red[NT / 32];
+    if (!sd->reinit) return;                      // uniform over the grid: every CTA agrees
+    KahanF acc;
+    const size_t n = hw * K;
+    for (size_t q = (size_t)blockIdx.x * NT + threadIdx.x; q < n; q += (size_t)gridDim.x * NT)
+        acc.add(Store<T>::st(B + q, (float)trav[q % hw] * value));
+    const double bt = block_sum<NT>(acc.value(), red);
+    finish_sum<NT>(bt, partials, &sd->counter, gridDim.x, red, [sd](double Z) {
+        sd->Z = Z;
+        sd->inv_Z = (float)(1.0 / Z);
+        sd->reinit = 0;
+    });
+}
+
 }  // namespace
+
+cudaError_t launch_materialize(void* B, int storage, const uint8_t* trav, SessionDev* sd, float value,
+                               size_t hw, int K, double* partials, unsigned int nparts, cudaStream_t st) {
+    unsigned int nb = (unsigned int)((hw * K + NT - 1) / NT);
+    if (nb > nparts) nb = nparts;
+    if (nb > 4096) nb = 4096;
+    switch (storage) {
+        case LOC_F32: materialize_kernel<float><<<nb, NT, 0, st>>>((float*)B, trav, sd, value, hw, K, partials); break;
+        case LOC_BF16: materialize_kernel<__nv_bfloat16><<<nb, NT, 0, st>>>((__nv_bfloat16*)B, trav, sd, value, hw, K, partials); break;
+        case LOC_F16: materialize_kernel<__half><<<nb, NT, 0, st>>>((__half*)B, trav, sd, value, hw, K, partials); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
 
 cudaError_t launch_edge_correction(const uint8_t* trav, float* corr, int H, int W,
                                    const float* gx, int r, cudaStream_t st) {

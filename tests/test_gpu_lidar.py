@@ -1,0 +1,206 @@
+"""GPU parity of the LIDAR sample update (Section III-B) through the C-ABI.
+
+* Floyd-Steinberg selection and the ray-cast expected ranges decide integers, so both are
+  compared bit for bit with the oracle's FP32 implementations on the same inputs.
+* The likelihood and the Eq. 9 reweighting of a given sample set are compared with the FP64
+  oracle within 1e-6 absolute and 2e-5 of the largest value (FP32 log-likelihoods: the
+  states that keep weight have |log L| of order 10, where FP32 is good to ~1e-6).
+* loc_lidar_update with the GPU's own dithering is checked by properties that hold for any
+  valid selection: the belief still sums to 1, unsampled states are untouched, the number of
+  samples follows the Floyd-Steinberg count bound, and the true pose gains weight.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import paper_1910_00572_gb300 as loc
+from oracle import filter as F
+from oracle import lidar as OL
+from oracle import readout as R
+from synth import fields, floorplan, scan, workloads
+
+pytestmark = pytest.mark.gpu
+
+ABS_TOL = 1e-6
+REL_TOL = 2e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1910_00572_gb300 import build
+    build.build()
+    loc.lib()
+
+
+def make(occ, K, cell, **kw):
+    p = loc.loc_params_default(H=occ.shape[0], W=occ.shape[1], K=K, cell_m=cell, **kw)
+    return loc.loc_create(occ, p)
+
+
+# ------------------------------------------------------------------ Floyd-Steinberg
+
+@pytest.mark.parametrize("H,W,n_s", [(5, 7, 6), (64, 64, 300), (100, 37, 500), (300, 257, 4096),
+                                     (97, 1100, 2000), (2048, 2048, 4096)])
+def test_dithering_is_bit_exact(H, W, n_s):
+    m = fields.map_like(H, W, seed=H + W)
+    fs = float(OL.fs_factor(m, n_s))
+    h = make(np.zeros((H, W), np.uint8), 8, 0.05)
+    try:
+        sel, count = loc.loc_dither(h, m, fs)
+    finally:
+        loc.loc_destroy(h)
+    want = OL.fs_select(m, fs)
+    assert count == int(want.sum())
+    assert np.array_equal(sel, want)
+
+
+def test_dithering_half_grey_checkerboard():
+    h = make(np.zeros((40, 72), np.uint8), 8, 0.05)
+    try:
+        sel, _ = loc.loc_dither(h, np.full((40, 72), 0.5, np.float32), 1.0)
+    finally:
+        loc.loc_destroy(h)
+    J, I = np.mgrid[0:40, 0:72]
+    assert (sel == ((I + J) % 2 == 0)).all()
+
+
+# ------------------------------------------------------------------ ray casting
+
+def test_ray_ranges_are_bit_exact():
+    occ = floorplan.crop(floorplan.office_map(3, size=512), 100, 60, 256, 256)
+    rng = np.random.default_rng(0)
+    free = np.flatnonzero(occ.reshape(-1) == 0)
+    cells = rng.choice(free, 300, replace=False).astype(np.int32)
+    cells = np.append(cells, np.flatnonzero(occ.reshape(-1) != 0)[:5]).astype(np.int32)  # occupied: 0
+    ang = np.concatenate([rng.uniform(-math.pi, math.pi, 200), np.arange(8) * math.pi / 4])
+    dirs = OL.beam_dirs32(ang)
+    h = make(occ, 8, 0.05)
+    try:
+        got = loc.loc_ray_ranges(h, cells, dirs, 10.0)
+    finally:
+        loc.loc_destroy(h)
+    want = OL.expected_ranges(occ, cells, dirs, 10.0, 0.05)
+    assert np.array_equal(got, want)
+
+
+# ------------------------------------------------------------------ Eq. 9 on a given set
+
+def lidar_case(seed, storage="f32", K=16, size=96, n_samples=400):
+    occ = floorplan.crop(floorplan.office_map(seed, size=256), 30, 40, size, size)
+    cell = 0.05
+    rng = np.random.default_rng(seed)
+    free = np.argwhere(occ == 0)
+    j, i = free[rng.integers(len(free))]
+    theta = 0.37
+    k_true = 5
+    pose = ((i + 0.5) * cell, (j + 0.5) * cell, 2 * math.pi * k_true / K + theta)
+    z = scan.simulate_scan(occ, cell, pose, seed=seed, n_beams=360, r_max=4.0, noise_sigma=0.02)
+    b = fields.belief_like(occ, K, seed=seed, dtype=np.float32)
+    return occ, cell, theta, z, b, (k_true, j, i)
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_reweight_with_given_cells_matches_oracle(seed):
+    occ, cell, theta, z, b, _ = lidar_case(seed)
+    K = b.shape[0]
+    b64 = b.astype(np.float64) / b.astype(np.float64).sum()
+    m32 = b64.max(axis=0).astype(np.float32)
+    cells = OL.samples_from_mask(OL.fs_select(m32, OL.fs_factor(m32, 400)))
+    assert cells.size > 50
+    h = make(occ, K, cell)
+    try:
+        loc.loc_set_belief(h, b)
+        loc.loc_step(h, 0.0, 0.0, theta)              # heading offset theta_t = theta (no motion:
+        ref = F.Filter(occ, K, cell)                 # the propagation is the blur only)
+        ref.B = b64.copy()
+        ref.step(0.0, 0.0, theta)
+        before = loc.loc_belief(h)
+        loc.loc_lidar_update_cells(h, cells, z, 0.0, math.pi / 180, 4.0, 4, 0.1)
+        got = loc.loc_belief(h)
+        st = loc.loc_stats(h)
+    finally:
+        loc.loc_destroy(h)
+    want, _ = OL.lidar_update(ref.B, occ, theta, z, cell, 0.0, math.pi / 180, 4.0, 4, 0.1, 400, cells=cells)
+    err = np.abs(got.astype(np.float64) - want).max()
+    assert err <= ABS_TOL and err <= REL_TOL * want.max(), err
+    flat_b, flat_g = before.reshape(K, -1), got.reshape(K, -1)
+    others = np.setdiff1d(np.arange(flat_b.shape[1]), cells)
+    assert np.array_equal(flat_b[:, others] * 1.0, flat_g[:, others] * 1.0) or \
+        np.abs(flat_b[:, others] - flat_g[:, others]).max() <= 1e-7 * flat_b.max()
+    assert abs(got.astype(np.float64).sum() - 1.0) < 1e-5
+
+
+def test_lidar_update_properties_with_device_dithering():
+    occ, cell, theta, z, b, (k_true, j_true, i_true) = lidar_case(4, n_samples=600)
+    K = b.shape[0]
+    p = loc.loc_params_default(H=occ.shape[0], W=occ.shape[1], K=K, cell_m=cell, n_samples=600)
+    h = loc.loc_create(occ, p)
+    try:
+        loc.loc_set_belief(h, b)
+        loc.loc_step(h, 0.0, 0.0, theta)
+        before = loc.loc_belief(h)
+        m_before = loc.loc_marginal(h, loc.LOC_MAP_MAX)
+        loc.loc_lidar_update(h, z, 0.0, math.pi / 180, 4.0, 4, 0.1)
+        got = loc.loc_belief(h)
+        cells = loc.loc_samples(h)
+    finally:
+        loc.loc_destroy(h)
+    H, W = occ.shape
+    v = np.minimum(1.0, 600 * m_before.astype(np.float64) / m_before.astype(np.float64).sum())
+    assert abs(cells.size - v.sum()) <= H + W
+    assert np.all(np.diff(cells) > 0)                                  # raster order, unique
+    flat_b, flat_g = before.reshape(K, -1), got.reshape(K, -1)
+    others = np.setdiff1d(np.arange(H * W), cells)
+    assert np.abs(flat_b[:, others] - flat_g[:, others]).max() <= 1e-7 * flat_b.max()
+    assert abs(flat_g[:, cells].sum() - flat_b[:, cells].sum()) <= 1e-5
+    assert abs(got.astype(np.float64).sum() - 1.0) < 1e-5
+
+
+# ------------------------------------------------------------------ trajectories with scans
+
+def run_lidar_trajectory(storage, size, K, steps, scan_every, seed):
+    wl = workloads.get("office2048")
+    occ = floorplan.crop(floorplan.office_map(seed, size=1024), 300, 280, size, size)
+    cell = 0.05
+    walk = workloads.make_walk(dict(wl, seed=seed), occ, steps=steps)
+    p = loc.loc_params_default(H=size, W=size, K=K, cell_m=cell, storage=storage)
+    h = loc.loc_create(occ, p)
+    ref = F.Filter(occ, K, cell)
+    out = []
+    try:
+        for t, (u, v, w) in enumerate(walk.odom, start=1):
+            loc.loc_step(h, u, v, w)
+            ref.step(u, v, w)
+            if t % scan_every == 0:
+                z = scan.simulate_scan(occ, cell, walk.poses[t], seed=seed * 7919 + t, n_beams=360,
+                                       r_max=10.0, noise_sigma=0.05, dropout=0.05)
+                m32 = ref.B.max(axis=0).astype(np.float32)
+                cells = OL.samples_from_mask(OL.fs_select(m32, OL.fs_factor(m32, 1024)))
+                loc.loc_lidar_update_cells(h, cells, z, 0.0, math.pi / 180, 10.0, 4, 0.1)
+                ref.B, _ = OL.lidar_update(ref.B, occ, ref.odo.theta, z, cell, 0.0, math.pi / 180,
+                                           10.0, 4, 0.1, 1024, cells=cells)
+                out.append((t, loc.loc_belief(h).astype(np.float64), ref.B.copy()))
+    finally:
+        loc.loc_destroy(h)
+    return out, walk
+
+
+def test_fp32_trajectory_with_scans_matches_oracle():
+    out, _ = run_lidar_trajectory("f32", 96, 16, 60, 10, seed=11)
+    for t, got, want in out:
+        err = np.abs(got - want).max()
+        assert err <= ABS_TOL and err <= 1e-4 * want.max(), (t, err)
+
+
+@pytest.mark.slow
+def test_bf16_crop_trajectory_with_scans_l1_and_argmax():
+    """The reduced-precision configuration on a 256 x 256 crop, 72 bins, a scan every 10 steps:
+    L1 <= 1e-2 against the FP64 oracle and the same argmax bin when it is unambiguous."""
+    out, walk = run_lidar_trajectory("bf16", 256, 72, 30, 10, seed=2)
+    for t, got, want in out:
+        l1 = np.abs(got - want).sum()
+        assert l1 <= 1e-2, (t, l1)
+        top2 = np.sort(want.reshape(-1))[-2:]
+        if top2[1] - top2[0] > 2e-2 * top2[1]:
+            assert np.unravel_index(np.argmax(got), got.shape) == np.unravel_index(np.argmax(want), want.shape)
