@@ -98,6 +98,9 @@ __global__ void __launch_bounds__(1024) fs_kernel(const float* __restrict__ m, c
                 __threadfence_block();
                 const int c = t + 1 + lane;
                 chunk = c < W ? ((volatile float*)bnd)[(size_t)rb * W + c] : 0.0f;
+                // lane 0 starts at column 0 at once: the row above at column 0 must already be
+                // in its register chain (other lanes shift theirs in while they wait to start)
+                if (t == 0 && lane == 0) up_new = ((volatile float*)bnd)[(size_t)rb * W];
             }
             const float from_above = __shfl_sync(0xffffffffu, chunk, t & 31);
             const float from_left = __shfl_up_sync(0xffffffffu, last, 1);
