@@ -171,6 +171,27 @@ def oracle_band_rate(wl, occ, odom, budget_s: float, steps: int | None = None):
     return rows * W * K / per_step, per_step, rows, n_steps, times
 
 
+# ----------------------------------------------------------------------------- ncu traffic
+
+def profiled_traffic(wl, args):
+    """DRAM bytes per launch of the propagation kernel from the committed ncu summary, only
+    while the kernel source is the one that was profiled (else None)."""
+    import hashlib
+    import re
+    if wl["name"] != "office512" or wl["storage"] != "f32" or args.tile not in (0, 6) or args.kernel not in (0, 2):
+        return None
+    try:
+        text = open(os.path.join(ROOT, "profiles", "step_ws_office512.md")).read()
+        src = open(os.path.join(ROOT, "paper_1910_00572_gb300", "csrc", "step_tiled.cu"), "rb").read()
+    except OSError:
+        return None
+    sha = re.search(r"source_sha256:\s*([0-9a-f]+)", text)
+    val = re.search(r"dram_bytes_per_launch:\s*([0-9]+)", text)
+    if not sha or not val or sha.group(1) != hashlib.sha256(src).hexdigest():
+        return None
+    return int(val.group(1))
+
+
 # ----------------------------------------------------------------------------- arms
 
 def run_reference(args, wl, occ, walk, ws, rank):
@@ -293,7 +314,7 @@ def run_ours(args, wl, occ, walk, ws, rank, local):
         "config": config_of(wl, args, extra={"tile": args.tile, "kernel": args.kernel}),
         "p50_step_ms": p50, "p99_step_ms": p99,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak, "traffic": profiled_traffic(wl, args),
                      "kernel": "step (fused propagation + normaliser)",
                      "algorithmic_bytes_per_launch": alg_bytes,
                      "peak_source": "MEASURED_PEAKS.json hbm_gbs" if "hbm_gbs" in peaks else "fallback"},
