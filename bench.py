@@ -182,7 +182,8 @@ def profiled_traffic(wl, args):
         return None
     try:
         text = open(os.path.join(ROOT, "profiles", "step_ws_office512.md")).read()
-        src = open(os.path.join(ROOT, "paper_1910_00572_gb300", "csrc", "step_tiled.cu"), "rb").read()
+        csrc = os.path.join(ROOT, "paper_1910_00572_gb300", "csrc")
+        src = b"".join(open(os.path.join(csrc, f), "rb").read() for f in ("tiled_common.cuh", "step_tiled.cu"))
     except OSError:
         return None
     sha = re.search(r"source_sha256:\s*([0-9a-f]+)", text)

@@ -1,0 +1,317 @@
+// Building blocks of the tiled propagation kernels (single session, warp-specialised and
+// batched): tile configurations, shared-memory layouts, TMA/mbarrier helpers, packed FP32
+// helpers and the S-, X- and P-passes.  Included by step_tiled.cu and batch.cu only.
+#pragma once
+#include <cuda.h>
+
+#include "kernels.h"
+
+namespace loc {
+namespace tiled {
+
+constexpr int R = 2, RT = 3;           // kernel radii this kernel is built for
+constexpr int TW = 64;                 // tile width (cells)
+constexpr int SW = 76;                 // S row pitch (68 used: tile cols -2 .. 65; 76 = 12 mod 32
+                                       // banks, so 8 consecutive rows hit 8 distinct bank groups)
+constexpr int MW = 76;                 // mask row pitch (floats, same bank spread as S)
+constexpr int XW_PITCH = 68;           // X row pitch (64 used; 68 = 4 mod 32 banks)
+constexpr int BW = 80;                 // raw box width in elements (76 needed + alignment)
+constexpr int RING = 2 * RT + 1;       // 7
+constexpr int NWRAP = 2 * RT;          // 6 planes kept for the circular wrap
+constexpr unsigned long long kWaitNs = 200ull * 1000 * 1000;   // bounded mbarrier wait
+
+// TH tile rows, MR rows per P-pass thread (2 columns each), SR S-pass rows per item, XW
+// X-pass columns per item, NSTAGE raw stages, MINB CTAs per SM asked of the compiler.
+template <int TH_, int MR_, int SR_, int XW_, int NSTAGE_, int MINB_>
+struct Cfg {
+    static constexpr int TH = TH_, MR = MR_, SR = SR_, XW = XW_, NSTAGE = NSTAGE_, MINB = MINB_;
+    static constexpr int NT = (TH / MR) * 32;
+    static constexpr int XR = TH + 2 * R;          // rows of S and X
+    static constexpr int RAW_H = XR + 1;           // raw rows (bilinear needs one more)
+    static_assert(XR % SR == 0, "S-pass row groups must tile the halo rows");
+    static_assert((72 / 4) * (XR / SR) <= NT, "one S-pass item per thread");
+    static_assert((TW / XW) * XR <= NT, "one X-pass item per thread");
+};
+
+struct FastArgs {
+    CUtensorMap tmap;                  // X_{t-1} as [K][H][W], box {BW, RAW_H, 1}
+    void* B_out;
+    const uint8_t* trav;
+    const float* corr;
+    SessionDev* sd;
+    double* partials;
+    float inv_uniform;
+    float out_mult;
+    double log_out_mult;
+    uint32_t seed;
+    int H, W, K;
+    float g0, g1, g2;                  // x/y taps: centre, +-1, +-2
+    float gt[RING];                    // theta taps -3 .. +3
+    Shift sh[LOC_MAX_K];
+};
+
+template <typename T> __host__ __device__ constexpr int align_elems() { return 16 / (int)sizeof(T); }
+
+template <typename T, typename C>
+constexpr int raw_stride() {          // elements per raw stage, padded to 128 bytes
+    return (int)(((C::RAW_H * BW * sizeof(T) + 127) / 128) * 128 / sizeof(T));
+}
+
+template <typename T, typename C>
+struct Smem {
+    T raw[C::NSTAGE][raw_stride<T, C>()];   // each stage [RAW_H][BW], 128-byte aligned
+    float S[C::XR][SW];
+    float X[C::XR][XW_PITCH];
+    float wrap[NWRAP][C::TH][TW];
+    float mk[C::XR][MW];                     // 1 free, 0 occupied / off-grid
+    unsigned long long bar[C::NSTAGE];
+    double red[C::NT / 32];
+};
+
+__device__ __forceinline__ uint32_t su32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ unsigned long long gtimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ void bar_init(unsigned long long* b, uint32_t n) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b)), "r"(n) : "memory");
+}
+__device__ __forceinline__ void bar_expect(unsigned long long* b, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool bar_try(unsigned long long* b, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred q;\n mbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, q;\n}\n"
+        : "=r"(ok) : "r"(su32(b)), "r"(parity) : "memory");
+    return ok != 0;
+}
+// Wait for phase `parity` of barrier b; gives up after kWaitNs (returns false).
+__device__ __forceinline__ bool bar_wait(unsigned long long* b, uint32_t parity) {
+    if (bar_try(b, parity)) return true;
+    const unsigned long long t0 = gtimer();
+    for (uint32_t it = 0; it < (1u << 26); ++it) {
+        if (bar_try(b, parity)) return true;
+        if (gtimer() - t0 > kWaitNs) return false;
+    }
+    return false;
+}
+__device__ __forceinline__ void tma_load(void* dst, const CUtensorMap* map,
+                                         unsigned long long* b, int x, int y, int z) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(su32(dst)), "l"((unsigned long long)map),
+        "r"(su32(b)), "r"(x), "r"(y), "r"(z)
+        : "memory");
+}
+
+// Packed pairs of FP32 (Blackwell's 2-wide FP32 pipe): lo = first element, hi = second.
+typedef unsigned long long f2;
+__device__ __forceinline__ f2 pk(float a, float b) {
+    f2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void upk(f2 v, float& a, float& b) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ f2 fadd2(f2 a, f2 b) {
+    f2 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2 fmul2(f2 a, f2 b) {
+    f2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2 ffma2(f2 a, f2 b, f2 c) {
+    f2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
+// Eight consecutive raw values starting at a 4-element boundary, as FP32.
+template <typename T> __device__ __forceinline__ void load8(const T* p, float (&v)[8]);
+template <> __device__ __forceinline__ void load8<float>(const float* p, float (&v)[8]) {
+    const float4 a = reinterpret_cast<const float4*>(p)[0], b = reinterpret_cast<const float4*>(p)[1];
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+}
+__device__ __forceinline__ float2 tof2(__nv_bfloat162 h) { return __bfloat1622float2(h); }
+__device__ __forceinline__ float2 tof2(__half2 h) { return __half22float2(h); }
+template <typename H2, typename T>
+__device__ __forceinline__ void load8_16(const T* p, float (&v)[8]) {
+    const uint2 a = reinterpret_cast<const uint2*>(p)[0], b = reinterpret_cast<const uint2*>(p)[1];
+    const uint32_t w[4] = {a.x, a.y, b.x, b.y};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const H2 h = *reinterpret_cast<const H2*>(&w[k]);
+        const float2 f = tof2(h);
+        v[2 * k] = f.x;
+        v[2 * k + 1] = f.y;
+    }
+}
+template <> __device__ __forceinline__ void load8<__nv_bfloat16>(const __nv_bfloat16* p, float (&v)[8]) {
+    load8_16<__nv_bfloat162>(p, v);
+}
+template <> __device__ __forceinline__ void load8<__half>(const __half* p, float (&v)[8]) {
+    load8_16<__half2>(p, v);
+}
+
+// Source x of the raw box for a plane: aligned down to 16 bytes; xo = in-box offset of the
+// first needed column.
+template <typename T>
+__device__ __forceinline__ void box_x(int tx0, const Shift& s, int& x_al, int& xo) {
+    const int x = tx0 - R + s.ox;
+    x_al = x & ~(align_elems<T>() - 1);
+    xo = x - x_al;
+}
+
+// S-pass: S[y][c] for y in [0, XR), c in [0, 72) (tile col c - 2); one item per thread: 4
+// columns x SR rows, the x-lerp of the shared raw row carried down.  XO is xo mod 4; the
+// runtime part xo - XO (0, or 4 for 16-bit types) moves the base address.
+template <typename T, typename C, int XO>
+__device__ __forceinline__ void s_pass(const T* raw, const float (*mk)[MW], float (*S)[SW], int t,
+                                       int xbase, float fx, float fy) {
+    constexpr int UNITS = 72 / 4;              // 18 items of 4 columns cover tile cols -2 .. 69
+    constexpr int ITEMS = UNITS * (C::XR / C::SR);
+    const int q = t;
+    if (q >= ITEMS) return;
+    const int u = q % UNITS, y0 = (q / UNITS) * C::SR;
+    const int c0 = 4 * u;
+    const float gy0 = 1.0f - fy;
+    float prev[4];
+#pragma unroll
+    for (int r = 0; r <= C::SR; ++r) {
+        float v[8];
+        load8<T>(&raw[(y0 + r) * BW + c0 + xbase], v);
+        float xl[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) xl[k] = fmaf(fx, v[XO + k + 1] - v[XO + k], v[XO + k]);
+        if (r > 0) {
+            const float4 m = *reinterpret_cast<const float4*>(&mk[y0 + r - 1][c0]);
+            const float mm[4] = {m.x, m.y, m.z, m.w};
+            float4 o;
+            float* op = &o.x;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) op[k] = mm[k] * fmaf(fy, xl[k], gy0 * prev[k]);
+            *reinterpret_cast<float4*>(&S[y0 + r - 1][c0]) = o;
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) prev[k] = xl[k];
+    }
+}
+
+// X-pass: X[y][c0..c0+XW) = x-blur of S, one item (XW columns of one row) per thread.
+template <typename C>
+__device__ __forceinline__ void x_pass(const float (*S)[SW], float (*X)[XW_PITCH], int t, float g0,
+                                       float g1, float g2) {
+    constexpr int UNITS = TW / C::XW;
+    const int q = t;
+    if (q >= UNITS * C::XR) return;
+    const int y = q % C::XR, u = q / C::XR;    // consecutive threads take consecutive rows
+    const int c0 = C::XW * u;
+    float s[C::XW + 4];
+#pragma unroll
+    for (int k = 0; k < C::XW + 4; k += 4) {
+        const float4 a = *reinterpret_cast<const float4*>(&S[y][c0 + k]);
+        s[k] = a.x; s[k + 1] = a.y; s[k + 2] = a.z; s[k + 3] = a.w;
+    }
+#pragma unroll
+    for (int k = 0; k < C::XW; k += 4) {
+        float4 o;
+        float* op = &o.x;
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            op[j] = fmaf(g2, s[k + j] + s[k + j + 4], fmaf(g1, s[k + j + 1] + s[k + j + 3], g0 * s[k + j + 2]));
+        *reinterpret_cast<float4*>(&X[y][c0 + k]) = o;
+    }
+}
+
+// Store two neighbouring outputs v = {a, b} (FP32 as is, BF16 stochastically rounded with the
+// 32 random bits h, FP16 round-to-nearest) and add the stored values to sum.
+template <typename T> __device__ __forceinline__ void store2(T* p, f2 v, uint32_t h, f2& sum);
+template <> __device__ __forceinline__ void store2<float>(float* p, f2 v, uint32_t, f2& sum) {
+    *reinterpret_cast<f2*>(p) = v;
+    sum = fadd2(sum, v);
+}
+template <> __device__ __forceinline__ void store2<__nv_bfloat16>(__nv_bfloat16* p, f2 v, uint32_t h, f2& sum) {
+    float a, b;
+    upk(v, a, b);
+    const uint32_t ua = __float_as_uint(a) + (h & 0xFFFFu);
+    const uint32_t ub = __float_as_uint(b) + (h >> 16);
+    *reinterpret_cast<uint32_t*>(p) = __byte_perm(ua, ub, 0x7632);   // high halves: {a, b}
+    // the stochastic rounding is unbiased: Z takes the unrounded values (within ~1e-7)
+    sum = fadd2(sum, v);
+}
+template <> __device__ __forceinline__ void store2<__half>(__half* p, f2 v, uint32_t, f2& sum) {
+    float a, b;
+    upk(v, a, b);
+    const __half2 hv = __floats2half2_rn(a, b);
+    *reinterpret_cast<__half2*>(p) = hv;
+    sum = fadd2(sum, pk(__low2float(hv), __high2float(hv)));
+}
+
+// Packed taps of the P-pass.
+struct Taps2 {
+    f2 g0, g1, g2;                     // y taps {g, g}
+    f2 gt[RING];                       // theta taps {g, g}
+};
+
+// P-pass for plane p with the newest ring slot PH = p mod 7.  The thread's cells are rows
+// r0 .. r0+MR-1 of the tile, columns 2cp and 2cp+1, handled as column pairs.
+template <typename T, typename C, int PH>
+__device__ __forceinline__ void p_pass(const float (*X)[XW_PITCH], float (*wrap)[C::TH][TW],
+                                       const FastArgs& a, const Taps2& tp,
+                                       f2 (&ring)[RING][C::MR], const f2 (&cs)[C::MR], int p,
+                                       int r0, int cp, int ty0, int gx, KahanF& acc) {
+    constexpr int MR = C::MR;
+    const int K = a.K;
+    if (p < K) {
+        f2 x[MR + 4];
+#pragma unroll
+        for (int q = 0; q < MR + 4; ++q) x[q] = *reinterpret_cast<const f2*>(&X[r0 + q][2 * cp]);
+#pragma unroll
+        for (int rr = 0; rr < MR; ++rr)
+            ring[PH][rr] = ffma2(tp.g2, fadd2(x[rr], x[rr + 4]),
+                                 ffma2(tp.g1, fadd2(x[rr + 1], x[rr + 3]), fmul2(tp.g0, x[rr + 2])));
+        if (p < NWRAP) {
+#pragma unroll
+            for (int rr = 0; rr < MR; ++rr) *reinterpret_cast<f2*>(&wrap[p][r0 + rr][2 * cp]) = ring[PH][rr];
+        }
+    } else {
+#pragma unroll
+        for (int rr = 0; rr < MR; ++rr) ring[PH][rr] = *reinterpret_cast<const f2*>(&wrap[p - K][r0 + rr][2 * cp]);
+    }
+    if (p >= 2 * RT) {
+        int o = p - RT;
+        if (o >= K) o -= K;
+        const size_t base = ((size_t)o * a.H + (ty0 + r0)) * a.W + gx;
+        T* out = static_cast<T*>(a.B_out) + base;
+        const uint32_t h = sizeof(T) == 2 ? pcg_hash((uint32_t)base ^ a.seed) : 0u;
+        const int rows = a.H - (ty0 + r0);             // rows of this thread inside the grid
+        const bool full = rows >= MR && gx < a.W;
+        f2 part = 0ull;
+#pragma unroll
+        for (int rr = 0; rr < MR; ++rr) {
+            f2 t = fmul2(tp.gt[0], ring[(PH + 1) % RING][rr]);
+#pragma unroll
+            for (int d = 1; d < RING; ++d) t = ffma2(tp.gt[d], ring[(PH + 1 + d) % RING][rr], t);
+            const f2 v = fmul2(cs[rr], t);
+            // 32 random bits per row: the thread's hash with a per-row odd constant mixed in
+            const uint32_t hr = h ^ (0x9E3779B9u * (uint32_t)(2 * rr + 1));
+            if (full || (rr < rows && gx < a.W)) store2<T>(out + (size_t)rr * a.W, v, hr, part);
+        }
+        float p0, p1;
+        upk(part, p0, p1);
+        acc.add(p0 + p1);
+    }
+}
+
+}  // namespace tiled
+}  // namespace loc
