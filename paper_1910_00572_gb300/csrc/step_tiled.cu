@@ -26,140 +26,48 @@ using namespace tiled;
 
 template <typename T, typename C>
 __global__ void __launch_bounds__(C::NT, C::MINB) step_tiled_kernel(const __grid_constant__ FastArgs a) {
-    constexpr int NT = C::NT, TH = C::TH, MR = C::MR, NSTAGE = C::NSTAGE, XR = C::XR;
+    constexpr int NT = C::NT, NSTAGE = C::NSTAGE;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     // the dynamic region is only guaranteed 16-byte aligned: round up to 128 bytes
     const uint32_t base = su32(smem_raw);
     Smem<T, C>& sm = *reinterpret_cast<Smem<T, C>*>(smem_raw + (((base + 127u) & ~127u) - base));
     const int tid = threadIdx.x;
-    const int H = a.H, W = a.W, K = a.K;
-    const int ty0 = blockIdx.y * TH, tx0 = blockIdx.x * TW;
-    const int reinit = a.sd->reinit;
-    // restart: the input is M / (K n_free); read M and fold 1 / (K n_free) into the scale
-    const float in_scale = (reinit ? a.inv_uniform : a.sd->inv_Z) * a.out_mult;
-    constexpr uint32_t kBoxBytes = C::RAW_H * BW * sizeof(T);
-
-    // map mask over the halo region: rows ty0-2 .., cols tx0-2 ..
-    for (int q = tid; q < XR * MW; q += NT) {
-        const int y = q / MW, c = q % MW;
-        const int gy = ty0 - R + y, gx = tx0 - R + c;
-        sm.mk[y][c] = (gy >= 0 && gy < H && gx >= 0 && gx < W && a.trav[(size_t)gy * W + gx]) ? 1.0f : 0.0f;
-    }
     if (tid == 0) {
         for (int s = 0; s < NSTAGE; ++s) bar_init(&sm.bar[s], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     __syncthreads();
-    auto issue = [&](int q) {       // TMA of plane q into stage q % NSTAGE (thread 0 only)
-        const Shift s = a.sh[q];
-        int x_al, xo;
-        box_x<T>(tx0, s, x_al, xo);
-        unsigned long long* b = &sm.bar[q % NSTAGE];
-        bar_expect(b, kBoxBytes);
-        tma_load(&sm.raw[q % NSTAGE][0], &a.tmap, b, x_al, ty0 - R + s.oy, q);
-    };
-    int next_issue = 0;             // planes [p, next_issue) have a copy in flight
-    if (!reinit) {
-        next_issue = NSTAGE < K ? NSTAGE : K;
-        if (tid == 0)
-            for (int q = 0; q < next_issue; ++q) issue(q);
-    }
-
-    // this thread's output cells in the P-pass: rows MR*rg .. +MR-1, cols 2cp, 2cp+1
-    const int cp = tid % 32, rg = tid / 32;
-    const int r0 = MR * rg, gxp = tx0 + 2 * cp;
-    f2 cs[MR];
-#pragma unroll
-    for (int rr = 0; rr < MR; ++rr) {
-        const int gy = ty0 + r0 + rr;
-        float c0 = 0.0f, c1 = 0.0f;
-        if (gy < H && gxp < W) {
-            c0 = a.corr[(size_t)gy * W + gxp] * in_scale;
-            c1 = a.corr[(size_t)gy * W + gxp + 1] * in_scale;
-        }
-        cs[rr] = pk(c0, c1);
-    }
-    Taps2 tp;
-    tp.g0 = pk(a.g0, a.g0);
-    tp.g1 = pk(a.g1, a.g1);
-    tp.g2 = pk(a.g2, a.g2);
-#pragma unroll
-    for (int d = 0; d < RING; ++d) tp.gt[d] = pk(a.gt[d], a.gt[d]);
-    f2 ring[RING][MR];
-#pragma unroll
-    for (int d = 0; d < RING; ++d)
-#pragma unroll
-        for (int k = 0; k < MR; ++k) ring[d][k] = 0ull;
+    TileJob j;
+    j.tmap = &a.tmap;
+    j.sh = a.sh;
+    j.o.B_out = a.B_out;
+    j.o.seed = a.seed;
+    j.o.H = a.H;
+    j.o.W = a.W;
+    j.o.K = a.K;
+    j.trav = a.trav;
+    j.corr = a.corr;
+    j.gt = a.gt;
+    j.reinit = a.sd->reinit;
+    // restart: the input is M / (K n_free); read M and fold 1 / (K n_free) into the scale
+    j.in_scale = (j.reinit ? a.inv_uniform : a.sd->inv_Z) * a.out_mult;
+    j.g0 = a.g0;
+    j.g1 = a.g1;
+    j.g2 = a.g2;
+    j.ty0 = blockIdx.y * C::TH;
+    j.tx0 = blockIdx.x * TW;
     KahanF acc;
-    int failed = 0;
-
-    int p = 0;
-    for (; p < K + NWRAP; ++p) {
-        if (p < K) {
-            const int stage = p % NSTAGE;
-            const Shift s = a.sh[p];
-            int x_al, xo;
-            box_x<T>(tx0, s, x_al, xo);
-            if (reinit) {
-                // the uniform input, written where TMA would have put the tile (M as 0/1)
-                const int y0 = ty0 - R + s.oy;
-                for (int q = tid; q < C::RAW_H * BW; q += NT) {
-                    const int y = q / BW, c = q % BW;
-                    const int gy = y0 + y, gx = x_al + c;
-                    float v = 0.0f;
-                    if (gy >= 0 && gy < H && gx >= 0 && gx < W) v = (float)a.trav[(size_t)gy * W + gx];
-                    sm.raw[stage][y * BW + c] = T(v);
-                }
-                __syncthreads();
-            } else if (!bar_wait(&sm.bar[stage], (uint32_t)((p / NSTAGE) & 1))) {
-                failed = 1;
-            }
-            if (!failed) {
-                const int xb = xo & ~3;
-                switch (xo & 3) {
-                    case 0: s_pass<T, C, 0>(sm.raw[stage], sm.mk, sm.S, tid, xb, s.fx, s.fy); break;
-                    case 1: s_pass<T, C, 1>(sm.raw[stage], sm.mk, sm.S, tid, xb, s.fx, s.fy); break;
-                    case 2: s_pass<T, C, 2>(sm.raw[stage], sm.mk, sm.S, tid, xb, s.fx, s.fy); break;
-                    default: s_pass<T, C, 3>(sm.raw[stage], sm.mk, sm.S, tid, xb, s.fx, s.fy); break;
-                }
-            }
-            if (__syncthreads_or(failed)) {
-                failed = 1;
-                break;
-            }
-            if (!reinit && p + NSTAGE < K) {
-                if (tid == 0) {
-                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                    issue(p + NSTAGE);
-                }
-                next_issue = p + NSTAGE + 1;
-            }
-            x_pass<C>(sm.S, sm.X, tid, a.g0, a.g1, a.g2);
-            __syncthreads();
-        }
-        switch (p % RING) {
-            case 0: p_pass<T, C, 0>(sm.X, sm.wrap, a, tp, ring, cs, p, r0, cp, ty0, gxp, acc); break;
-            case 1: p_pass<T, C, 1>(sm.X, sm.wrap, a, tp, ring, cs, p, r0, cp, ty0, gxp, acc); break;
-            case 2: p_pass<T, C, 2>(sm.X, sm.wrap, a, tp, ring, cs, p, r0, cp, ty0, gxp, acc); break;
-            case 3: p_pass<T, C, 3>(sm.X, sm.wrap, a, tp, ring, cs, p, r0, cp, ty0, gxp, acc); break;
-            case 4: p_pass<T, C, 4>(sm.X, sm.wrap, a, tp, ring, cs, p, r0, cp, ty0, gxp, acc); break;
-            case 5: p_pass<T, C, 5>(sm.X, sm.wrap, a, tp, ring, cs, p, r0, cp, ty0, gxp, acc); break;
-            default: p_pass<T, C, 6>(sm.X, sm.wrap, a, tp, ring, cs, p, r0, cp, ty0, gxp, acc); break;
-        }
-    }
-
-    if (failed) {
+    int p_stop = 0, next_issue = 0;
+    if (!run_tile<T, C>(sm, j, 0u, acc, p_stop, next_issue)) {
         // a TMA wait gave up: report it, let the copies still in flight land (bounded), and
         // leave without contributing a partial (the host sees the flag and fails the handle)
         if (tid == 0) {
             atomicOr(&a.sd->status, LOC_DEV_ERR_TIMEOUT);
-            for (int q = p; q < next_issue; ++q) bar_wait(&sm.bar[q % NSTAGE], (uint32_t)((q / NSTAGE) & 1));
+            for (int q = p_stop; q < next_issue; ++q) bar_wait(&sm.bar[q % NSTAGE], (uint32_t)((q / NSTAGE) & 1));
         }
         __syncthreads();
         return;
     }
-
     const double bt = block_sum<NT>(acc.value(), sm.red);
     SessionDev* sd = a.sd;
     const double log_mult = a.log_out_mult;
@@ -345,6 +253,12 @@ __global__ void __launch_bounds__(C::NT, C::MINB) step_ws_kernel(const __grid_co
         for (int d = 0; d < RING; ++d)
 #pragma unroll
             for (int k = 0; k < MR; ++k) ring[d][k] = 0ull;
+        TileOut o;
+        o.B_out = a.B_out;
+        o.seed = a.seed;
+        o.H = H;
+        o.W = W;
+        o.K = K;
         for (int p = 0; p < K + NWRAP; ++p) {
             const int b = p & 1;
             if (p < K && !bar_wait(&sm.full[b], (uint32_t)((p >> 1) & 1))) {
@@ -352,13 +266,13 @@ __global__ void __launch_bounds__(C::NT, C::MINB) step_ws_kernel(const __grid_co
                 break;
             }
             switch (p % RING) {
-                case 0: p_pass<T, C, 0>(sm.X[b], sm.wrap, a, tp, ring, cs, p, r0, cp, ty0, gxp, acc); break;
-                case 1: p_pass<T, C, 1>(sm.X[b], sm.wrap, a, tp, ring, cs, p, r0, cp, ty0, gxp, acc); break;
-                case 2: p_pass<T, C, 2>(sm.X[b], sm.wrap, a, tp, ring, cs, p, r0, cp, ty0, gxp, acc); break;
-                case 3: p_pass<T, C, 3>(sm.X[b], sm.wrap, a, tp, ring, cs, p, r0, cp, ty0, gxp, acc); break;
-                case 4: p_pass<T, C, 4>(sm.X[b], sm.wrap, a, tp, ring, cs, p, r0, cp, ty0, gxp, acc); break;
-                case 5: p_pass<T, C, 5>(sm.X[b], sm.wrap, a, tp, ring, cs, p, r0, cp, ty0, gxp, acc); break;
-                default: p_pass<T, C, 6>(sm.X[b], sm.wrap, a, tp, ring, cs, p, r0, cp, ty0, gxp, acc); break;
+                case 0: p_pass<T, C, 0>(sm.X[b], sm.wrap, o, tp, ring, cs, p, r0, cp, ty0, gxp, acc); break;
+                case 1: p_pass<T, C, 1>(sm.X[b], sm.wrap, o, tp, ring, cs, p, r0, cp, ty0, gxp, acc); break;
+                case 2: p_pass<T, C, 2>(sm.X[b], sm.wrap, o, tp, ring, cs, p, r0, cp, ty0, gxp, acc); break;
+                case 3: p_pass<T, C, 3>(sm.X[b], sm.wrap, o, tp, ring, cs, p, r0, cp, ty0, gxp, acc); break;
+                case 4: p_pass<T, C, 4>(sm.X[b], sm.wrap, o, tp, ring, cs, p, r0, cp, ty0, gxp, acc); break;
+                case 5: p_pass<T, C, 5>(sm.X[b], sm.wrap, o, tp, ring, cs, p, r0, cp, ty0, gxp, acc); break;
+                default: p_pass<T, C, 6>(sm.X[b], sm.wrap, o, tp, ring, cs, p, r0, cp, ty0, gxp, acc); break;
             }
             if (p + 2 < K) bar_arrive(&sm.empty[b]);  // a producer waits for this release
         }

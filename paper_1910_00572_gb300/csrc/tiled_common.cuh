@@ -257,6 +257,13 @@ template <> __device__ __forceinline__ void store2<__half>(__half* p, f2 v, uint
     sum = fadd2(sum, pk(__low2float(hv), __high2float(hv)));
 }
 
+// Where the P-pass writes: the output tensor, the rounding key and the grid.
+struct TileOut {
+    void* B_out;
+    uint32_t seed;
+    int H, W, K;
+};
+
 // Packed taps of the P-pass.
 struct Taps2 {
     f2 g0, g1, g2;                     // y taps {g, g}
@@ -267,7 +274,7 @@ struct Taps2 {
 // r0 .. r0+MR-1 of the tile, columns 2cp and 2cp+1, handled as column pairs.
 template <typename T, typename C, int PH>
 __device__ __forceinline__ void p_pass(const float (*X)[XW_PITCH], float (*wrap)[C::TH][TW],
-                                       const FastArgs& a, const Taps2& tp,
+                                       const TileOut& a, const Taps2& tp,
                                        f2 (&ring)[RING][C::MR], const f2 (&cs)[C::MR], int p,
                                        int r0, int cp, int ty0, int gx, KahanF& acc) {
     constexpr int MR = C::MR;
@@ -311,6 +318,144 @@ __device__ __forceinline__ void p_pass(const float (*X)[XW_PITCH], float (*wrap)
         upk(part, p0, p1);
         acc.add(p0 + p1);
     }
+}
+
+// One tile of the synchronous tiled kernel (every thread of the CTA takes part):
+// Alg. 1 lines 3-7 for all channels of a TH x 64 output tile, adding the stored values to acc.
+struct TileJob {
+    const CUtensorMap* tmap;          // X_{t-1} as [K][H][W]
+    const Shift* sh;                  // per-channel source offsets
+    TileOut o;
+    const uint8_t* trav;
+    const float* corr;
+    const float* gt;                  // theta taps (7)
+    float in_scale;                   // 1/Z (or the uniform value) times the storage multiplier
+    float g0, g1, g2;
+    int reinit;                       // read the input as M (uniform restart) instead of TMA
+    int ty0, tx0;
+};
+
+// gp0: planes this CTA has already loaded through the mbarriers (their phases continue).
+// Returns false when a bounded wait gave up; p_stop / next_issue then bound the copies that
+// may still be in flight.
+template <typename T, typename C>
+__device__ __forceinline__ bool run_tile(Smem<T, C>& sm, const TileJob& j, unsigned int gp0, KahanF& acc,
+                                         int& p_stop, int& next_issue) {
+    constexpr int NT = C::NT, MR = C::MR, NSTAGE = C::NSTAGE, XR = C::XR;
+    constexpr uint32_t kBoxBytes = C::RAW_H * BW * sizeof(T);
+    const int tid = threadIdx.x;
+    const int H = j.o.H, W = j.o.W, K = j.o.K;
+    const int ty0 = j.ty0, tx0 = j.tx0;
+    const int reinit = j.reinit;
+
+    // map mask over the halo region: rows ty0-2 .., cols tx0-2 ..
+    for (int q = tid; q < XR * MW; q += NT) {
+        const int y = q / MW, c = q % MW;
+        const int gy = ty0 - R + y, gx = tx0 - R + c;
+        sm.mk[y][c] = (gy >= 0 && gy < H && gx >= 0 && gx < W && j.trav[(size_t)gy * W + gx]) ? 1.0f : 0.0f;
+    }
+    __syncthreads();                // the S-passes read the whole mask
+    auto issue = [&](int q) {       // TMA of plane q (thread 0 only)
+        const Shift s = j.sh[q];
+        int x_al, xo;
+        box_x<T>(tx0, s, x_al, xo);
+        const unsigned int g = gp0 + (unsigned int)q;
+        unsigned long long* b = &sm.bar[g % NSTAGE];
+        bar_expect(b, kBoxBytes);
+        tma_load(&sm.raw[g % NSTAGE][0], j.tmap, b, x_al, ty0 - R + s.oy, q);
+    };
+    next_issue = 0;
+    if (!reinit) {
+        next_issue = NSTAGE < K ? NSTAGE : K;
+        if (tid == 0) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            for (int q = 0; q < next_issue; ++q) issue(q);
+        }
+    }
+    const int cp = tid % 32, rg = tid / 32;
+    const int r0 = MR * rg, gxp = tx0 + 2 * cp;
+    f2 cs[MR];
+#pragma unroll
+    for (int rr = 0; rr < MR; ++rr) {
+        const int gy = ty0 + r0 + rr;
+        float c0 = 0.0f, c1 = 0.0f;
+        if (gy < H && gxp < W) {
+            c0 = j.corr[(size_t)gy * W + gxp] * j.in_scale;
+            c1 = j.corr[(size_t)gy * W + gxp + 1] * j.in_scale;
+        }
+        cs[rr] = pk(c0, c1);
+    }
+    Taps2 tp;
+    tp.g0 = pk(j.g0, j.g0);
+    tp.g1 = pk(j.g1, j.g1);
+    tp.g2 = pk(j.g2, j.g2);
+#pragma unroll
+    for (int d = 0; d < RING; ++d) tp.gt[d] = pk(j.gt[d], j.gt[d]);
+    f2 ring[RING][MR];
+#pragma unroll
+    for (int d = 0; d < RING; ++d)
+#pragma unroll
+        for (int k = 0; k < MR; ++k) ring[d][k] = 0ull;
+    int failed = 0;
+    int p = 0;
+    for (; p < K + NWRAP; ++p) {
+        if (p < K) {
+            const unsigned int g = gp0 + (unsigned int)p;
+            const int stage = g % NSTAGE;
+            const Shift s = j.sh[p];
+            int x_al, xo;
+            box_x<T>(tx0, s, x_al, xo);
+            if (reinit) {
+                // the uniform input, written where TMA would have put the tile (M as 0/1)
+                const int y0 = ty0 - R + s.oy;
+                for (int q = tid; q < C::RAW_H * BW; q += NT) {
+                    const int y = q / BW, c = q % BW;
+                    const int gy = y0 + y, gx = x_al + c;
+                    float v = 0.0f;
+                    if (gy >= 0 && gy < H && gx >= 0 && gx < W) v = (float)j.trav[(size_t)gy * W + gx];
+                    sm.raw[stage][y * BW + c] = T(v);
+                }
+                __syncthreads();
+            } else if (!bar_wait(&sm.bar[stage], (g / NSTAGE) & 1u)) {
+                failed = 1;
+            }
+            if (!failed) {
+                const int xb = xo & ~3;
+                switch (xo & 3) {
+                    case 0: s_pass<T, C, 0>(sm.raw[stage], sm.mk, sm.S, tid, xb, s.fx, s.fy); break;
+                    case 1: s_pass<T, C, 1>(sm.raw[stage], sm.mk, sm.S, tid, xb, s.fx, s.fy); break;
+                    case 2: s_pass<T, C, 2>(sm.raw[stage], sm.mk, sm.S, tid, xb, s.fx, s.fy); break;
+                    default: s_pass<T, C, 3>(sm.raw[stage], sm.mk, sm.S, tid, xb, s.fx, s.fy); break;
+                }
+            }
+            if (__syncthreads_or(failed)) {
+                failed = 1;
+                break;
+            }
+            if (!reinit && p + NSTAGE < K) {
+                if (tid == 0) {
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    issue(p + NSTAGE);
+                }
+                next_issue = p + NSTAGE + 1;
+            }
+            x_pass<C>(sm.S, sm.X, tid, j.g0, j.g1, j.g2);
+            __syncthreads();
+        }
+        switch (p % RING) {
+            case 0: p_pass<T, C, 0>(sm.X, sm.wrap, j.o, tp, ring, cs, p, r0, cp, ty0, gxp, acc); break;
+            case 1: p_pass<T, C, 1>(sm.X, sm.wrap, j.o, tp, ring, cs, p, r0, cp, ty0, gxp, acc); break;
+            case 2: p_pass<T, C, 2>(sm.X, sm.wrap, j.o, tp, ring, cs, p, r0, cp, ty0, gxp, acc); break;
+            case 3: p_pass<T, C, 3>(sm.X, sm.wrap, j.o, tp, ring, cs, p, r0, cp, ty0, gxp, acc); break;
+            case 4: p_pass<T, C, 4>(sm.X, sm.wrap, j.o, tp, ring, cs, p, r0, cp, ty0, gxp, acc); break;
+            case 5: p_pass<T, C, 5>(sm.X, sm.wrap, j.o, tp, ring, cs, p, r0, cp, ty0, gxp, acc); break;
+            default: p_pass<T, C, 6>(sm.X, sm.wrap, j.o, tp, ring, cs, p, r0, cp, ty0, gxp, acc); break;
+        }
+    }
+    p_stop = p;
+    // the wrap planes and the X plane are read again by the next tile's first passes
+    __syncthreads();
+    return !failed;
 }
 
 }  // namespace tiled
