@@ -42,6 +42,7 @@ extern "C" {
 #endif
 
 typedef struct loc_session* loc_handle;
+typedef struct loc_batch_s* loc_batch;
 
 typedef enum {
     LOC_OK = 0,
@@ -198,6 +199,49 @@ loc_status loc_stats(loc_handle h, double* theta_t, double* last_Z, double* logs
 loc_status loc_propagate_noalloc(const loc_params* p, const uint8_t* occ_dev,
                                  const float* b_in_dev, float* b_out_dev, double* z_out_dev,
                                  double dx_m, double dy_m);
+
+/* ---- Batched propagation of many sessions (one persistent launch per tick).
+ * Alg. 1 lines 3-7 and the Eq. 9 normaliser for every session whose gate opens, over a work
+ * list of (session, tile) items that the launch's CTAs take from a device queue; the CTA that
+ * finishes a session's last tile sums that session's tile partials into Z in the same fixed
+ * order as loc_step's tiled kernel with the same tile configuration, so a session's result
+ * does not depend on the other sessions of the batch. */
+#define LOC_BATCH_CONFIGS 3    /* the synchronous tile configurations 1-3 of LOC_TILE_CONFIGS */
+
+/* Group n sessions (distinct handles on one device, one storage type, one stream, each able to
+ * use the tiled kernel: default radii, K >= 8, W a multiple of 4 (FP32) or 8 (16-bit)).  The
+ * batch does not own the sessions: destroy it before any of them.  tile: 0 = autotune (every
+ * configuration runs the whole batch in a dry run that leaves the sessions unchanged, the
+ * fastest is kept and remembered for this storage type and multiset of (H, W, K)), or
+ * 1 .. LOC_BATCH_CONFIGS.  use_graph != 0 captures the tick (host-to-device copy of the
+ * per-tick table, queue reset, kernel) in CUDA graphs, one launch per tick.  The batch runs on
+ * a stream of its own, ordered after and before the sessions' stream by events.
+ * Synchronous.  Errors: INVALID_ARG, STATE, OOM, CUDA. */
+loc_status loc_batch_create(const loc_handle* sessions, int n, int tile, int use_graph, loc_batch* out);
+
+/* One tick: u, v, w are host double[n], the odometry increments of the sessions in creation
+ * order (as loc_step takes them).  Each session's gate is evaluated as in loc_step; the
+ * sessions that pass are propagated together.  *n_moved (may be NULL) receives their number.
+ * Returns LOC_OK (work enqueued, asynchronous) or LOC_OK_DEFERRED (no session moved, nothing
+ * launched).  The host tables use two pinned buffers, so a call waits for the tick before the
+ * previous one.  Single-session calls on the same handles may be mixed in between ticks.
+ * Errors: INVALID_ARG (changes nothing), STATE, CUDA (fails the batch and its sessions). */
+loc_status loc_batch_step(loc_batch b, const double* u, const double* v, const double* w, int* n_moved);
+
+/* Wait for the batch's work; returns the first device-side error of the launches or of a
+ * session. */
+loc_status loc_batch_sync(loc_batch b);
+
+/* The tile configuration in use, the number of work items, the persistent grid (CTAs), and
+ * the autotuner's mean dry-run milliseconds per configuration (float[LOC_BATCH_CONFIGS], 0
+ * where not timed).  Any pointer may be NULL. */
+loc_status loc_batch_info(loc_batch b, int* tile, int* n_items, int* grid, float* tune_ms);
+
+/* Free the batch (waits for its work; the sessions stay).  b may be NULL. */
+loc_status loc_batch_destroy(loc_batch b);
+
+/* Description of the batch's last failure ("" if none; b may be NULL). */
+const char* loc_batch_last_error(loc_batch b);
 
 /* Wait for all enqueued work of the handle; returns the first device-side error if any. */
 loc_status loc_sync(loc_handle h);

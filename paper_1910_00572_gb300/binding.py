@@ -21,6 +21,8 @@ __all__ = [
     "loc_lidar_update_cells", "loc_belief", "loc_marginal", "loc_argmax", "loc_set_belief",
     "loc_stats", "loc_sync", "loc_destroy", "loc_last_error", "torch_stream",
     "use_torch_allocator", "loc_propagate_noalloc", "loc_samples", "loc_dither", "loc_ray_ranges",
+    "LOC_BATCH_CONFIGS", "Batch", "loc_batch_create", "loc_batch_step", "loc_batch_sync",
+    "loc_batch_info", "loc_batch_destroy", "loc_batch_last_error",
 ]
 
 LOC_OK, LOC_OK_DEFERRED = 0, 1
@@ -28,6 +30,7 @@ LOC_ERR_INVALID_ARG, LOC_ERR_OOM, LOC_ERR_CUDA, LOC_ERR_TIMEOUT, LOC_ERR_STATE =
 LOC_F32, LOC_BF16, LOC_F16 = 0, 1, 2
 LOC_MAP_SUM, LOC_MAP_MAX = 0, 1
 LOC_KERNEL_AUTO, LOC_KERNEL_GENERIC, LOC_KERNEL_TILED = 0, 1, 2
+LOC_BATCH_CONFIGS = 3
 _STORAGE = {"f32": LOC_F32, "bf16": LOC_BF16, "f16": LOC_F16}
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -85,6 +88,13 @@ _SIGS = {
     "loc_samples": (ctypes.c_int, [_P, _P, ctypes.c_size_t, ctypes.POINTER(ctypes.c_int)]),
     "loc_dither": (ctypes.c_int, [_P, _P, ctypes.c_float, _P, ctypes.POINTER(ctypes.c_int)]),
     "loc_ray_ranges": (ctypes.c_int, [_P, _P, ctypes.c_int, _P, ctypes.c_int, ctypes.c_double, _P]),
+    "loc_batch_create": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(_P)]),
+    "loc_batch_step": (ctypes.c_int, [_P, _P, _P, _P, ctypes.POINTER(ctypes.c_int)]),
+    "loc_batch_sync": (ctypes.c_int, [_P]),
+    "loc_batch_info": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                      ctypes.POINTER(ctypes.c_int), _P]),
+    "loc_batch_destroy": (ctypes.c_int, [_P]),
+    "loc_batch_last_error": (ctypes.c_char_p, [_P]),
 }
 
 
@@ -118,6 +128,9 @@ class Handle:
 
 def _check(h, status: int) -> int:
     if status < 0:
+        if isinstance(h, Batch) and h.ptr:
+            msg = lib().loc_batch_last_error(h)
+            raise LocError(status, msg.decode() if msg else "")
         ptr = h.ptr if isinstance(h, Handle) else None
         msg = lib().loc_last_error(ptr)
         raise LocError(status, msg.decode() if msg else "")
@@ -282,3 +295,53 @@ def loc_propagate_noalloc(params: loc_params, occ_dev: int, b_in_dev: int, b_out
     _check(None, lib().loc_propagate_noalloc(ctypes.byref(params), ctypes.c_void_p(occ_dev),
                                              ctypes.c_void_p(b_in_dev), ctypes.c_void_p(b_out_dev),
                                              ctypes.c_void_p(z_out_dev), float(dx_m), float(dy_m)))
+
+
+class Batch:
+    """A batch of sessions stepped by one persistent launch per tick."""
+
+    def __init__(self, ptr: int, handles):
+        self.ptr, self.handles = ptr, list(handles)
+
+    @property
+    def _as_parameter_(self):
+        return ctypes.c_void_p(self.ptr)
+
+
+def loc_batch_create(handles, tile: int = 0, use_graph: bool = True) -> Batch:
+    arr = (ctypes.c_void_p * len(handles))(*[h.ptr for h in handles])
+    out = ctypes.c_void_p()
+    _check(None, lib().loc_batch_create(ctypes.cast(arr, ctypes.c_void_p), len(handles), int(tile),
+                                        int(bool(use_graph)), ctypes.byref(out)))
+    return Batch(out.value, handles)
+
+
+def loc_batch_step(b: Batch, u, v, w) -> int:
+    """One tick; u, v, w hold one odometry increment per session.  Returns the number moved."""
+    n = len(b.handles)
+    arrs = [np.ascontiguousarray(np.broadcast_to(np.asarray(x, np.float64), (n,))) for x in (u, v, w)]
+    moved = ctypes.c_int()
+    _check(b, lib().loc_batch_step(b, _ptr(arrs[0]), _ptr(arrs[1]), _ptr(arrs[2]), ctypes.byref(moved)))
+    return moved.value
+
+
+def loc_batch_sync(b: Batch) -> None:
+    _check(b, lib().loc_batch_sync(b))
+
+
+def loc_batch_info(b: Batch) -> dict:
+    tile, items, grid = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    ms = np.zeros(LOC_BATCH_CONFIGS, np.float32)
+    _check(b, lib().loc_batch_info(b, ctypes.byref(tile), ctypes.byref(items), ctypes.byref(grid), _ptr(ms)))
+    return dict(tile=tile.value, n_items=items.value, grid=grid.value, tune_ms=ms.tolist())
+
+
+def loc_batch_destroy(b: Batch) -> None:
+    if b is not None and b.ptr:
+        lib().loc_batch_destroy(b)
+        b.ptr = None
+
+
+def loc_batch_last_error(b: Batch | None) -> str:
+    m = lib().loc_batch_last_error(b.ptr if b is not None else None)
+    return m.decode() if m else ""

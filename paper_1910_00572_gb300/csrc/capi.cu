@@ -9,7 +9,7 @@
 #include <unordered_map>
 #include <vector>
 
-#include "kernels.h"
+#include "session.h"
 
 #define LOC_API extern "C" __attribute__((visibility("default")))
 
@@ -26,58 +26,7 @@ void* g_alloc_ctx = nullptr;
 
 void loc::set_thread_error(const char* msg) { g_thread_err = msg ? msg : ""; }
 
-struct loc_session {
-    loc_params p{};
-    int r_xy = 0, r_th = 0;
-    float gx[2 * LOC_MAX_R_XY + 1]{};
-    float gt[2 * LOC_MAX_R_THETA + 1]{};
-    cudaStream_t stream = nullptr;
-    int device = 0;
-    size_t elem = 4;               // bytes per stored belief value
-    size_t hw = 0, n = 0;          // H*W, K*H*W
-    long long n_free = 0;
-    float inv_uniform = 0.0f;
-    // device buffers
-    void* B[2] = {nullptr, nullptr};
-    int cur = 0;                   // B[cur] holds the current stored tensor
-    uint8_t* trav = nullptr;
-    float* corr = nullptr;
-    SessionDev* sd = nullptr;
-    double* partials = nullptr;
-    unsigned int nparts = 0;
-    void* argmax_scratch = nullptr;
-    long long* argmax_idx = nullptr;
-    float* argmax_val = nullptr;
-    // LIDAR sample update scratch (allocated on first use)
-    bool lidar_ready = false;
-    int cap = 0;                   // capacity of the sample list
-    float* m = nullptr;            // belief map [H][W]
-    uint8_t* sel = nullptr;        // selection mask [H][W]
-    int* rowcnt = nullptr;         // per-row selections [H]
-    int* rowoff = nullptr;         // exclusive prefix [H]
-    float* bnd = nullptr;          // row-block boundary rows for the dithering wavefront
-    int* prog = nullptr;           // their progress counters
-    int32_t* samples = nullptr;    // sampled cells [cap]
-    float* logL = nullptr;         // log-likelihood [cap][K]
-    int* dscal = nullptr;          // device scalars: count, maxL (as uint), fs (as float)
-    void* rs = nullptr;            // reweight scalars
-    float* dirs = nullptr;         // distinct beam directions (cos, sin) [cap_dirs][2]
-    int32_t* dir_of = nullptr;     // direction of (bin, used beam) [K][cap_beams]
-    float* z = nullptr;            // used ranges [cap_beams]
-    int cap_dirs = 0, cap_beams = 0, cap_dir_of = 0;
-    long long n_lidar = 0;
-    bool tiled = false;            // use the TMA-tiled kernel
-    int tile_cfg = 0;              // its tile configuration
-    unsigned char tmap[2][128] __attribute__((aligned(128)));   // tensor maps of B[0], B[1]
-    // host-side state (FP64)
-    double theta = 0.0, px = 0.0, py = 0.0;
-    long long n_prop = 0;
-    bool failed = false;
-    std::string err;
-    std::vector<void*> owned;
-};
-
-namespace {
+namespace loc {
 
 loc_status fail(loc_session* s, loc_status code, const std::string& msg) {
     if (s) {
@@ -151,7 +100,7 @@ loc_status sync_and_check(loc_session* h) {
     return LOC_OK;
 }
 
-}  // namespace
+}  // namespace loc
 
 LOC_API void loc_params_default(loc_params* p) {
     if (!p) return;
@@ -273,18 +222,61 @@ LOC_API loc_status loc_create(const uint8_t* occ, const loc_params* p, loc_handl
     return LOC_OK;
 }
 
+namespace loc {
+
+// Section III-A / Eq. 2: accumulate the odometry increment (translate in the frame of
+// theta_{t-1}, then rotate).  Returns whether the gate lets a propagation through.
+bool odometry_advance(loc_session* h, double u, double v, double w) {
+    const double c = std::cos(h->theta), s = std::sin(h->theta);
+    h->px += c * u - s * v;
+    h->py += s * u + c * v;
+    h->theta += w;
+    return std::hypot(h->px, h->py) / h->p.cell_m >= h->p.min_shift_cells;
+}
+
+// Eq. 2-3: the per-bin source offsets of the accumulated translation.
+void shift_table(const loc_session* h, Shift* sh) {
+    const double cell = h->p.cell_m;
+    const int K = h->p.K;
+    for (int k = 0; k < K; ++k) {
+        const double ang = 2.0 * M_PI * k / K;
+        const double ck = std::cos(ang), sk = std::sin(ang);
+        const double sx = (ck * h->px - sk * h->py) / cell;   // R(k dTheta) p, in cells
+        const double sy = (sk * h->px + ck * h->py) / cell;
+        // pull source: integer part and fraction of -s.  A fraction within 1e-9 of a whole
+        // cell (e.g. 3 cos(pi/2) = 1.8e-16) is snapped, which changes the result by under
+        // 1e-9 relative and keeps integer shifts exact permutations.
+        double ox = std::floor(-sx), oy = std::floor(-sy);
+        double fx = -sx - ox, fy = -sy - oy;
+        if (fx < 1e-9) fx = 0.0;
+        if (fx > 1.0 - 1e-9) { fx = 0.0; ox += 1.0; }
+        if (fy < 1e-9) fy = 0.0;
+        if (fy > 1.0 - 1e-9) { fy = 0.0; oy += 1.0; }
+        sh[k].ox = (int)ox;
+        sh[k].oy = (int)oy;
+        sh[k].fx = (float)fx;
+        sh[k].fy = (float)fy;
+    }
+}
+
+// Key of the stochastic rounding of propagation number n_prop.
+uint32_t step_seed(const loc_session* h) { return pcg_hash((uint32_t)h->n_prop * 0x9E3779B9u + 0x632BE5ABu); }
+
+// After a propagation was enqueued: the output buffer becomes current.
+void step_done(loc_session* h) {
+    h->cur = 1 - h->cur;
+    h->px = h->py = 0.0;
+    h->n_prop += 1;
+}
+
+}  // namespace loc
+
 LOC_API loc_status loc_step(loc_handle h, double u, double v, double w) {
     loc_status st = check_live(h);
     if (st != LOC_OK) return st;
     if (!std::isfinite(u) || !std::isfinite(v) || !std::isfinite(w))
         return fail(h, LOC_ERR_INVALID_ARG, "odometry must be finite");
-    // Section III-A / Eq. 2: translate in the frame of theta_{t-1}, then rotate.
-    const double c = std::cos(h->theta), s = std::sin(h->theta);
-    h->px += c * u - s * v;
-    h->py += s * u + c * v;
-    h->theta += w;
-    const double cell = h->p.cell_m;
-    if (std::hypot(h->px, h->py) / cell < h->p.min_shift_cells) return LOC_OK_DEFERRED;
+    if (!odometry_advance(h, u, v, w)) return LOC_OK_DEFERRED;
 
     StepArgs a{};
     a.B_in = h->B[h->cur];
@@ -296,7 +288,7 @@ LOC_API loc_status loc_step(loc_handle h, double u, double v, double w) {
     a.inv_uniform = h->inv_uniform;
     a.out_mult = storage_mult(h->p.storage);
     a.log_out_mult = std::log((double)a.out_mult);
-    a.seed = pcg_hash((uint32_t)h->n_prop * 0x9E3779B9u + 0x632BE5ABu);
+    a.seed = step_seed(h);
     a.H = h->p.H;
     a.W = h->p.W;
     a.K = h->p.K;
@@ -304,32 +296,11 @@ LOC_API loc_status loc_step(loc_handle h, double u, double v, double w) {
     a.r_th = h->r_th;
     std::memcpy(a.gx, h->gx, sizeof(a.gx));
     std::memcpy(a.gt, h->gt, sizeof(a.gt));
-    const int K = h->p.K;
-    for (int k = 0; k < K; ++k) {
-        const double ang = 2.0 * M_PI * k / K;
-        const double ck = std::cos(ang), sk = std::sin(ang);
-        const double sx = (ck * h->px - sk * h->py) / cell;   // Eq. 2: R(k dTheta) p, in cells
-        const double sy = (sk * h->px + ck * h->py) / cell;
-        // Eq. 3 pull source: integer part and fraction of -s.  A fraction within 1e-9 of a
-        // whole cell (e.g. 3 cos(pi/2) = 1.8e-16) is snapped, which changes the result by
-        // under 1e-9 relative and keeps integer shifts exact permutations.
-        double ox = std::floor(-sx), oy = std::floor(-sy);
-        double fx = -sx - ox, fy = -sy - oy;
-        if (fx < 1e-9) fx = 0.0;
-        if (fx > 1.0 - 1e-9) { fx = 0.0; ox += 1.0; }
-        if (fy < 1e-9) fy = 0.0;
-        if (fy > 1.0 - 1e-9) { fy = 0.0; oy += 1.0; }
-        a.sh[k].ox = (int)ox;
-        a.sh[k].oy = (int)oy;
-        a.sh[k].fx = (float)fx;
-        a.sh[k].fy = (float)fy;
-    }
+    shift_table(h, a.sh);
     cudaError_t e = h->tiled ? launch_step_tiled(a, h->tmap[h->cur], h->p.storage, h->tile_cfg, h->stream)
                              : launch_step(a, h->p.storage, h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "step launch");
-    h->cur = 1 - h->cur;
-    h->px = h->py = 0.0;
-    h->n_prop += 1;
+    step_done(h);
     return LOC_OK;
 }
 

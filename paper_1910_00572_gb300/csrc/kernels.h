@@ -25,6 +25,46 @@ size_t step_tmap_bytes();
 cudaError_t make_step_tmap(void* tmap_out, const void* B, int storage, int H, int W, int K, int cfg);
 cudaError_t launch_step_tiled(const StepArgs& a, const void* tmap, int storage, int cfg, cudaStream_t st);
 
+// ---- Batched propagation (batch.cu): one persistent launch over (session, tile) items of
+// many sessions.  Batch configurations 1 .. batch_num_cfgs() are the synchronous tiled
+// configurations of the same number (same tile rows, same tensor maps).
+struct alignas(128) BatchStatic {           // per session, uploaded once
+    unsigned char tmap[2][128];             // tensor maps of B[0], B[1] (CUtensorMap)
+    void* B[2];
+    const uint8_t* trav;
+    const float* corr;
+    SessionDev* sd;
+    double* partials;                       // >= ntiles doubles
+    float inv_uniform, out_mult;
+    double log_out_mult;
+    int H, W, K, ntx, ntiles, sh_off;       // sh_off: first entry of the session in the shift table
+    float g0, g1, g2;
+    float gt[7];
+};
+struct BatchTick {                          // per session, uploaded every tick
+    int cur;                                // input buffer
+    int active;                             // propagate this tick
+    uint32_t seed;                          // stochastic-rounding key
+    int pad;
+};
+struct BatchItem {
+    int s, tile;                            // session, tile (row-major over the session's tile grid)
+};
+struct BatchCtl {
+    int head;                               // work-queue head (zeroed before every launch)
+    int n_items;
+    int status;                             // LOC_DEV_ERR_* of the launch
+    int pad;
+};
+int batch_num_cfgs();
+int batch_tile_rows(int cfg);
+// Sets the kernel's shared-memory limit and returns the persistent grid (CTAs per SM x SMs).
+cudaError_t batch_prepare(int storage, int cfg, int* grid);
+// tick: n_sessions BatchTick headers followed (16-byte aligned, at shifts_off bytes) by the
+// shift table.  dry != 0 runs every tile but leaves partials, Z and the counters untouched.
+cudaError_t launch_batch(int storage, int cfg, int grid, const BatchStatic* ss, const void* tick,
+                         size_t shifts_off, const BatchItem* items, BatchCtl* ctl, int dry, cudaStream_t st);
+
 // corr[j][i] = trav ? 1 / G(M)(j, i) : 0 with G(M) the x/y blur of M by gx (Eq. 8).
 cudaError_t launch_edge_correction(const uint8_t* trav, float* corr, int H, int W,
                                    const float* gx, int r, cudaStream_t st);

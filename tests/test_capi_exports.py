@@ -55,3 +55,15 @@ def test_invalid_arguments_fail_without_gpu_work(libloc):
     p = loc.loc_params_default(H=4, W=4, K=4, cell_m=0.1, sigma_xy_cells=5.0)
     with pytest.raises(loc.LocError):
         loc.loc_create(np.zeros((4, 4), np.uint8), p)          # radius 15 > LOC_MAX_R_XY
+
+
+def test_batch_arguments_fail_without_gpu_work(libloc):
+    import paper_1910_00572_gb300 as loc
+    with pytest.raises(loc.LocError) as e:
+        loc.loc_batch_create([])
+    assert e.value.status == loc.LOC_ERR_INVALID_ARG
+    assert "no sessions" in loc.loc_last_error()
+    with pytest.raises(loc.LocError) as e:
+        loc.loc_batch_step(loc.Batch(0, []), [], [], [])
+    assert e.value.status == loc.LOC_ERR_INVALID_ARG
+    assert loc.loc_batch_destroy(None) is None
