@@ -331,18 +331,273 @@ def run_ours(args, wl, occ, walk, ws, rank, local):
     print(json.dumps(line), flush=True)
 
 
+# ----------------------------------------------------------------------------- many sessions
+
+def session_params(loc, s, storage, **kw):
+    return loc.loc_params_default(H=s["H"], W=s["W"], K=s["K"], cell_m=s["cell"], storage=storage, **kw)
+
+
+def read_peak():
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        return peaks["hbm_gbs"], "MEASURED_PEAKS.json hbm_gbs"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def run_batch64(args, wl, ws, rank, local):
+    """64 sessions of uneven size: one persistent batched launch per tick (autotuned tiles, CUDA
+    graph) against the plain path (one loc_step launch per session), FP32 and BF16."""
+    import torch
+
+    import paper_1910_00572_gb300 as loc
+    from paper_1910_00572_gb300 import build
+    build.build()
+    torch.cuda.set_device(local)
+    steps = min(args.steps, 300)
+    sess = workloads.make_sessions(wl, steps + args.warmup)
+    cells = sum(s["H"] * s["W"] * s["K"] for s in sess)
+    hw = sum(s["H"] * s["W"] for s in sess)
+    odo = np.stack([s["odom"] for s in sess], axis=1)          # [t][session][3]
+    res = {}
+    clk_summary = None
+    for storage in ("f32", "bf16"):
+        hs = [loc.loc_create(s["occ"], session_params(loc, s, storage)) for s in sess]
+        try:
+            b = loc.loc_batch_create(hs, tile=0, use_graph=True)
+            info = loc.loc_batch_info(b)
+            try:
+                def batch_tick(t):
+                    loc.loc_batch_step(b, odo[t, :, 0], odo[t, :, 1], odo[t, :, 2])
+
+                def singles_tick(t):
+                    for q, h in enumerate(hs):
+                        loc.loc_step(h, *odo[t, q])
+
+                out = {}
+                for name, tick in (("batched", batch_tick), ("singles", singles_tick)):
+                    for t in range(args.warmup):
+                        tick(t)
+                    torch.cuda.synchronize()
+                    barrier(ws)
+                    ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+                    with ClockSampler(None) as clk:
+                        ev[0].record()
+                        for t in range(steps):
+                            tick(args.warmup + t)
+                            ev[t + 1].record()
+                        torch.cuda.synchronize()
+                    ms = [ev[t].elapsed_time(ev[t + 1]) for t in range(steps)]
+                    total = max_over_ranks(ev[0].elapsed_time(ev[steps]) / 1e3, ws)
+                    out[name] = {"ms_per_tick": total / steps * 1e3, "value": cells * ws * steps / total,
+                                 "p50_tick_ms": float(np.percentile(ms, 50)),
+                                 "p99_tick_ms": float(np.percentile(ms, 99))}
+                    if storage == "bf16" and name == "batched":
+                        clk_summary = clk.summary()
+                loc.loc_batch_sync(b)
+                # end to end: odometry from host arrays in, every session's pose estimate out
+                n_e2e = 0 if args.no_e2e else min(steps, 50)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                for t in range(n_e2e):
+                    batch_tick(t)
+                    for h in hs:
+                        loc.loc_argmax(h)
+                e2e_t = max_over_ranks(time.perf_counter() - t0, ws)
+                out["e2e"] = cells * ws * n_e2e / e2e_t if n_e2e else None
+                out["tile"] = info["tile"]
+                out["tune_ms"] = info["tune_ms"]
+                out["grid"] = info["grid"]
+            finally:
+                loc.loc_batch_destroy(b)
+        finally:
+            for h in hs:
+                loc.loc_destroy(h)
+        res[storage] = out
+    if rank != 0:
+        return
+    peak, src = read_peak()
+    bf = res["bf16"]
+    alg_bytes = cells * 2 * 2 + hw * 5
+    achieved = alg_bytes / (bf["batched"]["ms_per_tick"] / 1e3) / 1e9
+    line = {
+        "metric": METRIC, "value": bf["batched"]["value"], "unit": UNIT, "n_gpus": ws, "steps": steps,
+        "warmup": args.warmup, "ms_per_step": bf["batched"]["ms_per_tick"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+        "config": {"workload": "batch64", "sessions": len(sess), "cells_per_tick": cells,
+                   "sides": sorted({s["H"] for s in sess}), "K": sorted({s["K"] for s in sess}),
+                   "global_batch": len(sess), "parallelism": f"replicas{ws}" if ws > 1 else "single",
+                   "l2": "inputs larger than L2 (every tick reads and writes all sessions' tensors)"},
+        "p50_step_ms": bf["batched"]["p50_tick_ms"], "p99_step_ms": bf["batched"]["p99_tick_ms"],
+        "batched_vs_singles": res,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": None, "kernel": "batch (persistent propagation over all sessions)",
+                     "algorithmic_bytes_per_launch": alg_bytes, "peak_source": src},
+        "cpu_baseline": None,
+        "e2e": {"value": bf["e2e"], "unit": UNIT, "h2d_bytes_per_step": 24 * len(sess),
+                "d2h_bytes_per_step": 12 * len(sess),
+                "path": "loc_batch_step (host odometry arrays) + loc_argmax of every session, host wall clock"},
+        "gpu_launches": steps,
+        "clocks": clk_summary,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def serve_schedule(wl, sess, duration, rng):
+    """Message times: odometry at odom_hz per session with exponential jitter (Poisson
+    arrivals), a scan with every (odom_hz / scan_hz)-th odometry message of even sessions."""
+    per = int(round(wl["odom_hz"] / wl["scan_hz"]))
+    odo_t, odo_s, odo_i = [], [], []
+    scans = []
+    for q, s in enumerate(sess):
+        n = len(s["odom"])
+        t = np.cumsum(rng.exponential(1.0 / wl["odom_hz"], n))
+        k = int(np.searchsorted(t, duration))
+        odo_t.append(t[:k])
+        odo_s.append(np.full(k, q))
+        odo_i.append(np.arange(k))
+        if q % 2 == 0:
+            for i in range(per - 1, k, per):
+                scans.append((float(t[i]) + 1e-6, q, i))
+    odo_t, odo_s, odo_i = (np.concatenate(x) for x in (odo_t, odo_s, odo_i))
+    order = np.argsort(odo_t, kind="stable")
+    scans.sort()
+    return odo_t[order], odo_s[order], odo_i[order], scans
+
+
+def run_serve256(args, wl, ws, rank, local):
+    """256 sessions on 10 maps served by the library's serving loop.  Three runs on the same
+    message streams: BF16 with continuous batching at real-time arrival, the same saturated
+    (every message submitted at once: capacity), and the plain FP32 per-session path at
+    real-time arrival under the same memory budget."""
+    import torch
+
+    import paper_1910_00572_gb300 as loc
+    from paper_1910_00572_gb300 import build
+    from synth import scan as synth_scan
+    build.build()
+    torch.cuda.set_device(local)
+    duration = float(os.environ.get("SERVE_SECONDS", "6"))
+    steps = int(duration * wl["odom_hz"] * 1.5) + 50
+    sess = workloads.make_sessions(wl, steps)
+    rng = np.random.Generator(np.random.PCG64(wl["seed"] + 991))
+    odo_t, odo_s, odo_i, scans = serve_schedule(wl, sess, duration, rng)
+    # a pool of four scans per scanning session along its walk (coarse ray march)
+    pool = {}
+    for q, s in enumerate(sess):
+        if q % 2 == 0:
+            idx = np.linspace(0, min(len(s["poses"]) - 1, int(duration * wl["odom_hz"])), 4).astype(int)
+            pool[q] = [synth_scan.simulate_scan(s["occ"], s["cell"], s["poses"][i], seed=q * 7 + j,
+                                                n_beams=wl["n_beams"], angle_inc=wl["angle_inc"],
+                                                r_max=wl["r_max"], noise_sigma=wl["scan_noise"],
+                                                dropout=wl["dropout"], march=0.25)
+                       for j, i in enumerate(idx)]
+    odom = [s["odom"] for s in sess]
+
+    def one(storage, batching, realtime):
+        srv = loc.loc_server_create(loc.loc_server_params_default(
+            hbm_budget_bytes=wl["hbm_budget_gb"] * 1e9, storage=storage, batching=batching, tile=0))
+        try:
+            ids = [loc.loc_server_open(srv, s["occ"], session_params(loc, s, storage,
+                                                                      min_shift_cells=wl["min_shift_cells"],
+                                                                      n_samples=wl["n_samples"]))
+                   for s in sess]
+            loc.loc_server_drain(srv, 600.0)                 # admissions (and the autotuner) first
+            st0 = loc.loc_server_stats(srv)
+            loc.loc_server_reset_stats(srv)
+            ids_a = np.asarray(ids, np.int32)
+            u = np.array([odom[q][i][0] for q, i in zip(odo_s, odo_i)])
+            v = np.array([odom[q][i][1] for q, i in zip(odo_s, odo_i)])
+            w = np.array([odom[q][i][2] for q, i in zip(odo_s, odo_i)])
+            t0 = loc.loc_server_now(srv) + 0.05
+            j = 0
+            sc = 0
+            n = len(odo_t)
+            per_session = max(1, int(duration * wl["odom_hz"]))
+
+            def odometry_upto(k):
+                nonlocal j
+                if k > j:
+                    loc.loc_server_odometry(srv, ids_a[odo_s[j:k]], u[j:k], v[j:k], w[j:k],
+                                            t0 + odo_t[j:k] if realtime else None)
+                    j = k
+
+            with ClockSampler(None) as clk:
+                while j < n or sc < len(scans):
+                    now = loc.loc_server_now(srv) - t0 if realtime else float("inf")
+                    # each scan goes right after the odometry message it rides on
+                    while sc < len(scans) and scans[sc][0] <= now:
+                        ts, q, i = scans[sc]
+                        odometry_upto(int(np.searchsorted(odo_t, ts, side="right")))
+                        loc.loc_server_scan(srv, ids[q], pool[q][min(3, 4 * i // per_session)], 0.0,
+                                            wl["angle_inc"], wl["r_max"], wl["beam_stride"], wl["sigma_r"],
+                                            t0 + ts if realtime else -1.0)
+                        sc += 1
+                    odometry_upto(int(np.searchsorted(odo_t, now, side="right")) if realtime else n)
+                    if realtime and (j < n or sc < len(scans)):
+                        time.sleep(0.0005)
+                loc.loc_server_drain(srv, 600.0)
+            st = loc.loc_server_stats(srv)
+            span = max(st["last_s"] - st["first_s"], 1e-9)
+            return {"storage": storage, "batching": batching, "realtime": realtime,
+                    "admitted": st0["n_active"], "pending": st0["n_pending"],
+                    "bytes_used_gb": st0["bytes_used"] / 1e9,
+                    "value": st["cell_updates"] / span, "span_s": span,
+                    "propagations": st["n_propagations"], "scans": st["n_scans"], "messages": st["n_messages"],
+                    "mean_batch": st["mean_batch"], "step_p50_ms": st["step_p50_ms"],
+                    "step_p99_ms": st["step_p99_ms"], "step_max_ms": st["step_max_ms"],
+                    "scan_p50_ms": st["scan_p50_ms"], "scan_p99_ms": st["scan_p99_ms"],
+                    "clocks": clk.summary()}
+        finally:
+            loc.loc_server_destroy(srv)
+
+    served = one("bf16", 1, True)
+    capacity = one("bf16", 1, False)
+    plain = one("f32", 0, True)
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": capacity["value"], "unit": UNIT, "n_gpus": ws, "steps": int(served["propagations"]),
+        "warmup": 0, "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16", "data": "synthetic",
+        "config": {"workload": "serve256", "sessions": len(sess), "maps": wl["n_maps"],
+                   "seconds_of_messages": duration, "odom_hz": wl["odom_hz"], "scan_hz": wl["scan_hz"],
+                   "hbm_budget_gb": wl["hbm_budget_gb"], "min_shift_cells": wl["min_shift_cells"],
+                   "cells_all_sessions": sum(s["H"] * s["W"] * s["K"] for s in sess),
+                   "parallelism": "single", "l2": "inputs larger than L2"},
+        "p50_step_ms": served["step_p50_ms"], "p99_step_ms": served["step_p99_ms"],
+        "served_bf16_realtime": served, "served_bf16_saturated": capacity, "plain_f32_realtime": plain,
+        "roofline": None, "cpu_baseline": None,
+        "e2e": {"value": served["value"], "unit": UNIT, "h2d_bytes_per_step": None, "d2h_bytes_per_step": None,
+                "path": "loc_server_odometry / loc_server_scan from host arrays at the messages' arrival times"},
+        "gpu_launches": None,
+        "clocks": served["clocks"],
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     ws, rank, local = dist_init(args.gpus)
     wl = workloads.get(args.workload)
     if args.storage:
         wl["storage"] = args.storage
-    occ = workloads.make_map(wl)
-    walk = workloads.make_walk(wl, occ, seed_offset=rank)
-    if args.impl == "reference":
-        run_reference(args, wl, occ, walk, ws, rank)
+    if args.workload in ("batch64", "serve256"):
+        if args.impl == "reference":
+            if rank == 0:
+                print(json.dumps({"impl": "reference", "unavailable":
+                                  "the oracle arm is timed on the single-session workloads"}), flush=True)
+        elif args.workload == "batch64":
+            run_batch64(args, wl, ws, rank, local)
+        else:
+            run_serve256(args, wl, ws, rank, local)
     else:
-        run_ours(args, wl, occ, walk, ws, rank, local)
+        occ = workloads.make_map(wl)
+        walk = workloads.make_walk(wl, occ, seed_offset=rank)
+        if args.impl == "reference":
+            run_reference(args, wl, occ, walk, ws, rank)
+        else:
+            run_ours(args, wl, occ, walk, ws, rank, local)
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()

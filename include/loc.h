@@ -43,6 +43,7 @@ extern "C" {
 
 typedef struct loc_session* loc_handle;
 typedef struct loc_batch_s* loc_batch;
+typedef struct loc_server_s* loc_server;
 
 typedef enum {
     LOC_OK = 0,
@@ -242,6 +243,92 @@ loc_status loc_batch_destroy(loc_batch b);
 
 /* Description of the batch's last failure ("" if none; b may be NULL). */
 const char* loc_batch_last_error(loc_batch b);
+
+/* Device bytes a session created with p holds once it has run a LIDAR update (the belief
+ * tensors, map, correction, reduction and sampling scratch, each allocation rounded up to
+ * 512 bytes).  Used for admission against a memory budget.  No device work. */
+loc_status loc_session_bytes(const loc_params* p, size_t* bytes);
+
+/* ---- Serving loop: many robot sessions stepped as their messages arrive (continuous batching).
+ * Sessions are opened against a device-memory budget (loc_session_bytes each) and admitted
+ * first come, first served as memory frees up.  Odometry and scan messages may be submitted
+ * from any thread; each session's messages are applied in submission order.  A worker thread
+ * forms a tick from whatever sessions have work: a session's odometry messages run through its
+ * Alg. 1 gate one by one until one opens it (that propagation joins the tick's batched launch)
+ * or a scan message comes next (the scan runs in that tick if the session was not propagated,
+ * on a stream of its own, overlapping the batched launch).  So the propagation points and every
+ * result depend only on the session's own message stream, never on the load: a session gives
+ * the same belief served alone or in any mix (with the same tile configuration).  A completion
+ * thread timestamps finished work for the latency statistics. */
+#define LOC_SESSION_PENDING 0      /* waiting for admission */
+#define LOC_SESSION_ACTIVE 1
+#define LOC_SESSION_CLOSED 2
+#define LOC_SESSION_FAILED 3
+
+typedef struct {
+    double hbm_budget_bytes;       /* device bytes all admitted sessions may hold together */
+    int storage;                   /* belief storage of every session (LOC_F32/BF16/F16) */
+    int batching;                  /* 1: one persistent batched launch per tick (default);
+                                      0: one loc_step per odometry message (the plain path) */
+    int tile;                      /* batch tile configuration; 0 = autotune on the first batch
+                                      and keep it */
+    int use_graph;                 /* capture each tick in a CUDA graph (default 1) */
+    int n_streams;                 /* streams for scan updates and plain steps (default 16) */
+} loc_server_params;
+
+typedef struct {
+    int n_active, n_pending, n_closed, n_failed;    /* sessions by state */
+    double bytes_used, bytes_budget;
+    long long n_ticks;             /* worker iterations that launched work */
+    long long n_messages;          /* messages fully processed */
+    long long n_propagations, n_scans;
+    double cell_updates;           /* sum of K * H * W over the propagations */
+    double mean_batch;             /* propagations per batched launch */
+    double step_p50_ms, step_p99_ms, step_max_ms;   /* odometry message arrival (the one that
+                                      opened the gate) to the end of its propagation */
+    double scan_p50_ms, scan_p99_ms, scan_max_ms;   /* scan arrival to the end of its update */
+    double first_s, last_s;        /* server clock of the first arrival and last completion */
+} loc_server_stats_t;
+
+void loc_server_params_default(loc_server_params* p);
+/* Start a server (its worker and completion threads) on the current device.  Errors:
+ * INVALID_ARG, CUDA. */
+loc_status loc_server_create(const loc_server_params* p, loc_server* out);
+/* Open a session: the map and parameters as loc_create takes them (storage and stream are the
+ * server's).  *id receives its id; it starts LOC_SESSION_PENDING and is admitted when its
+ * loc_session_bytes fit in the budget next to the admitted sessions and every earlier pending
+ * session is admitted.  Messages may be submitted at once; they run after admission.
+ * INVALID_ARG when the parameters are invalid, the map has no free cell, the session can never
+ * fit the budget, or a batched server gets a session the tiled kernel cannot take. */
+loc_status loc_server_open(loc_server s, const uint8_t* occ, const loc_params* p, int* id);
+/* Close a session after its queued messages: its memory returns to the budget. */
+loc_status loc_server_close(loc_server s, int id);
+/* n odometry messages: session ids[i] moved by (u[i], v[i], w[i]) as loc_step takes them, at
+ * t_arrival[i] seconds of loc_server_now (NULL: now).  Non-finite values or unknown/closed ids
+ * fail the whole call (INVALID_ARG) before any message is queued. */
+loc_status loc_server_odometry(loc_server s, int n, const int* ids, const double* u, const double* v,
+                               const double* w, const double* t_arrival);
+/* A scan message for session id (arguments as loc_lidar_update; the ranges are copied);
+ * t_arrival < 0 means now. */
+loc_status loc_server_scan(loc_server s, int id, const float* ranges, int n_beams, double angle_min,
+                           double angle_inc, double r_max, int beam_stride, double sigma_r, double t_arrival);
+/* Seconds since the server started (steady clock). */
+double loc_server_now(loc_server s);
+/* Wait until every pending session that fits the budget is admitted, every submitted message
+ * of the admitted sessions is processed and its device work has finished (sessions that must
+ * wait for memory are not waited for).  TIMEOUT after timeout_s seconds. */
+loc_status loc_server_drain(loc_server s, double timeout_s);
+loc_status loc_server_stats(loc_server s, loc_server_stats_t* out);
+/* Clear the counters and latency samples (not the sessions). */
+loc_status loc_server_reset_stats(loc_server s);
+/* State of session id and its handle (NULL unless active).  Readbacks through the handle are
+ * valid only while no message of that session is queued or running, e.g. after
+ * loc_server_drain. */
+loc_status loc_server_session(loc_server s, int id, int* state, loc_handle* h);
+/* Stop the threads (messages still queued are dropped), wait for the device work in flight
+ * and free every session.  s may be NULL. */
+loc_status loc_server_destroy(loc_server s);
+const char* loc_server_last_error(loc_server s);
 
 /* Wait for all enqueued work of the handle; returns the first device-side error if any. */
 loc_status loc_sync(loc_handle h);

@@ -22,7 +22,12 @@ __all__ = [
     "loc_stats", "loc_sync", "loc_destroy", "loc_last_error", "torch_stream",
     "use_torch_allocator", "loc_propagate_noalloc", "loc_samples", "loc_dither", "loc_ray_ranges",
     "LOC_BATCH_CONFIGS", "Batch", "loc_batch_create", "loc_batch_step", "loc_batch_sync",
-    "loc_batch_info", "loc_batch_destroy", "loc_batch_last_error",
+    "loc_batch_info", "loc_batch_destroy", "loc_batch_last_error", "loc_session_bytes",
+    "LOC_SESSION_PENDING", "LOC_SESSION_ACTIVE", "LOC_SESSION_CLOSED", "LOC_SESSION_FAILED",
+    "loc_server_params", "loc_server_stats_t", "Server", "loc_server_params_default",
+    "loc_server_create", "loc_server_open", "loc_server_close", "loc_server_odometry",
+    "loc_server_scan", "loc_server_now", "loc_server_drain", "loc_server_stats",
+    "loc_server_reset_stats", "loc_server_session", "loc_server_destroy", "loc_server_last_error",
 ]
 
 LOC_OK, LOC_OK_DEFERRED = 0, 1
@@ -31,6 +36,7 @@ LOC_F32, LOC_BF16, LOC_F16 = 0, 1, 2
 LOC_MAP_SUM, LOC_MAP_MAX = 0, 1
 LOC_KERNEL_AUTO, LOC_KERNEL_GENERIC, LOC_KERNEL_TILED = 0, 1, 2
 LOC_BATCH_CONFIGS = 3
+LOC_SESSION_PENDING, LOC_SESSION_ACTIVE, LOC_SESSION_CLOSED, LOC_SESSION_FAILED = 0, 1, 2, 3
 _STORAGE = {"f32": LOC_F32, "bf16": LOC_BF16, "f16": LOC_F16}
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -54,6 +60,25 @@ class loc_params(ctypes.Structure):
                 ("storage", ctypes.c_int), ("n_samples", ctypes.c_int),
                 ("stream", ctypes.c_void_p), ("kernel", ctypes.c_int),
                 ("tile", ctypes.c_int)]
+
+
+class loc_server_params(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_double), ("storage", ctypes.c_int),
+                ("batching", ctypes.c_int), ("tile", ctypes.c_int), ("use_graph", ctypes.c_int),
+                ("n_streams", ctypes.c_int)]
+
+
+class loc_server_stats_t(ctypes.Structure):
+    _fields_ = [("n_active", ctypes.c_int), ("n_pending", ctypes.c_int), ("n_closed", ctypes.c_int),
+                ("n_failed", ctypes.c_int), ("bytes_used", ctypes.c_double),
+                ("bytes_budget", ctypes.c_double), ("n_ticks", ctypes.c_longlong),
+                ("n_messages", ctypes.c_longlong), ("n_propagations", ctypes.c_longlong),
+                ("n_scans", ctypes.c_longlong), ("cell_updates", ctypes.c_double),
+                ("mean_batch", ctypes.c_double), ("step_p50_ms", ctypes.c_double),
+                ("step_p99_ms", ctypes.c_double), ("step_max_ms", ctypes.c_double),
+                ("scan_p50_ms", ctypes.c_double), ("scan_p99_ms", ctypes.c_double),
+                ("scan_max_ms", ctypes.c_double), ("first_s", ctypes.c_double),
+                ("last_s", ctypes.c_double)]
 
 
 _lib = None
@@ -95,6 +120,21 @@ _SIGS = {
                                       ctypes.POINTER(ctypes.c_int), _P]),
     "loc_batch_destroy": (ctypes.c_int, [_P]),
     "loc_batch_last_error": (ctypes.c_char_p, [_P]),
+    "loc_session_bytes": (ctypes.c_int, [ctypes.POINTER(loc_params), ctypes.POINTER(ctypes.c_size_t)]),
+    "loc_server_params_default": (None, [ctypes.POINTER(loc_server_params)]),
+    "loc_server_create": (ctypes.c_int, [ctypes.POINTER(loc_server_params), ctypes.POINTER(_P)]),
+    "loc_server_open": (ctypes.c_int, [_P, _P, ctypes.POINTER(loc_params), ctypes.POINTER(ctypes.c_int)]),
+    "loc_server_close": (ctypes.c_int, [_P, ctypes.c_int]),
+    "loc_server_odometry": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P, _P, _P]),
+    "loc_server_scan": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                       ctypes.c_double, ctypes.c_int, ctypes.c_double, ctypes.c_double]),
+    "loc_server_now": (ctypes.c_double, [_P]),
+    "loc_server_drain": (ctypes.c_int, [_P, ctypes.c_double]),
+    "loc_server_stats": (ctypes.c_int, [_P, ctypes.POINTER(loc_server_stats_t)]),
+    "loc_server_reset_stats": (ctypes.c_int, [_P]),
+    "loc_server_session": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(_P)]),
+    "loc_server_destroy": (ctypes.c_int, [_P]),
+    "loc_server_last_error": (ctypes.c_char_p, [_P]),
 }
 
 
@@ -128,6 +168,9 @@ class Handle:
 
 def _check(h, status: int) -> int:
     if status < 0:
+        if isinstance(h, Server) and h.ptr:
+            msg = lib().loc_last_error(None)
+            raise LocError(status, msg.decode() if msg else "")
         if isinstance(h, Batch) and h.ptr:
             msg = lib().loc_batch_last_error(h)
             raise LocError(status, msg.decode() if msg else "")
@@ -344,4 +387,107 @@ def loc_batch_destroy(b: Batch) -> None:
 
 def loc_batch_last_error(b: Batch | None) -> str:
     m = lib().loc_batch_last_error(b.ptr if b is not None else None)
+    return m.decode() if m else ""
+
+
+def loc_session_bytes(params: loc_params) -> int:
+    out = ctypes.c_size_t()
+    _check(None, lib().loc_session_bytes(ctypes.byref(params), ctypes.byref(out)))
+    return out.value
+
+
+class Server:
+    """A serving loop (its worker and completion threads run inside the library)."""
+
+    def __init__(self, ptr: int):
+        self.ptr = ptr
+        self.shapes = {}
+
+    @property
+    def _as_parameter_(self):
+        return ctypes.c_void_p(self.ptr)
+
+
+def loc_server_params_default(**kw) -> loc_server_params:
+    p = loc_server_params()
+    lib().loc_server_params_default(ctypes.byref(p))
+    for k, v in kw.items():
+        if k == "storage" and isinstance(v, str):
+            v = _STORAGE[v]
+        setattr(p, k, v)
+    return p
+
+
+def loc_server_create(params: loc_server_params) -> Server:
+    out = ctypes.c_void_p()
+    _check(None, lib().loc_server_create(ctypes.byref(params), ctypes.byref(out)))
+    return Server(out.value)
+
+
+def loc_server_open(s: Server, occ: np.ndarray, params: loc_params) -> int:
+    occ = np.ascontiguousarray(occ, dtype=np.uint8)
+    if occ.shape != (params.H, params.W):
+        raise ValueError(f"map shape {occ.shape} != ({params.H}, {params.W})")
+    sid = ctypes.c_int()
+    _check(s, lib().loc_server_open(s, _ptr(occ), ctypes.byref(params), ctypes.byref(sid)))
+    s.shapes[sid.value] = (params.K, params.H, params.W)
+    return sid.value
+
+
+def loc_server_close(s: Server, sid: int) -> None:
+    _check(s, lib().loc_server_close(s, int(sid)))
+
+
+def loc_server_odometry(s: Server, ids, u, v, w, t_arrival=None) -> None:
+    ids = np.ascontiguousarray(np.atleast_1d(ids), np.int32)
+    n = ids.size
+    arrs = [np.ascontiguousarray(np.broadcast_to(np.asarray(x, np.float64), (n,))) for x in (u, v, w)]
+    t = None if t_arrival is None else np.ascontiguousarray(np.broadcast_to(np.asarray(t_arrival, np.float64), (n,)))
+    _check(s, lib().loc_server_odometry(s, n, _ptr(ids), _ptr(arrs[0]), _ptr(arrs[1]), _ptr(arrs[2]),
+                                        None if t is None else _ptr(t)))
+
+
+def loc_server_scan(s: Server, sid: int, ranges: np.ndarray, angle_min: float, angle_inc: float, r_max: float,
+                    beam_stride: int, sigma_r: float, t_arrival: float = -1.0) -> None:
+    r = np.ascontiguousarray(ranges, np.float32)
+    _check(s, lib().loc_server_scan(s, int(sid), _ptr(r), r.size, float(angle_min), float(angle_inc),
+                                    float(r_max), int(beam_stride), float(sigma_r), float(t_arrival)))
+
+
+def loc_server_now(s: Server) -> float:
+    return lib().loc_server_now(s)
+
+
+def loc_server_drain(s: Server, timeout_s: float = 60.0) -> None:
+    _check(s, lib().loc_server_drain(s, float(timeout_s)))
+
+
+def loc_server_stats(s: Server) -> dict:
+    st = loc_server_stats_t()
+    _check(s, lib().loc_server_stats(s, ctypes.byref(st)))
+    return {name: getattr(st, name) for name, _ in st._fields_}
+
+
+def loc_server_reset_stats(s: Server) -> None:
+    _check(s, lib().loc_server_reset_stats(s))
+
+
+def loc_server_session(s: Server, sid: int):
+    """(state, Handle or None); readbacks through the handle only after loc_server_drain."""
+    state, h = ctypes.c_int(), ctypes.c_void_p()
+    _check(s, lib().loc_server_session(s, int(sid), ctypes.byref(state), ctypes.byref(h)))
+    if not h.value:
+        return state.value, None
+    K, H, W = s.shapes[sid]
+    return state.value, Handle(h.value, H, W, K)
+
+
+def loc_server_destroy(s: Server) -> None:
+    if s is not None and s.ptr:
+        lib().loc_server_destroy(s)
+        s.ptr = None
+
+
+def loc_server_last_error(s: Server | None) -> str:
+    m = lib().loc_server_last_error(s.ptr if s is not None else None)
     return m.decode() if m else ""

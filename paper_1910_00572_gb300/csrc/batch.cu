@@ -16,32 +16,42 @@ using namespace tiled;
 
 template <typename T, typename C>
 __global__ void __launch_bounds__(C::NT, C::MINB)
-batch_kernel(const BatchStatic* __restrict__ ss, const BatchTick* __restrict__ tk, const Shift* __restrict__ shifts,
-             const BatchItem* __restrict__ items, BatchCtl* ctl, int dry) {
+batch_kernel(const BatchStatic* __restrict__ ss, const BatchTick* __restrict__ tk, const BatchList* __restrict__ list,
+             const BatchActive* __restrict__ act, const Shift* __restrict__ shifts, BatchCtl* ctl, int dry) {
     constexpr int NT = C::NT, NSTAGE = C::NSTAGE;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const uint32_t base = su32(smem_raw);
     Smem<T, C>& sm = *reinterpret_cast<Smem<T, C>*>(smem_raw + (((base + 127u) & ~127u) - base));
-    __shared__ int s_item, s_last;
+    __shared__ int s_sess, s_tile, s_last;
     const int tid = threadIdx.x;
     if (tid == 0) {
         for (int s = 0; s < NSTAGE; ++s) bar_init(&sm.bar[s], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    const int n_items = ctl->n_items;
+    const int total = list->total, n_active = list->n_active;
     unsigned int gp = 0;                   // planes this CTA has loaded through the mbarriers
     for (;;) {
-        if (tid == 0) s_item = atomicAdd(&ctl->head, 1);
-        __syncthreads();
-        const int it = s_item;
-        if (it >= n_items) break;
-        const BatchItem item = items[it];
-        const BatchTick t = tk[item.s];
-        if (!t.active) {
-            __syncthreads();               // s_item is rewritten by the next iteration
-            continue;
+        if (tid == 0) {
+            const int q = atomicAdd(&ctl->head, 1);
+            int sess = -1, tile = 0;
+            if (q < total) {
+                int lo = 0, hi = n_active - 1;           // last entry with start <= q
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (act[mid].start <= q) lo = mid;
+                    else hi = mid - 1;
+                }
+                sess = act[lo].s;
+                tile = q - act[lo].start;
+            }
+            s_sess = sess;
+            s_tile = tile;
         }
-        const BatchStatic& S = ss[item.s];
+        __syncthreads();
+        const int sess = s_sess, tile = s_tile;
+        if (sess < 0) break;
+        const BatchTick t = tk[sess];
+        const BatchStatic& S = ss[sess];
         const CUtensorMap* tmap = reinterpret_cast<const CUtensorMap*>(S.tmap[t.cur]);
         TileJob j;
         j.tmap = tmap;
@@ -61,8 +71,8 @@ batch_kernel(const BatchStatic* __restrict__ ss, const BatchTick* __restrict__ t
         j.g0 = S.g0;
         j.g1 = S.g1;
         j.g2 = S.g2;
-        j.ty0 = (item.tile / S.ntx) * C::TH;
-        j.tx0 = (item.tile % S.ntx) * TW;
+        j.ty0 = (tile / S.ntx) * C::TH;
+        j.tx0 = (tile % S.ntx) * TW;
         if (tid == 0)   // the tensor map lives in global memory, written by a copy before the launch
             asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(tmap) : "memory");
         KahanF acc;
@@ -85,7 +95,7 @@ batch_kernel(const BatchStatic* __restrict__ ss, const BatchTick* __restrict__ t
         const double bt = block_sum<NT>(acc.value(), sm.red);
         if (dry) continue;                 // block_sum ended with a barrier
         if (tid == 0) {
-            S.partials[item.tile] = bt;
+            S.partials[tile] = bt;
             __threadfence();
             s_last = atomicAdd(&S.sd->counter, 1u) == (unsigned int)(S.ntiles - 1);
         }
@@ -114,7 +124,7 @@ batch_kernel(const BatchStatic* __restrict__ ss, const BatchTick* __restrict__ t
                 }
             }
         }
-        __syncthreads();                   // s_last and s_item are rewritten next iteration
+        __syncthreads();                   // s_last, s_sess and s_tile are rewritten next iteration
     }
 }
 
@@ -138,12 +148,14 @@ cudaError_t prepare_typed(int* grid) {
 }
 
 template <typename T, typename C>
-cudaError_t launch_typed(int grid, const BatchStatic* ss, const void* tick, size_t shifts_off,
-                         const BatchItem* items, BatchCtl* ctl, int dry, cudaStream_t st) {
+cudaError_t launch_typed(int grid, const BatchStatic* ss, const void* tick, const BatchLayout& lay, BatchCtl* ctl,
+                         int dry, cudaStream_t st) {
     const size_t sb = sizeof(Smem<T, C>) + 128;
-    const BatchTick* tk = static_cast<const BatchTick*>(tick);
-    const Shift* sh = reinterpret_cast<const Shift*>(static_cast<const unsigned char*>(tick) + shifts_off);
-    batch_kernel<T, C><<<grid, C::NT, sb, st>>>(ss, tk, sh, items, ctl, dry);
+    const unsigned char* b = static_cast<const unsigned char*>(tick);
+    batch_kernel<T, C><<<grid, C::NT, sb, st>>>(ss, reinterpret_cast<const BatchTick*>(b),
+                                                 reinterpret_cast<const BatchList*>(b + lay.list_off),
+                                                 reinterpret_cast<const BatchActive*>(b + lay.act_off),
+                                                 reinterpret_cast<const Shift*>(b + lay.shifts_off), ctl, dry);
     return cudaGetLastError();
 }
 
@@ -158,15 +170,17 @@ cudaError_t prepare_cfg(int cfg, int* grid) {
 }
 
 template <typename T>
-cudaError_t launch_cfg(int cfg, int grid, const BatchStatic* ss, const void* tick, size_t shifts_off,
-                       const BatchItem* items, BatchCtl* ctl, int dry, cudaStream_t st) {
+cudaError_t launch_cfg(int cfg, int grid, const BatchStatic* ss, const void* tick, const BatchLayout& lay,
+                       BatchCtl* ctl, int dry, cudaStream_t st) {
     switch (cfg) {
-        case 1: return launch_typed<T, BCfg1>(grid, ss, tick, shifts_off, items, ctl, dry, st);
-        case 2: return launch_typed<T, BCfg2>(grid, ss, tick, shifts_off, items, ctl, dry, st);
-        case 3: return launch_typed<T, BCfg3>(grid, ss, tick, shifts_off, items, ctl, dry, st);
+        case 1: return launch_typed<T, BCfg1>(grid, ss, tick, lay, ctl, dry, st);
+        case 2: return launch_typed<T, BCfg2>(grid, ss, tick, lay, ctl, dry, st);
+        case 3: return launch_typed<T, BCfg3>(grid, ss, tick, lay, ctl, dry, st);
         default: return cudaErrorInvalidValue;
     }
 }
+
+size_t up16(size_t x) { return (x + 15) & ~(size_t)15; }
 
 }  // namespace
 
@@ -183,13 +197,22 @@ cudaError_t batch_prepare(int storage, int cfg, int* grid) {
     }
 }
 
-cudaError_t launch_batch(int storage, int cfg, int grid, const BatchStatic* ss, const void* tick, size_t shifts_off,
-                         const BatchItem* items, BatchCtl* ctl, int dry, cudaStream_t st) {
-    if (grid <= 0 || (shifts_off & 15)) return cudaErrorInvalidValue;
+BatchLayout batch_tick_layout(int n_sessions, int sum_k) {
+    BatchLayout l;
+    l.list_off = up16(sizeof(BatchTick) * (size_t)n_sessions);
+    l.act_off = up16(l.list_off + sizeof(BatchList));
+    l.shifts_off = up16(l.act_off + sizeof(BatchActive) * (size_t)n_sessions);
+    l.bytes = l.shifts_off + sizeof(Shift) * (size_t)sum_k;
+    return l;
+}
+
+cudaError_t launch_batch(int storage, int cfg, int grid, const BatchStatic* ss, const void* tick,
+                         const BatchLayout& lay, BatchCtl* ctl, int dry, cudaStream_t st) {
+    if (grid <= 0) return cudaErrorInvalidValue;
     switch (storage) {
-        case LOC_F32: return launch_cfg<float>(cfg, grid, ss, tick, shifts_off, items, ctl, dry, st);
-        case LOC_BF16: return launch_cfg<__nv_bfloat16>(cfg, grid, ss, tick, shifts_off, items, ctl, dry, st);
-        case LOC_F16: return launch_cfg<__half>(cfg, grid, ss, tick, shifts_off, items, ctl, dry, st);
+        case LOC_F32: return launch_cfg<float>(cfg, grid, ss, tick, lay, ctl, dry, st);
+        case LOC_BF16: return launch_cfg<__nv_bfloat16>(cfg, grid, ss, tick, lay, ctl, dry, st);
+        case LOC_F16: return launch_cfg<__half>(cfg, grid, ss, tick, lay, ctl, dry, st);
         default: return cudaErrorInvalidValue;
     }
 }

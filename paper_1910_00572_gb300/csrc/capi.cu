@@ -123,6 +123,31 @@ LOC_API void loc_set_allocator(loc_alloc_fn alloc, loc_free_fn release, void* ct
     g_alloc_ctx = (alloc && release) ? ctx : nullptr;
 }
 
+LOC_API loc_status loc_session_bytes(const loc_params* p, size_t* bytes) {
+    if (!p || !bytes) return fail(nullptr, LOC_ERR_INVALID_ARG, "null argument");
+    if (p->H <= 0 || p->W <= 0 || p->K <= 0 || p->K > LOC_MAX_K || p->n_samples < 0)
+        return fail(nullptr, LOC_ERR_INVALID_ARG, "H, W must be > 0, 0 < K <= LOC_MAX_K, n_samples >= 0");
+    if (p->storage != LOC_F32 && p->storage != LOC_BF16 && p->storage != LOC_F16)
+        return fail(nullptr, LOC_ERR_INVALID_ARG, "unknown storage type");
+    // every allocation rounded up to 512 bytes, as the device allocators hand them out
+    auto r = [](size_t b) { return (b + 511) & ~(size_t)511; };
+    const size_t H = (size_t)p->H, W = (size_t)p->W, K = (size_t)p->K, hw = H * W, n = hw * K;
+    const size_t elem = p->storage == LOC_F32 ? 4 : 2;
+    size_t nparts = step_num_blocks(p->H, p->W);
+    if (nparts < 4096) nparts = 4096;
+    size_t b = 2 * r(n * elem) + r(hw) + r(hw * 4) + r(sizeof(SessionDev)) + r(nparts * 8) +
+               r(argmax_scratch_bytes(n)) + r(16);
+    // LIDAR scratch (allocated by the first scan update); the scan tables are sized for a
+    // 1080-beam scan
+    size_t cap = 2 * (size_t)p->n_samples + 4 * (H + W) + 1024;
+    if (cap > hw) cap = hw;
+    const size_t nrb = (H + 31) / 32;
+    b += r(hw * 4) + r(hw) + 2 * r(H * 4) + r((nrb + 1) * W * 4) + r((nrb + 2) * 4) + r(cap * 4) +
+         r(cap * K * 4) + r(64) + r(reweight_scalars_bytes()) + r(K * 1080 * 8) + r(1080 * 4) + r(K * 1080 * 4);
+    *bytes = b;
+    return LOC_OK;
+}
+
 LOC_API loc_status loc_create(const uint8_t* occ, const loc_params* p, loc_handle* out) {
     if (!out) return fail(nullptr, LOC_ERR_INVALID_ARG, "out is null");
     *out = nullptr;

@@ -43,27 +43,37 @@ struct alignas(128) BatchStatic {           // per session, uploaded once
 };
 struct BatchTick {                          // per session, uploaded every tick
     int cur;                                // input buffer
-    int active;                             // propagate this tick
+    int pad0;
     uint32_t seed;                          // stochastic-rounding key
-    int pad;
+    int pad1;
 };
-struct BatchItem {
-    int s, tile;                            // session, tile (row-major over the session's tile grid)
+struct BatchActive {                        // the sessions propagated this tick, in work order
+    int s;                                  // session
+    int start;                              // index of its first tile in the tick's work list
+};
+struct BatchList {
+    int n_active;
+    int total;                              // tiles of all active sessions
+    int pad[2];
 };
 struct BatchCtl {
     int head;                               // work-queue head (zeroed before every launch)
-    int n_items;
     int status;                             // LOC_DEV_ERR_* of the launch
-    int pad;
 };
 int batch_num_cfgs();
 int batch_tile_rows(int cfg);
 // Sets the kernel's shared-memory limit and returns the persistent grid (CTAs per SM x SMs).
 cudaError_t batch_prepare(int storage, int cfg, int* grid);
-// tick: n_sessions BatchTick headers followed (16-byte aligned, at shifts_off bytes) by the
-// shift table.  dry != 0 runs every tile but leaves partials, Z and the counters untouched.
+// The per-tick table (device): BatchTick hdr[n] | BatchList | BatchActive act[n] | Shift sh[sum K],
+// each part starting on a 16-byte boundary (batch_tick_layout gives the offsets).  Work item q
+// of the tick is tile q - act[i].start of session act[i].s for the last i with act[i].start <= q.
+// dry != 0 runs every listed tile but leaves partials, Z and the counters untouched.
+struct BatchLayout {
+    size_t list_off, act_off, shifts_off, bytes;
+};
+BatchLayout batch_tick_layout(int n_sessions, int sum_k);
 cudaError_t launch_batch(int storage, int cfg, int grid, const BatchStatic* ss, const void* tick,
-                         size_t shifts_off, const BatchItem* items, BatchCtl* ctl, int dry, cudaStream_t st);
+                         const BatchLayout& lay, BatchCtl* ctl, int dry, cudaStream_t st);
 
 // corr[j][i] = trav ? 1 / G(M)(j, i) : 0 with G(M) the x/y blur of M by gx (Eq. 8).
 cudaError_t launch_edge_correction(const uint8_t* trav, float* corr, int H, int W,

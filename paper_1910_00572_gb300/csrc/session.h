@@ -67,6 +67,8 @@ loc_status cuda_fail(loc_session* s, cudaError_t e, const char* what);
 void* dev_alloc(loc_session* s, size_t bytes);
 void release_all(loc_session* s);
 loc_status check_live(loc_session* h);
+// Kernel radius for sigma (given >= 0 overrides), as loc_create derives it.
+int radius(double sigma, int given);
 // Synchronise the session's stream and turn device-side error flags into a status.
 loc_status sync_and_check(loc_session* h);
 

@@ -34,6 +34,14 @@ WORKLOADS = {
                        steps=1000, dt=0.01, storage="bf16", plan="office", scan_every=10,
                        n_beams=360, angle_inc=math.pi / 180, r_max=10.0, scan_noise=0.05,
                        dropout=0.05, beam_stride=4, sigma_r=0.1, n_samples=4096, crop=256),
+    "batch64": dict(COMMON, name="batch64", seed=3, n_sessions=64, side=(128, 1024),
+                    ks=(36, 48, 64, 72), cell=0.05, steps=2000, dt=0.01, storage="bf16",
+                    plan="office"),
+    "serve256": dict(COMMON, name="serve256", seed=4, n_sessions=256, n_maps=10, side=(256, 2048),
+                     ks=tuple(range(36, 73, 4)), cell=0.05, dt=0.01, odom_hz=100.0, scan_hz=10.0,
+                     storage="bf16", plan="office", hbm_budget_gb=120.0, min_shift_cells=1.0,
+                     n_beams=360, angle_inc=math.pi / 180, r_max=10.0, scan_noise=0.05,
+                     dropout=0.05, beam_stride=4, sigma_r=0.1, n_samples=1024),
 }
 
 
@@ -52,6 +60,34 @@ def make_walk(wl: dict, occ: np.ndarray, steps: int | None = None, seed_offset: 
                                   wl["dt"], wl["seed"] + 1000 + seed_offset,
                                   trans_noise_frac=wl["trans_noise_frac"],
                                   rot_sigma=wl["rot_sigma"])
+
+
+def make_sessions(wl: dict, steps: int):
+    """The sessions of a multi-session workload: map, odometry stream (steps increments) and
+    ground-truth poses of each.  ``batch64``: one office plan per session.  ``serve256``:
+    n_maps plans, sessions assigned to them round-robin."""
+    if "n_maps" in wl:
+        maps = session_mix(wl["seed"], wl["n_maps"], side=wl["side"], ks=wl["ks"], cell=wl["cell"])
+        occs = [floorplan.office_map(m["seed"], size=m["H"], cell=wl["cell"]) for m in maps]
+        rng = np.random.Generator(np.random.PCG64(wl["seed"] + 77))
+        mix = []
+        for s in range(wl["n_sessions"]):
+            m = dict(maps[s % wl["n_maps"]])
+            m["K"] = int(wl["ks"][int(rng.integers(len(wl["ks"])))])
+            m["map"] = s % wl["n_maps"]
+            mix.append(m)
+    else:
+        mix = session_mix(wl["seed"], wl["n_sessions"], side=wl["side"], ks=wl["ks"], cell=wl["cell"])
+        occs = [floorplan.office_map(m["seed"], size=m["H"], cell=wl["cell"]) for m in mix]
+        for i, m in enumerate(mix):
+            m["map"] = i
+    out = []
+    for i, m in enumerate(mix):
+        occ = occs[m["map"]]
+        walk = trajectory.random_walk(occ, wl["cell"], steps, wl["dt"], wl["seed"] * 100000 + 31 * i + 5,
+                                      trans_noise_frac=wl["trans_noise_frac"], rot_sigma=wl["rot_sigma"])
+        out.append(dict(m, occ=occ, odom=np.asarray(walk.odom, np.float64), poses=walk.poses))
+    return out
 
 
 def session_mix(seed: int, n: int, side=(128, 1024), ks=(36, 48, 64, 72), cell=0.05):

@@ -67,3 +67,18 @@ def test_batch_arguments_fail_without_gpu_work(libloc):
         loc.loc_batch_step(loc.Batch(0, []), [], [], [])
     assert e.value.status == loc.LOC_ERR_INVALID_ARG
     assert loc.loc_batch_destroy(None) is None
+
+
+def test_server_and_admission_arguments_fail_without_gpu_work(libloc):
+    import paper_1910_00572_gb300 as loc
+    for kw in (dict(hbm_budget_bytes=0.0), dict(storage=7), dict(tile=9), dict(n_streams=0)):
+        with pytest.raises(loc.LocError) as e:
+            loc.loc_server_create(loc.loc_server_params_default(**kw))
+        assert e.value.status == loc.LOC_ERR_INVALID_ARG
+    p = loc.loc_params_default(H=100, W=60, K=8, cell_m=0.05, storage="bf16", n_samples=0)
+    b = loc.loc_session_bytes(p)
+    # two 16-bit belief tensors, the map, the correction and the sampling scratch
+    assert b >= 2 * 2 * 100 * 60 * 8 + 100 * 60 * (1 + 4 + 4 + 1)
+    p.K = 0
+    with pytest.raises(loc.LocError):
+        loc.loc_session_bytes(p)
