@@ -50,40 +50,143 @@ __global__ void __launch_bounds__(NT) belief_map_kernel(const T* __restrict__ B,
     });
 }
 
+// The same with V consecutive cells per thread and 16-byte loads (hw a multiple of V).
+template <typename T, int V>
+__global__ void __launch_bounds__(NT) belief_map_vec_kernel(const T* __restrict__ B, const uint8_t* __restrict__ trav,
+                                                            SessionDev* sd, float inv_uniform, size_t hw, int K,
+                                                            float* __restrict__ m, double* partials,
+                                                            unsigned int* counter, int n_samples, float* fs_out) {
+    static_assert(V * sizeof(T) == 16, "one 16-byte load per plane");
+    __shared__ double red[NT / 32];
+    const int reinit = sd->reinit;
+    const float scale = sd->inv_Z;
+    KahanF acc;
+    const size_t ng = hw / V;
+    for (size_t g = (size_t)blockIdx.x * NT + threadIdx.x; g < ng; g += (size_t)gridDim.x * NT) {
+        float v[V];
+#pragma unroll
+        for (int e = 0; e < V; ++e) v[e] = 0.0f;
+        if (reinit) {
+#pragma unroll
+            for (int e = 0; e < V; ++e) v[e] = (float)trav[g * V + e] * inv_uniform;
+        } else {
+            for (int k = 0; k < K; ++k) {
+                union {
+                    uint4 u;
+                    T x[V];
+                } raw;
+                raw.u = __ldg(reinterpret_cast<const uint4*>(B + (size_t)k * hw) + g);
+#pragma unroll
+                for (int e = 0; e < V; ++e) v[e] = fmaxf(v[e], Store<T>::ld(&raw.x[e]) * scale);
+            }
+        }
+#pragma unroll
+        for (int e = 0; e < V; e += 4)
+            *reinterpret_cast<float4*>(m + g * V + e) = make_float4(v[e], v[e + 1], v[e + 2], v[e + 3]);
+#pragma unroll
+        for (int e = 0; e < V; ++e) acc.add(v[e]);
+    }
+    const double bt = block_sum<NT>(acc.value(), red);
+    finish_sum<NT>(bt, partials, counter, gridDim.x, red, [fs_out, n_samples](double S) {
+        *fs_out = S > 0.0 ? (float)((double)n_samples / S) : 0.0f;
+    });
+}
+
 // ------------------------------------------------------------------ Floyd-Steinberg
 
-// One CTA of 32 warps.  Warp w takes the 32-row blocks rb = w, w + 32, ...; lane l owns row
-// 32 rb + l and handles column i = t - 2l at step t, so the three errors it needs from the
-// row above (columns i-1, i, i+1) were produced by lane l-1 at steps t-3, t-2, t-1 and arrive
-// by warp shuffle.  Lane 0 takes the row above from the previous block's last row, which that
-// block's lane 31 writes into bnd[rb][*] and publishes in prog[rb] (columns written);
-// every wait on prog is bounded.
-__global__ void __launch_bounds__(1024) fs_kernel(const float* __restrict__ m, const float* fs_ptr, int H, int W,
-                                                  uint8_t* __restrict__ sel, int* __restrict__ rowcnt,
-                                                  float* bnd, int* prog, int* status) {
+// One CTA of kFsWarps warps.  Warp w takes the 32-row blocks rb = w, w + kFsWarps, ...; lane l
+// owns row 32 rb + l and handles column i = t - 2l at step t, so the three errors it needs from
+// the row above (columns i-1, i, i+1) were produced by lane l-1 at steps t-3, t-2, t-1 and
+// arrive by warp shuffle.  Lane 0 takes the row above from the previous block's last row,
+// which that block's lane 31 writes into bnd[rb][*] and publishes in prog[rb] (columns
+// written); every wait on prog is bounded.
+//
+// Each warp keeps a ring of three 32-column chunks per row in shared memory (column i at
+// position i mod 96).  A lane reads min(1, m fs) of its cell there and writes its selection
+// back in its place.  Steps run in windows of 32: at step 32 T the last lane has finished chunk
+// T - 3 (at step 32 T - 3), so the warp copies that chunk's selections to sel (each lane its own
+// row) and stores chunk T of the map (loaded into registers, coalesced, one window earlier) in
+// its place.  Terms of the error sum whose source lies outside the grid are zero (their errors
+// were never produced), so the sum always takes the same four terms in the same order; only
+// the right neighbour above is masked at the last column.
+constexpr int kFsWarps = 16;
+constexpr int kFsPitch = 97;              // 3 x 32 columns + 1: lane accesses hit distinct banks
+
+__global__ void __launch_bounds__(kFsWarps * 32) fs_kernel(const float* __restrict__ m, const float* fs_ptr, int H,
+                                                           int W, uint8_t* __restrict__ sel, int* __restrict__ rowcnt,
+                                                           float* bnd, int* prog, int* status) {
+    extern __shared__ float fs_ring_all[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float* ring = fs_ring_all + (size_t)warp * 32 * kFsPitch;
+    float* own = ring + lane * kFsPitch;                       // this lane's row
     const float fs = *fs_ptr;
-    const int nrb = (H + 31) / 32;
+    const int nrb = (H + 31) / 32, nch = (W + 31) / 32;
+    const int vec = (W & 3) == 0 ? 4 : 1;
     const float w7 = 0.4375f, w3 = 0.1875f, w5 = 0.3125f, w1 = 0.0625f;
-    for (int rb = warp; rb < nrb; rb += 32) {
-        const int j = 32 * rb + lane;
+    for (int rb = warp; rb < nrb; rb += kFsWarps) {
+        const int j0 = 32 * rb, j = j0 + lane;
         const bool row_ok = j < H;
+        float pre[32];                                         // column 32 c + lane of rows j0 ..
+        auto load_chunk = [&](int c) {
+            const int col = 32 * c + lane;
+#pragma unroll
+            for (int r = 0; r < 32; ++r)
+                pre[r] = (j0 + r < H && col < W) ? m[(size_t)(j0 + r) * W + col] : 0.0f;
+        };
+        auto store_chunk = [&](int c) {
+            float* dst = ring + (c % 3) * 32 + lane;
+#pragma unroll
+            for (int r = 0; r < 32; ++r) {
+                float v = __fmul_rn(pre[r], fs);
+                if (v > 1.0f) v = 1.0f;
+                dst[r * kFsPitch] = v;
+            }
+        };
+        int cnt = 0;
+        auto copy_out = [&](int c) {                           // this lane's selections of chunk c
+            const float* src = own + (c % 3) * 32;
+            const int c0 = 32 * c, n = min(32, W - c0);
+            uint8_t* out = sel + (size_t)j * W + c0;
+            if (!row_ok) return;
+            if (vec == 4) {
+                for (int k = 0; k < n; k += 4) {
+                    const uint32_t b = (uint32_t)__float_as_uint(src[k]) | ((uint32_t)__float_as_uint(src[k + 1]) << 8) |
+                                       ((uint32_t)__float_as_uint(src[k + 2]) << 16) |
+                                       ((uint32_t)__float_as_uint(src[k + 3]) << 24);
+                    *reinterpret_cast<uint32_t*>(out + k) = b;
+                    cnt += __popc(b);
+                }
+            } else {
+                for (int k = 0; k < n; ++k) {
+                    const uint32_t b = __float_as_uint(src[k]);
+                    out[k] = (uint8_t)b;
+                    cnt += (int)b;
+                }
+            }
+        };
+        __syncwarp();                                          // the previous block's reads are done
+        load_chunk(0);
+        store_chunk(0);
+        if (nch > 1) load_chunk(1);
+        __syncwarp();
         float up_old = 0.0f, up_mid = 0.0f, up_new = 0.0f;   // row above: columns i-1, i, i+1
         float e_prev = 0.0f, last = 0.0f;                      // own error at i-1; newest error
         float chunk = 0.0f;                                    // lane L: bnd[rb][t0 + 1 + L]
-        int cnt = 0;
         bool failed = false;
         const int steps = W + 62;
-        for (int t = 0; t < steps; ++t) {
-            if (rb > 0 && (t & 31) == 0) {
-                // the row above for columns t+1 .. t+32 must be published before lane 0 uses it
-                const int need = min(W, t + 33);
+        const int nwin = (steps + 31) / 32;
+        int ri = (96 - 2 * lane) % 96;                         // (t - 2 lane) mod 96
+        for (int T = 0; T < nwin; ++T) {
+            const int t0 = 32 * T;
+            if (rb > 0) {
+                // the row above for columns t0+1 .. t0+32 must be published before lane 0 uses it
+                const int need = min(W, t0 + 33);
                 int ok = 1;
                 if (lane == 0) {
-                    const unsigned long long t0 = gtime();
+                    const unsigned long long g0 = gtime();
                     unsigned int it = 0;
                     while (((volatile int*)prog)[rb] < need) {
-                        if (++it > (1u << 26) || gtime() - t0 > kSpinNs) {
+                        if (++it > (1u << 26) || gtime() - g0 > kSpinNs) {
                             ok = 0;
                             break;
                         }
@@ -96,46 +199,54 @@ __global__ void __launch_bounds__(1024) fs_kernel(const float* __restrict__ m, c
                     break;
                 }
                 __threadfence_block();
-                const int c = t + 1 + lane;
+                const int c = t0 + 1 + lane;
                 chunk = c < W ? ((volatile float*)bnd)[(size_t)rb * W + c] : 0.0f;
                 // lane 0 starts at column 0 at once: the row above at column 0 must already be
                 // in its register chain (other lanes shift theirs in while they wait to start)
-                if (t == 0 && lane == 0) up_new = ((volatile float*)bnd)[(size_t)rb * W];
+                if (T == 0 && lane == 0) up_new = ((volatile float*)bnd)[(size_t)rb * W];
             }
-            const float from_above = __shfl_sync(0xffffffffu, chunk, t & 31);
-            const float from_left = __shfl_up_sync(0xffffffffu, last, 1);
-            const float incoming = lane == 0 ? (rb > 0 ? from_above : 0.0f) : from_left;
-            up_old = up_mid;
-            up_mid = up_new;
-            up_new = incoming;
-            const int i = t - 2 * lane;
-            if (i >= 0 && i < W && row_ok) {
-                float E = 0.0f;
-                if (j > 0) {
-                    if (i > 0) E = __fadd_rn(E, __fmul_rn(up_old, w1));
+            if (T >= 3 && T - 3 < nch) copy_out(T - 3);
+            if (T > 0 && T < nch) {
+                __syncwarp();                                  // chunk T - 3 is read and copied
+                store_chunk(T);
+                __syncwarp();
+                if (T + 1 < nch) load_chunk(T + 1);
+            }
+#pragma unroll
+            for (int s = 0; s < 32; ++s) {
+                const float from_above = __shfl_sync(0xffffffffu, chunk, s);
+                const float from_left = __shfl_up_sync(0xffffffffu, last, 1);
+                const float incoming = lane == 0 ? (rb > 0 ? from_above : 0.0f) : from_left;
+                up_old = up_mid;
+                up_mid = up_new;
+                up_new = incoming;
+                const int i = t0 + s - 2 * lane;
+                const float v = own[ri];
+                if ((unsigned)i < (unsigned)W && row_ok) {
+                    float E = __fadd_rn(0.0f, __fmul_rn(up_old, w1));
                     E = __fadd_rn(E, __fmul_rn(up_mid, w5));
-                    if (i + 1 < W) E = __fadd_rn(E, __fmul_rn(up_new, w3));
-                }
-                if (i > 0) E = __fadd_rn(E, __fmul_rn(e_prev, w7));
-                float v = __fmul_rn(m[(size_t)j * W + i], fs);
-                if (v > 1.0f) v = 1.0f;
-                const float val = __fadd_rn(v, E);
-                const bool on = val >= 0.5f;
-                const float err = on ? __fsub_rn(val, 1.0f) : val;
-                sel[(size_t)j * W + i] = on ? 1 : 0;
-                cnt += on ? 1 : 0;
-                e_prev = err;
-                last = err;
-                if (lane == 31 && rb + 1 < nrb) {
-                    bnd[(size_t)(rb + 1) * W + i] = err;
-                    if (((i + 1) & 31) == 0 || i == W - 1) {
-                        __threadfence_block();
-                        ((volatile int*)prog)[rb + 1] = i + 1;
+                    E = __fadd_rn(E, __fmul_rn(i + 1 < W ? up_new : 0.0f, w3));
+                    E = __fadd_rn(E, __fmul_rn(e_prev, w7));
+                    const float val = __fadd_rn(v, E);
+                    const bool on = val >= 0.5f;
+                    const float err = on ? __fsub_rn(val, 1.0f) : val;
+                    own[ri] = __uint_as_float(on ? 1u : 0u);
+                    e_prev = err;
+                    last = err;
+                    if (lane == 31 && rb + 1 < nrb) {
+                        bnd[(size_t)(rb + 1) * W + i] = err;
+                        if (((i + 1) & 31) == 0 || i == W - 1) {
+                            __threadfence_block();
+                            ((volatile int*)prog)[rb + 1] = i + 1;
+                        }
                     }
                 }
+                ri = ri == 95 ? 0 : ri + 1;
             }
         }
         if (failed) return;
+        __syncwarp();
+        for (int c = max(0, nwin - 3); c < nch; ++c) copy_out(c);   // chunks not copied in the loop
         if (row_ok) rowcnt[j] = cnt;
     }
 }
@@ -378,8 +489,15 @@ cudaError_t launch_belief_map(const void* B, int storage, const uint8_t* trav, S
                               unsigned int* counter, int n_samples, float* fs_out, cudaStream_t st) {
     const size_t hw = (size_t)H * W;
     const unsigned int nb = grid_for(hw, nparts < 2048 ? nparts : 2048);
-    LOC_DISPATCH(storage, (belief_map_kernel<T><<<nb, NT, 0, st>>>((const T*)B, trav, sd, inv_uniform, hw, K, m,
-                                                                      partials, counter, n_samples, fs_out)));
+    const size_t vec = storage == LOC_F32 ? 4 : 8;
+    if (hw % vec == 0) {
+        const unsigned int nbv = grid_for(hw / vec, nparts < 2048 ? nparts : 2048);
+        LOC_DISPATCH(storage, (belief_map_vec_kernel<T, 16 / sizeof(T)><<<nbv, NT, 0, st>>>(
+                                  (const T*)B, trav, sd, inv_uniform, hw, K, m, partials, counter, n_samples, fs_out)));
+    } else {
+        LOC_DISPATCH(storage, (belief_map_kernel<T><<<nb, NT, 0, st>>>((const T*)B, trav, sd, inv_uniform, hw, K, m,
+                                                                          partials, counter, n_samples, fs_out)));
+    }
     return cudaGetLastError();
 }
 
@@ -389,7 +507,16 @@ cudaError_t launch_dither(const float* m, const float* fs, int H, int W, uint8_t
     const int nrb = (H + 31) / 32;
     cudaError_t e = cudaMemsetAsync(prog, 0, sizeof(int) * (size_t)(nrb + 1), st);
     if (e != cudaSuccess) return e;
-    fs_kernel<<<1, 1024, 0, st>>>(m, fs, H, W, sel, rowcnt, bnd, prog, status);
+    const size_t smem = sizeof(float) * kFsWarps * 32 * kFsPitch;
+    static bool attr_set[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64 || !attr_set[dev]) {
+        e = cudaFuncSetAttribute(fs_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        if (dev >= 0 && dev < 64) attr_set[dev] = true;
+    }
+    fs_kernel<<<1, kFsWarps * 32, smem, st>>>(m, fs, H, W, sel, rowcnt, bnd, prog, status);
     row_scan_kernel<<<1, 1024, 0, st>>>(rowcnt, H, rowoff, count);
     if (samples) compact_kernel<<<grid_for((size_t)H * 32, 1024), NT, 0, st>>>(sel, rowoff, H, W, cap, samples);
     return cudaGetLastError();

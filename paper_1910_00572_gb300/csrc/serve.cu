@@ -11,7 +11,7 @@
 // A completion thread polls the events recorded after each piece of work and timestamps it.
 //
 // Ordering.  A session's work runs in message order: a batch waits for the scan updates
-// launched since the previous batch, and a scan update waits for the batch that last
+// of its sessions launched since their last batch, and a scan update waits for the batch that last
 // propagated its session.  Because a session is propagated at most once per tick and its
 // gate only sees its own messages, the propagation points, the rounding keys and therefore the
 // results do not depend on the load or on the other sessions.
@@ -63,6 +63,8 @@ struct SrvSession {
     int stream_idx = 0;
     int ci = -1;                       // index in the batched launch
     long long last_prop_tick = -1;
+    cudaEvent_t scan_ev = nullptr;     // recorded after the session's latest scan update
+    bool scan_pending = false;         // a scan update was launched since its last propagation
 };
 
 struct Inflight {
@@ -98,8 +100,6 @@ struct loc_server_s {
     std::string err;
     // worker-owned
     std::vector<cudaStream_t> pool;
-    std::vector<cudaEvent_t> pool_ev;
-    std::vector<char> pool_dirty;      // scans launched on the stream since the last batch
     cudaEvent_t ring[kRing] = {};
     BatchCore core;
     bool core_live = false;
@@ -271,6 +271,14 @@ bool membership(loc_server s) {
             ss->q.clear();
             continue;
         }
+        if (!ss->scan_ev && cudaEventCreateWithFlags(&ss->scan_ev, cudaEventDisableTiming) != cudaSuccess) {
+            ss->scan_ev = nullptr;
+            loc_destroy(h);
+            ss->state = LOC_SESSION_FAILED;
+            for (SrvMsg& m : ss->q) delete m.scan;
+            ss->q.clear();
+            continue;
+        }
         ss->h = h;
         ss->state = LOC_SESSION_ACTIVE;
         s->used_bytes += ss->bytes;
@@ -363,12 +371,11 @@ void gather(loc_server s, TickWork& t) {
 bool launch(loc_server s, TickWork& t) {
     cudaError_t e = cudaSuccess;
     if (!t.props.empty()) {
-        // the batch follows the scan updates launched since the previous batch
-        for (size_t p = 0; p < s->pool.size() && e == cudaSuccess; ++p)
-            if (s->pool_dirty[p]) {
-                e = cudaEventRecord(s->pool_ev[p], s->pool[p]);
-                if (e == cudaSuccess) e = cudaStreamWaitEvent(s->core.bs, s->pool_ev[p], 0);
-                s->pool_dirty[p] = 0;
+        // the batch follows the scan updates of its sessions launched since their last batch
+        for (auto& pr : t.props)
+            if (pr.first->scan_pending && e == cudaSuccess) {
+                e = cudaStreamWaitEvent(s->core.bs, pr.first->scan_ev, 0);
+                pr.first->scan_pending = false;
             }
         BatchTick* ht = nullptr;
         Shift* hs = nullptr;
@@ -450,11 +457,12 @@ bool launch(loc_server s, TickWork& t) {
             return false;
         }
         cudaEvent_t ev = get_event(s);
-        if (!ev || cudaEventRecord(ev, ps) != cudaSuccess) {
+        if (!ev || cudaEventRecord(ev, ps) != cudaSuccess ||
+            (s->prm.batching && cudaEventRecord(ss->scan_ev, ps) != cudaSuccess)) {
             set_failed(s, "event record failed");
             return false;
         }
-        s->pool_dirty[(size_t)ss->stream_idx] = 1;
+        ss->scan_pending = true;
         {
             std::lock_guard<std::mutex> ls(s->mu_st);
             s->n_scans += 1;
@@ -532,18 +540,13 @@ LOC_API loc_status loc_server_create(const loc_server_params* p, loc_server* out
     cudaError_t e = cudaGetDevice(&s->device);
     for (int i = 0; i < p->n_streams && e == cudaSuccess; ++i) {
         cudaStream_t st = nullptr;
-        cudaEvent_t ev = nullptr;
         e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
         if (e == cudaSuccess) s->pool.push_back(st);
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
-        if (e == cudaSuccess) s->pool_ev.push_back(ev);
     }
-    s->pool_dirty.assign(s->pool.size(), 0);
     for (int i = 0; i < kRing && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&s->ring[i], cudaEventDisableTiming);
     if (e != cudaSuccess) {
         const std::string m = std::string("loc_server_create: ") + cudaGetErrorString(e);
         for (cudaStream_t st : s->pool) cudaStreamDestroy(st);
-        for (cudaEvent_t ev : s->pool_ev) cudaEventDestroy(ev);
         for (cudaEvent_t& ev : s->ring)
             if (ev) cudaEventDestroy(ev);
         delete s;
@@ -796,10 +799,10 @@ LOC_API loc_status loc_server_destroy(loc_server s) {
     for (SrvSession* ss : s->sessions) {
         for (SrvMsg& m : ss->q) delete m.scan;
         if (ss->h) loc_destroy(ss->h);
+        if (ss->scan_ev) cudaEventDestroy(ss->scan_ev);
         delete ss;
     }
     for (cudaEvent_t ev : s->ev_free) cudaEventDestroy(ev);
-    for (cudaEvent_t ev : s->pool_ev) cudaEventDestroy(ev);
     for (cudaEvent_t ev : s->ring) cudaEventDestroy(ev);
     for (cudaStream_t st : s->pool) cudaStreamDestroy(st);
     delete s;
