@@ -78,9 +78,12 @@ typedef struct {
                                   1 .. LOC_TILE_CONFIGS forces one */
 } loc_params;
 
-#define LOC_TILE_CONFIGS 7     /* tile rows x 64 columns, threads: 1: 32 (256), 2: 16 (256),
+#define LOC_TILE_CONFIGS 12    /* tile rows x 64 columns, threads: 1: 32 (256), 2: 16 (256),
                                   3: 16 (128), 4: 16 (512), 5: 32 (512); warp-specialised
-                                  producer/consumer pipelines: 6: 16 (256), 7: 8 (256) */
+                                  producer/consumer pipelines: 6: 16 (256), 7: 8 (256); with
+                                  cells paired 32 columns apart on the packed FP32 pipe:
+                                  8: 16 (128), 9: 16 (256), 10: 32 (256), 11: 8 (128),
+                                  12: 16 (128, 2 raw stages) */
 
 /* Propagation kernel selection: AUTO takes the TMA-tiled kernel when it applies (x/y radius
  * 2, theta radius 3, K >= 8, W a multiple of 16 bytes of storage) and the generic one

@@ -17,7 +17,9 @@
 //
 // Tile configurations (Cfg1..Cfg3) trade halo overhead against the number of resident CTAs;
 // the session picks one per grid shape.
-#include "tiled_common.cuh"
+#include <type_traits>
+
+#include "tiled_pairs.cuh"
 
 namespace loc {
 namespace {
@@ -27,10 +29,12 @@ using namespace tiled;
 template <typename T, typename C>
 __global__ void __launch_bounds__(C::NT, C::MINB) step_tiled_kernel(const __grid_constant__ FastArgs a) {
     constexpr int NT = C::NT, NSTAGE = C::NSTAGE;
+    constexpr bool PAIRS = C::PAIRS;
+    using SM = std::conditional_t<PAIRS, pairs::PSmem<T, C>, Smem<T, C>>;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     // the dynamic region is only guaranteed 16-byte aligned: round up to 128 bytes
     const uint32_t base = su32(smem_raw);
-    Smem<T, C>& sm = *reinterpret_cast<Smem<T, C>*>(smem_raw + (((base + 127u) & ~127u) - base));
+    SM& sm = *reinterpret_cast<SM*>(smem_raw + (((base + 127u) & ~127u) - base));
     const int tid = threadIdx.x;
     if (tid == 0) {
         for (int s = 0; s < NSTAGE; ++s) bar_init(&sm.bar[s], 1);
@@ -58,7 +62,10 @@ __global__ void __launch_bounds__(C::NT, C::MINB) step_tiled_kernel(const __grid
     j.tx0 = blockIdx.x * TW;
     KahanF acc;
     int p_stop = 0, next_issue = 0;
-    if (!run_tile<T, C>(sm, j, 0u, acc, p_stop, next_issue)) {
+    bool ok;
+    if constexpr (PAIRS) ok = pairs::run_tile<T, C>(sm, j, 0u, acc, p_stop, next_issue);
+    else ok = run_tile<T, C>(sm, j, 0u, acc, p_stop, next_issue);
+    if (!ok) {
         // a TMA wait gave up: report it, let the copies still in flight land (bounded), and
         // leave without contributing a partial (the host sees the flag and fails the handle)
         if (tid == 0) {
@@ -315,8 +322,19 @@ using Cfg4 = Cfg<16, 1, 2, 8, 3, 2>;
 using Cfg5 = Cfg<32, 2, 3, 16, 3, 1>;
 using Cfg6 = WsCfg<16, 4, 16, 3, 2>;   // warp-specialised, 16-row tiles
 using Cfg7 = WsCfg<8, 2, 8, 3, 4>;     // warp-specialised, 8-row tiles
+// Paired-column passes (tiled_pairs.cuh): 8: 16-row tiles, 128 threads; 9: 16-row tiles, 256
+// threads; 10: 32-row tiles, 256 threads, 2 raw stages; 11: 8-row tiles, 128 threads;
+// 12: 16-row tiles, 128 threads, 2 raw stages, 4 CTAs per SM.
+using Cfg8 = pairs::PCfg<16, 4, 2, 8, 3, 3>;
+using Cfg9 = pairs::PCfg<16, 2, 2, 4, 3, 2>;
+using Cfg10 = pairs::PCfg<32, 4, 2, 8, 2, 2>;
+using Cfg11 = pairs::PCfg<8, 2, 2, 8, 3, 4>;
+using Cfg12 = pairs::PCfg<16, 4, 2, 8, 2, 4>;
 
-template <typename T, typename C> size_t smem_bytes() { return sizeof(Smem<T, C>) + 128; }
+template <typename T, typename C> size_t smem_bytes() {
+    using SM = std::conditional_t<C::PAIRS, pairs::PSmem<T, C>, Smem<T, C>>;
+    return sizeof(SM) + 128;
+}
 
 // Launch with the dynamic shared memory size; the attribute is set once per device.
 template <typename T, typename C>
@@ -359,6 +377,11 @@ cudaError_t launch_cfg(int cfg, const FastArgs& a, int W, int H, cudaStream_t st
         case 5: return launch_typed<T, Cfg5>(a, dim3((W + TW - 1) / TW, (H + Cfg5::TH - 1) / Cfg5::TH), st);
         case 6: return launch_ws<T, Cfg6>(a, dim3((W + TW - 1) / TW, (H + Cfg6::TH - 1) / Cfg6::TH), st);
         case 7: return launch_ws<T, Cfg7>(a, dim3((W + TW - 1) / TW, (H + Cfg7::TH - 1) / Cfg7::TH), st);
+        case 8: return launch_typed<T, Cfg8>(a, dim3((W + TW - 1) / TW, (H + Cfg8::TH - 1) / Cfg8::TH), st);
+        case 9: return launch_typed<T, Cfg9>(a, dim3((W + TW - 1) / TW, (H + Cfg9::TH - 1) / Cfg9::TH), st);
+        case 10: return launch_typed<T, Cfg10>(a, dim3((W + TW - 1) / TW, (H + Cfg10::TH - 1) / Cfg10::TH), st);
+        case 11: return launch_typed<T, Cfg11>(a, dim3((W + TW - 1) / TW, (H + Cfg11::TH - 1) / Cfg11::TH), st);
+        case 12: return launch_typed<T, Cfg12>(a, dim3((W + TW - 1) / TW, (H + Cfg12::TH - 1) / Cfg12::TH), st);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -371,7 +394,12 @@ int cfg_tile_rows(int cfg) {
         case 4: return Cfg4::TH;
         case 5: return Cfg5::TH;
         case 6: return Cfg6::TH;
-        default: return Cfg7::TH;
+        case 7: return Cfg7::TH;
+        case 8: return Cfg8::TH;
+        case 9: return Cfg9::TH;
+        case 10: return Cfg10::TH;
+        case 11: return Cfg11::TH;
+        default: return Cfg12::TH;
     }
 }
 
@@ -399,7 +427,7 @@ bool step_tiled_eligible(int H, int W, int K, int r_xy, int r_th, int storage) {
     return r_xy == R && r_th == RT && K >= 8 && K <= LOC_MAX_K && W % align == 0 && W >= 8 && H >= 1;
 }
 
-int step_tiled_num_cfgs() { return 7; }
+int step_tiled_num_cfgs() { return 12; }
 
 int step_tiled_default_cfg(int H, int W, int K, int storage) {
     (void)K;
@@ -420,7 +448,8 @@ cudaError_t make_step_tmap(void* tmap_out, const void* B, int storage, int H, in
                                                          : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
     const cuuint64_t dims[3] = {(cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)K};
     const cuuint64_t strides[2] = {(cuuint64_t)W * e, (cuuint64_t)W * H * e};
-    const cuuint32_t box[3] = {(cuuint32_t)BW, (cuuint32_t)(cfg_tile_rows(cfg) + 2 * R + 1), 1};
+    const int bw = cfg < 8 ? BW : (storage == LOC_F32 ? pairs::pbw<float>() : pairs::pbw<__half>());
+    const cuuint32_t box[3] = {(cuuint32_t)bw, (cuuint32_t)(cfg_tile_rows(cfg) + 2 * R + 1), 1};
     const cuuint32_t estr[3] = {1, 1, 1};
     CUresult r = enc(static_cast<CUtensorMap*>(tmap_out), dt, 3, const_cast<void*>(B), dims, strides, box,
                      estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,

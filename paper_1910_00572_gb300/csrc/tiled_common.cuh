@@ -25,6 +25,7 @@ constexpr unsigned long long kWaitNs = 200ull * 1000 * 1000;   // bounded mbarri
 template <int TH_, int MR_, int SR_, int XW_, int NSTAGE_, int MINB_>
 struct Cfg {
     static constexpr int TH = TH_, MR = MR_, SR = SR_, XW = XW_, NSTAGE = NSTAGE_, MINB = MINB_;
+    static constexpr bool PAIRS = false;
     static constexpr int NT = (TH / MR) * 32;
     static constexpr int XR = TH + 2 * R;          // rows of S and X
     static constexpr int RAW_H = XR + 1;           // raw rows (bilinear needs one more)

@@ -45,7 +45,7 @@ SHAPES = [
 ]
 
 
-@pytest.mark.parametrize("tile", [1, 2, 3, 4, 5, 6, 7])
+@pytest.mark.parametrize("tile", list(range(1, 13)))
 @pytest.mark.parametrize("H,W,K,mot", SHAPES, ids=[f"{s[0]}x{s[1]}x{s[2]}" for s in SHAPES])
 def test_tiled_matches_oracle_and_generic(H, W, K, mot, tile):
     rng = np.random.default_rng(H * 7 + W * 3 + K)
@@ -119,7 +119,7 @@ def test_tiled_is_refused_where_it_does_not_apply():
     with pytest.raises(loc.LocError):
         make(np.zeros((32, 32), np.uint8), 16, 0.1, sigma_xy_cells=1.0)
     with pytest.raises(loc.LocError):
-        make(np.zeros((32, 32), np.uint8), 16, 0.1, tile=9)
+        make(np.zeros((32, 32), np.uint8), 16, 0.1, tile=13)   # beyond LOC_TILE_CONFIGS
 
 
 @pytest.mark.parametrize("storage", ["bf16", "f16"])
