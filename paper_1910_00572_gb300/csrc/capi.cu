@@ -6,7 +6,6 @@
 #include <cstring>
 #include <new>
 #include <string>
-#include <unordered_map>
 #include <vector>
 
 #include "session.h"
@@ -396,7 +395,13 @@ loc_status upload_scan(loc_session* h, const float* ranges, int n_beams, double 
     const int nu = (int)used.size();
     std::vector<float> dirs;
     std::vector<int32_t> dir_of((size_t)K * std::max(nu, 1));
-    std::unordered_map<unsigned long long, int> uniq;
+    // distinct FP32 direction pairs through an open-addressing table (keys are the bit
+    // patterns of (cos, sin); a zero key marks an empty slot, so that pattern is kept aside)
+    size_t cap = 64;
+    while (cap < 2 * (size_t)K * std::max(nu, 1)) cap <<= 1;
+    std::vector<unsigned long long> keys(cap, 0ull);
+    std::vector<int> ids(cap, -1);
+    int zero_id = -1;
     for (int k = 0; k < K; ++k)
         for (int u = 0; u < nu; ++u) {
             const double a = (2.0 * M_PI / K) * k + h->theta + (angle_min + angle_inc * used[u]);
@@ -405,15 +410,21 @@ loc_status upload_scan(loc_session* h, const float* ranges, int n_beams, double 
             std::memcpy(&bc, &c, 4);
             std::memcpy(&bs, &sn, 4);
             const unsigned long long key = ((unsigned long long)bc << 32) | bs;
-            auto it = uniq.find(key);
-            int id;
-            if (it == uniq.end()) {
+            int id = -1;
+            if (key == 0ull) {
+                id = zero_id;
+            } else {
+                size_t slot = (size_t)((key * 0x9E3779B97F4A7C15ull) >> 40) & (cap - 1);
+                while (keys[slot] != 0ull && keys[slot] != key) slot = (slot + 1) & (cap - 1);
+                if (keys[slot] == key) id = ids[slot];
+                else keys[slot] = key;
+                if (id < 0) ids[slot] = (int)(dirs.size() / 2);
+            }
+            if (id < 0) {
                 id = (int)(dirs.size() / 2);
-                uniq.emplace(key, id);
+                if (key == 0ull) zero_id = id;
                 dirs.push_back(c);
                 dirs.push_back(sn);
-            } else {
-                id = it->second;
             }
             dir_of[(size_t)k * nu + u] = id;
         }

@@ -74,6 +74,7 @@ struct Inflight {
 };
 
 constexpr int kRing = 64;              // batch events kept for scan ordering
+constexpr size_t kScanThreads = 8;     // host threads preparing a tick's scan updates
 
 double pct(std::vector<double> v, double q) {
     if (v.empty()) return 0.0;
@@ -439,35 +440,58 @@ bool launch(loc_server s, TickWork& t) {
             s->n_msgs += 1;
         }
     }
-    for (auto& pm : t.scans) {
-        SrvSession* ss = pm.first;
-        SrvScan* sc = pm.second.scan;
-        cudaStream_t ps = s->pool[(size_t)ss->stream_idx];
-        if (s->prm.batching && ss->last_prop_tick >= 0)
-            e = cudaStreamWaitEvent(ps, s->ring[ss->last_prop_tick % kRing], 0);
-        if (e != cudaSuccess) {
-            set_failed(s, std::string("scan ordering: ") + cudaGetErrorString(e));
-            return false;
+    // Scan updates: distinct sessions on their own streams.  Their host work (direction tables,
+    // uploads, launches) runs on up to kScanThreads threads.
+    std::atomic<int> next{0};
+    std::atomic<bool> bad{false};
+    auto scan_worker = [&]() {
+        cudaSetDevice(s->device);
+        for (;;) {
+            const int i = next.fetch_add(1);
+            if (i >= (int)t.scans.size() || bad.load()) return;
+            SrvSession* ss = t.scans[(size_t)i].first;
+            SrvScan* sc = t.scans[(size_t)i].second.scan;
+            cudaStream_t ps = s->pool[(size_t)ss->stream_idx];
+            cudaError_t we = cudaSuccess;
+            if (s->prm.batching && ss->last_prop_tick >= 0)
+                we = cudaStreamWaitEvent(ps, s->ring[ss->last_prop_tick % kRing], 0);
+            if (we != cudaSuccess) {
+                set_failed(s, std::string("scan ordering: ") + cudaGetErrorString(we));
+                bad = true;
+                return;
+            }
+            const loc_status st = loc_lidar_update(ss->h, sc->ranges.data(), (int)sc->ranges.size(), sc->angle_min,
+                                                   sc->angle_inc, sc->r_max, sc->stride, sc->sigma_r);
+            delete sc;
+            t.scans[(size_t)i].second.scan = nullptr;
+            if (st < 0) {
+                set_failed(s, std::string("loc_lidar_update: ") + loc_last_error(ss->h));
+                bad = true;
+                return;
+            }
+            cudaEvent_t ev = get_event(s);
+            if (!ev || cudaEventRecord(ev, ps) != cudaSuccess ||
+                (s->prm.batching && cudaEventRecord(ss->scan_ev, ps) != cudaSuccess)) {
+                set_failed(s, "event record failed");
+                bad = true;
+                return;
+            }
+            ss->scan_pending = true;
+            {
+                std::lock_guard<std::mutex> ls(s->mu_st);
+                s->n_scans += 1;
+            }
+            push_inflight(s, ev, MSG_SCAN, std::vector<double>{t.scans[(size_t)i].second.t_arr});
         }
-        const loc_status st = loc_lidar_update(ss->h, sc->ranges.data(), (int)sc->ranges.size(), sc->angle_min,
-                                               sc->angle_inc, sc->r_max, sc->stride, sc->sigma_r);
-        delete sc;
-        if (st < 0) {
-            set_failed(s, std::string("loc_lidar_update: ") + loc_last_error(ss->h));
-            return false;
-        }
-        cudaEvent_t ev = get_event(s);
-        if (!ev || cudaEventRecord(ev, ps) != cudaSuccess ||
-            (s->prm.batching && cudaEventRecord(ss->scan_ev, ps) != cudaSuccess)) {
-            set_failed(s, "event record failed");
-            return false;
-        }
-        ss->scan_pending = true;
-        {
-            std::lock_guard<std::mutex> ls(s->mu_st);
-            s->n_scans += 1;
-        }
-        push_inflight(s, ev, MSG_SCAN, std::vector<double>{pm.second.t_arr});
+    };
+    const int nthreads = (int)std::min<size_t>(kScanThreads, t.scans.size());
+    if (nthreads > 0) {
+        std::vector<std::thread> helpers;
+        for (int k = 1; k < nthreads; ++k) helpers.emplace_back(scan_worker);
+        scan_worker();
+        for (std::thread& th : helpers) th.join();
+        for (auto& pm : t.scans) delete pm.second.scan;     // left over after a failure
+        if (bad.load()) return false;
     }
     {
         std::lock_guard<std::mutex> ls(s->mu_st);
