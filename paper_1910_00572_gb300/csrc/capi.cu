@@ -54,6 +54,8 @@ void* dev_alloc(loc_session* s, size_t bytes) {
 }
 
 void release_all(loc_session* s) {
+    if (s->pinned) cudaFreeHost(s->pinned);
+    s->pinned = nullptr;
     for (void* p : s->owned) {
         if (g_free) g_free(p, (void*)s->stream, g_alloc_ctx);
         else cudaFree(p);
@@ -91,6 +93,10 @@ loc_status sync_and_check(loc_session* h) {
     int status = 0;
     e = cudaMemcpy(&status, &h->sd->status, sizeof(int), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemcpy(status)");
+    return check_status(h, status);
+}
+
+loc_status check_status(loc_session* h, int status) {
     if (status & LOC_DEV_ERR_TIMEOUT) return fail(h, LOC_ERR_TIMEOUT, "device wait timed out");
     if (status & LOC_DEV_ERR_NONFINITE_Z) {
         h->failed = true;
@@ -215,6 +221,12 @@ LOC_API loc_status loc_create(const uint8_t* occ, const loc_params* p, loc_handl
         return fail(nullptr, LOC_ERR_OOM, "device allocation failed");
     }
     s->argmax_val = (float*)(s->argmax_idx + 1);
+    if (cudaMallocHost(&s->pinned, 64) != cudaSuccess) {
+        cudaGetLastError();
+        release_all(s);
+        delete s;
+        return fail(nullptr, LOC_ERR_OOM, "pinned host allocation failed");
+    }
     s->tiled = tiled_ok && p->kernel != LOC_KERNEL_GENERIC;
     if (s->tiled) {
         s->tile_cfg = p->tile > 0 ? p->tile : step_tiled_default_cfg(p->H, p->W, p->K, p->storage);
@@ -232,6 +244,8 @@ LOC_API loc_status loc_create(const uint8_t* occ, const loc_params* p, loc_handl
     init.inv_Z = 1.0f;
     init.reinit = 1;               // the stored tensor reads as uniform over free cells
     cudaError_t e = cudaMemcpyAsync(s->trav, trav.data(), hw, cudaMemcpyHostToDevice, s->stream);
+    if (e == cudaSuccess)   // the argmax pass's arrival counter starts at zero
+        e = cudaMemsetAsync(s->argmax_scratch, 0, argmax_scratch_bytes(s->n), s->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(s->sd, &init, sizeof(init), cudaMemcpyHostToDevice, s->stream);
     if (e == cudaSuccess) e = launch_edge_correction(s->trav, s->corr, p->H, p->W, s->gx, rxy, s->stream);
@@ -653,18 +667,26 @@ LOC_API loc_status loc_argmax(loc_handle h, int* k, int* j, int* i, float* p) {
     cudaError_t e = launch_argmax(h->B[h->cur], h->p.storage, h->trav, h->sd, h->inv_uniform,
                                   h->p.H, h->p.W, h->p.K, h->argmax_scratch, h->argmax_idx,
                                   h->argmax_val, h->stream);
-    struct { long long idx; float val; } res{};
+    // the result and the device status in one round trip, through pinned memory
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(&res, h->argmax_idx, sizeof(long long) + sizeof(float),
-                            cudaMemcpyDeviceToHost, h->stream);
+        e = cudaMemcpyAsync(h->pinned, h->argmax_idx, sizeof(long long) + sizeof(float), cudaMemcpyDeviceToHost,
+                            h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h->pinned + 16, &h->sd->status, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "loc_argmax");
+    long long idx;
+    float val;
+    int status;
+    std::memcpy(&idx, h->pinned, sizeof(idx));
+    std::memcpy(&val, h->pinned + sizeof(long long), sizeof(val));
+    std::memcpy(&status, h->pinned + 16, sizeof(status));
     const long long hw = (long long)h->hw;
-    *k = (int)(res.idx / hw);
-    *j = (int)((res.idx % hw) / h->p.W);
-    *i = (int)(res.idx % h->p.W);
-    *p = res.val;
-    return sync_and_check(h);
+    *k = (int)(idx / hw);
+    *j = (int)((idx % hw) / h->p.W);
+    *i = (int)(idx % h->p.W);
+    *p = val;
+    return check_status(h, status);
 }
 
 LOC_API loc_status loc_set_belief(loc_handle h, const float* b, size_t n) {

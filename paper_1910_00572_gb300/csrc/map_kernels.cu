@@ -102,6 +102,111 @@ __global__ void argmax_partial_kernel(const T* __restrict__ B, const uint8_t* __
     }
 }
 
+// The same over the stored values with V consecutive elements per 16-byte load (n a multiple
+// of V).  Every thread scans its elements in increasing index order, so a strict '>' keeps the
+// lowest index among equal values; threads, warps and CTAs combine with better().
+// The CTA that finishes last combines the per-CTA results (fixed order, so the result does not
+// depend on which CTA is last) and writes the index and the normalised value.
+template <typename T, int V>
+__global__ void __launch_bounds__(NT) argmax_vec_kernel(const T* __restrict__ B, const uint8_t* __restrict__ trav,
+                                                        const SessionDev* sd, float inv_uniform, size_t hw, size_t n,
+                                                        float* __restrict__ pv, long long* __restrict__ pi,
+                                                        unsigned int* counter, long long* out_idx, float* out_val) {
+    static_assert(V * sizeof(T) == 16, "one 16-byte load");
+    __shared__ float sv[NT / 32];
+    __shared__ long long si[NT / 32];
+    float bv = -FLT_MAX;
+    long long bi = (long long)n;
+    const size_t ng = sd->reinit ? 0 : n / V;
+    if (sd->reinit) {                 // the belief reads as uniform over free cells
+        for (size_t q = (size_t)blockIdx.x * NT + threadIdx.x; q < n; q += (size_t)gridDim.x * NT) {
+            const float v = (float)trav[q % hw] * inv_uniform;
+            if (v > bv) {
+                bv = v;
+                bi = (long long)q;
+            }
+        }
+    }
+    for (size_t g = (size_t)blockIdx.x * NT + threadIdx.x; g < ng; g += (size_t)gridDim.x * NT) {
+        union {
+            uint4 u;
+            T x[V];
+        } raw;
+        raw.u = __ldg(reinterpret_cast<const uint4*>(B) + g);
+#pragma unroll
+        for (int e = 0; e < V; ++e) {
+            const float v = Store<T>::ld(&raw.x[e]);
+            if (v > bv) {
+                bv = v;
+                bi = (long long)(g * V + e);
+            }
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const float ov = __shfl_down_sync(0xffffffffu, bv, o);
+        const long long oi = __shfl_down_sync(0xffffffffu, bi, o);
+        if (better(ov, oi, bv, bi)) {
+            bv = ov;
+            bi = oi;
+        }
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) {
+        sv[warp] = bv;
+        si[warp] = bi;
+    }
+    __syncthreads();
+    __shared__ int s_last;
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < NT / 32; ++w)
+            if (better(sv[w], si[w], bv, bi)) {
+                bv = sv[w];
+                bi = si[w];
+            }
+        pv[blockIdx.x] = bv;
+        pi[blockIdx.x] = bi;
+        __threadfence();
+        s_last = atomicAdd(counter, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    bv = -FLT_MAX;
+    bi = LLONG_MAX;
+    for (unsigned int b = threadIdx.x; b < gridDim.x; b += NT) {
+        const float v = ((volatile float*)pv)[b];
+        const long long q = ((volatile long long*)pi)[b];
+        if (better(v, q, bv, bi)) {
+            bv = v;
+            bi = q;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const float ov = __shfl_down_sync(0xffffffffu, bv, o);
+        const long long oi = __shfl_down_sync(0xffffffffu, bi, o);
+        if (better(ov, oi, bv, bi)) {
+            bv = ov;
+            bi = oi;
+        }
+    }
+    __syncthreads();
+    if (lane == 0) {
+        sv[warp] = bv;
+        si[warp] = bi;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < NT / 32; ++w)
+            if (better(sv[w], si[w], bv, bi)) {
+                bv = sv[w];
+                bi = si[w];
+            }
+        *out_idx = bi;
+        *out_val = sd->reinit ? bv : (float)((double)bv / sd->Z);
+        *counter = 0u;
+    }
+}
+
 __global__ void argmax_final_kernel(const float* __restrict__ pv, const long long* __restrict__ pi,
                                     int nb, const SessionDev* sd, long long* out_idx,
                                     float* out_val) {
@@ -226,7 +331,7 @@ cudaError_t launch_read_marginal(const void* B, int storage, const uint8_t* trav
 }
 
 size_t argmax_scratch_bytes(size_t) {
-    return (size_t)kArgmaxBlocks * (sizeof(float) + sizeof(long long));
+    return (size_t)kArgmaxBlocks * (sizeof(float) + sizeof(long long)) + 16;   // + arrival counter
 }
 
 cudaError_t launch_argmax(const void* B, int storage, const uint8_t* trav,
@@ -237,8 +342,19 @@ cudaError_t launch_argmax(const void* B, int storage, const uint8_t* trav,
     float* pv = (float*)(pi + kArgmaxBlocks);
     unsigned int nb = grid_for(n);
     if (nb > kArgmaxBlocks) nb = kArgmaxBlocks;
-    LOC_DISPATCH(storage, (argmax_partial_kernel<T><<<nb, NT, 0, st>>>(
-                              (const T*)B, trav, sd, inv_uniform, hw, n, pv, pi)));
+    const size_t vec = storage == LOC_F32 ? 4 : 8;
+    if (n % vec == 0) {
+        // the stored values order the states like the belief (one positive scale)
+        nb = grid_for(n / vec);
+        if (nb > kArgmaxBlocks) nb = kArgmaxBlocks;
+        unsigned int* counter = reinterpret_cast<unsigned int*>(pv + kArgmaxBlocks);
+        LOC_DISPATCH(storage, (argmax_vec_kernel<T, 16 / sizeof(T)><<<nb, NT, 0, st>>>(
+                                  (const T*)B, trav, sd, inv_uniform, hw, n, pv, pi, counter, out_idx, out_val)));
+        return cudaGetLastError();
+    } else {
+        LOC_DISPATCH(storage, (argmax_partial_kernel<T><<<nb, NT, 0, st>>>(
+                                  (const T*)B, trav, sd, inv_uniform, hw, n, pv, pi)));
+    }
     argmax_final_kernel<<<1, NT, 0, st>>>(pv, pi, (int)nb, sd, out_idx, out_val);
     return cudaGetLastError();
 }

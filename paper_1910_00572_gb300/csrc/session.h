@@ -30,6 +30,7 @@ struct loc_session {
     void* argmax_scratch = nullptr;
     long long* argmax_idx = nullptr;
     float* argmax_val = nullptr;
+    unsigned char* pinned = nullptr;   // 64 bytes of pinned host memory for small readbacks
     // LIDAR sample update scratch (allocated on first use)
     bool lidar_ready = false;
     int cap = 0;                   // capacity of the sample list
@@ -71,6 +72,8 @@ loc_status check_live(loc_session* h);
 int radius(double sigma, int given);
 // Synchronise the session's stream and turn device-side error flags into a status.
 loc_status sync_and_check(loc_session* h);
+// The status for device-side error flags already read back.
+loc_status check_status(loc_session* h, int status);
 
 // Odometry bookkeeping of Section III-A (Eq. 2-3): accumulate an increment and report whether
 // the gate lets a propagation through; the per-bin shift table of the accumulated

@@ -272,3 +272,32 @@ def test_office512_one_step_replay_sampled():
     assert err.max() <= ABS_TOL and err.max() <= REL_TOL * b_in.max(), err.max()
     # Z is the FP64 sum of the stored tensor (a property at any size)
     assert abs(got.astype(np.float64).sum() - 1.0) < 1e-5
+
+
+@pytest.mark.parametrize("storage", ["f32", "bf16", "f16"])
+@pytest.mark.parametrize("H,W,K", [(16, 24, 8), (7, 9, 3)])
+def test_argmax_ties_restart_and_ragged_sizes(storage, H, W, K):
+    """loc_argmax: the most probable state with ties going to the lowest [K][H][W] index, the
+    uniform restart state (first free cell of bin 0), and element counts that are not a
+    multiple of the vector width (7 x 9 x 3)."""
+    occ = np.zeros((H, W), np.uint8)
+    occ[0, :2] = 1                                    # the first free cell is (0, 0, 2)
+    p = loc.loc_params_default(H=H, W=W, K=K, cell_m=0.1, storage=storage)
+    h = loc.loc_create(occ, p)
+    try:
+        k, j, i, pr = loc.loc_argmax(h)                # restart state: uniform over free cells
+        n_free = int((occ == 0).sum())
+        assert (k, j, i) == (0, 0, 2)
+        assert abs(pr - 1.0 / (K * n_free)) <= 1e-6 / (K * n_free)
+        b = np.full((K, H, W), 0.25, np.float32)
+        b[:, occ != 0] = 0.0
+        peaks = [(K - 1, H - 1, W - 1), (1, 2, 3), (1, 2, 5), (K // 2, 1, 0)]
+        for q in peaks:
+            b[q] = 2.0                                 # equal maxima: the lowest index wins
+        loc.loc_set_belief(h, b)
+        got = loc.loc_argmax(h)
+        assert got[:3] == tuple(int(x) for x in np.unravel_index(np.argmax(b), b.shape))   # first of the ties
+        flat = loc.loc_belief(h).reshape(-1)
+        assert abs(got[3] - flat.max()) <= 1e-6 * flat.max()
+    finally:
+        loc.loc_destroy(h)
