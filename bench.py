@@ -361,10 +361,12 @@ def run_batch64(args, wl, ws, rank, local):
     odo = np.stack([s["odom"] for s in sess], axis=1)          # [t][session][3]
     res = {}
     clk_summary = None
-    for storage in ("f32", "bf16"):
+    storages = ("f32", "bf16") if args.storage is None else (args.storage,)
+    for storage in storages:
         hs = [loc.loc_create(s["occ"], session_params(loc, s, storage)) for s in sess]
         try:
-            b = loc.loc_batch_create(hs, tile=0, use_graph=True)
+            b = loc.loc_batch_create(hs, tile=args.tile if 0 < args.tile <= loc.LOC_BATCH_CONFIGS else 0,
+                                     use_graph=True)
             info = loc.loc_batch_info(b)
             try:
                 def batch_tick(t):
@@ -392,7 +394,7 @@ def run_batch64(args, wl, ws, rank, local):
                     out[name] = {"ms_per_tick": total / steps * 1e3, "value": cells * ws * steps / total,
                                  "p50_tick_ms": float(np.percentile(ms, 50)),
                                  "p99_tick_ms": float(np.percentile(ms, 99))}
-                    if storage == "bf16" and name == "batched":
+                    if name == "batched":
                         clk_summary = clk.summary()
                 loc.loc_batch_sync(b)
                 # end to end: odometry from host arrays in, every session's pose estimate out
@@ -417,13 +419,15 @@ def run_batch64(args, wl, ws, rank, local):
     if rank != 0:
         return
     peak, src = read_peak()
-    bf = res["bf16"]
-    alg_bytes = cells * 2 * 2 + hw * 5
+    head = "bf16" if "bf16" in res else storages[0]
+    bf = res[head]
+    elem = ELEM[head]
+    alg_bytes = cells * 2 * elem + hw * 5
     achieved = alg_bytes / (bf["batched"]["ms_per_tick"] / 1e3) / 1e9
     line = {
         "metric": METRIC, "value": bf["batched"]["value"], "unit": UNIT, "n_gpus": ws, "steps": steps,
         "warmup": args.warmup, "ms_per_step": bf["batched"]["ms_per_tick"], "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": head, "data": "synthetic",
         "config": {"workload": "batch64", "sessions": len(sess), "cells_per_tick": cells,
                    "sides": sorted({s["H"] for s in sess}), "K": sorted({s["K"] for s in sess}),
                    "global_batch": len(sess), "parallelism": f"replicas{ws}" if ws > 1 else "single",
