@@ -101,8 +101,9 @@ struct PThread {
     int r0, cp;                        // P-pass: first row, pair column
 };
 
+// tid: the thread's index among the S/X-pass threads; ptid: among the P-pass threads.
 template <typename T, typename C>
-__device__ __forceinline__ PThread<T, C> pthread_coords(int tid) {
+__device__ __forceinline__ PThread<T, C> pthread_coords(int tid, int ptid) {
     PThread<T, C> t;
     t.s_on = tid < C::S_ITEMS;
     const int su = tid % (SPAIRS / 4), sg = tid / (SPAIRS / 4);
@@ -112,15 +113,15 @@ __device__ __forceinline__ PThread<T, C> pthread_coords(int tid) {
     t.x_on = tid < C::X_ITEMS;
     t.x_row = tid % C::XR;             // consecutive threads take consecutive rows
     t.x_pair = C::XP * (tid / C::XR);
-    t.cp = tid % 32;
-    t.r0 = C::MR * (tid / 32);
+    t.cp = ptid % 32;
+    t.r0 = C::MR * (ptid / 32);
     return t;
 }
 
 // S-pass of one item: SR rows of 4 S pairs.  XO = xo mod 4 of the plane; xbase = xo - XO.
 template <typename T, typename C, int XO>
-__device__ __forceinline__ void s_pass(const T* raw, PSmem<T, C>& sm, const PThread<T, C>& th, int xbase,
-                                       float fx, float fy) {
+__device__ __forceinline__ void s_pass(const T* raw, const float (*mk)[SPW], float (*S)[SPW], const PThread<T, C>& th,
+                                       int xbase, float fx, float fy) {
     if (!th.s_on) return;
     const f2 fy2 = pk(fy, fy), gy2 = pk(1.0f - fy, 1.0f - fy);
     const T* rp = raw + th.s_raw + xbase;
@@ -137,13 +138,13 @@ __device__ __forceinline__ void s_pass(const T* raw, PSmem<T, C>& sm, const PThr
                         fmaf(fx, vb[XO + k + 1] - vb[XO + k], vb[XO + k]));
         if (r > 0) {
             const int y = th.s_row + r - 1;
-            const float4 m0 = *reinterpret_cast<const float4*>(&sm.mk[y][2 * th.s_pair]);
-            const float4 m1 = *reinterpret_cast<const float4*>(&sm.mk[y][2 * th.s_pair + 4]);
+            const float4 m0 = *reinterpret_cast<const float4*>(&mk[y][2 * th.s_pair]);
+            const float4 m1 = *reinterpret_cast<const float4*>(&mk[y][2 * th.s_pair + 4]);
             const f2 mm[4] = {pk(m0.x, m0.y), pk(m0.z, m0.w), pk(m1.x, m1.y), pk(m1.z, m1.w)};
             f2 o[4];
 #pragma unroll
             for (int k = 0; k < 4; ++k) o[k] = fmul2(mm[k], ffma2(fy2, cur[k], fmul2(gy2, prev[k])));
-            f2* dst = reinterpret_cast<f2*>(&sm.S[y][2 * th.s_pair]);
+            f2* dst = reinterpret_cast<f2*>(&S[y][2 * th.s_pair]);
             reinterpret_cast<ulonglong2*>(dst)[0] = make_ulonglong2(o[0], o[1]);
             reinterpret_cast<ulonglong2*>(dst)[1] = make_ulonglong2(o[2], o[3]);
         }
@@ -154,18 +155,19 @@ __device__ __forceinline__ void s_pass(const T* raw, PSmem<T, C>& sm, const PThr
 
 // X-pass of one item: XP X pairs of one row.
 template <typename T, typename C>
-__device__ __forceinline__ void x_pass(PSmem<T, C>& sm, const PThread<T, C>& th, const Taps2& tp) {
+__device__ __forceinline__ void x_pass(const float (*S)[SPW], float (*X)[XPW], const PThread<T, C>& th,
+                                       const Taps2& tp) {
     if (!th.x_on) return;
     constexpr int NS = C::XP + 4;
     f2 s[NS];
-    const ulonglong2* src = reinterpret_cast<const ulonglong2*>(&sm.S[th.x_row][2 * th.x_pair]);
+    const ulonglong2* src = reinterpret_cast<const ulonglong2*>(&S[th.x_row][2 * th.x_pair]);
 #pragma unroll
     for (int k = 0; k < NS / 2; ++k) {
         const ulonglong2 v = src[k];
         s[2 * k] = v.x;
         s[2 * k + 1] = v.y;
     }
-    ulonglong2* dst = reinterpret_cast<ulonglong2*>(&sm.X[th.x_row][2 * th.x_pair]);
+    ulonglong2* dst = reinterpret_cast<ulonglong2*>(&X[th.x_row][2 * th.x_pair]);
 #pragma unroll
     for (int k = 0; k < C::XP; k += 2) {
         f2 o[2];
@@ -181,7 +183,8 @@ __device__ __forceinline__ void x_pass(PSmem<T, C>& sm, const PThread<T, C>& th,
 // P-pass for plane p with the newest ring slot PH = p mod 7: y blur of the thread's MR rows of
 // its pair column into the theta ring, then (from p = 6 on) output plane p - 3.
 template <typename T, typename C, int PH>
-__device__ __forceinline__ void p_pass(PSmem<T, C>& sm, const PThread<T, C>& th, const TileOut& a, const Taps2& tp,
+__device__ __forceinline__ void p_pass(const float (*X)[XPW], float (*wrap)[C::TH][TW], const PThread<T, C>& th,
+                                       const TileOut& a, const Taps2& tp,
                                        f2 (&ring)[RING][C::MR], const f2 (&cs)[C::MR], int p, T* out_tile,
                                        size_t plane, uint32_t h_tile, int rows, bool ok0, bool ok1, KahanF& acc) {
     constexpr int MR = C::MR;
@@ -189,18 +192,18 @@ __device__ __forceinline__ void p_pass(PSmem<T, C>& sm, const PThread<T, C>& th,
     if (p < K) {
         f2 x[MR + 4];
 #pragma unroll
-        for (int q = 0; q < MR + 4; ++q) x[q] = *reinterpret_cast<const f2*>(&sm.X[th.r0 + q][2 * th.cp]);
+        for (int q = 0; q < MR + 4; ++q) x[q] = *reinterpret_cast<const f2*>(&X[th.r0 + q][2 * th.cp]);
 #pragma unroll
         for (int rr = 0; rr < MR; ++rr)
             ring[PH][rr] = ffma2(tp.g2, fadd2(x[rr], x[rr + 4]),
                                  ffma2(tp.g1, fadd2(x[rr + 1], x[rr + 3]), fmul2(tp.g0, x[rr + 2])));
         if (p < NWRAP) {
 #pragma unroll
-            for (int rr = 0; rr < MR; ++rr) *reinterpret_cast<f2*>(&sm.wrap[p][th.r0 + rr][2 * th.cp]) = ring[PH][rr];
+            for (int rr = 0; rr < MR; ++rr) *reinterpret_cast<f2*>(&wrap[p][th.r0 + rr][2 * th.cp]) = ring[PH][rr];
         }
     } else {
 #pragma unroll
-        for (int rr = 0; rr < MR; ++rr) ring[PH][rr] = *reinterpret_cast<const f2*>(&sm.wrap[p - K][th.r0 + rr][2 * th.cp]);
+        for (int rr = 0; rr < MR; ++rr) ring[PH][rr] = *reinterpret_cast<const f2*>(&wrap[p - K][th.r0 + rr][2 * th.cp]);
     }
     if (p >= 2 * RT) {
         int o = p - RT;
@@ -236,7 +239,7 @@ __device__ __forceinline__ bool run_tile(PSmem<T, C>& sm, const TileJob& j, unsi
     const int H = j.o.H, W = j.o.W, K = j.o.K;
     const int ty0 = j.ty0, tx0 = j.tx0;
     const int reinit = j.reinit;
-    const PThread<T, C> th = pthread_coords<T, C>(tid);
+    const PThread<T, C> th = pthread_coords<T, C>(tid, tid);
 
     // mask pairs over the halo rows: mk[y][2s] = M(ty0-2+y, tx0+s-2), mk[y][2s+1] = M(.., tx0+s+30)
     for (int q = tid; q < XR * SPAIRS * 2; q += NT) {
@@ -319,10 +322,10 @@ __device__ __forceinline__ bool run_tile(PSmem<T, C>& sm, const TileJob& j, unsi
             if (!failed) {
                 const int xb = xo & ~3;
                 switch (xo & 3) {
-                    case 0: s_pass<T, C, 0>(sm.raw[stage], sm, th, xb, s.fx, s.fy); break;
-                    case 1: s_pass<T, C, 1>(sm.raw[stage], sm, th, xb, s.fx, s.fy); break;
-                    case 2: s_pass<T, C, 2>(sm.raw[stage], sm, th, xb, s.fx, s.fy); break;
-                    default: s_pass<T, C, 3>(sm.raw[stage], sm, th, xb, s.fx, s.fy); break;
+                    case 0: s_pass<T, C, 0>(sm.raw[stage], sm.mk, sm.S, th, xb, s.fx, s.fy); break;
+                    case 1: s_pass<T, C, 1>(sm.raw[stage], sm.mk, sm.S, th, xb, s.fx, s.fy); break;
+                    case 2: s_pass<T, C, 2>(sm.raw[stage], sm.mk, sm.S, th, xb, s.fx, s.fy); break;
+                    default: s_pass<T, C, 3>(sm.raw[stage], sm.mk, sm.S, th, xb, s.fx, s.fy); break;
                 }
             }
             if (__syncthreads_or(failed)) {
@@ -336,17 +339,17 @@ __device__ __forceinline__ bool run_tile(PSmem<T, C>& sm, const TileJob& j, unsi
                 }
                 next_issue = p + NSTAGE + 1;
             }
-            x_pass<T, C>(sm, th, tp);
+            x_pass<T, C>(sm.S, sm.X, th, tp);
             __syncthreads();
         }
         switch (p % RING) {
-            case 0: p_pass<T, C, 0>(sm, th, j.o, tp, ring, cs, p, out_tile, plane, h_tile, rows, ok0, ok1, acc); break;
-            case 1: p_pass<T, C, 1>(sm, th, j.o, tp, ring, cs, p, out_tile, plane, h_tile, rows, ok0, ok1, acc); break;
-            case 2: p_pass<T, C, 2>(sm, th, j.o, tp, ring, cs, p, out_tile, plane, h_tile, rows, ok0, ok1, acc); break;
-            case 3: p_pass<T, C, 3>(sm, th, j.o, tp, ring, cs, p, out_tile, plane, h_tile, rows, ok0, ok1, acc); break;
-            case 4: p_pass<T, C, 4>(sm, th, j.o, tp, ring, cs, p, out_tile, plane, h_tile, rows, ok0, ok1, acc); break;
-            case 5: p_pass<T, C, 5>(sm, th, j.o, tp, ring, cs, p, out_tile, plane, h_tile, rows, ok0, ok1, acc); break;
-            default: p_pass<T, C, 6>(sm, th, j.o, tp, ring, cs, p, out_tile, plane, h_tile, rows, ok0, ok1, acc); break;
+            case 0: p_pass<T, C, 0>(sm.X, sm.wrap, th, j.o, tp, ring, cs, p, out_tile, plane, h_tile, rows, ok0, ok1, acc); break;
+            case 1: p_pass<T, C, 1>(sm.X, sm.wrap, th, j.o, tp, ring, cs, p, out_tile, plane, h_tile, rows, ok0, ok1, acc); break;
+            case 2: p_pass<T, C, 2>(sm.X, sm.wrap, th, j.o, tp, ring, cs, p, out_tile, plane, h_tile, rows, ok0, ok1, acc); break;
+            case 3: p_pass<T, C, 3>(sm.X, sm.wrap, th, j.o, tp, ring, cs, p, out_tile, plane, h_tile, rows, ok0, ok1, acc); break;
+            case 4: p_pass<T, C, 4>(sm.X, sm.wrap, th, j.o, tp, ring, cs, p, out_tile, plane, h_tile, rows, ok0, ok1, acc); break;
+            case 5: p_pass<T, C, 5>(sm.X, sm.wrap, th, j.o, tp, ring, cs, p, out_tile, plane, h_tile, rows, ok0, ok1, acc); break;
+            default: p_pass<T, C, 6>(sm.X, sm.wrap, th, j.o, tp, ring, cs, p, out_tile, plane, h_tile, rows, ok0, ok1, acc); break;
         }
     }
     p_stop = p;
