@@ -105,16 +105,18 @@ __global__ void __launch_bounds__(C::NT, C::MINB) step_tiled_kernel(const __grid
 __device__ __forceinline__ void bar_arrive(unsigned long long* b) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(b)) : "memory");
 }
+template <int NP>
 __device__ __forceinline__ void producers_sync() {       // named barrier 1, producer threads only
-    asm volatile("bar.sync 1, 128;" ::: "memory");
+    asm volatile("bar.sync 1, %0;" ::"n"(NP) : "memory");
 }
 
 // TH tile rows (consumers: TH/4 rows x 2 columns each), SR S-pass rows per item, XW X-pass
 // columns per item, NSTAGE raw stages, MINB CTAs per SM asked of the compiler.
-template <int TH_, int SR_, int XW_, int NSTAGE_, int MINB_>
+template <int TH_, int SR_, int XW_, int NSTAGE_, int MINB_, int NP_ = 128>
 struct WsCfg {
     static constexpr int TH = TH_, SR = SR_, XW = XW_, NSTAGE = NSTAGE_, MINB = MINB_;
-    static constexpr int NP = 128, NC = 128, NT = NP + NC;
+    static constexpr int NP = NP_, NC = 128, NT = NP + NC;
+    static_assert(NP % 32 == 0, "whole producer warps");
     static constexpr int MR = TH * TW / (2 * NC);          // consumer rows per thread
     static constexpr int XR = TH + 2 * R;
     static constexpr int RAW_H = XR + 1;
@@ -202,7 +204,7 @@ __global__ void __launch_bounds__(C::NT, C::MINB) step_ws_kernel(const __grid_co
                     if (gy >= 0 && gy < H && gx >= 0 && gx < W) v = (float)a.trav[(size_t)gy * W + gx];
                     sm.raw[stage][y * BW + c] = T(v);
                 }
-                producers_sync();
+                producers_sync<NP>();
             } else if (!bar_wait(&sm.tma[stage], (uint32_t)((p / NSTAGE) & 1))) {
                 sm.fail_a = 1;
             }
@@ -215,7 +217,7 @@ __global__ void __launch_bounds__(C::NT, C::MINB) step_ws_kernel(const __grid_co
                     default: s_pass<T, C, 3>(sm.raw[stage], sm.mk, sm.S, t, xb, s.fx, s.fy); break;
                 }
             }
-            producers_sync();                        // S complete; raw stage free
+            producers_sync<NP>();                        // S complete; raw stage free
             if (sm.fail_a) break;                    // the same decision in every producer
             if (!reinit && p + NSTAGE < K) {
                 if (t == 0) {
@@ -226,11 +228,11 @@ __global__ void __launch_bounds__(C::NT, C::MINB) step_ws_kernel(const __grid_co
             }
             const int b = p & 1;
             if (p >= 2 && !bar_wait(&sm.empty[b], (uint32_t)(((p - 2) >> 1) & 1))) sm.fail_b = 1;
-            producers_sync();
+            producers_sync<NP>();
             if (sm.fail_b) break;
             x_pass<C>(sm.S, sm.X[b], t, a.g0, a.g1, a.g2);
             bar_arrive(&sm.full[b]);                 // X[b] of plane p is ready
-            producers_sync();                        // the X-pass has read S: S may be rewritten
+            producers_sync<NP>();                        // the X-pass has read S: S may be rewritten
             p_done = p + 1;
         }
     } else {
