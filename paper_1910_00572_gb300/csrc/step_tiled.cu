@@ -112,10 +112,10 @@ __device__ __forceinline__ void producers_sync() {       // named barrier 1, pro
 
 // TH tile rows (consumers: TH/4 rows x 2 columns each), SR S-pass rows per item, XW X-pass
 // columns per item, NSTAGE raw stages, MINB CTAs per SM asked of the compiler.
-template <int TH_, int SR_, int XW_, int NSTAGE_, int MINB_, int NP_ = 128>
+template <int TH_, int SR_, int XW_, int NSTAGE_, int MINB_, int NP_ = 128, int NC_ = 128>
 struct WsCfg {
     static constexpr int TH = TH_, SR = SR_, XW = XW_, NSTAGE = NSTAGE_, MINB = MINB_;
-    static constexpr int NP = NP_, NC = 128, NT = NP + NC;
+    static constexpr int NP = NP_, NC = NC_, NT = NP + NC;
     static_assert(NP % 32 == 0, "whole producer warps");
     static constexpr int MR = TH * TW / (2 * NC);          // consumer rows per thread
     static constexpr int XR = TH + 2 * R;
