@@ -217,3 +217,55 @@ def test_batch_rejects_bad_groups():
     finally:
         for h in (a, c, g):
             loc.loc_destroy(h)
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("storage", ["f32", "bf16"])
+def test_batch64_full_size_sampled_against_oracle(storage):
+    """The 64-session workload at full size (0.95 G cells), one batched tick in the launch
+    configuration the benchmark times (autotuned tile, CUDA graph): on four sessions (the two
+    largest and two smaller, different K), sampled states are recomputed one by one from the
+    definitions by the oracle from the same input belief.  FP32: 1e-6; BF16: the propagated
+    value of the stored input within the stochastic-rounding error of the output."""
+    from oracle.odometry import Odometry
+    wl = workloads.get("batch64")
+    sess = workloads.make_sessions(wl, 2)
+    order = sorted(range(len(sess)), key=lambda q: -sess[q]["H"] * sess[q]["W"] * sess[q]["K"])
+    check = [order[0], order[1], order[len(order) // 2], order[-1]]
+    hs = [loc.loc_create(s["occ"], loc.loc_params_default(H=s["H"], W=s["W"], K=s["K"], cell_m=s["cell"],
+                                                          storage=storage)) for s in sess]
+    try:
+        for q in check:
+            loc.loc_set_belief(hs[q], fields.belief_like(sess[q]["occ"], sess[q]["K"], seed=q, dtype=np.float32))
+        before = {q: loc.loc_belief(hs[q]).astype(np.float64) for q in check}
+        b = loc.loc_batch_create(hs, tile=0, use_graph=True)
+        try:
+            odo = np.stack([s["odom"][0] for s in sess])
+            assert loc.loc_batch_step(b, odo[:, 0], odo[:, 1], odo[:, 2]) == len(sess)
+            loc.loc_batch_sync(b)
+        finally:
+            loc.loc_batch_destroy(b)
+        for q in check:
+            s = sess[q]
+            K, H, W = s["K"], s["H"], s["W"]
+            got = loc.loc_belief(hs[q]).astype(np.float64)
+            Z = loc.loc_stats(hs[q])["last_Z"]
+            od = Odometry(K, s["cell"])
+            od.add(*s["odom"][0])
+            g = F.motion_kernel(wl["sigma_xy_cells"], wl["sigma_theta_bins"])
+            rng = np.random.default_rng(q)
+            idx = [(int(rng.integers(K)), int(rng.integers(H)), int(rng.integers(W))) for _ in range(400)]
+            for flat in np.argsort(before[q].reshape(-1))[-10:]:
+                k, rem = divmod(int(flat), H * W)
+                idx.append((k, rem // W, rem % W))
+            T = F.propagate_at(before[q], F.traversability(s["occ"]), od.shifts(), g, idx)
+            gotT = np.array([got[k, j, i] for (k, j, i) in idx]) * Z
+            err = np.abs(gotT - T).max()
+            if storage == "f32":
+                assert err <= ABS_TOL and err <= REL_TOL * before[q].max(), (q, err)
+            else:
+                assert err <= 2.0 ** -7 * T.max() + 1e-9, (q, err)       # one BF16 rounding step
+            assert abs(got.sum() - 1.0) < 1e-4
+    finally:
+        for h in hs:
+            loc.loc_destroy(h)

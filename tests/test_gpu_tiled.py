@@ -76,6 +76,26 @@ def test_tiled_matches_oracle_and_generic(H, W, K, mot, tile):
         loc.loc_destroy(hg)
 
 
+@pytest.mark.parametrize("tile", [1, 3, 6, 8])
+def test_largest_theta_count(tile):
+    """K = LOC_MAX_K (256 bins): the theta ring and the wrap planes at the largest size."""
+    H, W, K = 20, 72, 256
+    rng = np.random.default_rng(256)
+    occ = (rng.random((H, W)) < 0.1).astype(np.uint8)
+    b = fields.belief_like(occ, K, seed=3, dtype=np.float32)
+    h = make(occ, K, 0.05, tile=tile)
+    ref = F.Filter(occ, K, 0.05)
+    ref.B = b.astype(np.float64) / b.astype(np.float64).sum()
+    try:
+        loc.loc_set_belief(h, b)
+        for u, v, w in [(0.031, -0.012, 0.07), (-0.02, 0.044, -0.03)]:
+            loc.loc_step(h, u, v, w)
+            ref.step(u, v, w)
+            close(loc.loc_belief(h), ref.B)
+    finally:
+        loc.loc_destroy(h)
+
+
 def test_tiled_first_step_reads_uniform_and_walls_hold_no_mass():
     occ = floorplan.rooms_map(9, size=64)
     h = make(occ, 16, 0.1)
