@@ -13,6 +13,9 @@ What is here, each function citing the passage it follows:
                 Eq. 5-7, mask, edge normalisation of Eq. 8), the normaliser eta of Eq. 9 --
                 FP64, direct sums (the 3-D convolution is the plain triple sum with the joint
                 kernel exp(-1/2 d^T Sigma^-1 d), not a separable pass).
+* ``aniso``     Eq. 5-6 with sigma_x != sigma_y: the motion kernel rotated to each output
+                channel's heading, the per-channel 3-D convolution and edge correction --
+                FP64, direct sums.
 * ``readout``   belief map (max over channels) and the estimate (its argmax), Section III-A.3.
 * ``lidar``     Section III-B: Floyd-Steinberg sample selection (III-B.1), the expected range
                 of a state by grid ray casting, the Gaussian range likelihood and the Eq. 9
