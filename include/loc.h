@@ -76,6 +76,14 @@ typedef struct {
     int kernel;                /* LOC_KERNEL_AUTO, or force LOC_KERNEL_GENERIC / LOC_KERNEL_TILED */
     int tile;                  /* tiled kernel: 0 picks a tile configuration for the grid,
                                   1 .. LOC_TILE_CONFIGS forces one */
+    double sigma_cross_cells;  /* anisotropic motion noise (Eq. 6, sigma_x != sigma_y): > 0
+                                  sets the sigma across each bin's heading, sigma_xy_cells is
+                                  then the sigma along it; the x/y kernel of bin k is rotated
+                                  to its heading 2 pi k / K + theta_t, and the default radius is
+                                  ceil(3 max(sigma_xy, sigma_cross)).  0 (default) or equal to
+                                  sigma_xy_cells: isotropic.  Anisotropic sessions take the
+                                  generic-kernel path (kernel must be AUTO or GENERIC) and
+                                  cannot join a batch. */
 } loc_params;
 
 #define LOC_TILE_CONFIGS 12    /* tile rows x 64 columns, threads: 1: 32 (256), 2: 16 (256),
@@ -191,7 +199,8 @@ loc_status loc_stats(loc_handle h, double* theta_t, double* last_Z, double* logs
  *              (Alg. 1 lines 3-7 with the edge correction of Eq. 8);
  *   z_out_dev  device double, receives Z = sum of b_out (the Eq. 9 normaliser);
  *   dx_m, dy_m translation in metres in the frame of bin 0 (bin k moves by R(2 pi k / K)).
- * From p it uses H, W, K, cell_m, the sigmas and radii and stream; storage must be LOC_F32.
+ * From p it uses H, W, K, cell_m, the sigmas and radii and stream; storage must be LOC_F32
+ * and the noise isotropic (sigma_cross_cells 0 or equal to sigma_xy_cells).
  * The only other memory it touches is a 64 KiB + 256 B scratch array compiled into the
  * library, which every GPU that loads the library keeps until the process exits.  That
  * bounds the grid: ceil(W / 32) * ceil(H / 16) must be <= 8192 (e.g. 2048 x 2048 cells);

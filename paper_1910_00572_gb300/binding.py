@@ -59,7 +59,7 @@ class loc_params(ctypes.Structure):
                 ("r_theta", ctypes.c_int), ("min_shift_cells", ctypes.c_double),
                 ("storage", ctypes.c_int), ("n_samples", ctypes.c_int),
                 ("stream", ctypes.c_void_p), ("kernel", ctypes.c_int),
-                ("tile", ctypes.c_int)]
+                ("tile", ctypes.c_int), ("sigma_cross_cells", ctypes.c_double)]
 
 
 class loc_server_params(ctypes.Structure):

@@ -208,7 +208,7 @@ std::string batch_check(loc_session* const* sessions, int n) {
         if (!h) return "a session is null";
         if (h->failed) return "a session failed earlier: " + h->err;
         if (!step_tiled_eligible(h->p.H, h->p.W, h->p.K, h->r_xy, h->r_th, h->p.storage) ||
-            h->p.kernel == LOC_KERNEL_GENERIC)
+            h->p.kernel == LOC_KERNEL_GENERIC || h->aniso)
             return "batched sessions need the tiled kernel (radii 2/3, K >= 8, aligned W)";
         if (h->p.storage != sessions[0]->p.storage || h->stream != sessions[0]->stream || h->device != dev)
             return "sessions of a batch share one storage type, stream and device";

@@ -120,6 +120,7 @@ LOC_API void loc_params_default(loc_params* p) {
     p->stream = nullptr;
     p->kernel = LOC_KERNEL_AUTO;
     p->tile = 0;
+    p->sigma_cross_cells = 0.0;
 }
 
 LOC_API void loc_set_allocator(loc_alloc_fn alloc, loc_free_fn release, void* ctx) {
@@ -168,13 +169,22 @@ LOC_API loc_status loc_create(const uint8_t* occ, const loc_params* p, loc_handl
         return fail(nullptr, LOC_ERR_INVALID_ARG, "unknown storage type");
     if (!(p->min_shift_cells >= 0.0) || !std::isfinite(p->min_shift_cells))
         return fail(nullptr, LOC_ERR_INVALID_ARG, "min_shift_cells must be finite and >= 0");
-    const int rxy = radius(p->sigma_xy_cells, p->r_xy), rth = radius(p->sigma_theta_bins, p->r_theta);
+    if (!(p->sigma_cross_cells >= 0.0) || !std::isfinite(p->sigma_cross_cells))
+        return fail(nullptr, LOC_ERR_INVALID_ARG, "sigma_cross_cells must be finite and >= 0");
+    // Eq. 6 with sigma_x != sigma_y: the x/y kernel of each bin is rotated to its heading
+    const bool aniso = p->sigma_cross_cells > 0.0 && p->sigma_cross_cells != p->sigma_xy_cells;
+    if (aniso && !(p->sigma_xy_cells > 0.0))
+        return fail(nullptr, LOC_ERR_INVALID_ARG, "anisotropic noise needs sigma_xy_cells > 0");
+    const int rxy = radius(aniso ? std::max(p->sigma_xy_cells, p->sigma_cross_cells) : p->sigma_xy_cells, p->r_xy);
+    const int rth = radius(p->sigma_theta_bins, p->r_theta);
     if (rxy > LOC_MAX_R_XY || rth > LOC_MAX_R_THETA)
         return fail(nullptr, LOC_ERR_INVALID_ARG, "kernel radius above LOC_MAX_R_XY / LOC_MAX_R_THETA");
     if (p->n_samples < 0) return fail(nullptr, LOC_ERR_INVALID_ARG, "n_samples must be >= 0");
     if (p->kernel < LOC_KERNEL_AUTO || p->kernel > LOC_KERNEL_TILED)
         return fail(nullptr, LOC_ERR_INVALID_ARG, "unknown kernel selection");
-    const bool tiled_ok = step_tiled_eligible(p->H, p->W, p->K, rxy, rth, p->storage);
+    if (aniso && p->kernel == LOC_KERNEL_TILED)
+        return fail(nullptr, LOC_ERR_INVALID_ARG, "anisotropic noise runs on the generic kernel path");
+    const bool tiled_ok = !aniso && step_tiled_eligible(p->H, p->W, p->K, rxy, rth, p->storage);
     if (p->tile < 0 || p->tile > step_tiled_num_cfgs())
         return fail(nullptr, LOC_ERR_INVALID_ARG, "tile configuration out of range");
     if (p->kernel == LOC_KERNEL_TILED && !tiled_ok)
@@ -192,6 +202,7 @@ LOC_API loc_status loc_create(const uint8_t* occ, const loc_params* p, loc_handl
     loc_session* s = new (std::nothrow) loc_session();
     if (!s) return fail(nullptr, LOC_ERR_OOM, "host allocation failed");
     s->p = *p;
+    s->aniso = aniso;
     s->r_xy = rxy;
     s->r_th = rth;
     taps(p->sigma_xy_cells, rxy, s->gx);
@@ -335,8 +346,20 @@ LOC_API loc_status loc_step(loc_handle h, double u, double v, double w) {
     std::memcpy(a.gx, h->gx, sizeof(a.gx));
     std::memcpy(a.gt, h->gt, sizeof(a.gt));
     shift_table(h, a.sh);
-    cudaError_t e = h->tiled ? launch_step_tiled(a, h->tmap[h->cur], h->p.storage, h->tile_cfg, h->stream)
-                             : launch_step(a, h->p.storage, h->stream);
+    cudaError_t e;
+    if (h->aniso) {
+        // channel k's heading 2 pi k / K + theta_t, theta_t reduced to [0, 2 pi) in FP64
+        double th = std::fmod(h->theta, 2.0 * M_PI);
+        if (th < 0.0) th += 2.0 * M_PI;
+        a.phi0 = (float)th;
+        a.dphi = (float)(2.0 * M_PI / a.K);
+        a.sigma_a = (float)h->p.sigma_xy_cells;
+        a.sigma_c = (float)h->p.sigma_cross_cells;
+        e = launch_step_aniso(a, h->p.storage, h->stream);
+    } else {
+        e = h->tiled ? launch_step_tiled(a, h->tmap[h->cur], h->p.storage, h->tile_cfg, h->stream)
+                     : launch_step(a, h->p.storage, h->stream);
+    }
     if (e != cudaSuccess) return cuda_fail(h, e, "step launch");
     step_done(h);
     return LOC_OK;

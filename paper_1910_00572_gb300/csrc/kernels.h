@@ -15,6 +15,10 @@ constexpr int kGenTH = 16, kGenTW = 32;
 // `partials` must hold step_num_blocks(H, W) doubles.
 cudaError_t launch_step(const StepArgs& a, int storage, cudaStream_t st);
 unsigned int step_num_blocks(int H, int W);
+// The same with anisotropic motion noise (Eq. 5-6, sigma_x != sigma_y): a.phi0, a.dphi,
+// a.sigma_a, a.sigma_c give channel k's rotated x/y kernel; a.gx is unused.  Same grid and
+// partials as launch_step.
+cudaError_t launch_step_aniso(const StepArgs& a, int storage, cudaStream_t st);
 
 // Tiled TMA-pipelined propagation for the default kernel radii (x/y 2, theta 3).  Tile
 // configurations are numbered 1 .. step_tiled_num_cfgs(); each needs its own tensor map.

@@ -65,6 +65,9 @@ struct StepArgs {
     int r_xy, r_th;
     float gx[2 * LOC_MAX_R_XY + 1];     // x and y taps (isotropic), normalised
     float gt[2 * LOC_MAX_R_THETA + 1];  // theta taps, normalised
+    // anisotropic motion noise (step_aniso.cu only): channel k's heading is phi0 + dphi * k,
+    // sigma_a along it and sigma_c across it (cells)
+    float phi0, dphi, sigma_a, sigma_c;
     Shift sh[LOC_MAX_K];
 };
 

@@ -188,6 +188,8 @@ LOC_API loc_status loc_propagate_noalloc(const loc_params* p, const uint8_t* occ
         return noalloc_fail(LOC_ERR_INVALID_ARG, "cell_m and the translation must be finite, cell_m > 0");
     if (!(p->sigma_xy_cells >= 0.0) || !(p->sigma_theta_bins >= 0.0))
         return noalloc_fail(LOC_ERR_INVALID_ARG, "sigmas must be >= 0");
+    if (p->sigma_cross_cells != 0.0 && p->sigma_cross_cells != p->sigma_xy_cells)
+        return noalloc_fail(LOC_ERR_INVALID_ARG, "anisotropic noise (sigma_cross_cells) needs a session (loc_create)");
     const int rxy = p->r_xy >= 0 ? p->r_xy : (p->sigma_xy_cells <= 0.0 ? 0 : (int)std::ceil(3.0 * p->sigma_xy_cells));
     const int rth = p->r_theta >= 0 ? p->r_theta : (p->sigma_theta_bins <= 0.0 ? 0 : (int)std::ceil(3.0 * p->sigma_theta_bins));
     if (rxy > LOC_MAX_R_XY || rth > LOC_MAX_R_THETA)

@@ -598,7 +598,7 @@ LOC_API loc_status loc_server_open(loc_server s, const uint8_t* occ, const loc_p
     if ((double)bytes > s->prm.hbm_budget_bytes)
         return sfail(s, LOC_ERR_INVALID_ARG, "the session can never fit the memory budget");
     if (s->prm.batching) {
-        if (q.kernel == LOC_KERNEL_GENERIC ||
+        if (q.kernel == LOC_KERNEL_GENERIC || (q.sigma_cross_cells > 0.0 && q.sigma_cross_cells != q.sigma_xy_cells) ||
             !step_tiled_eligible(q.H, q.W, q.K, radius(q.sigma_xy_cells, q.r_xy), radius(q.sigma_theta_bins, q.r_theta),
                                  q.storage))
             return sfail(s, LOC_ERR_INVALID_ARG, "a batched server needs sessions the tiled kernel can take");

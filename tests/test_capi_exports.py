@@ -82,3 +82,31 @@ def test_server_and_admission_arguments_fail_without_gpu_work(libloc):
     p.K = 0
     with pytest.raises(loc.LocError):
         loc.loc_session_bytes(p)
+
+
+def test_anisotropic_arguments_fail_without_gpu_work(libloc):
+    import math
+    import paper_1910_00572_gb300 as loc
+    import numpy as np
+    occ = np.zeros((8, 8), np.uint8)
+    for bad in (-0.5, math.nan, math.inf):
+        p = loc.loc_params_default(H=8, W=8, K=4, cell_m=0.1, sigma_cross_cells=bad)
+        with pytest.raises(loc.LocError) as e:
+            loc.loc_create(occ, p)
+        assert e.value.status == loc.LOC_ERR_INVALID_ARG
+    # the default radius follows the larger sigma: ceil(3 * 1.5) = 5 > LOC_MAX_R_XY
+    p = loc.loc_params_default(H=8, W=8, K=4, cell_m=0.1, sigma_xy_cells=0.5, sigma_cross_cells=1.5)
+    with pytest.raises(loc.LocError):
+        loc.loc_create(occ, p)
+    p = loc.loc_params_default(H=8, W=8, K=4, cell_m=0.1, sigma_xy_cells=0.0, sigma_cross_cells=0.5)
+    with pytest.raises(loc.LocError):
+        loc.loc_create(occ, p)                                  # no sigma along the heading
+    p = loc.loc_params_default(H=8, W=8, K=4, cell_m=0.1, sigma_cross_cells=0.8, kernel=loc.LOC_KERNEL_TILED)
+    with pytest.raises(loc.LocError) as e:
+        loc.loc_create(occ, p)
+    assert "generic" in loc.loc_last_error()
+    # the allocation-free call takes isotropic noise only; it refuses before touching the pointers
+    p = loc.loc_params_default(H=8, W=8, K=4, cell_m=0.1, sigma_cross_cells=0.8)
+    with pytest.raises(loc.LocError) as e:
+        loc.loc_propagate_noalloc(p, 256, 256, 256, 256, 0.0, 0.0)
+    assert e.value.status == loc.LOC_ERR_INVALID_ARG and "anisotropic" in loc.loc_last_error()
