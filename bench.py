@@ -149,19 +149,27 @@ class ClockSampler:
 def oracle_band_rate(wl, occ, odom, budget_s: float, steps: int | None = None):
     """Time the FP64 oracle's whole step (Filter.step) on a band of map rows (all bins).
     Returns (cell-updates/s, seconds per step, rows, steps run)."""
+    from oracle import aniso as A
     from oracle import filter as F
     H, W, K = wl["H"], wl["W"], wl["K"]
+
+    def make(band):
+        if wl.get("sigma_cross_cells", 0.0) > 0.0:
+            return A.Filter(band, K, wl["cell"], wl["sigma_xy_cells"], wl["sigma_cross_cells"],
+                            wl["sigma_theta_bins"])
+        return F.Filter(band, K, wl["cell"], wl["sigma_xy_cells"], wl["sigma_theta_bins"])
+
     # cost model from a 16-row probe, then size the band to fit the budget
     probe_rows = min(H, 16)
     j0 = (H - probe_rows) // 2
-    f = F.Filter(occ[j0:j0 + probe_rows], K, wl["cell"], wl["sigma_xy_cells"], wl["sigma_theta_bins"])
+    f = make(occ[j0:j0 + probe_rows])
     t = time.perf_counter()
     f.step(*odom[0])
     per_row = (time.perf_counter() - t) / probe_rows
     n_steps = steps if steps is not None else 2
     rows = int(max(4, min(H, budget_s / max(n_steps, 1) / max(per_row, 1e-9))))
     j0 = (H - rows) // 2
-    f = F.Filter(occ[j0:j0 + rows], K, wl["cell"], wl["sigma_xy_cells"], wl["sigma_theta_bins"])
+    f = make(occ[j0:j0 + rows])
     times = []
     for s in range(n_steps):
         t = time.perf_counter()
@@ -222,6 +230,7 @@ def config_of(wl, args, extra=None):
     c = {"workload": wl["name"], "H": wl["H"], "W": wl["W"], "K": wl["K"], "cell_m": wl["cell"],
          "storage": wl["storage"], "sigma_xy_cells": wl["sigma_xy_cells"],
          "sigma_theta_bins": wl["sigma_theta_bins"], "global_batch": 1,
+         "sigma_cross_cells": wl.get("sigma_cross_cells", 0.0),
          "parallelism": f"replicas{args.gpus}" if args.gpus > 1 else "single",
          "l2": "flushed (512 MiB device write) before every timed step"}
     if extra:
@@ -241,6 +250,7 @@ def run_ours(args, wl, occ, walk, ws, rank, local):
     p = loc.loc_params_default(H=wl["H"], W=wl["W"], K=wl["K"], cell_m=wl["cell"],
                                sigma_xy_cells=wl["sigma_xy_cells"],
                                sigma_theta_bins=wl["sigma_theta_bins"], storage=storage,
+                               sigma_cross_cells=wl.get("sigma_cross_cells", 0.0),
                                stream=loc.torch_stream(), tile=args.tile, kernel=args.kernel)
     h = loc.loc_create(occ, p)
     odom = walk.odom
@@ -293,14 +303,35 @@ def run_ours(args, wl, occ, walk, ws, rank, local):
     if rank != 0:
         return
     elem = ELEM[storage]
-    alg_bytes = n_cells * 2 * elem + wl["H"] * wl["W"] * (1 + 4)
-    achieved = alg_bytes / (statistics.mean(ms) / 1e3) / 1e9
+    aniso = wl.get("sigma_cross_cells", 0.0) > 0.0
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except OSError:
         pass
-    peak = peaks.get("hbm_gbs", 6800.0)
+    if aniso:
+        # ALU-bound: the FP32 operations the definition takes per output cell (the theta sum,
+        # the rotated x/y stencil over C_k and over the map for G_k, the bilinear pull) against
+        # 152 SMs x 128 FP32 lanes x 2 flop x the maximum SM clock of 2070 MHz
+        side = 2 * math.ceil(3 * max(wl["sigma_xy_cells"], wl["sigma_cross_cells"])) + 1
+        rt = math.ceil(3 * wl["sigma_theta_bins"])
+        flops_cell = 2 * ((2 * rt + 1) + 2 * side * side + 4)
+        achieved = n_cells * flops_cell / (statistics.mean(ms) / 1e3) / 1e12
+        peak = 152 * 128 * 2 * 2.070e9 / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "kernel": "step_aniso (fused propagation with the per-bin rotated stencil + normaliser)",
+                "algorithmic_flops_per_launch": n_cells * flops_cell,
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"}
+    else:
+        alg_bytes = n_cells * 2 * elem + wl["H"] * wl["W"] * (1 + 4)
+        achieved = alg_bytes / (statistics.mean(ms) / 1e3) / 1e9
+        peak = peaks.get("hbm_gbs", 6800.0)
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": profiled_traffic(wl, args),
+                "kernel": "step (fused propagation + normaliser)",
+                "algorithmic_bytes_per_launch": alg_bytes,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs" if "hbm_gbs" in peaks else "fallback"}
     cpu = None
     if ws == 1 and not args.no_cpu_baseline:
         rate, per_step, rows, n, _ = oracle_band_rate(wl, occ, odom, budget_s=15.0, steps=2)
@@ -314,11 +345,7 @@ def run_ours(args, wl, occ, walk, ws, rank, local):
         "scaling": "weak", "vs_baseline": None, "dtype": storage, "data": "synthetic",
         "config": config_of(wl, args, extra={"tile": args.tile, "kernel": args.kernel}),
         "p50_step_ms": p50, "p99_step_ms": p99,
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": profiled_traffic(wl, args),
-                     "kernel": "step (fused propagation + normaliser)",
-                     "algorithmic_bytes_per_launch": alg_bytes,
-                     "peak_source": "MEASURED_PEAKS.json hbm_gbs" if "hbm_gbs" in peaks else "fallback"},
+        "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 16 * wl["K"],
                 "d2h_bytes_per_step": 12, "steps": n_e2e,

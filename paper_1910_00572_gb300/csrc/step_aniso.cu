@@ -11,37 +11,147 @@
 //   C_k   = sum_d gt[d] S_{k+d}                               (theta part, circular)
 //   T_k   = g_k (x/y) applied to C_k;  G_k = g_k applied to M  (Eq. 7, Eq. 8 for B_0)
 //   X_t[k] = M * T_k / G_k * (1 / Z_{t-1})                    (Alg. 1 lines 6-7)
-// One CTA owns a kGenTH x kGenTW tile of output cells and streams the source planes
-// kk = -r_th .. K-1+r_th through a shared-memory ring over the tile and its halo.  Channel
-// k's stencil is computed in the CTA from phi_k (FP32 sin/cos/exp); its normalisation
+// Channel k's stencil is computed in the CTA from phi_k (FP32 sin/cos/exp); its normalisation
 // cancels in T_k / G_k.
+//
+// Layout.  One CTA of 128 threads owns a 32 x 32 tile of output cells and streams the source
+// planes kk = -r_th .. K-1+r_th.  Shared memory holds, over the tile plus R rows above and
+// below and 4 columns left and right (a 40-column region, so that every 4-cell group is
+// 16-byte aligned): the ring of the last 2 r_th + 1 planes S, the theta sum C, the map M,
+// and the raw (shifted) input box of the current plane.  The input box of the plane after
+// next is loaded into registers (one column per thread, coalesced across a warp) while the
+// current plane is computed.
+//
+// Each thread owns a 2 x 4 block of output cells (lanes 8 wide x 4 high per warp); each
+// stencil row is three 16-byte loads of C (and of M), conflict-free across each 8-lane
+// quarter warp, reused by up to 2 x 4 x (2R+1) taps, with the row loop unrolled at compile
+// time.  Where every map cell under the block's stencil window is free, G_k is the stencil's
+// own sum taken in the same order, so the block skips the M loads and half the FMAs with a
+// bit-identical result.
 #include "kernels.h"
 
 namespace loc {
 namespace {
 
-constexpr int TH = kGenTH, TW = kGenTW, NT = 256;
-constexpr int RM = LOC_MAX_R_XY, RTM = LOC_MAX_R_THETA;
-constexpr int RAW_H = TH + 2 * RM + 1, RAW_W = TW + 2 * RM + 1;
-constexpr int S_H = TH + 2 * RM, S_W = TW + 2 * RM;
-constexpr int RING = 2 * RTM + 1;
-constexpr int NTAP = (2 * RM + 1) * (2 * RM + 1);
+constexpr int TH = 32, TW = 32, NT = 128;
+constexpr int BY = 2;                          // output rows per thread (4 columns each)
+constexpr int HX = 4;                          // region columns left of the tile
+constexpr int RCOLS = TW + 2 * HX;             // 40 region columns
+constexpr int P = RCOLS;                       // row pitch of ring, C and M (floats)
+constexpr int RAW_COLS = RCOLS + 1;            // 41 input columns per row
+constexpr int RAW_P = 44;                      // raw row pitch (16-byte multiple)
+constexpr int NG = RCOLS / 4;                  // 4-cell groups per region row
 
-template <typename T>
-__global__ void __launch_bounds__(NT) step_aniso_kernel(const __grid_constant__ StepArgs a) {
-    __shared__ float raw[RAW_H][RAW_W + 1];
-    __shared__ float ring[RING][S_H][S_W + 1];
-    __shared__ float C[S_H][S_W + 1];
-    __shared__ float Mt[S_H][S_W + 1];
-    __shared__ float g[NTAP];
+template <int R>
+struct Geo {
+    static constexpr int RR = TH + 2 * R;                 // region rows
+    static constexpr int RAW_ROWS = RR + 1;
+    static constexpr int NPF = (RAW_ROWS + 2) / 3;        // prefetch registers per thread
+    static constexpr int D = 2 * R + 1;                   // stencil side
+    static constexpr int GP = (D + 3) / 4 * 4;            // stencil row pitch
+    static constexpr int NR = BY + 2 * R;                 // source rows under a block
+};
+
+template <int R>
+size_t aniso_smem_bytes(int rt) {
+    using G = Geo<R>;
+    const size_t nring = 2 * (size_t)rt + 1;
+    return (nring + 2) * G::RR * P * sizeof(float) + (size_t)G::RAW_ROWS * RAW_P * sizeof(float) +
+           (size_t)G::D * G::GP * sizeof(float);
+}
+
+template <typename T> __device__ __forceinline__ float load_in(const T* p) { return Store<T>::ld(p); }
+
+template <typename T> __device__ __forceinline__ T round_out(float v, uint32_t r16);
+template <> __device__ __forceinline__ float round_out<float>(float v, uint32_t) { return v; }
+template <> __device__ __forceinline__ __nv_bfloat16 round_out<__nv_bfloat16>(float v, uint32_t r16) {
+    return bf16_sr(v, r16);
+}
+template <> __device__ __forceinline__ __half round_out<__half>(float v, uint32_t) { return __float2half_rn(v); }
+
+__device__ __forceinline__ float as_float(float v) { return v; }
+__device__ __forceinline__ float as_float(__nv_bfloat16 v) { return __bfloat162float(v); }
+__device__ __forceinline__ float as_float(__half v) { return __half2float(v); }
+
+template <typename T> struct Vec4;
+template <> struct Vec4<float> {
+    static __device__ __forceinline__ void st(float* p, const float (&v)[4]) {
+        *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    }
+};
+template <> struct Vec4<__nv_bfloat16> {
+    static __device__ __forceinline__ void st(__nv_bfloat16* p, const __nv_bfloat16 (&v)[4]) {
+        uint2 u;
+        u.x = (uint32_t)__bfloat16_as_ushort(v[0]) | ((uint32_t)__bfloat16_as_ushort(v[1]) << 16);
+        u.y = (uint32_t)__bfloat16_as_ushort(v[2]) | ((uint32_t)__bfloat16_as_ushort(v[3]) << 16);
+        *reinterpret_cast<uint2*>(p) = u;
+    }
+};
+template <> struct Vec4<__half> {
+    static __device__ __forceinline__ void st(__half* p, const __half (&v)[4]) {
+        uint2 u;
+        u.x = (uint32_t)__half_as_ushort(v[0]) | ((uint32_t)__half_as_ushort(v[1]) << 16);
+        u.y = (uint32_t)__half_as_ushort(v[2]) | ((uint32_t)__half_as_ushort(v[3]) << 16);
+        *reinterpret_cast<uint2*>(p) = u;
+    }
+};
+
+__device__ __forceinline__ void ld4(const float* p, float* d) {
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    d[0] = v.x; d[1] = v.y; d[2] = v.z; d[3] = v.w;
+}
+
+// The stencil over one 2 x 4 block: t[oy][ox] = sum g[dj][di] C[oy+dj][ox+di] and, unless the
+// block is interior, gm[oy][ox] = sum g[dj][di] M[oy+dj][ox+di], both in row-major tap order.
+// `c0` / `m0` point at the block's first source row, 4 - R columns left of its first cell
+// rounded down to the 16-byte group (the window is columns 4 - R .. 7 + R of 12).
+template <int R, bool WITH_M>
+__device__ __forceinline__ void stencil_block(const float* c0, const float* m0, const float* gs,
+                                              float (&t)[BY][4], float (&gm)[BY][4]) {
+    using G = Geo<R>;
+#pragma unroll
+    for (int sr = 0; sr < G::NR; ++sr) {
+        float c[12], m[12];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            ld4(c0 + sr * P + 4 * q, c + 4 * q);
+            if (WITH_M) ld4(m0 + sr * P + 4 * q, m + 4 * q);
+        }
+#pragma unroll
+        for (int oy = 0; oy < BY; ++oy) {
+            const int dj = sr - oy;
+            if (dj < 0 || dj >= G::D) continue;
+            float w[G::GP];
+#pragma unroll
+            for (int q = 0; q < G::GP / 4; ++q) ld4(gs + dj * G::GP + 4 * q, w + 4 * q);
+#pragma unroll
+            for (int di = 0; di < G::D; ++di) {
+#pragma unroll
+                for (int ox = 0; ox < 4; ++ox) {
+                    t[oy][ox] = fmaf(w[di], c[ox + di + 4 - R], t[oy][ox]);
+                    if (WITH_M) gm[oy][ox] = fmaf(w[di], m[ox + di + 4 - R], gm[oy][ox]);
+                }
+            }
+        }
+    }
+}
+
+template <typename T, int R>
+__global__ void __launch_bounds__(NT, 3) step_aniso_kernel(const __grid_constant__ StepArgs a) {
+    using G = Geo<R>;
+    extern __shared__ __align__(16) float smem[];
     __shared__ double red[NT / 32];
 
-    const int tid = threadIdx.x;
-    const int H = a.H, W = a.W, K = a.K, r = a.r_xy, rt = a.r_th;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int H = a.H, W = a.W, K = a.K, rt = a.r_th;
+    const int nring = 2 * rt + 1;
     const int ty0 = blockIdx.y * TH, tx0 = blockIdx.x * TW;
-    const int sh_h = TH + 2 * r, sh_w = TW + 2 * r;          // S region actually used
-    const int rw_h = sh_h + 1, rw_w = sh_w + 1;               // raw region actually used
-    const int nring = 2 * rt + 1, side = 2 * r + 1, ntap = side * side;
+
+    float* ring = smem;                                   // [nring][RR][P]
+    float* Cs = ring + (size_t)nring * G::RR * P;         // [RR][P]
+    float* Ms = Cs + G::RR * P;                           // [RR][P]
+    float* raw = Ms + G::RR * P;                          // [RAW_ROWS][RAW_P]
+    float* gs = raw + G::RAW_ROWS * RAW_P;                // [D][GP]
 
     const int reinit = a.sd->reinit;
     // restart: the input is M / (K n_free); read M and fold 1 / (K n_free) into the scale
@@ -49,83 +159,189 @@ __global__ void __launch_bounds__(NT) step_aniso_kernel(const __grid_constant__ 
     const T* Bin = static_cast<const T*>(a.B_in);
     T* Bout = static_cast<T*>(a.B_out);
 
-    for (int q = tid; q < sh_h * sh_w; q += NT) {
-        const int jj = q / sh_w, ii = q % sh_w;
-        const int j = ty0 - r + jj, i = tx0 - r + ii;
-        Mt[jj][ii] = (j >= 0 && j < H && i >= 0 && i < W) ? (float)a.trav[(size_t)j * W + i] : 0.0f;
+    // the map over the region (0 outside the grid)
+    for (int q = tid; q < G::RR * RCOLS; q += NT) {
+        const int row = q / RCOLS, col = q % RCOLS;
+        const int j = ty0 - R + row, i = tx0 - HX + col;
+        Ms[row * P + col] = (j >= 0 && j < H && i >= 0 && i < W) ? (float)a.trav[(size_t)j * W + i] : 0.0f;
     }
 
-    KahanF acc;
-    for (int kk = -rt; kk < K + rt; ++kk) {
+    // the raw box of plane kk: thread (frow0, fcol) holds rows frow0, frow0 + 3, ... of
+    // column fcol (threads 123 .. 127 idle)
+    const int fcol = tid % RAW_COLS, frow0 = tid / RAW_COLS;
+    float pf[G::NPF];
+    auto fetch = [&](int kk) {
         const int c = ((kk % K) + K) % K;
         const Shift s = a.sh[c];
-        const T* plane = Bin + (size_t)c * H * W;
-        for (int q = tid; q < rw_h * rw_w; q += NT) {
-            const int jj = q / rw_w, ii = q % rw_w;
-            const int j = ty0 - r + s.oy + jj, i = tx0 - r + s.ox + ii;
+        const int gi = tx0 - HX + s.ox + fcol;
+        const bool col_ok = frow0 < 3 && gi >= 0 && gi < W;
+        const int gj0 = ty0 - R + s.oy + frow0;
+#pragma unroll
+        for (int n = 0; n < G::NPF; ++n) {
+            const int gj = gj0 + 3 * n;
             float v = 0.0f;
-            if (j >= 0 && j < H && i >= 0 && i < W) {
-                const size_t o = (size_t)j * W + i;
-                v = reinit ? (float)a.trav[o] : Store<T>::ld(plane + o);
+            if (col_ok && frow0 + 3 * n < G::RAW_ROWS && gj >= 0 && gj < H) {
+                const size_t o = (size_t)gj * W + gi;
+                v = reinit ? (float)a.trav[o] : load_in<T>(Bin + (size_t)c * H * W + o);
             }
-            raw[jj][ii] = v;
+            pf[n] = v;
         }
-        __syncthreads();
+    };
+    auto commit = [&]() {
+        if (frow0 >= 3) return;
+#pragma unroll
+        for (int n = 0; n < G::NPF; ++n)
+            if (frow0 + 3 * n < G::RAW_ROWS) raw[(frow0 + 3 * n) * RAW_P + fcol] = pf[n];
+    };
+
+    const int kk0 = -rt, kk_end = K + rt;                 // source planes kk0 .. kk_end - 1
+    fetch(kk0);
+    commit();
+    if (kk0 + 1 < kk_end) fetch(kk0 + 1);
+    __syncthreads();
+
+    // this thread's block: output rows oy0 .. oy0+BY-1, columns ox0 .. ox0+3 of the tile
+    const int lx = lane & 7, ly = lane >> 3;
+    const int oy0 = 4 * BY * warp + BY * ly, ox0 = 4 * lx;
+    bool interior = true, any_free = false;
+    for (int r = 0; r < G::NR; ++r)
+        for (int cc = HX - R; cc < HX + 4 + R; ++cc) interior &= Ms[(oy0 + r) * P + ox0 + cc] > 0.0f;
+#pragma unroll
+    for (int oy = 0; oy < BY; ++oy)
+#pragma unroll
+        for (int ox = 0; ox < 4; ++ox) any_free |= Ms[(oy0 + oy + R) * P + HX + ox0 + ox] > 0.0f;
+
+    KahanF acc;
+    for (int kk = kk0; kk < kk_end; ++kk) {
+        const Shift s = a.sh[((kk % K) + K) % K];
         const float fx = s.fx, fy = s.fy, gx0 = 1.0f - fx, gy0 = 1.0f - fy;
-        const int slot = (kk + rt) % nring;
-        for (int q = tid; q < sh_h * sh_w; q += NT) {
-            const int jj = q / sh_w, ii = q % sh_w;
-            const float top = gx0 * raw[jj][ii] + fx * raw[jj][ii + 1];
-            const float bot = gx0 * raw[jj + 1][ii] + fx * raw[jj + 1][ii + 1];
-            ring[slot][jj][ii] = Mt[jj][ii] * (gy0 * top + fy * bot);
+        float* slot = ring + (size_t)((kk - kk0) % nring) * G::RR * P;
+        // S = M * bilinear(raw) over the region, 4 cells per item
+        for (int q = tid; q < G::RR * NG; q += NT) {
+            const int row = q / NG, g4 = (q % NG) * 4;
+            float r0[5], r1[5], mk[4];
+            ld4(raw + row * RAW_P + g4, r0);
+            r0[4] = raw[row * RAW_P + g4 + 4];
+            ld4(raw + (row + 1) * RAW_P + g4, r1);
+            r1[4] = raw[(row + 1) * RAW_P + g4 + 4];
+            ld4(Ms + row * P + g4, mk);
+            float4 o;
+            float* ov = &o.x;
+#pragma unroll
+            for (int x = 0; x < 4; ++x) {
+                const float top = gx0 * r0[x] + fx * r0[x + 1];
+                const float bot = gx0 * r1[x] + fx * r1[x + 1];
+                ov[x] = mk[x] * (gy0 * top + fy * bot);
+            }
+            *reinterpret_cast<float4*>(slot + row * P + g4) = o;
         }
-        __syncthreads();                    // the theta sum below reads the slot just written
-        if (kk >= rt) {
-            const int o = kk - rt;
-            // channel o's x/y stencil (unnormalised), offsets dj, di in -r..r
+        __syncthreads();                                  // raw consumed, the slot written
+        if (kk + 1 < kk_end) {
+            commit();                                     // plane kk + 1 into raw
+            if (kk + 2 < kk_end) fetch(kk + 2);           // plane kk + 2 in flight
+        }
+        if (kk - kk0 >= 2 * rt) {
+            const int o = kk - rt;                        // output channel
+            // channel o's x/y stencil (unnormalised), row-major with pitch GP
             const float phi = a.phi0 + a.dphi * (float)o;
             float sp, cp;
             sincosf(phi, &sp, &cp);
-            for (int q = tid; q < ntap; q += NT) {
-                const float dj = (float)(q / side - r), di = (float)(q % side - r);
-                const float along = (di * cp + dj * sp) / a.sigma_a;
-                const float across = (dj * cp - di * sp) / a.sigma_c;
-                g[q] = expf(-0.5f * (along * along + across * across));
+            for (int q = tid; q < G::D * G::GP; q += NT) {
+                const int dj = q / G::GP, di = q % G::GP;
+                float w = 0.0f;
+                if (di < G::D) {
+                    const float fdj = (float)(dj - R), fdi = (float)(di - R);
+                    const float along = (fdi * cp + fdj * sp) / a.sigma_a;
+                    const float across = (fdj * cp - fdi * sp) / a.sigma_c;
+                    w = expf(-0.5f * (along * along + across * across));
+                }
+                gs[q] = w;
             }
-            // C = theta part over the tile and its halo
-            for (int q = tid; q < sh_h * sh_w; q += NT) {
-                const int jj = q / sh_w, ii = q % sh_w;
-                float v = 0.0f;
-                for (int d = -rt; d <= rt; ++d) v += a.gt[d + rt] * ring[(o + d + rt) % nring][jj][ii];
-                C[jj][ii] = v;
+            // C = theta sum of the ring over the region, 4 cells per item
+            int sl[2 * LOC_MAX_R_THETA + 1];
+#pragma unroll
+            for (int d = 0; d < 2 * LOC_MAX_R_THETA + 1; ++d) sl[d] = (o + d - kk0 - rt) % nring;
+            for (int q = tid; q < G::RR * NG; q += NT) {
+                const int off = (q / NG) * P + (q % NG) * 4;
+                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                for (int d = 0; d < 2 * LOC_MAX_R_THETA + 1; ++d) {
+                    if (d < nring) {
+                        const float g = a.gt[d];
+                        const float4 x = *reinterpret_cast<const float4*>(ring + (size_t)sl[d] * G::RR * P + off);
+                        v.x += g * x.x; v.y += g * x.y; v.z += g * x.z; v.w += g * x.w;
+                    }
+                }
+                *reinterpret_cast<float4*>(Cs + off) = v;
             }
             __syncthreads();
-            T* oplane = Bout + (size_t)o * H * W;
             float part = 0.0f;
-            for (int q = tid; q < TH * TW; q += NT) {
-                const int j = q / TW, i = q % TW;
-                const int gj = ty0 + j, gi = tx0 + i;
-                if (gj >= H || gi >= W) continue;
-                float v = 0.0f;
-                if (Mt[j + r][i + r] > 0.0f) {
-                    float t = 0.0f, gm = 0.0f;
-                    for (int dj = 0; dj < side; ++dj)
-                        for (int di = 0; di < side; ++di) {
-                            const float w = g[dj * side + di];
-                            t += w * C[j + dj][i + di];
-                            gm += w * Mt[j + dj][i + di];
-                        }
-                    // the stencil's normalisation cancels in t / gm (the theta taps are
-                    // normalised); gm >= 1 on a free cell (its own tap is exp(0))
-                    v = t / gm * in_scale;
+            if (any_free) {
+                float t[BY][4], gm[BY][4];
+#pragma unroll
+                for (int y = 0; y < BY; ++y)
+#pragma unroll
+                    for (int x = 0; x < 4; ++x) t[y][x] = gm[y][x] = 0.0f;
+                const int base = oy0 * P + ox0;
+                if (interior) {
+                    stencil_block<R, false>(Cs + base, Ms + base, gs, t, gm);
+                    // every map cell under the window is 1: G_k is the stencil's sum, taken in
+                    // the row-major order of the FMAs it replaces (fma(w, 1, s) = s + w)
+                    float sum = 0.0f;
+#pragma unroll
+                    for (int dj = 0; dj < G::D; ++dj)
+#pragma unroll
+                        for (int di = 0; di < G::D; ++di) sum = fmaf(gs[dj * G::GP + di], 1.0f, sum);
+#pragma unroll
+                    for (int y = 0; y < BY; ++y)
+#pragma unroll
+                        for (int x = 0; x < 4; ++x) gm[y][x] = sum;
+                } else {
+                    stencil_block<R, true>(Cs + base, Ms + base, gs, t, gm);
                 }
-                const size_t off = (size_t)gj * W + gi;
-                const uint32_t q_lin = (uint32_t)((size_t)o * H * W + off);
-                part += store_out<T>(oplane + off, v, pcg_hash(q_lin ^ a.seed));
+                T* oplane = Bout + (size_t)o * H * W;
+#pragma unroll
+                for (int y = 0; y < BY; ++y) {
+                    const int gj = ty0 + oy0 + y, gi = tx0 + ox0;
+                    if (gj >= H) break;
+                    T ov[4];
+                    const size_t off = (size_t)gj * W + gi;
+#pragma unroll
+                    for (int x = 0; x < 4; ++x) {
+                        const float mc = Ms[(oy0 + y + R) * P + HX + ox0 + x];
+                        // gm >= 1 on a free cell (its own tap is exp(0))
+                        const float v = mc > 0.0f ? __fdividef(t[y][x], gm[y][x]) * in_scale : 0.0f;
+                        const uint32_t q_lin = (uint32_t)((size_t)o * H * W + off + x);
+                        ov[x] = round_out<T>(v, pcg_hash(q_lin ^ a.seed));
+                    }
+                    if ((W & 3) == 0 && gi + 3 < W) {
+                        Vec4<T>::st(oplane + off, ov);
+#pragma unroll
+                        for (int x = 0; x < 4; ++x) part += as_float(ov[x]);
+                    } else {
+#pragma unroll
+                        for (int x = 0; x < 4; ++x)
+                            if (gi + x < W) {
+                                oplane[off + x] = ov[x];
+                                part += as_float(ov[x]);
+                            }
+                    }
+                }
+            } else {
+                T* oplane = Bout + (size_t)o * H * W;
+                const T zero = round_out<T>(0.0f, 0u);
+#pragma unroll
+                for (int y = 0; y < BY; ++y) {
+                    const int gj = ty0 + oy0 + y, gi = tx0 + ox0;
+                    if (gj >= H) break;
+#pragma unroll
+                    for (int x = 0; x < 4; ++x)
+                        if (gi + x < W) oplane[(size_t)gj * W + gi + x] = zero;
+                }
             }
             acc.add(part);
         }
-        // the next plane overwrites raw, one ring slot, C and the stencil: wait for every thread
+        // the next plane overwrites raw's consumer (the S pass), a ring slot, C and the stencil
         __syncthreads();
     }
 
@@ -150,18 +366,48 @@ __global__ void __launch_bounds__(NT) step_aniso_kernel(const __grid_constant__ 
     });
 }
 
+template <typename T, int R>
+cudaError_t launch_r(const StepArgs& a, cudaStream_t st) {
+    const size_t smem = aniso_smem_bytes<R>(a.r_th);
+    static bool attr_set = false;                 // the largest size any session can ask for
+    if (!attr_set) {
+        const cudaError_t e = cudaFuncSetAttribute(step_aniso_kernel<T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   (int)aniso_smem_bytes<R>(LOC_MAX_R_THETA));
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    dim3 grid((a.W + TW - 1) / TW, (a.H + TH - 1) / TH);
+    step_aniso_kernel<T, R><<<grid, NT, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_t(const StepArgs& a, cudaStream_t st) {
+    switch (a.r_xy) {
+        case 0: return launch_r<T, 0>(a, st);
+        case 1: return launch_r<T, 1>(a, st);
+        case 2: return launch_r<T, 2>(a, st);
+        case 3: return launch_r<T, 3>(a, st);
+        case 4: return launch_r<T, 4>(a, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_step_aniso(const StepArgs& a, int storage, cudaStream_t st) {
-    if (a.r_xy > RM || a.r_th > RTM || !(a.sigma_a > 0.0f) || !(a.sigma_c > 0.0f)) return cudaErrorInvalidValue;
-    dim3 grid((a.W + TW - 1) / TW, (a.H + TH - 1) / TH);
+    static_assert(LOC_MAX_R_XY <= HX, "the region's left margin must cover the x/y radius");
+    static_assert(3 * RAW_COLS <= NT && NT == 4 * 32 && TH == 4 * 4 * BY && TW == 32,
+                  "three rows of input columns per fetch pass; 4 warps of 8 x 4 lanes cover the tile");
+    if (a.r_xy < 0 || a.r_xy > LOC_MAX_R_XY || a.r_th < 0 || a.r_th > LOC_MAX_R_THETA ||
+        !(a.sigma_a > 0.0f) || !(a.sigma_c > 0.0f))
+        return cudaErrorInvalidValue;
     switch (storage) {
-        case LOC_F32: step_aniso_kernel<float><<<grid, NT, 0, st>>>(a); break;
-        case LOC_BF16: step_aniso_kernel<__nv_bfloat16><<<grid, NT, 0, st>>>(a); break;
-        case LOC_F16: step_aniso_kernel<__half><<<grid, NT, 0, st>>>(a); break;
+        case LOC_F32: return launch_t<float>(a, st);
+        case LOC_BF16: return launch_t<__nv_bfloat16>(a, st);
+        case LOC_F16: return launch_t<__half>(a, st);
         default: return cudaErrorInvalidValue;
     }
-    return cudaGetLastError();
 }
 
 }  // namespace loc
