@@ -211,37 +211,65 @@ __global__ void __launch_bounds__(NT, 3) step_aniso_kernel(const __grid_constant
 #pragma unroll
         for (int ox = 0; ox < 4; ++ox) any_free |= Ms[(oy0 + oy + R) * P + HX + ox0 + ox] > 0.0f;
 
+    // per warp: every lane interior (G_k is the stencil sum) / some lane with a free cell
+    const bool warp_interior = __all_sync(0xffffffffu, interior);
+    const bool warp_any_free = __any_sync(0xffffffffu, any_free);
+    uint32_t free_bits = 0;                               // centres of this block that are free
+#pragma unroll
+    for (int y = 0; y < BY; ++y)
+#pragma unroll
+        for (int x = 0; x < 4; ++x)
+            if (Ms[(oy0 + y + R) * P + HX + ox0 + x] > 0.0f) free_bits |= 1u << (4 * y + x);
+    const float inv_sa = 1.0f / a.sigma_a, inv_sc = 1.0f / a.sigma_c;
+
     KahanF acc;
     for (int kk = kk0; kk < kk_end; ++kk) {
         const Shift s = a.sh[((kk % K) + K) % K];
         const float fx = s.fx, fy = s.fy, gx0 = 1.0f - fx, gy0 = 1.0f - fy;
+        const int o = kk - rt;                            // output channel, once the ring is full
+        const bool out = kk - kk0 >= 2 * rt;
         float* slot = ring + (size_t)((kk - kk0) % nring) * G::RR * P;
-        // S = M * bilinear(raw) over the region, 4 cells per item
+        int sl[2 * LOC_MAX_R_THETA];                      // ring slots of planes o - rt .. o + rt - 1
+#pragma unroll
+        for (int d = 0; d < 2 * LOC_MAX_R_THETA; ++d) sl[d] = (o + d - kk0 - rt) % nring;
+        // S = M * bilinear(raw) into the ring and, once the ring is full, C = theta sum of the
+        // ring, 4 cells per item.  A thread always owns the same items, so the ring cells it
+        // sums are its own writes: no barrier between the two.
         for (int q = tid; q < G::RR * NG; q += NT) {
-            const int row = q / NG, g4 = (q % NG) * 4;
+            const int row = q / NG, g4 = (q % NG) * 4, off = row * P + g4;
             float r0[5], r1[5], mk[4];
             ld4(raw + row * RAW_P + g4, r0);
             r0[4] = raw[row * RAW_P + g4 + 4];
             ld4(raw + (row + 1) * RAW_P + g4, r1);
             r1[4] = raw[(row + 1) * RAW_P + g4 + 4];
-            ld4(Ms + row * P + g4, mk);
-            float4 o;
-            float* ov = &o.x;
+            ld4(Ms + off, mk);
+            float sv[4];
 #pragma unroll
             for (int x = 0; x < 4; ++x) {
                 const float top = gx0 * r0[x] + fx * r0[x + 1];
                 const float bot = gx0 * r1[x] + fx * r1[x + 1];
-                ov[x] = mk[x] * (gy0 * top + fy * bot);
+                sv[x] = mk[x] * (gy0 * top + fy * bot);
             }
-            *reinterpret_cast<float4*>(slot + row * P + g4) = o;
+            *reinterpret_cast<float4*>(slot + off) = make_float4(sv[0], sv[1], sv[2], sv[3]);
+            if (out) {
+                float v[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+                for (int d = 0; d < 2 * LOC_MAX_R_THETA; ++d) {
+                    if (d < 2 * rt) {
+                        const float g = a.gt[d];
+                        float x4[4];
+                        ld4(ring + (size_t)sl[d] * G::RR * P + off, x4);
+#pragma unroll
+                        for (int x = 0; x < 4; ++x) v[x] += g * x4[x];
+                    }
+                }
+                const float g = a.gt[2 * rt];             // the newest plane, o + rt
+#pragma unroll
+                for (int x = 0; x < 4; ++x) v[x] += g * sv[x];
+                *reinterpret_cast<float4*>(Cs + off) = make_float4(v[0], v[1], v[2], v[3]);
+            }
         }
-        __syncthreads();                                  // raw consumed, the slot written
-        if (kk + 1 < kk_end) {
-            commit();                                     // plane kk + 1 into raw
-            if (kk + 2 < kk_end) fetch(kk + 2);           // plane kk + 2 in flight
-        }
-        if (kk - kk0 >= 2 * rt) {
-            const int o = kk - rt;                        // output channel
+        if (out) {
             // channel o's x/y stencil (unnormalised), row-major with pitch GP
             const float phi = a.phi0 + a.dphi * (float)o;
             float sp, cp;
@@ -251,39 +279,29 @@ __global__ void __launch_bounds__(NT, 3) step_aniso_kernel(const __grid_constant
                 float w = 0.0f;
                 if (di < G::D) {
                     const float fdj = (float)(dj - R), fdi = (float)(di - R);
-                    const float along = (fdi * cp + fdj * sp) / a.sigma_a;
-                    const float across = (fdj * cp - fdi * sp) / a.sigma_c;
+                    const float along = (fdi * cp + fdj * sp) * inv_sa;
+                    const float across = (fdj * cp - fdi * sp) * inv_sc;
                     w = expf(-0.5f * (along * along + across * across));
                 }
                 gs[q] = w;
             }
-            // C = theta sum of the ring over the region, 4 cells per item
-            int sl[2 * LOC_MAX_R_THETA + 1];
-#pragma unroll
-            for (int d = 0; d < 2 * LOC_MAX_R_THETA + 1; ++d) sl[d] = (o + d - kk0 - rt) % nring;
-            for (int q = tid; q < G::RR * NG; q += NT) {
-                const int off = (q / NG) * P + (q % NG) * 4;
-                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-                for (int d = 0; d < 2 * LOC_MAX_R_THETA + 1; ++d) {
-                    if (d < nring) {
-                        const float g = a.gt[d];
-                        const float4 x = *reinterpret_cast<const float4*>(ring + (size_t)sl[d] * G::RR * P + off);
-                        v.x += g * x.x; v.y += g * x.y; v.z += g * x.z; v.w += g * x.w;
-                    }
-                }
-                *reinterpret_cast<float4*>(Cs + off) = v;
-            }
-            __syncthreads();
+        }
+        __syncthreads();                                  // raw consumed; C and the stencil written
+        if (kk + 1 < kk_end) {
+            commit();                                     // plane kk + 1 into raw
+            if (kk + 2 < kk_end) fetch(kk + 2);           // plane kk + 2 in flight
+        }
+        if (out) {
             float part = 0.0f;
-            if (any_free) {
+            T* oplane = Bout + (size_t)o * H * W;
+            if (warp_any_free) {
                 float t[BY][4], gm[BY][4];
 #pragma unroll
                 for (int y = 0; y < BY; ++y)
 #pragma unroll
                     for (int x = 0; x < 4; ++x) t[y][x] = gm[y][x] = 0.0f;
                 const int base = oy0 * P + ox0;
-                if (interior) {
+                if (warp_interior) {
                     stencil_block<R, false>(Cs + base, Ms + base, gs, t, gm);
                     // every map cell under the window is 1: G_k is the stencil's sum, taken in
                     // the row-major order of the FMAs it replaces (fma(w, 1, s) = s + w)
@@ -299,7 +317,6 @@ __global__ void __launch_bounds__(NT, 3) step_aniso_kernel(const __grid_constant
                 } else {
                     stencil_block<R, true>(Cs + base, Ms + base, gs, t, gm);
                 }
-                T* oplane = Bout + (size_t)o * H * W;
 #pragma unroll
                 for (int y = 0; y < BY; ++y) {
                     const int gj = ty0 + oy0 + y, gi = tx0 + ox0;
@@ -308,9 +325,8 @@ __global__ void __launch_bounds__(NT, 3) step_aniso_kernel(const __grid_constant
                     const size_t off = (size_t)gj * W + gi;
 #pragma unroll
                     for (int x = 0; x < 4; ++x) {
-                        const float mc = Ms[(oy0 + y + R) * P + HX + ox0 + x];
                         // gm >= 1 on a free cell (its own tap is exp(0))
-                        const float v = mc > 0.0f ? __fdividef(t[y][x], gm[y][x]) * in_scale : 0.0f;
+                        const float v = (free_bits >> (4 * y + x)) & 1u ? __fdividef(t[y][x], gm[y][x]) * in_scale : 0.0f;
                         const uint32_t q_lin = (uint32_t)((size_t)o * H * W + off + x);
                         ov[x] = round_out<T>(v, pcg_hash(q_lin ^ a.seed));
                     }
@@ -328,7 +344,6 @@ __global__ void __launch_bounds__(NT, 3) step_aniso_kernel(const __grid_constant
                     }
                 }
             } else {
-                T* oplane = Bout + (size_t)o * H * W;
                 const T zero = round_out<T>(0.0f, 0u);
 #pragma unroll
                 for (int y = 0; y < BY; ++y) {
@@ -341,7 +356,7 @@ __global__ void __launch_bounds__(NT, 3) step_aniso_kernel(const __grid_constant
             }
             acc.add(part);
         }
-        // the next plane overwrites raw's consumer (the S pass), a ring slot, C and the stencil
+        // the next plane overwrites raw's consumer (the S pass), C and the stencil
         __syncthreads();
     }
 
