@@ -239,6 +239,16 @@ LOC_API loc_status loc_create(const uint8_t* occ, const loc_params* p, loc_handl
         return fail(nullptr, LOC_ERR_OOM, "pinned host allocation failed");
     }
     s->tiled = tiled_ok && p->kernel != LOC_KERNEL_GENERIC;
+    if (aniso && aniso_tma_eligible(p->W, p->storage)) {
+        s->aniso_tma = true;
+        for (int b = 0; b < 2; ++b) {
+            if (make_aniso_tmap(s->tmap[b], s->B[b], p->storage, p->H, p->W, p->K, rxy) != cudaSuccess) {
+                release_all(s);
+                delete s;
+                return fail(nullptr, LOC_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+            }
+        }
+    }
     if (s->tiled) {
         s->tile_cfg = p->tile > 0 ? p->tile : step_tiled_default_cfg(p->H, p->W, p->K, p->storage);
         for (int b = 0; b < 2; ++b) {
@@ -355,7 +365,7 @@ LOC_API loc_status loc_step(loc_handle h, double u, double v, double w) {
         a.dphi = (float)(2.0 * M_PI / a.K);
         a.sigma_a = (float)h->p.sigma_xy_cells;
         a.sigma_c = (float)h->p.sigma_cross_cells;
-        e = launch_step_aniso(a, h->p.storage, h->stream);
+        e = launch_step_aniso(a, h->aniso_tma ? h->tmap[h->cur] : nullptr, h->p.storage, h->stream);
     } else {
         e = h->tiled ? launch_step_tiled(a, h->tmap[h->cur], h->p.storage, h->tile_cfg, h->stream)
                      : launch_step(a, h->p.storage, h->stream);

@@ -18,7 +18,12 @@ unsigned int step_num_blocks(int H, int W);
 // The same with anisotropic motion noise (Eq. 5-6, sigma_x != sigma_y): a.phi0, a.dphi,
 // a.sigma_a, a.sigma_c give channel k's rotated x/y kernel; a.gx is unused.  Same grid and
 // partials as launch_step.
-cudaError_t launch_step_aniso(const StepArgs& a, int storage, cudaStream_t st);
+// Anisotropic propagation (step_aniso.cu).  `tmap` is the tensor map of B_in built by
+// make_aniso_tmap, or null (plain loads).
+cudaError_t launch_step_aniso(const StepArgs& a, const void* tmap, int storage, cudaStream_t st);
+// Whether the TMA input path takes this grid, and its tensor map of one belief buffer.
+bool aniso_tma_eligible(int W, int storage);
+cudaError_t make_aniso_tmap(void* tmap_out, const void* B, int storage, int H, int W, int K, int r_xy);
 
 // Tiled TMA-pipelined propagation for the default kernel radii (x/y 2, theta 3).  Tile
 // configurations are numbered 1 .. step_tiled_num_cfgs(); each needs its own tensor map.
@@ -27,6 +32,8 @@ int step_tiled_num_cfgs();
 int step_tiled_default_cfg(int H, int W, int K, int storage);
 size_t step_tmap_bytes();
 cudaError_t make_step_tmap(void* tmap_out, const void* B, int storage, int H, int W, int K, int cfg);
+// Tensor map of a [K][H][W] belief buffer loaded in boxes of box_w x box_h cells of one plane.
+cudaError_t make_box_tmap(void* tmap_out, const void* B, int storage, int H, int W, int K, int box_w, int box_h);
 cudaError_t launch_step_tiled(const StepArgs& a, const void* tmap, int storage, int cfg, cudaStream_t st);
 
 // ---- Batched propagation (batch.cu): one persistent launch over (session, tile) items of

@@ -50,6 +50,7 @@ struct loc_session {
     int cap_dirs = 0, cap_beams = 0, cap_dir_of = 0;
     long long n_lidar = 0;
     bool aniso = false;            // anisotropic motion noise (step_aniso.cu)
+    bool aniso_tma = false;        // ... with its input boxes by TMA (tmap holds its maps)
     bool tiled = false;            // use the TMA-tiled kernel
     int tile_cfg = 0;              // its tile configuration
     unsigned char tmap[2][128] __attribute__((aligned(128)));   // tensor maps of B[0], B[1]

@@ -17,21 +17,32 @@
 // Layout.  One CTA of 128 threads owns a 32 x 32 tile of output cells and streams the source
 // planes kk = -r_th .. K-1+r_th.  Shared memory holds, over the tile plus R rows above and
 // below and 4 columns left and right (a 40-column region, so that every 4-cell group is
-// 16-byte aligned): the ring of the last 2 r_th + 1 planes S, the theta sum C, the map M,
-// and the raw (shifted) input box of the current plane.  The input box of the plane after
-// next is loaded into registers (one column per thread, coalesced across a warp) while the
-// current plane is computed.
+// 16-byte aligned): the ring of the last 2 r_th + 1 planes S, the theta sum C and the map M;
+// and, in the storage type, the raw (shifted) input boxes of the current and the next plane.
+// The box of the plane after next is fetched while the current plane is computed: by one TMA
+// copy (x rounded down to 16 bytes, zeros outside the grid, an mbarrier with a bounded wait)
+// where the row pitch allows it, else by plain loads into registers (one column per thread,
+// coalesced across a warp) stored after the current plane's S pass; the restart input (the
+// map) always takes the plain loads.
 //
 // Each thread owns a 2 x 4 block of output cells (lanes 8 wide x 4 high per warp); each
 // stencil row is three 16-byte loads of C (and of M), conflict-free across each 8-lane
 // quarter warp, reused by up to 2 x 4 x (2R+1) taps, with the row loop unrolled at compile
-// time.  Where every map cell under the block's stencil window is free, G_k is the stencil's
-// own sum taken in the same order, so the block skips the M loads and half the FMAs with a
-// bit-identical result.
-#include "kernels.h"
+// time.  A thread always computes S and C for the same region cells, so the ring cells it sums
+// are its own writes and the two passes are fused.  Where every map cell under a warp's
+// stencil windows is free, G_k is the stencil's own sum taken in the same order, so the warp
+// skips the M loads and half the FMAs with a bit-identical result.
+#include <type_traits>
+
+#include "tiled_common.cuh"
 
 namespace loc {
 namespace {
+
+using tiled::bar_expect;
+using tiled::bar_init;
+using tiled::bar_wait;
+using tiled::tma_load;
 
 constexpr int TH = 32, TW = 32, NT = 128;
 constexpr int BY = 2;                          // output rows per thread (4 columns each)
@@ -39,8 +50,11 @@ constexpr int HX = 4;                          // region columns left of the til
 constexpr int RCOLS = TW + 2 * HX;             // 40 region columns
 constexpr int P = RCOLS;                       // row pitch of ring, C and M (floats)
 constexpr int RAW_COLS = RCOLS + 1;            // 41 input columns per row
-constexpr int RAW_P = 44;                      // raw row pitch (16-byte multiple)
 constexpr int NG = RCOLS / 4;                  // 4-cell groups per region row
+
+// raw box row pitch in elements of T: 41 columns plus the offset of the first one within its
+// 16-byte group (TMA x is rounded down to 16 bytes): 44 FP32, 48 16-bit
+template <typename T> __host__ __device__ constexpr int raw_pitch() { return sizeof(T) == 4 ? 44 : 48; }
 
 template <int R>
 struct Geo {
@@ -52,15 +66,30 @@ struct Geo {
     static constexpr int NR = BY + 2 * R;                 // source rows under a block
 };
 
-template <int R>
+template <typename T, int R>
+__host__ __device__ constexpr size_t raw_buf_bytes() {                        // one raw box, rounded to 128 bytes
+    return ((size_t)Geo<R>::RAW_ROWS * raw_pitch<T>() * sizeof(T) + 127) / 128 * 128;
+}
+
+template <typename T, int R>
 size_t aniso_smem_bytes(int rt) {
     using G = Geo<R>;
     const size_t nring = 2 * (size_t)rt + 1;
-    return (nring + 2) * G::RR * P * sizeof(float) + (size_t)G::RAW_ROWS * RAW_P * sizeof(float) +
+    return 2 * raw_buf_bytes<T, R>() + (nring + 2) * G::RR * P * sizeof(float) +
            (size_t)G::D * G::GP * sizeof(float);
 }
 
-template <typename T> __device__ __forceinline__ float load_in(const T* p) { return Store<T>::ld(p); }
+template <typename T> __device__ __forceinline__ float to_f(T v);
+template <> __device__ __forceinline__ float to_f<float>(float v) { return v; }
+template <> __device__ __forceinline__ float to_f<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
+template <> __device__ __forceinline__ float to_f<__half>(__half v) { return __half2float(v); }
+
+template <typename T> __device__ __forceinline__ T from_u8(uint8_t v);
+template <> __device__ __forceinline__ float from_u8<float>(uint8_t v) { return (float)v; }
+template <> __device__ __forceinline__ __nv_bfloat16 from_u8<__nv_bfloat16>(uint8_t v) {
+    return __float2bfloat16_rn((float)v);
+}
+template <> __device__ __forceinline__ __half from_u8<__half>(uint8_t v) { return __float2half_rn((float)v); }
 
 template <typename T> __device__ __forceinline__ T round_out(float v, uint32_t r16);
 template <> __device__ __forceinline__ float round_out<float>(float v, uint32_t) { return v; }
@@ -68,10 +97,6 @@ template <> __device__ __forceinline__ __nv_bfloat16 round_out<__nv_bfloat16>(fl
     return bf16_sr(v, r16);
 }
 template <> __device__ __forceinline__ __half round_out<__half>(float v, uint32_t) { return __float2half_rn(v); }
-
-__device__ __forceinline__ float as_float(float v) { return v; }
-__device__ __forceinline__ float as_float(__nv_bfloat16 v) { return __bfloat162float(v); }
-__device__ __forceinline__ float as_float(__half v) { return __half2float(v); }
 
 template <typename T> struct Vec4;
 template <> struct Vec4<float> {
@@ -102,7 +127,7 @@ __device__ __forceinline__ void ld4(const float* p, float* d) {
 }
 
 // The stencil over one 2 x 4 block: t[oy][ox] = sum g[dj][di] C[oy+dj][ox+di] and, unless the
-// block is interior, gm[oy][ox] = sum g[dj][di] M[oy+dj][ox+di], both in row-major tap order.
+// warp is interior, gm[oy][ox] = sum g[dj][di] M[oy+dj][ox+di], both in row-major tap order.
 // `c0` / `m0` point at the block's first source row, 4 - R columns left of its first cell
 // rounded down to the 16-byte group (the window is columns 4 - R .. 7 + R of 12).
 template <int R, bool WITH_M>
@@ -137,27 +162,36 @@ __device__ __forceinline__ void stencil_block(const float* c0, const float* m0, 
 }
 
 template <typename T, int R>
-__global__ void __launch_bounds__(NT, 3) step_aniso_kernel(const __grid_constant__ StepArgs a) {
+__global__ void __launch_bounds__(NT, 3) step_aniso_kernel(const __grid_constant__ StepArgs a,
+                                                           const __grid_constant__ CUtensorMap tmap,
+                                                           int use_tma) {
     using G = Geo<R>;
-    extern __shared__ __align__(16) float smem[];
+    constexpr int RPT = raw_pitch<T>();
+    constexpr size_t RAW_BUF = raw_buf_bytes<T, R>();
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ double red[NT / 32];
+    __shared__ unsigned long long tbar[2];
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int H = a.H, W = a.W, K = a.K, rt = a.r_th;
     const int nring = 2 * rt + 1;
     const int ty0 = blockIdx.y * TH, tx0 = blockIdx.x * TW;
 
-    float* ring = smem;                                   // [nring][RR][P]
-    float* Cs = ring + (size_t)nring * G::RR * P;         // [RR][P]
-    float* Ms = Cs + G::RR * P;                           // [RR][P]
-    float* raw = Ms + G::RR * P;                          // [RAW_ROWS][RAW_P]
-    float* gs = raw + G::RAW_ROWS * RAW_P;                // [D][GP]
+    float* ring = reinterpret_cast<float*>(smem_raw + 2 * RAW_BUF);       // [nring][RR][P]
+    float* Cs = ring + (size_t)nring * G::RR * P;                         // [RR][P]
+    float* Ms = Cs + G::RR * P;                                           // [RR][P]
+    float* gs = Ms + G::RR * P;                                           // [D][GP]
+    // raw box of buffer b: [RAW_ROWS][RPT] elements of T
+    auto rawbuf = [&](int b) { return reinterpret_cast<T*>(smem_raw + (size_t)b * RAW_BUF); };
 
     const int reinit = a.sd->reinit;
     // restart: the input is M / (K n_free); read M and fold 1 / (K n_free) into the scale
     const float in_scale = (reinit ? a.inv_uniform : a.sd->inv_Z) * a.out_mult;
     const T* Bin = static_cast<const T*>(a.B_in);
     T* Bout = static_cast<T*>(a.B_out);
+    // TMA writes whole boxes into 128-byte aligned buffers
+    const bool tma = use_tma && !reinit && (tiled::su32(smem_raw) & 127u) == 0;
+    constexpr int AL = 16 / (int)sizeof(T);              // TMA x alignment in elements
 
     // the map over the region (0 outside the grid)
     for (int q = tid; q < G::RR * RCOLS; q += NT) {
@@ -166,12 +200,14 @@ __global__ void __launch_bounds__(NT, 3) step_aniso_kernel(const __grid_constant
         Ms[row * P + col] = (j >= 0 && j < H && i >= 0 && i < W) ? (float)a.trav[(size_t)j * W + i] : 0.0f;
     }
 
-    // the raw box of plane kk: thread (frow0, fcol) holds rows frow0, frow0 + 3, ... of
-    // column fcol (threads 123 .. 127 idle)
+    // Source planes kk0 .. kk_end - 1; plane kk sits in raw buffer (kk - kk0) & 1, its box
+    // starting at input column tx0 - HX + ox - xo (xo = 0 on the plain-load path).
+    const int kk0 = -rt, kk_end = K + rt;
+    // plain loads: thread (frow0, fcol) holds rows frow0, frow0 + 3, ... of column fcol
+    // (threads 123 .. 127 idle)
     const int fcol = tid % RAW_COLS, frow0 = tid / RAW_COLS;
-    float pf[G::NPF];
-    auto fetch = [&](int kk) {
-        const int c = ((kk % K) + K) % K;
+    T pf[G::NPF];
+    auto fetch = [&](int c) {
         const Shift s = a.sh[c];
         const int gi = tx0 - HX + s.ox + fcol;
         const bool col_ok = frow0 < 3 && gi >= 0 && gi < W;
@@ -179,69 +215,101 @@ __global__ void __launch_bounds__(NT, 3) step_aniso_kernel(const __grid_constant
 #pragma unroll
         for (int n = 0; n < G::NPF; ++n) {
             const int gj = gj0 + 3 * n;
-            float v = 0.0f;
+            T v = from_u8<T>(0);
             if (col_ok && frow0 + 3 * n < G::RAW_ROWS && gj >= 0 && gj < H) {
                 const size_t o = (size_t)gj * W + gi;
-                v = reinit ? (float)a.trav[o] : load_in<T>(Bin + (size_t)c * H * W + o);
+                v = reinit ? from_u8<T>(a.trav[o]) : Bin[(size_t)c * H * W + o];
             }
             pf[n] = v;
         }
     };
-    auto commit = [&]() {
+    auto commit = [&](int kk) {
         if (frow0 >= 3) return;
+        T* rb = rawbuf((kk - kk0) & 1);
 #pragma unroll
         for (int n = 0; n < G::NPF; ++n)
-            if (frow0 + 3 * n < G::RAW_ROWS) raw[(frow0 + 3 * n) * RAW_P + fcol] = pf[n];
+            if (frow0 + 3 * n < G::RAW_ROWS) rb[(frow0 + 3 * n) * RPT + fcol] = pf[n];
+    };
+    auto issue = [&](int kk, int c) {                    // one thread: TMA of plane kk's box
+        const Shift s = a.sh[c];
+        const int x = tx0 - HX + s.ox;
+        const int b = (kk - kk0) & 1;
+        bar_expect(&tbar[b], (uint32_t)(G::RAW_ROWS * RPT * sizeof(T)));
+        tma_load(rawbuf(b), &tmap, &tbar[b], x & ~(AL - 1), ty0 - R + s.oy, c);
+    };
+    auto box_ready = [&](int kk) {                       // every thread: plane kk's box landed
+        const int b = (kk - kk0) & 1;
+        if (!bar_wait(&tbar[b], (uint32_t)(((kk - kk0) >> 1) & 1)) && tid == 0)
+            atomicOr(&a.sd->status, (unsigned int)LOC_DEV_ERR_TIMEOUT);
     };
 
-    const int kk0 = -rt, kk_end = K + rt;                 // source planes kk0 .. kk_end - 1
-    fetch(kk0);
-    commit();
-    if (kk0 + 1 < kk_end) fetch(kk0 + 1);
+    // channels of the planes, kept incrementally: c(kk) = kk mod K
+    auto chan_step = [&](int c) { return c + 1 == K ? 0 : c + 1; };
+    const int c0 = ((kk0 % K) + K) % K, c1 = chan_step(c0), c2 = chan_step(c1);
+    if (tma) {
+        if (tid == 0) {
+            bar_init(&tbar[0], 1);
+            bar_init(&tbar[1], 1);
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
+        __syncthreads();
+        if (tid == 0) {
+            issue(kk0, c0);
+            if (kk0 + 1 < kk_end) issue(kk0 + 1, c1);
+        }
+        box_ready(kk0);
+    } else {
+        fetch(c0);
+        commit(kk0);
+        if (kk0 + 1 < kk_end) fetch(c1);
+    }
     __syncthreads();
 
     // this thread's block: output rows oy0 .. oy0+BY-1, columns ox0 .. ox0+3 of the tile
     const int lx = lane & 7, ly = lane >> 3;
     const int oy0 = 4 * BY * warp + BY * ly, ox0 = 4 * lx;
-    bool interior = true, any_free = false;
+    bool interior = true;
     for (int r = 0; r < G::NR; ++r)
         for (int cc = HX - R; cc < HX + 4 + R; ++cc) interior &= Ms[(oy0 + r) * P + ox0 + cc] > 0.0f;
-#pragma unroll
-    for (int oy = 0; oy < BY; ++oy)
-#pragma unroll
-        for (int ox = 0; ox < 4; ++ox) any_free |= Ms[(oy0 + oy + R) * P + HX + ox0 + ox] > 0.0f;
-
-    // per warp: every lane interior (G_k is the stencil sum) / some lane with a free cell
-    const bool warp_interior = __all_sync(0xffffffffu, interior);
-    const bool warp_any_free = __any_sync(0xffffffffu, any_free);
     uint32_t free_bits = 0;                               // centres of this block that are free
 #pragma unroll
     for (int y = 0; y < BY; ++y)
 #pragma unroll
         for (int x = 0; x < 4; ++x)
             if (Ms[(oy0 + y + R) * P + HX + ox0 + x] > 0.0f) free_bits |= 1u << (4 * y + x);
+    // per warp: every lane interior (G_k is the stencil sum) / some lane with a free cell
+    const bool warp_interior = __all_sync(0xffffffffu, interior);
+    const bool warp_any_free = __any_sync(0xffffffffu, free_bits != 0);
     const float inv_sa = 1.0f / a.sigma_a, inv_sc = 1.0f / a.sigma_c;
 
     KahanF acc;
+    int cur = 0;                                          // ring slot of plane kk: (kk - kk0) mod nring
+    int c_cur = c0, c_pre = c2;                           // channels of planes kk and kk + 2
     for (int kk = kk0; kk < kk_end; ++kk) {
-        const Shift s = a.sh[((kk % K) + K) % K];
+        const Shift s = a.sh[c_cur];
         const float fx = s.fx, fy = s.fy, gx0 = 1.0f - fx, gy0 = 1.0f - fy;
+        const int xo = tma ? ((tx0 - HX + s.ox) & (AL - 1)) : 0;
         const int o = kk - rt;                            // output channel, once the ring is full
         const bool out = kk - kk0 >= 2 * rt;
-        float* slot = ring + (size_t)((kk - kk0) % nring) * G::RR * P;
-        int sl[2 * LOC_MAX_R_THETA];                      // ring slots of planes o - rt .. o + rt - 1
+        float* slot = ring + (size_t)cur * G::RR * P;
+        // ring slots of planes o - rt .. o + rt - 1: (cur + 1 + d) mod nring
+        int sl[2 * LOC_MAX_R_THETA];
 #pragma unroll
-        for (int d = 0; d < 2 * LOC_MAX_R_THETA; ++d) sl[d] = (o + d - kk0 - rt) % nring;
+        for (int d = 0; d < 2 * LOC_MAX_R_THETA; ++d) {
+            const int v = cur + 1 + d;
+            sl[d] = v >= nring ? v - nring : v;
+        }
+        const T* rb = rawbuf((kk - kk0) & 1) + xo;
         // S = M * bilinear(raw) into the ring and, once the ring is full, C = theta sum of the
-        // ring, 4 cells per item.  A thread always owns the same items, so the ring cells it
-        // sums are its own writes: no barrier between the two.
+        // ring, 4 cells per item
         for (int q = tid; q < G::RR * NG; q += NT) {
             const int row = q / NG, g4 = (q % NG) * 4, off = row * P + g4;
             float r0[5], r1[5], mk[4];
-            ld4(raw + row * RAW_P + g4, r0);
-            r0[4] = raw[row * RAW_P + g4 + 4];
-            ld4(raw + (row + 1) * RAW_P + g4, r1);
-            r1[4] = raw[(row + 1) * RAW_P + g4 + 4];
+#pragma unroll
+            for (int x = 0; x < 5; ++x) {
+                r0[x] = to_f<T>(rb[row * RPT + g4 + x]);
+                r1[x] = to_f<T>(rb[(row + 1) * RPT + g4 + x]);
+            }
             ld4(Ms + off, mk);
             float sv[4];
 #pragma unroll
@@ -287,9 +355,11 @@ __global__ void __launch_bounds__(NT, 3) step_aniso_kernel(const __grid_constant
             }
         }
         __syncthreads();                                  // raw consumed; C and the stencil written
-        if (kk + 1 < kk_end) {
-            commit();                                     // plane kk + 1 into raw
-            if (kk + 2 < kk_end) fetch(kk + 2);           // plane kk + 2 in flight
+        if (tma) {
+            if (tid == 0 && kk + 2 < kk_end) issue(kk + 2, c_pre);   // into the buffer just consumed
+        } else if (kk + 1 < kk_end) {
+            commit(kk + 1);
+            if (kk + 2 < kk_end) fetch(c_pre);           // plane kk + 2 in flight
         }
         if (out) {
             float part = 0.0f;
@@ -333,13 +403,13 @@ __global__ void __launch_bounds__(NT, 3) step_aniso_kernel(const __grid_constant
                     if ((W & 3) == 0 && gi + 3 < W) {
                         Vec4<T>::st(oplane + off, ov);
 #pragma unroll
-                        for (int x = 0; x < 4; ++x) part += as_float(ov[x]);
+                        for (int x = 0; x < 4; ++x) part += to_f<T>(ov[x]);
                     } else {
 #pragma unroll
                         for (int x = 0; x < 4; ++x)
                             if (gi + x < W) {
                                 oplane[off + x] = ov[x];
-                                part += as_float(ov[x]);
+                                part += to_f<T>(ov[x]);
                             }
                     }
                 }
@@ -356,8 +426,12 @@ __global__ void __launch_bounds__(NT, 3) step_aniso_kernel(const __grid_constant
             }
             acc.add(part);
         }
-        // the next plane overwrites raw's consumer (the S pass), C and the stencil
+        if (tma && kk + 1 < kk_end) box_ready(kk + 1);
+        // the next plane reads its raw box and overwrites C and the stencil
         __syncthreads();
+        cur = cur + 1 == nring ? 0 : cur + 1;
+        c_cur = chan_step(c_cur);
+        c_pre = chan_step(c_pre);
     }
 
     const double bt = block_sum<NT>(acc.value(), red);
@@ -382,45 +456,60 @@ __global__ void __launch_bounds__(NT, 3) step_aniso_kernel(const __grid_constant
 }
 
 template <typename T, int R>
-cudaError_t launch_r(const StepArgs& a, cudaStream_t st) {
-    const size_t smem = aniso_smem_bytes<R>(a.r_th);
+cudaError_t launch_r(const StepArgs& a, const void* tmap, cudaStream_t st) {
+    const size_t smem = aniso_smem_bytes<T, R>(a.r_th);
     static bool attr_set = false;                 // the largest size any session can ask for
     if (!attr_set) {
         const cudaError_t e = cudaFuncSetAttribute(step_aniso_kernel<T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                   (int)aniso_smem_bytes<R>(LOC_MAX_R_THETA));
+                                                   (int)aniso_smem_bytes<T, R>(LOC_MAX_R_THETA));
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
+    CUtensorMap tm;
+    memset(&tm, 0, sizeof(tm));
+    if (tmap) memcpy(&tm, tmap, sizeof(tm));
     dim3 grid((a.W + TW - 1) / TW, (a.H + TH - 1) / TH);
-    step_aniso_kernel<T, R><<<grid, NT, smem, st>>>(a);
+    step_aniso_kernel<T, R><<<grid, NT, smem, st>>>(a, tm, tmap ? 1 : 0);
     return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_t(const StepArgs& a, cudaStream_t st) {
+cudaError_t launch_t(const StepArgs& a, const void* tmap, cudaStream_t st) {
     switch (a.r_xy) {
-        case 0: return launch_r<T, 0>(a, st);
-        case 1: return launch_r<T, 1>(a, st);
-        case 2: return launch_r<T, 2>(a, st);
-        case 3: return launch_r<T, 3>(a, st);
-        case 4: return launch_r<T, 4>(a, st);
+        case 0: return launch_r<T, 0>(a, tmap, st);
+        case 1: return launch_r<T, 1>(a, tmap, st);
+        case 2: return launch_r<T, 2>(a, tmap, st);
+        case 3: return launch_r<T, 3>(a, tmap, st);
+        case 4: return launch_r<T, 4>(a, tmap, st);
         default: return cudaErrorInvalidValue;
     }
 }
 
 }  // namespace
 
-cudaError_t launch_step_aniso(const StepArgs& a, int storage, cudaStream_t st) {
+bool aniso_tma_eligible(int W, int storage) {
+    // the row pitch of a belief plane must be a multiple of 16 bytes
+    return storage == LOC_F32 ? W % 4 == 0 : W % 8 == 0;
+}
+
+cudaError_t make_aniso_tmap(void* tmap_out, const void* B, int storage, int H, int W, int K, int r_xy) {
+    if (!aniso_tma_eligible(W, storage) || r_xy < 0 || r_xy > LOC_MAX_R_XY) return cudaErrorInvalidValue;
+    const int bw = storage == LOC_F32 ? raw_pitch<float>() : raw_pitch<__half>();
+    return make_box_tmap(tmap_out, B, storage, H, W, K, bw, TH + 2 * r_xy + 1);
+}
+
+cudaError_t launch_step_aniso(const StepArgs& a, const void* tmap, int storage, cudaStream_t st) {
     static_assert(LOC_MAX_R_XY <= HX, "the region's left margin must cover the x/y radius");
     static_assert(3 * RAW_COLS <= NT && NT == 4 * 32 && TH == 4 * 4 * BY && TW == 32,
                   "three rows of input columns per fetch pass; 4 warps of 8 x 4 lanes cover the tile");
+    static_assert(RAW_COLS + 3 <= 44 && RAW_COLS + 7 <= 48, "the box covers 41 columns after the x rounding");
     if (a.r_xy < 0 || a.r_xy > LOC_MAX_R_XY || a.r_th < 0 || a.r_th > LOC_MAX_R_THETA ||
         !(a.sigma_a > 0.0f) || !(a.sigma_c > 0.0f))
         return cudaErrorInvalidValue;
     switch (storage) {
-        case LOC_F32: return launch_t<float>(a, st);
-        case LOC_BF16: return launch_t<__nv_bfloat16>(a, st);
-        case LOC_F16: return launch_t<__half>(a, st);
+        case LOC_F32: return launch_t<float>(a, tmap, st);
+        case LOC_BF16: return launch_t<__nv_bfloat16>(a, tmap, st);
+        case LOC_F16: return launch_t<__half>(a, tmap, st);
         default: return cudaErrorInvalidValue;
     }
 }

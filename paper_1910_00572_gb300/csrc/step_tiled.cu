@@ -441,17 +441,21 @@ int step_tiled_default_cfg(int H, int W, int K, int storage) {
 }
 
 cudaError_t make_step_tmap(void* tmap_out, const void* B, int storage, int H, int W, int K, int cfg) {
+    if (cfg < 1 || cfg > step_tiled_num_cfgs()) return cudaErrorInvalidValue;
+    const int bw = cfg < 8 ? BW : (storage == LOC_F32 ? pairs::pbw<float>() : pairs::pbw<__half>());
+    return make_box_tmap(tmap_out, B, storage, H, W, K, bw, cfg_tile_rows(cfg) + 2 * R + 1);
+}
+
+cudaError_t make_box_tmap(void* tmap_out, const void* B, int storage, int H, int W, int K, int box_w, int box_h) {
     EncodeTiled enc = encoder();
     if (!enc) return cudaErrorNotSupported;
-    if (cfg < 1 || cfg > step_tiled_num_cfgs()) return cudaErrorInvalidValue;
     const size_t e = storage == LOC_F32 ? 4 : 2;
     const CUtensorMapDataType dt = storage == LOC_F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
                                    : storage == LOC_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
                                                          : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
     const cuuint64_t dims[3] = {(cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)K};
     const cuuint64_t strides[2] = {(cuuint64_t)W * e, (cuuint64_t)W * H * e};
-    const int bw = cfg < 8 ? BW : (storage == LOC_F32 ? pairs::pbw<float>() : pairs::pbw<__half>());
-    const cuuint32_t box[3] = {(cuuint32_t)bw, (cuuint32_t)(cfg_tile_rows(cfg) + 2 * R + 1), 1};
+    const cuuint32_t box[3] = {(cuuint32_t)box_w, (cuuint32_t)box_h, 1};
     const cuuint32_t estr[3] = {1, 1, 1};
     CUresult r = enc(static_cast<CUtensorMap*>(tmap_out), dt, 3, const_cast<void*>(B), dims, strides, box,
                      estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,

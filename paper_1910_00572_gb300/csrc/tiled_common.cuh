@@ -1,6 +1,7 @@
 // Building blocks of the tiled propagation kernels (single session, warp-specialised and
 // batched): tile configurations, shared-memory layouts, TMA/mbarrier helpers, packed FP32
-// helpers and the S-, X- and P-passes.  Included by step_tiled.cu and batch.cu only.
+// helpers and the S-, X- and P-passes.  Included by step_tiled.cu and batch.cu; step_aniso.cu
+// uses its TMA and mbarrier helpers.
 #pragma once
 #include <cuda.h>
 

@@ -44,10 +44,12 @@ def check_close(gpu, ref):
     return float(err.max())
 
 
-def test_trajectory_matches_oracle():
-    """A walk with turns on a ragged 52 x 75 crop of a rooms map (tiles of 16 x 32 cells leave
-    a tail in both directions), radius 4 in x/y and 3 in theta, from a peaked belief."""
-    occ = floorplan.rooms_map(4, size=80)[:52, :75].copy()
+@pytest.mark.parametrize("H,W", [(52, 75), (56, 72)], ids=["plain loads", "TMA boxes"])
+def test_trajectory_matches_oracle(H, W):
+    """A walk with turns on a crop of a rooms map that leaves a ragged tail of the 32 x 32
+    tiles in both directions, radius 4 in x/y and 3 in theta, from a peaked belief.  A row
+    pitch of 75 cells takes the plain-load input path, 72 the TMA path."""
+    occ = floorplan.rooms_map(4, size=80)[:H, :W].copy()
     K, cell, sx, sy, sth = 16, 0.1, 1.2, 0.5, 1.0
     walk = trajectory.random_walk(occ, cell, 12, 0.1, 7)
     b0 = fields.belief_like(occ, K, seed=3, dtype=np.float32)
