@@ -126,6 +126,43 @@ __device__ __forceinline__ void ld4(const float* p, float* d) {
     d[0] = v.x; d[1] = v.y; d[2] = v.z; d[3] = v.w;
 }
 
+// Raw elements p[0 .. NV) as float by aligned vector loads: 8 FP32 (two 16-byte loads, p
+// 16-byte aligned) or 12 16-bit (three 8-byte loads, p 8-byte aligned).
+template <typename T> struct RawRow;
+template <> struct RawRow<float> {
+    static constexpr int NV = 8;
+    static __device__ __forceinline__ void ld(const float* p, float (&v)[NV]) {
+        ld4(p, v);
+        ld4(p + 4, v + 4);
+    }
+};
+template <typename H2, float2 (*CVT)(H2)>
+__device__ __forceinline__ void ld12_16(const void* p, float (&v)[12]) {
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        const uint2 u = reinterpret_cast<const uint2*>(p)[q];
+        H2 a, b;
+        memcpy(&a, &u.x, 4);
+        memcpy(&b, &u.y, 4);
+        const float2 fa = CVT(a), fb = CVT(b);
+        v[4 * q] = fa.x; v[4 * q + 1] = fa.y; v[4 * q + 2] = fb.x; v[4 * q + 3] = fb.y;
+    }
+}
+__device__ __forceinline__ float2 cvt_bf2(__nv_bfloat162 h) { return __bfloat1622float2(h); }
+__device__ __forceinline__ float2 cvt_h2(__half2 h) { return __half22float2(h); }
+template <> struct RawRow<__nv_bfloat16> {
+    static constexpr int NV = 12;
+    static __device__ __forceinline__ void ld(const __nv_bfloat16* p, float (&v)[NV]) {
+        ld12_16<__nv_bfloat162, cvt_bf2>(p, v);
+    }
+};
+template <> struct RawRow<__half> {
+    static constexpr int NV = 12;
+    static __device__ __forceinline__ void ld(const __half* p, float (&v)[NV]) { ld12_16<__half2, cvt_h2>(p, v); }
+};
+
+template <int V> using IC = std::integral_constant<int, V>;
+
 // The stencil over one 2 x 4 block: t[oy][ox] = sum g[dj][di] C[oy+dj][ox+di] and, unless the
 // warp is interior, gm[oy][ox] = sum g[dj][di] M[oy+dj][ox+di], both in row-major tap order.
 // `c0` / `m0` point at the block's first source row, 4 - R columns left of its first cell
@@ -299,43 +336,62 @@ __global__ void __launch_bounds__(NT, 3) step_aniso_kernel(const __grid_constant
             const int v = cur + 1 + d;
             sl[d] = v >= nring ? v - nring : v;
         }
-        const T* rb = rawbuf((kk - kk0) & 1) + xo;
+        const T* rb = rawbuf((kk - kk0) & 1);
         // S = M * bilinear(raw) into the ring and, once the ring is full, C = theta sum of the
-        // ring, 4 cells per item
-        for (int q = tid; q < G::RR * NG; q += NT) {
-            const int row = q / NG, g4 = (q % NG) * 4, off = row * P + g4;
-            float r0[5], r1[5], mk[4];
+        // ring, 4 cells per item; XO = the box's column offset (uniform over the CTA)
+        auto fused = [&](auto xo_c) {
+            constexpr int XO = decltype(xo_c)::value;
+            constexpr int NQ = (G::RR * NG + NT - 1) / NT;
 #pragma unroll
-            for (int x = 0; x < 5; ++x) {
-                r0[x] = to_f<T>(rb[row * RPT + g4 + x]);
-                r1[x] = to_f<T>(rb[(row + 1) * RPT + g4 + x]);
+            for (int n = 0; n < NQ; ++n) {
+                const int q = tid + n * NT;
+                if (q >= G::RR * NG) break;
+                const int row = q / NG, g4 = (q % NG) * 4, off = row * P + g4;
+                float r0[RawRow<T>::NV], r1[RawRow<T>::NV], mk[4];
+                RawRow<T>::ld(rb + row * RPT + g4, r0);
+                RawRow<T>::ld(rb + (row + 1) * RPT + g4, r1);
+                ld4(Ms + off, mk);
+                float sv[4];
+#pragma unroll
+                for (int x = 0; x < 4; ++x) {
+                    const float top = gx0 * r0[XO + x] + fx * r0[XO + x + 1];
+                    const float bot = gx0 * r1[XO + x] + fx * r1[XO + x + 1];
+                    sv[x] = mk[x] * (gy0 * top + fy * bot);
+                }
+                *reinterpret_cast<float4*>(slot + off) = make_float4(sv[0], sv[1], sv[2], sv[3]);
+                if (out) {
+                    float v[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+                    for (int d = 0; d < 2 * LOC_MAX_R_THETA; ++d) {
+                        if (d < 2 * rt) {
+                            const float g = a.gt[d];
+                            float x4[4];
+                            ld4(ring + (size_t)sl[d] * G::RR * P + off, x4);
+#pragma unroll
+                            for (int x = 0; x < 4; ++x) v[x] += g * x4[x];
+                        }
+                    }
+                    const float g = a.gt[2 * rt];         // the newest plane, o + rt
+#pragma unroll
+                    for (int x = 0; x < 4; ++x) v[x] += g * sv[x];
+                    *reinterpret_cast<float4*>(Cs + off) = make_float4(v[0], v[1], v[2], v[3]);
+                }
             }
-            ld4(Ms + off, mk);
-            float sv[4];
-#pragma unroll
-            for (int x = 0; x < 4; ++x) {
-                const float top = gx0 * r0[x] + fx * r0[x + 1];
-                const float bot = gx0 * r1[x] + fx * r1[x + 1];
-                sv[x] = mk[x] * (gy0 * top + fy * bot);
-            }
-            *reinterpret_cast<float4*>(slot + off) = make_float4(sv[0], sv[1], sv[2], sv[3]);
-            if (out) {
-                float v[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-                for (int d = 0; d < 2 * LOC_MAX_R_THETA; ++d) {
-                    if (d < 2 * rt) {
-                        const float g = a.gt[d];
-                        float x4[4];
-                        ld4(ring + (size_t)sl[d] * G::RR * P + off, x4);
-#pragma unroll
-                        for (int x = 0; x < 4; ++x) v[x] += g * x4[x];
+        };
+        switch (xo) {
+            case 0: fused(IC<0>{}); break;
+            case 1: fused(IC<1>{}); break;
+            case 2: fused(IC<2>{}); break;
+            case 3: fused(IC<3>{}); break;
+            default:
+                if constexpr (AL == 8) {
+                    switch (xo) {
+                        case 4: fused(IC<4>{}); break;
+                        case 5: fused(IC<5>{}); break;
+                        case 6: fused(IC<6>{}); break;
+                        default: fused(IC<7>{}); break;
                     }
                 }
-                const float g = a.gt[2 * rt];             // the newest plane, o + rt
-#pragma unroll
-                for (int x = 0; x < 4; ++x) v[x] += g * sv[x];
-                *reinterpret_cast<float4*>(Cs + off) = make_float4(v[0], v[1], v[2], v[3]);
-            }
         }
         if (out) {
             // channel o's x/y stencil (unnormalised), row-major with pitch GP
