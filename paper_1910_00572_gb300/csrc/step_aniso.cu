@@ -14,24 +14,30 @@
 // Channel k's stencil is computed in the CTA from phi_k (FP32 sin/cos/exp); its normalisation
 // cancels in T_k / G_k.
 //
-// Layout.  One CTA of 128 threads owns a 32 x 32 tile of output cells and streams the source
-// planes kk = -r_th .. K-1+r_th.  Shared memory holds, over the tile plus R rows above and
-// below and 4 columns left and right (a 40-column region, so that every 4-cell group is
-// 16-byte aligned): the ring of the last 2 r_th + 1 planes S, the theta sum C and the map M;
-// and, in the storage type, the raw (shifted) input boxes of the current and the next plane.
-// The box of the plane after next is fetched while the current plane is computed: by one TMA
-// copy (x rounded down to 16 bytes, zeros outside the grid, an mbarrier with a bounded wait)
-// where the row pitch allows it, else by plain loads into registers (one column per thread,
-// coalesced across a warp) stored after the current plane's S pass; the restart input (the
-// map) always takes the plain loads.
+// Layout.  One CTA owns a 32 x 32 tile of output cells and streams the source planes
+// kk = -r_th .. K-1+r_th.  Shared memory holds, over the tile plus R rows above and below and
+// 4 columns left and right (a 40-column region, so that every 4-cell group is 16-byte
+// aligned): the ring of the last 2 r_th + 1 planes S, two buffers of the theta sum C and of
+// the channel's stencil, and the map M; and, in the storage type, the raw (shifted) input
+// boxes of two planes.
 //
-// Each thread owns a 2 x 4 block of output cells (lanes 8 wide x 4 high per warp); each
-// stencil row is three 16-byte loads of C (and of M), conflict-free across each 8-lane
+// Warp-specialised pipeline.  Two producer warps take plane kk: its input box (one TMA copy
+// per plane, x rounded down to 16 bytes, zeros outside the grid, issued two planes ahead,
+// where the row pitch allows; else plain loads, and always for the restart input, the map),
+// the S pass into the ring and, once the ring is full, C of channel o = kk - r_th and its
+// stencil into buffer o & 1.  A producer always computes S and C for the same region cells,
+// so the ring cells it sums are its own writes.  Four consumer warps take channel o from that
+// buffer: the stencil, the division by G_k, the store and the Z partial sums.  The hand-offs
+// are mbarriers (FULL[b]: the 64 producers arrive after writing; EMPTY[b]: the 128 consumers
+// arrive after reading) with bounded waits; the producers also meet at a named barrier
+// before a raw box is overwritten.
+//
+// Each consumer thread owns a 2 x 4 block of output cells (lanes 8 wide x 4 high per warp);
+// each stencil row is three 16-byte loads of C (and of M), conflict-free across each 8-lane
 // quarter warp, reused by up to 2 x 4 x (2R+1) taps, with the row loop unrolled at compile
-// time.  A thread always computes S and C for the same region cells, so the ring cells it sums
-// are its own writes and the two passes are fused.  Where every map cell under a warp's
-// stencil windows is free, G_k is the stencil's own sum taken in the same order, so the warp
-// skips the M loads and half the FMAs with a bit-identical result.
+// time.  Where every map cell under a warp's stencil windows is free, G_k is the stencil's own
+// sum taken in the same order, so the warp skips the M loads and half the FMAs with a
+// bit-identical result.
 #include <type_traits>
 
 #include "tiled_common.cuh"
@@ -44,7 +50,8 @@ using tiled::bar_init;
 using tiled::bar_wait;
 using tiled::tma_load;
 
-constexpr int TH = 32, TW = 32, NT = 128;
+constexpr int TH = 32, TW = 32;
+constexpr int NP = 128, NC = 128, NT = NP + NC;  // producer and consumer threads
 constexpr int BY = 2;                          // output rows per thread (4 columns each)
 constexpr int HX = 4;                          // region columns left of the tile
 constexpr int RCOLS = TW + 2 * HX;             // 40 region columns
@@ -60,7 +67,6 @@ template <int R>
 struct Geo {
     static constexpr int RR = TH + 2 * R;                 // region rows
     static constexpr int RAW_ROWS = RR + 1;
-    static constexpr int NPF = (RAW_ROWS + 2) / 3;        // prefetch registers per thread
     static constexpr int D = 2 * R + 1;                   // stencil side
     static constexpr int GP = (D + 3) / 4 * 4;            // stencil row pitch
     static constexpr int NR = BY + 2 * R;                 // source rows under a block
@@ -75,8 +81,8 @@ template <typename T, int R>
 size_t aniso_smem_bytes(int rt) {
     using G = Geo<R>;
     const size_t nring = 2 * (size_t)rt + 1;
-    return 2 * raw_buf_bytes<T, R>() + (nring + 2) * G::RR * P * sizeof(float) +
-           (size_t)G::D * G::GP * sizeof(float);
+    return 2 * raw_buf_bytes<T, R>() + (nring + 3) * G::RR * P * sizeof(float) +
+           2 * (size_t)G::D * G::GP * sizeof(float);
 }
 
 template <typename T> __device__ __forceinline__ float to_f(T v);
@@ -163,6 +169,12 @@ template <> struct RawRow<__half> {
 
 template <int V> using IC = std::integral_constant<int, V>;
 
+__device__ __forceinline__ void bar_arrive(unsigned long long* b) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tiled::su32(b)) : "memory");
+}
+// named barrier 1 among the producer threads only (every producer reaches each one)
+__device__ __forceinline__ void producers_sync() { asm volatile("bar.sync 1, %0;" ::"n"(NP) : "memory"); }
+
 // The stencil over one 2 x 4 block: t[oy][ox] = sum g[dj][di] C[oy+dj][ox+di] and, unless the
 // warp is interior, gm[oy][ox] = sum g[dj][di] M[oy+dj][ox+di], both in row-major tap order.
 // `c0` / `m0` point at the block's first source row, 4 - R columns left of its first cell
@@ -199,15 +211,17 @@ __device__ __forceinline__ void stencil_block(const float* c0, const float* m0, 
 }
 
 template <typename T, int R>
-__global__ void __launch_bounds__(NT, 3) step_aniso_kernel(const __grid_constant__ StepArgs a,
+__global__ void __launch_bounds__(NT, 2) step_aniso_kernel(const __grid_constant__ StepArgs a,
                                                            const __grid_constant__ CUtensorMap tmap,
                                                            int use_tma) {
     using G = Geo<R>;
     constexpr int RPT = raw_pitch<T>();
     constexpr size_t RAW_BUF = raw_buf_bytes<T, R>();
+    constexpr int AL = 16 / (int)sizeof(T);              // TMA x alignment in elements
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ double red[NT / 32];
-    __shared__ unsigned long long tbar[2];
+    __shared__ unsigned long long tbar[2], full[2], empty[2];
+    __shared__ int fail_p, fail_c;                        // a bounded wait gave up (per role)
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int H = a.H, W = a.W, K = a.K, rt = a.r_th;
@@ -215,9 +229,9 @@ __global__ void __launch_bounds__(NT, 3) step_aniso_kernel(const __grid_constant
     const int ty0 = blockIdx.y * TH, tx0 = blockIdx.x * TW;
 
     float* ring = reinterpret_cast<float*>(smem_raw + 2 * RAW_BUF);       // [nring][RR][P]
-    float* Cs = ring + (size_t)nring * G::RR * P;                         // [RR][P]
-    float* Ms = Cs + G::RR * P;                                           // [RR][P]
-    float* gs = Ms + G::RR * P;                                           // [D][GP]
+    float* Cbuf = ring + (size_t)nring * G::RR * P;                       // [2][RR][P]
+    float* Ms = Cbuf + 2 * G::RR * P;                                     // [RR][P]
+    float* gsb = Ms + G::RR * P;                                          // [2][D][GP]
     // raw box of buffer b: [RAW_ROWS][RPT] elements of T
     auto rawbuf = [&](int b) { return reinterpret_cast<T*>(smem_raw + (size_t)b * RAW_BUF); };
 
@@ -228,7 +242,6 @@ __global__ void __launch_bounds__(NT, 3) step_aniso_kernel(const __grid_constant
     T* Bout = static_cast<T*>(a.B_out);
     // TMA writes whole boxes into 128-byte aligned buffers
     const bool tma = use_tma && !reinit && (tiled::su32(smem_raw) & 127u) == 0;
-    constexpr int AL = 16 / (int)sizeof(T);              // TMA x alignment in elements
 
     // the map over the region (0 outside the grid)
     for (int q = tid; q < G::RR * RCOLS; q += NT) {
@@ -236,188 +249,190 @@ __global__ void __launch_bounds__(NT, 3) step_aniso_kernel(const __grid_constant
         const int j = ty0 - R + row, i = tx0 - HX + col;
         Ms[row * P + col] = (j >= 0 && j < H && i >= 0 && i < W) ? (float)a.trav[(size_t)j * W + i] : 0.0f;
     }
+    if (tid == 0) {
+        bar_init(&tbar[0], 1);
+        bar_init(&tbar[1], 1);
+        bar_init(&full[0], NP);
+        bar_init(&full[1], NP);
+        bar_init(&empty[0], NC);
+        bar_init(&empty[1], NC);
+        fail_p = fail_c = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
 
     // Source planes kk0 .. kk_end - 1; plane kk sits in raw buffer (kk - kk0) & 1, its box
     // starting at input column tx0 - HX + ox - xo (xo = 0 on the plain-load path).
     const int kk0 = -rt, kk_end = K + rt;
-    // plain loads: thread (frow0, fcol) holds rows frow0, frow0 + 3, ... of column fcol
-    // (threads 123 .. 127 idle)
-    const int fcol = tid % RAW_COLS, frow0 = tid / RAW_COLS;
-    T pf[G::NPF];
-    auto fetch = [&](int c) {
-        const Shift s = a.sh[c];
-        const int gi = tx0 - HX + s.ox + fcol;
-        const bool col_ok = frow0 < 3 && gi >= 0 && gi < W;
-        const int gj0 = ty0 - R + s.oy + frow0;
-#pragma unroll
-        for (int n = 0; n < G::NPF; ++n) {
-            const int gj = gj0 + 3 * n;
-            T v = from_u8<T>(0);
-            if (col_ok && frow0 + 3 * n < G::RAW_ROWS && gj >= 0 && gj < H) {
-                const size_t o = (size_t)gj * W + gi;
-                v = reinit ? from_u8<T>(a.trav[o]) : Bin[(size_t)c * H * W + o];
-            }
-            pf[n] = v;
-        }
-    };
-    auto commit = [&](int kk) {
-        if (frow0 >= 3) return;
-        T* rb = rawbuf((kk - kk0) & 1);
-#pragma unroll
-        for (int n = 0; n < G::NPF; ++n)
-            if (frow0 + 3 * n < G::RAW_ROWS) rb[(frow0 + 3 * n) * RPT + fcol] = pf[n];
-    };
-    auto issue = [&](int kk, int c) {                    // one thread: TMA of plane kk's box
-        const Shift s = a.sh[c];
-        const int x = tx0 - HX + s.ox;
-        const int b = (kk - kk0) & 1;
-        bar_expect(&tbar[b], (uint32_t)(G::RAW_ROWS * RPT * sizeof(T)));
-        tma_load(rawbuf(b), &tmap, &tbar[b], x & ~(AL - 1), ty0 - R + s.oy, c);
-    };
-    auto box_ready = [&](int kk) {                       // every thread: plane kk's box landed
-        const int b = (kk - kk0) & 1;
-        if (!bar_wait(&tbar[b], (uint32_t)(((kk - kk0) >> 1) & 1)) && tid == 0)
-            atomicOr(&a.sd->status, (unsigned int)LOC_DEV_ERR_TIMEOUT);
-    };
-
-    // channels of the planes, kept incrementally: c(kk) = kk mod K
     auto chan_step = [&](int c) { return c + 1 == K ? 0 : c + 1; };
-    const int c0 = ((kk0 % K) + K) % K, c1 = chan_step(c0), c2 = chan_step(c1);
-    if (tma) {
-        if (tid == 0) {
-            bar_init(&tbar[0], 1);
-            bar_init(&tbar[1], 1);
-            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        }
-        __syncthreads();
-        if (tid == 0) {
-            issue(kk0, c0);
-            if (kk0 + 1 < kk_end) issue(kk0 + 1, c1);
-        }
-        box_ready(kk0);
-    } else {
-        fetch(c0);
-        commit(kk0);
-        if (kk0 + 1 < kk_end) fetch(c1);
-    }
-    __syncthreads();
-
-    // this thread's block: output rows oy0 .. oy0+BY-1, columns ox0 .. ox0+3 of the tile
-    const int lx = lane & 7, ly = lane >> 3;
-    const int oy0 = 4 * BY * warp + BY * ly, ox0 = 4 * lx;
-    bool interior = true;
-    for (int r = 0; r < G::NR; ++r)
-        for (int cc = HX - R; cc < HX + 4 + R; ++cc) interior &= Ms[(oy0 + r) * P + ox0 + cc] > 0.0f;
-    uint32_t free_bits = 0;                               // centres of this block that are free
-#pragma unroll
-    for (int y = 0; y < BY; ++y)
-#pragma unroll
-        for (int x = 0; x < 4; ++x)
-            if (Ms[(oy0 + y + R) * P + HX + ox0 + x] > 0.0f) free_bits |= 1u << (4 * y + x);
-    // per warp: every lane interior (G_k is the stencil sum) / some lane with a free cell
-    const bool warp_interior = __all_sync(0xffffffffu, interior);
-    const bool warp_any_free = __any_sync(0xffffffffu, free_bits != 0);
-    const float inv_sa = 1.0f / a.sigma_a, inv_sc = 1.0f / a.sigma_c;
-
+    const int c0 = ((kk0 % K) + K) % K;
     KahanF acc;
-    int cur = 0;                                          // ring slot of plane kk: (kk - kk0) mod nring
-    int c_cur = c0, c_pre = c2;                           // channels of planes kk and kk + 2
-    for (int kk = kk0; kk < kk_end; ++kk) {
-        const Shift s = a.sh[c_cur];
-        const float fx = s.fx, fy = s.fy, gx0 = 1.0f - fx, gy0 = 1.0f - fy;
-        const int xo = tma ? ((tx0 - HX + s.ox) & (AL - 1)) : 0;
-        const int o = kk - rt;                            // output channel, once the ring is full
-        const bool out = kk - kk0 >= 2 * rt;
-        float* slot = ring + (size_t)cur * G::RR * P;
-        // ring slots of planes o - rt .. o + rt - 1: (cur + 1 + d) mod nring
-        int sl[2 * LOC_MAX_R_THETA];
-#pragma unroll
-        for (int d = 0; d < 2 * LOC_MAX_R_THETA; ++d) {
-            const int v = cur + 1 + d;
-            sl[d] = v >= nring ? v - nring : v;
-        }
-        const T* rb = rawbuf((kk - kk0) & 1);
-        // S = M * bilinear(raw) into the ring and, once the ring is full, C = theta sum of the
-        // ring, 4 cells per item; XO = the box's column offset (uniform over the CTA)
-        auto fused = [&](auto xo_c) {
-            constexpr int XO = decltype(xo_c)::value;
-            constexpr int NQ = (G::RR * NG + NT - 1) / NT;
-#pragma unroll
-            for (int n = 0; n < NQ; ++n) {
-                const int q = tid + n * NT;
-                if (q >= G::RR * NG) break;
-                const int row = q / NG, g4 = (q % NG) * 4, off = row * P + g4;
-                float r0[RawRow<T>::NV], r1[RawRow<T>::NV], mk[4];
-                RawRow<T>::ld(rb + row * RPT + g4, r0);
-                RawRow<T>::ld(rb + (row + 1) * RPT + g4, r1);
-                ld4(Ms + off, mk);
-                float sv[4];
-#pragma unroll
-                for (int x = 0; x < 4; ++x) {
-                    const float top = gx0 * r0[XO + x] + fx * r0[XO + x + 1];
-                    const float bot = gx0 * r1[XO + x] + fx * r1[XO + x + 1];
-                    sv[x] = mk[x] * (gy0 * top + fy * bot);
-                }
-                *reinterpret_cast<float4*>(slot + off) = make_float4(sv[0], sv[1], sv[2], sv[3]);
-                if (out) {
-                    float v[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-                    for (int d = 0; d < 2 * LOC_MAX_R_THETA; ++d) {
-                        if (d < 2 * rt) {
-                            const float g = a.gt[d];
-                            float x4[4];
-                            ld4(ring + (size_t)sl[d] * G::RR * P + off, x4);
-#pragma unroll
-                            for (int x = 0; x < 4; ++x) v[x] += g * x4[x];
-                        }
-                    }
-                    const float g = a.gt[2 * rt];         // the newest plane, o + rt
-#pragma unroll
-                    for (int x = 0; x < 4; ++x) v[x] += g * sv[x];
-                    *reinterpret_cast<float4*>(Cs + off) = make_float4(v[0], v[1], v[2], v[3]);
-                }
+
+    if (warp < NP / 32) {
+        // ------------------------------------------------------------ producers
+        const int ptid = tid;
+        auto issue = [&](int kk, int c) {                // one thread: TMA of plane kk's box
+            const Shift s = a.sh[c];
+            const int x = tx0 - HX + s.ox;
+            const int b = (kk - kk0) & 1;
+            bar_expect(&tbar[b], (uint32_t)(G::RAW_ROWS * RPT * sizeof(T)));
+            tma_load(rawbuf(b), &tmap, &tbar[b], x & ~(AL - 1), ty0 - R + s.oy, c);
+        };
+        auto wait_p = [&](unsigned long long* b, uint32_t parity) {
+            if (fail_p) return;
+            if (!bar_wait(b, parity)) {
+                fail_p = 1;
+                atomicOr(&a.sd->status, (unsigned int)LOC_DEV_ERR_TIMEOUT);
             }
         };
-        switch (xo) {
-            case 0: fused(IC<0>{}); break;
-            case 1: fused(IC<1>{}); break;
-            case 2: fused(IC<2>{}); break;
-            case 3: fused(IC<3>{}); break;
-            default:
-                if constexpr (AL == 8) {
-                    switch (xo) {
-                        case 4: fused(IC<4>{}); break;
-                        case 5: fused(IC<5>{}); break;
-                        case 6: fused(IC<6>{}); break;
-                        default: fused(IC<7>{}); break;
+        if (tma && ptid == 0) {
+            issue(kk0, c0);
+            if (kk0 + 1 < kk_end) issue(kk0 + 1, chan_step(c0));
+        }
+        const float inv_sa = 1.0f / a.sigma_a, inv_sc = 1.0f / a.sigma_c;
+        int cur = 0;                                      // ring slot of plane kk: (kk - kk0) mod nring
+        int c_cur = c0, c_pre = chan_step(chan_step(c0)); // channels of planes kk and kk + 2
+        for (int kk = kk0; kk < kk_end; ++kk) {
+            const Shift s = a.sh[c_cur];
+            T* rbw = rawbuf((kk - kk0) & 1);
+            if (tma) {
+                wait_p(&tbar[(kk - kk0) & 1], (uint32_t)(((kk - kk0) >> 1) & 1));
+            } else {
+                // plain loads of plane kk's box (its buffer was last read two planes ago)
+                for (int q = ptid; q < G::RAW_ROWS * RAW_COLS; q += NP) {
+                    const int row = q / RAW_COLS, col = q % RAW_COLS;
+                    const int gj = ty0 - R + s.oy + row, gi = tx0 - HX + s.ox + col;
+                    T v = from_u8<T>(0);
+                    if (gj >= 0 && gj < H && gi >= 0 && gi < W) {
+                        const size_t o = (size_t)gj * W + gi;
+                        v = reinit ? from_u8<T>(a.trav[o]) : Bin[(size_t)c_cur * H * W + o];
+                    }
+                    rbw[row * RPT + col] = v;
+                }
+                producers_sync();
+            }
+            const float fx = s.fx, fy = s.fy, gx0 = 1.0f - fx, gy0 = 1.0f - fy;
+            const int xo = tma ? ((tx0 - HX + s.ox) & (AL - 1)) : 0;
+            const int o = kk - rt;                        // output channel, once the ring is full
+            const bool out = kk - kk0 >= 2 * rt;
+            const int b = o & 1;
+            // C and the stencil of channel o reuse the buffers of channel o - 2
+            if (out && o >= 2) wait_p(&empty[b], (uint32_t)(((o >> 1) - 1) & 1));
+            float* slot = ring + (size_t)cur * G::RR * P;
+            float* Cs = Cbuf + (size_t)b * G::RR * P;
+            // ring slots of planes o - rt .. o + rt - 1: (cur + 1 + d) mod nring
+            int sl[2 * LOC_MAX_R_THETA];
+#pragma unroll
+            for (int d = 0; d < 2 * LOC_MAX_R_THETA; ++d) {
+                const int v = cur + 1 + d;
+                sl[d] = v >= nring ? v - nring : v;
+            }
+            const T* rb = rbw;
+            // S = M * bilinear(raw) into the ring and, once the ring is full, C = theta sum of
+            // the ring, 4 cells per item; a producer always owns the same items, so the ring
+            // cells it sums are its own writes.  XO = the box's column offset.
+            auto fused = [&](auto xo_c) {
+                constexpr int XO = decltype(xo_c)::value;
+#pragma unroll 2
+                for (int q = ptid; q < G::RR * NG; q += NP) {
+                    const int row = q / NG, g4 = (q % NG) * 4, off = row * P + g4;
+                    float r0[RawRow<T>::NV], r1[RawRow<T>::NV], mk[4];
+                    RawRow<T>::ld(rb + row * RPT + g4, r0);
+                    RawRow<T>::ld(rb + (row + 1) * RPT + g4, r1);
+                    ld4(Ms + off, mk);
+                    float sv[4];
+#pragma unroll
+                    for (int x = 0; x < 4; ++x) {
+                        const float top = gx0 * r0[XO + x] + fx * r0[XO + x + 1];
+                        const float bot = gx0 * r1[XO + x] + fx * r1[XO + x + 1];
+                        sv[x] = mk[x] * (gy0 * top + fy * bot);
+                    }
+                    *reinterpret_cast<float4*>(slot + off) = make_float4(sv[0], sv[1], sv[2], sv[3]);
+                    if (out) {
+                        float v[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+                        for (int d = 0; d < 2 * LOC_MAX_R_THETA; ++d) {
+                            if (d < 2 * rt) {
+                                const float g = a.gt[d];
+                                float x4[4];
+                                ld4(ring + (size_t)sl[d] * G::RR * P + off, x4);
+#pragma unroll
+                                for (int x = 0; x < 4; ++x) v[x] += g * x4[x];
+                            }
+                        }
+                        const float g = a.gt[2 * rt];     // the newest plane, o + rt
+#pragma unroll
+                        for (int x = 0; x < 4; ++x) v[x] += g * sv[x];
+                        *reinterpret_cast<float4*>(Cs + off) = make_float4(v[0], v[1], v[2], v[3]);
                     }
                 }
-        }
-        if (out) {
-            // channel o's x/y stencil (unnormalised), row-major with pitch GP
-            const float phi = a.phi0 + a.dphi * (float)o;
-            float sp, cp;
-            sincosf(phi, &sp, &cp);
-            for (int q = tid; q < G::D * G::GP; q += NT) {
-                const int dj = q / G::GP, di = q % G::GP;
-                float w = 0.0f;
-                if (di < G::D) {
-                    const float fdj = (float)(dj - R), fdi = (float)(di - R);
-                    const float along = (fdi * cp + fdj * sp) * inv_sa;
-                    const float across = (fdj * cp - fdi * sp) * inv_sc;
-                    w = expf(-0.5f * (along * along + across * across));
-                }
-                gs[q] = w;
+            };
+            switch (xo) {
+                case 0: fused(IC<0>{}); break;
+                case 1: fused(IC<1>{}); break;
+                case 2: fused(IC<2>{}); break;
+                case 3: fused(IC<3>{}); break;
+                default:
+                    if constexpr (AL == 8) {
+                        switch (xo) {
+                            case 4: fused(IC<4>{}); break;
+                            case 5: fused(IC<5>{}); break;
+                            case 6: fused(IC<6>{}); break;
+                            default: fused(IC<7>{}); break;
+                        }
+                    }
             }
+            if (out) {
+                // channel o's x/y stencil (unnormalised), row-major with pitch GP
+                const float phi = a.phi0 + a.dphi * (float)o;
+                float sp, cp;
+                sincosf(phi, &sp, &cp);
+                float* gs = gsb + b * G::D * G::GP;
+                for (int q = ptid; q < G::D * G::GP; q += NP) {
+                    const int dj = q / G::GP, di = q % G::GP;
+                    float w = 0.0f;
+                    if (di < G::D) {
+                        const float fdj = (float)(dj - R), fdi = (float)(di - R);
+                        const float along = (fdi * cp + fdj * sp) * inv_sa;
+                        const float across = (fdj * cp - fdi * sp) * inv_sc;
+                        w = expf(-0.5f * (along * along + across * across));
+                    }
+                    gs[q] = w;
+                }
+            }
+            producers_sync();                             // every producer has read the raw box
+            if (tma && ptid == 0 && kk + 2 < kk_end) issue(kk + 2, c_pre);   // into the box just read
+            if (out) bar_arrive(&full[b]);                // C and the stencil of channel o are ready
+            cur = cur + 1 == nring ? 0 : cur + 1;
+            c_cur = chan_step(c_cur);
+            c_pre = chan_step(c_pre);
         }
-        __syncthreads();                                  // raw consumed; C and the stencil written
-        if (tma) {
-            if (tid == 0 && kk + 2 < kk_end) issue(kk + 2, c_pre);   // into the buffer just consumed
-        } else if (kk + 1 < kk_end) {
-            commit(kk + 1);
-            if (kk + 2 < kk_end) fetch(c_pre);           // plane kk + 2 in flight
-        }
-        if (out) {
+    } else {
+        // ------------------------------------------------------------ consumers
+        // this thread's block: output rows oy0 .. oy0+BY-1, columns ox0 .. ox0+3 of the tile
+        const int cw = warp - NP / 32;
+        const int lx = lane & 7, ly = lane >> 3;
+        const int oy0 = 4 * BY * cw + BY * ly, ox0 = 4 * lx;
+        bool interior = true;
+        for (int r = 0; r < G::NR; ++r)
+            for (int cc = HX - R; cc < HX + 4 + R; ++cc) interior &= Ms[(oy0 + r) * P + ox0 + cc] > 0.0f;
+        uint32_t free_bits = 0;                           // centres of this block that are free
+#pragma unroll
+        for (int y = 0; y < BY; ++y)
+#pragma unroll
+            for (int x = 0; x < 4; ++x)
+                if (Ms[(oy0 + y + R) * P + HX + ox0 + x] > 0.0f) free_bits |= 1u << (4 * y + x);
+        // per warp: every lane interior (G_k is the stencil sum) / some lane with a free cell
+        const bool warp_interior = __all_sync(0xffffffffu, interior);
+        const bool warp_any_free = __any_sync(0xffffffffu, free_bits != 0);
+        for (int o = 0; o < K; ++o) {
+            const int b = o & 1;
+            if (!fail_c && !bar_wait(&full[b], (uint32_t)((o >> 1) & 1))) {
+                fail_c = 1;
+                atomicOr(&a.sd->status, (unsigned int)LOC_DEV_ERR_TIMEOUT);
+            }
+            const float* Cs = Cbuf + (size_t)b * G::RR * P;
+            const float* gs = gsb + b * G::D * G::GP;
             float part = 0.0f;
             T* oplane = Bout + (size_t)o * H * W;
             if (warp_any_free) {
@@ -443,6 +458,7 @@ __global__ void __launch_bounds__(NT, 3) step_aniso_kernel(const __grid_constant
                 } else {
                     stencil_block<R, true>(Cs + base, Ms + base, gs, t, gm);
                 }
+                bar_arrive(&empty[b]);                    // C and the stencil of channel o are read
 #pragma unroll
                 for (int y = 0; y < BY; ++y) {
                     const int gj = ty0 + oy0 + y, gi = tx0 + ox0;
@@ -470,6 +486,7 @@ __global__ void __launch_bounds__(NT, 3) step_aniso_kernel(const __grid_constant
                     }
                 }
             } else {
+                bar_arrive(&empty[b]);
                 const T zero = round_out<T>(0.0f, 0u);
 #pragma unroll
                 for (int y = 0; y < BY; ++y) {
@@ -482,13 +499,8 @@ __global__ void __launch_bounds__(NT, 3) step_aniso_kernel(const __grid_constant
             }
             acc.add(part);
         }
-        if (tma && kk + 1 < kk_end) box_ready(kk + 1);
-        // the next plane reads its raw box and overwrites C and the stencil
-        __syncthreads();
-        cur = cur + 1 == nring ? 0 : cur + 1;
-        c_cur = chan_step(c_cur);
-        c_pre = chan_step(c_pre);
     }
+    __syncthreads();
 
     const double bt = block_sum<NT>(acc.value(), red);
     const unsigned int nblocks = gridDim.x * gridDim.y;
@@ -556,8 +568,8 @@ cudaError_t make_aniso_tmap(void* tmap_out, const void* B, int storage, int H, i
 
 cudaError_t launch_step_aniso(const StepArgs& a, const void* tmap, int storage, cudaStream_t st) {
     static_assert(LOC_MAX_R_XY <= HX, "the region's left margin must cover the x/y radius");
-    static_assert(3 * RAW_COLS <= NT && NT == 4 * 32 && TH == 4 * 4 * BY && TW == 32,
-                  "three rows of input columns per fetch pass; 4 warps of 8 x 4 lanes cover the tile");
+    static_assert(NC == 4 * 32 && TH == 4 * 4 * BY && TW == 32 && NP % 32 == 0,
+                  "4 consumer warps of 8 x 4 lanes cover the tile; whole producer warps");
     static_assert(RAW_COLS + 3 <= 44 && RAW_COLS + 7 <= 48, "the box covers 41 columns after the x rounding");
     if (a.r_xy < 0 || a.r_xy > LOC_MAX_R_XY || a.r_th < 0 || a.r_th > LOC_MAX_R_THETA ||
         !(a.sigma_a > 0.0f) || !(a.sigma_c > 0.0f))
