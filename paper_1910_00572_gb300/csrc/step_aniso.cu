@@ -21,14 +21,14 @@
 // the channel's stencil, and the map M; and, in the storage type, the raw (shifted) input
 // boxes of two planes.
 //
-// Warp-specialised pipeline.  Two producer warps take plane kk: its input box (one TMA copy
+// Warp-specialised pipeline.  Six producer warps take plane kk: its input box (one TMA copy
 // per plane, x rounded down to 16 bytes, zeros outside the grid, issued two planes ahead,
 // where the row pitch allows; else plain loads, and always for the restart input, the map),
 // the S pass into the ring and, once the ring is full, C of channel o = kk - r_th and its
 // stencil into buffer o & 1.  A producer always computes S and C for the same region cells,
 // so the ring cells it sums are its own writes.  Four consumer warps take channel o from that
 // buffer: the stencil, the division by G_k, the store and the Z partial sums.  The hand-offs
-// are mbarriers (FULL[b]: the 64 producers arrive after writing; EMPTY[b]: the 128 consumers
+// are mbarriers (FULL[b]: the 192 producers arrive after writing; EMPTY[b]: the 128 consumers
 // arrive after reading) with bounded waits; the producers also meet at a named barrier
 // before a raw box is overwritten.
 //
@@ -51,7 +51,7 @@ using tiled::bar_wait;
 using tiled::tma_load;
 
 constexpr int TH = 32, TW = 32;
-constexpr int NP = 128, NC = 128, NT = NP + NC;  // producer and consumer threads
+constexpr int NP = 192, NC = 128, NT = NP + NC;  // producer and consumer threads
 constexpr int BY = 2;                          // output rows per thread (4 columns each)
 constexpr int HX = 4;                          // region columns left of the tile
 constexpr int RCOLS = TW + 2 * HX;             // 40 region columns
@@ -333,8 +333,11 @@ __global__ void __launch_bounds__(NT, 2) step_aniso_kernel(const __grid_constant
             // cells it sums are its own writes.  XO = the box's column offset.
             auto fused = [&](auto xo_c) {
                 constexpr int XO = decltype(xo_c)::value;
-#pragma unroll 2
-                for (int q = ptid; q < G::RR * NG; q += NP) {
+                constexpr int NQ = (G::RR * NG + NP - 1) / NP;
+#pragma unroll
+                for (int n = 0; n < NQ; ++n) {
+                    const int q = ptid + n * NP;
+                    if (q >= G::RR * NG) break;
                     const int row = q / NG, g4 = (q % NG) * 4, off = row * P + g4;
                     float r0[RawRow<T>::NV], r1[RawRow<T>::NV], mk[4];
                     RawRow<T>::ld(rb + row * RPT + g4, r0);
@@ -388,7 +391,12 @@ __global__ void __launch_bounds__(NT, 2) step_aniso_kernel(const __grid_constant
                 float sp, cp;
                 sincosf(phi, &sp, &cp);
                 float* gs = gsb + b * G::D * G::GP;
-                for (int q = ptid; q < G::D * G::GP; q += NP) {
+                // taps spread over all producer warps (q = 2 ptid, 2 ptid + 1 ...)
+                constexpr int NTAP = G::D * G::GP;
+                constexpr int SPREAD = NTAP * 2 <= NP ? 2 : 1;
+                for (int q0 = ptid; q0 < NTAP * SPREAD; q0 += NP) {
+                    if (q0 % SPREAD) continue;
+                    const int q = q0 / SPREAD;
                     const int dj = q / G::GP, di = q % G::GP;
                     float w = 0.0f;
                     if (di < G::D) {
