@@ -25,7 +25,7 @@
 // per plane, x rounded down to 16 bytes, zeros outside the grid, issued two planes ahead,
 // where the row pitch allows; else plain loads, and always for the restart input, the map),
 // the S pass into the ring and, once the ring is full, C of channel o = kk - r_th and its
-// stencil into buffer o & 1.  A producer always computes S and C for the same region cells,
+// stencil into buffer o mod 3.  A producer always computes S and C for the same region cells,
 // so the ring cells it sums are its own writes.  Four consumer warps take channel o from that
 // buffer: the stencil, the division by G_k, the store and the Z partial sums.  The hand-offs
 // are mbarriers (FULL[b]: the 192 producers arrive after writing; EMPTY[b]: the 128 consumers
@@ -53,6 +53,7 @@ using tiled::tma_load;
 constexpr int TH = 32, TW = 32;
 constexpr int NP = 192, NC = 128, NT = NP + NC;  // producer and consumer threads
 constexpr int BY = 2;                          // output rows per thread (4 columns each)
+constexpr int NBUF = 3;                        // C / stencil buffers between producers and consumers
 constexpr int HX = 4;                          // region columns left of the tile
 constexpr int RCOLS = TW + 2 * HX;             // 40 region columns
 constexpr int P = RCOLS;                       // row pitch of ring, C and M (floats)
@@ -81,8 +82,8 @@ template <typename T, int R>
 size_t aniso_smem_bytes(int rt) {
     using G = Geo<R>;
     const size_t nring = 2 * (size_t)rt + 1;
-    return 2 * raw_buf_bytes<T, R>() + (nring + 3) * G::RR * P * sizeof(float) +
-           2 * (size_t)G::D * G::GP * sizeof(float);
+    return 2 * raw_buf_bytes<T, R>() + (nring + NBUF + 1) * G::RR * P * sizeof(float) +
+           NBUF * (size_t)G::D * G::GP * sizeof(float);
 }
 
 template <typename T> __device__ __forceinline__ float to_f(T v);
@@ -220,7 +221,7 @@ __global__ void __launch_bounds__(NT, 2) step_aniso_kernel(const __grid_constant
     constexpr int AL = 16 / (int)sizeof(T);              // TMA x alignment in elements
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ double red[NT / 32];
-    __shared__ unsigned long long tbar[2], full[2], empty[2];
+    __shared__ unsigned long long tbar[2], full[NBUF], empty[NBUF];
     __shared__ int fail_p, fail_c;                        // a bounded wait gave up (per role)
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -229,9 +230,9 @@ __global__ void __launch_bounds__(NT, 2) step_aniso_kernel(const __grid_constant
     const int ty0 = blockIdx.y * TH, tx0 = blockIdx.x * TW;
 
     float* ring = reinterpret_cast<float*>(smem_raw + 2 * RAW_BUF);       // [nring][RR][P]
-    float* Cbuf = ring + (size_t)nring * G::RR * P;                       // [2][RR][P]
-    float* Ms = Cbuf + 2 * G::RR * P;                                     // [RR][P]
-    float* gsb = Ms + G::RR * P;                                          // [2][D][GP]
+    float* Cbuf = ring + (size_t)nring * G::RR * P;                       // [NBUF][RR][P]
+    float* Ms = Cbuf + NBUF * G::RR * P;                                  // [RR][P]
+    float* gsb = Ms + G::RR * P;                                          // [NBUF][D][GP]
     // raw box of buffer b: [RAW_ROWS][RPT] elements of T
     auto rawbuf = [&](int b) { return reinterpret_cast<T*>(smem_raw + (size_t)b * RAW_BUF); };
 
@@ -252,10 +253,10 @@ __global__ void __launch_bounds__(NT, 2) step_aniso_kernel(const __grid_constant
     if (tid == 0) {
         bar_init(&tbar[0], 1);
         bar_init(&tbar[1], 1);
-        bar_init(&full[0], NP);
-        bar_init(&full[1], NP);
-        bar_init(&empty[0], NC);
-        bar_init(&empty[1], NC);
+        for (int b = 0; b < NBUF; ++b) {
+            bar_init(&full[b], NP);
+            bar_init(&empty[b], NC);
+        }
         fail_p = fail_c = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -315,9 +316,9 @@ __global__ void __launch_bounds__(NT, 2) step_aniso_kernel(const __grid_constant
             const int xo = tma ? ((tx0 - HX + s.ox) & (AL - 1)) : 0;
             const int o = kk - rt;                        // output channel, once the ring is full
             const bool out = kk - kk0 >= 2 * rt;
-            const int b = o & 1;
-            // C and the stencil of channel o reuse the buffers of channel o - 2
-            if (out && o >= 2) wait_p(&empty[b], (uint32_t)(((o >> 1) - 1) & 1));
+            const int b = o % NBUF;
+            // C and the stencil of channel o reuse the buffers of channel o - NBUF
+            if (out && o >= NBUF) wait_p(&empty[b], (uint32_t)((o / NBUF - 1) & 1));
             float* slot = ring + (size_t)cur * G::RR * P;
             float* Cs = Cbuf + (size_t)b * G::RR * P;
             // ring slots of planes o - rt .. o + rt - 1: (cur + 1 + d) mod nring
@@ -434,8 +435,8 @@ __global__ void __launch_bounds__(NT, 2) step_aniso_kernel(const __grid_constant
         const bool warp_interior = __all_sync(0xffffffffu, interior);
         const bool warp_any_free = __any_sync(0xffffffffu, free_bits != 0);
         for (int o = 0; o < K; ++o) {
-            const int b = o & 1;
-            if (!fail_c && !bar_wait(&full[b], (uint32_t)((o >> 1) & 1))) {
+            const int b = o % NBUF;
+            if (!fail_c && !bar_wait(&full[b], (uint32_t)((o / NBUF) & 1))) {
                 fail_c = 1;
                 atomicOr(&a.sd->status, (unsigned int)LOC_DEV_ERR_TIMEOUT);
             }
