@@ -58,6 +58,9 @@ def _ref():
         lib.dda_ranges.restype = None
         lib.dda_ranges.argtypes = [P, ctypes.c_int, ctypes.c_int, P, ctypes.c_int, P,
                                    ctypes.c_int, ctypes.c_float, ctypes.c_float, P]
+        lib.range_table.restype = None
+        lib.range_table.argtypes = [P, ctypes.c_int, ctypes.c_int, P, ctypes.c_int,
+                                    ctypes.c_float, ctypes.c_float, P]
         _lib = lib
     return _lib
 

@@ -14,6 +14,10 @@
  *              direction (dx, dy) (Amanatides-Woo traversal) until an occupied cell or the
  *              grid edge; a tie between the next x and y crossings steps x first.  Returns
  *              the distance in cells, capped at rmax.
+ *  range_table The expected-range table of the dense scan update: dda_cells from every cell
+ *              along A fixed directions, quantised to 8 bits with the FP32 operations
+ *              q = floor(t * inv_step + 0.5) (the product rounded, then the sum), capped
+ *              at 255.
  */
 #include <math.h>
 #include <stdint.h>
@@ -78,4 +82,20 @@ void dda_ranges(const uint8_t* occ, int H, int W, const int32_t* cells, int n_ce
             out[(size_t)s * n_rays + r] =
                 dda_cells(occ, H, W, j, i, dirs[2 * r], dirs[2 * r + 1], rmax_cells) * cell_m;
     }
+}
+
+/* out[(a * H + j) * W + i] = the 8-bit code of dda_cells(j, i, dirs[a]) (0 on occupied
+ * cells, whose walk returns 0). */
+void range_table(const uint8_t* occ, int H, int W, const float* dirs, int A, float rmax_cells,
+                 float inv_step, uint8_t* out)
+{
+    for (int a = 0; a < A; ++a)
+        for (int j = 0; j < H; ++j)
+            for (int i = 0; i < W; ++i) {
+                float t = dda_cells(occ, H, W, j, i, dirs[2 * a], dirs[2 * a + 1], rmax_cells);
+                float x = t * inv_step;
+                float y = x + 0.5f;
+                float f = floorf(y);
+                out[((size_t)a * H + j) * W + i] = (uint8_t)(f > 255.0f ? 255.0f : f);
+            }
 }
