@@ -213,6 +213,43 @@ loc_status loc_propagate_noalloc(const loc_params* p, const uint8_t* occ_dev,
                                  const float* b_in_dev, float* b_out_dev, double* z_out_dev,
                                  double dx_m, double dy_m);
 
+/* ---- Dense scan update: Eq. 9 on every state from a precomputed expected-range table.
+ *
+ * The map is static, so the expected range of every cell along n_angles fixed directions
+ * 2 pi a / n_angles can be cast once (Section III-B's ray model, the same FP32 grid walk as
+ * the sampled update) and stored in 8 bits.  A scan then scores every (cell, bin) state from
+ * that table and reweights the whole tensor, the dense limit of Eq. 9 (no dithering). */
+
+#define LOC_MAX_TABLE_DIRS 1440    /* table directions per session */
+#define LOC_MAX_DENSE_BEAMS 2048   /* used beams (every beam_stride-th, range < r_max) per scan */
+
+/* Builds (or rebuilds) the session's table: code (a, j, i) = floor(t * inv_step + 0.5)
+ * capped at 255, t = the FP32 walk from the centre of cell (j, i) along direction a in cells,
+ * capped at float(r_max / cell_m), inv_step = float(255 / that cap); each FP32 operation
+ * rounded.  The code stands for code * float(r_max / 255) metres; occupied cells hold 0.
+ * n_angles: a positive multiple of K, <= LOC_MAX_TABLE_DIRS (bin k's heading is direction
+ * k n_angles / K).  r_max (m) > 0: the range cap, also the dropout threshold of the dense
+ * update.  Allocates n_angles * H * W bytes on the device; synchronous.
+ * Errors: INVALID_ARG, OOM, CUDA, STATE. */
+loc_status loc_range_table(loc_handle h, int n_angles, double r_max);
+
+/* Copies the table, [n_angles][H][W] uint8, to `out` (n = n_angles * H * W); synchronous.
+ * Errors: INVALID_ARG (no table, or n mismatch), CUDA, STATE. */
+loc_status loc_range_table_read(loc_handle h, uint8_t* out, size_t n);
+
+/* Dense scan update (Eq. 9 on every state).  ranges: host float[n_beams] in metres, finite,
+ * >= 0; beam b of a state in bin k points at 2 pi k / K + theta_t + angle_min + b angle_inc
+ * and reads table direction (k n_angles / K + m_b) mod n_angles, where
+ * m_b = floor((theta_t + (angle_min + angle_inc b)) / (2 pi / n_angles) + 0.5) mod n_angles
+ * (FP64, host).  Used beams: b % beam_stride == 0 and range < the table's r_max (at most
+ * LOC_MAX_DENSE_BEAMS).  log L = -sum over used beams of (z_b - code * step)^2 / (2 sigma_r^2)
+ * for every state (FP32); the tensor becomes b w / sum(b w) with w = exp(log L - max), the
+ * maximum over the states of free cells, and the log-scale grows by log(sum(b w)) + max.  No
+ * used beam: no change.  Allocates K * H * W floats of scratch on first use.  Asynchronous
+ * on the session's stream.  Errors: INVALID_ARG (including no table), OOM, CUDA, STATE. */
+loc_status loc_lidar_update_dense(loc_handle h, const float* ranges, int n_beams, double angle_min,
+                                  double angle_inc, int beam_stride, double sigma_r);
+
 /* ---- Batched propagation of many sessions (one persistent launch per tick).
  * Alg. 1 lines 3-7 and the Eq. 9 normaliser for every session whose gate opens, over a work
  * list of (session, tile) items that the launch's CTAs take from a device queue; the CTA that

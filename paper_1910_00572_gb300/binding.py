@@ -21,6 +21,7 @@ __all__ = [
     "loc_lidar_update_cells", "loc_belief", "loc_marginal", "loc_argmax", "loc_set_belief",
     "loc_stats", "loc_sync", "loc_destroy", "loc_last_error", "torch_stream",
     "use_torch_allocator", "loc_propagate_noalloc", "loc_samples", "loc_dither", "loc_ray_ranges",
+    "loc_range_table", "loc_range_table_read", "loc_lidar_update_dense",
     "LOC_BATCH_CONFIGS", "Batch", "loc_batch_create", "loc_batch_step", "loc_batch_sync",
     "loc_batch_info", "loc_batch_destroy", "loc_batch_last_error", "loc_session_bytes",
     "LOC_SESSION_PENDING", "LOC_SESSION_ACTIVE", "LOC_SESSION_CLOSED", "LOC_SESSION_FAILED",
@@ -113,6 +114,10 @@ _SIGS = {
     "loc_samples": (ctypes.c_int, [_P, _P, ctypes.c_size_t, ctypes.POINTER(ctypes.c_int)]),
     "loc_dither": (ctypes.c_int, [_P, _P, ctypes.c_float, _P, ctypes.POINTER(ctypes.c_int)]),
     "loc_ray_ranges": (ctypes.c_int, [_P, _P, ctypes.c_int, _P, ctypes.c_int, ctypes.c_double, _P]),
+    "loc_range_table": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_double]),
+    "loc_range_table_read": (ctypes.c_int, [_P, _P, ctypes.c_size_t]),
+    "loc_lidar_update_dense": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                              ctypes.c_int, ctypes.c_double]),
     "loc_batch_create": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(_P)]),
     "loc_batch_step": (ctypes.c_int, [_P, _P, _P, _P, ctypes.POINTER(ctypes.c_int)]),
     "loc_batch_sync": (ctypes.c_int, [_P]),
@@ -280,6 +285,27 @@ def loc_ray_ranges(h: Handle, cells: np.ndarray, dirs: np.ndarray, r_max: float)
     _check(h, lib().loc_ray_ranges(h, _ptr(c), int(c.size), _ptr(d), int(d.shape[0]), float(r_max),
                                    _ptr(out)))
     return out
+
+
+def loc_range_table(h: Handle, n_angles: int, r_max: float) -> None:
+    """Build the session's expected-range table for the dense scan update."""
+    _check(h, lib().loc_range_table(h, int(n_angles), float(r_max)))
+    h.table_A = int(n_angles)
+
+
+def loc_range_table_read(h: Handle) -> np.ndarray:
+    """The table as uint8 [n_angles][H][W]."""
+    A = getattr(h, "table_A", 0)
+    out = np.empty((max(A, 1), h.H, h.W), np.uint8)
+    _check(h, lib().loc_range_table_read(h, _ptr(out), A * h.H * h.W))
+    return out
+
+
+def loc_lidar_update_dense(h: Handle, ranges: np.ndarray, angle_min: float, angle_inc: float,
+                           beam_stride: int, sigma_r: float) -> int:
+    z = np.ascontiguousarray(ranges, dtype=np.float32)
+    return _check(h, lib().loc_lidar_update_dense(h, _ptr(z), int(z.size), float(angle_min),
+                                                  float(angle_inc), int(beam_stride), float(sigma_r)))
 
 
 def loc_belief(h: Handle, out: np.ndarray | None = None) -> np.ndarray:

@@ -660,6 +660,100 @@ LOC_API loc_status loc_ray_ranges(loc_handle h, const int32_t* cells, int n_cell
     return sync_and_check(h);
 }
 
+LOC_API loc_status loc_range_table(loc_handle h, int n_angles, double r_max) {
+    loc_status st = check_live(h);
+    if (st != LOC_OK) return st;
+    if (n_angles <= 0 || n_angles > LOC_MAX_TABLE_DIRS || n_angles % h->p.K != 0)
+        return fail(h, LOC_ERR_INVALID_ARG, "n_angles must be a positive multiple of K, <= LOC_MAX_TABLE_DIRS");
+    if (!(r_max > 0.0) || !std::isfinite(r_max)) return fail(h, LOC_ERR_INVALID_ARG, "r_max must be finite and > 0");
+    if (h->table) {
+        dev_release(h, h->table);
+        h->table = nullptr;
+        h->table_A = 0;
+    }
+    uint8_t* t = (uint8_t*)dev_alloc(h, (size_t)n_angles * h->hw);
+    float* dd = (float*)dev_alloc(h, sizeof(float) * 2 * (size_t)n_angles);
+    if (!t || !dd) return fail(h, LOC_ERR_OOM, "range table");
+    // table direction a: 2 pi a / A, its unit vector in FP64 rounded to FP32
+    std::vector<float> dirs(2 * (size_t)n_angles);
+    for (int a = 0; a < n_angles; ++a) {
+        const double ang = (2.0 * M_PI / n_angles) * a;
+        dirs[2 * a] = (float)std::cos(ang);
+        dirs[2 * a + 1] = (float)std::sin(ang);
+    }
+    const float rmax_cells = (float)(r_max / h->p.cell_m);
+    const float inv_step = (float)(255.0 / (double)rmax_cells);
+    cudaError_t e = cudaMemcpyAsync(dd, dirs.data(), sizeof(float) * dirs.size(), cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = launch_range_table(h->trav, h->p.H, h->p.W, dd, n_angles, rmax_cells, inv_step, t, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    dev_release(h, dd);
+    if (e != cudaSuccess) return cuda_fail(h, e, "loc_range_table");
+    h->table = t;
+    h->table_A = n_angles;
+    h->table_rmax = r_max;
+    return sync_and_check(h);
+}
+
+LOC_API loc_status loc_range_table_read(loc_handle h, uint8_t* out, size_t n) {
+    loc_status st = check_live(h);
+    if (st != LOC_OK) return st;
+    if (!h->table) return fail(h, LOC_ERR_INVALID_ARG, "no range table: call loc_range_table first");
+    if (!out || n != (size_t)h->table_A * h->hw) return fail(h, LOC_ERR_INVALID_ARG, "out null or n != n_angles*H*W");
+    cudaError_t e = cudaMemcpyAsync(out, h->table, n, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "loc_range_table_read");
+    return sync_and_check(h);
+}
+
+LOC_API loc_status loc_lidar_update_dense(loc_handle h, const float* ranges, int n_beams, double angle_min,
+                                          double angle_inc, int beam_stride, double sigma_r) {
+    loc_status st = check_live(h);
+    if (st != LOC_OK) return st;
+    if (!h->table) return fail(h, LOC_ERR_INVALID_ARG, "no range table: call loc_range_table first");
+    const double r_max = h->table_rmax;
+    st = check_scan(h, ranges, n_beams, angle_min, angle_inc, r_max, beam_stride, sigma_r);
+    if (st != LOC_OK) return st;
+    const int A = h->table_A, K = h->p.K;
+    // the used beams: offsets from the bin heading rounded to the table grid, ranges in code steps
+    const double step = (double)(float)(r_max / 255.0);
+    std::vector<int> mb;
+    std::vector<float> zs;
+    for (int b = 0; b < n_beams; b += beam_stride) {
+        if (!(ranges[b] < r_max)) continue;
+        const double x = (h->theta + (angle_min + angle_inc * b)) / (2.0 * M_PI / A);
+        long long q = (long long)std::floor(x + 0.5) % A;
+        if (q < 0) q += A;
+        mb.push_back((int)q);
+        zs.push_back((float)((double)ranges[b] / step));
+    }
+    const int nu = (int)mb.size();
+    if (nu > LOC_MAX_DENSE_BEAMS) return fail(h, LOC_ERR_INVALID_ARG, "more than LOC_MAX_DENSE_BEAMS used beams");
+    if (nu == 0) return LOC_OK;                       // every beam a dropout: nothing to weigh
+    if (!h->dense_logL) {
+        h->dense_logL = (float*)dev_alloc(h, sizeof(float) * h->n);
+        h->dense_max = (unsigned int*)dev_alloc(h, 16);
+        if (!h->dense_logL || !h->dense_max) return fail(h, LOC_ERR_OOM, "dense scan buffers");
+    }
+    if (!grow(h, h->dense_m, h->cap_dense, nu, sizeof(int)) || !grow(h, h->dense_z, h->cap_dense_z, nu, sizeof(float)))
+        return fail(h, LOC_ERR_OOM, "dense scan buffers");
+    if ((st = materialize(h)) != LOC_OK) return st;
+    cudaError_t e = cudaMemcpyAsync(h->dense_m, mb.data(), sizeof(int) * nu, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->dense_z, zs.data(), sizeof(float) * nu, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->dense_max, 0, sizeof(unsigned int), h->stream);
+    if (e == cudaSuccess)
+        e = launch_dense_score(h->table, h->trav, h->B[h->cur], h->p.storage, h->p.H, h->p.W, K, A, h->dense_m,
+                               h->dense_z, nu, (float)(step * step / (2.0 * sigma_r * sigma_r)), h->dense_logL,
+                               h->dense_max, h->stream);
+    if (e == cudaSuccess)
+        e = launch_dense_apply(h->B[h->cur], h->p.storage, h->dense_logL, h->n, h->dense_max,
+                               (float)std::log((double)storage_mult(h->p.storage)),
+                               pcg_hash((uint32_t)h->n_dense * 0x9E3779B1u + 0x7F4A7C15u), h->partials, h->nparts,
+                               h->sd, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "dense scan update launch");
+    h->n_dense += 1;
+    return LOC_OK;
+}
+
 LOC_API loc_status loc_belief(loc_handle h, float* out, size_t n) {
     loc_status st = check_live(h);
     if (st != LOC_OK) return st;

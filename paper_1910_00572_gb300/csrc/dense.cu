@@ -1,0 +1,232 @@
+// Dense scan update: Eq. 9 on every state from a precomputed expected-range table.
+//
+// The map is static, so the expected range of every cell along A fixed directions 2 pi a / A
+// (A a multiple of K, so bin k's heading is direction k A / K) is cast once with the FP32
+// grid walk of the sampled update and stored as an 8-bit code [A][H][W]:
+// q = floor(t * inv_step + 0.5) capped at 255, t in cells, each FP32 operation rounded.
+// A scan then scores every state: beam b of bin k reads direction (k s + m_b) mod A, s = A/K,
+// m_b its offset from the bin heading rounded to the table grid (host), and
+//   log L(k, j, i) = -sum_b (z_b - q step)^2 / (2 sigma^2)
+// over the used beams; then X <- X exp(log L - c) mult, c = max over states of
+// (log L + log X): the most probable state after the update is stored at the storage
+// multiplier, so an informative scan (Eq. 9's normaliser far below 1) cannot underflow FP16
+// storage.  The new sum becomes the lazy normaliser (Eq. 9's eta).
+//
+// Kernels:
+//  * range_table_kernel: one thread per cell walks all A directions; the writes of one
+//    direction are consecutive across a warp.
+//  * dense_score_kernel: a CTA of DC = 64 cells stages their table columns in shared memory
+//    twice over (directions 0 .. 2A-1, so k s + m_b needs no wrap); per thread, beams in the
+//    outer loop and KC = 16 bins of accumulators in registers.  The code is turned into a
+//    float by the 2^23 exponent trick (exact for 0 .. 255) and compared with z_b / step.  It
+//    also reads the stored belief for the offset c.
+//  * dense_apply_kernel: X exp(log L - c) mult stored with the storage type's rounding, FP32
+//    Kahan partial sums per thread, FP64 per CTA, the last CTA combining them in a fixed
+//    order.
+#include <cfloat>
+
+#include "dda.cuh"
+#include "kernels.h"
+
+namespace loc {
+namespace {
+
+constexpr int NT = 256;
+constexpr int DC = 64;            // cells per score CTA (one per thread)
+constexpr int KC = 16;            // bins per register chunk
+
+// Order-preserving map of floats to unsigned ints (for atomicMax on floats).
+__device__ __forceinline__ unsigned int f2ord(float f) {
+    const unsigned int u = __float_as_uint(f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float ord2f(unsigned int u) {
+    return __uint_as_float((u & 0x80000000u) ? (u & 0x7FFFFFFFu) : ~u);
+}
+
+__global__ void __launch_bounds__(NT) range_table_kernel(const uint8_t* __restrict__ trav, int H, int W,
+                                                         const float* __restrict__ dirs, int A, float rmax,
+                                                         float inv_step, uint8_t* __restrict__ out) {
+    const size_t hw = (size_t)H * W;
+    for (size_t c = (size_t)blockIdx.x * NT + threadIdx.x; c < hw; c += (size_t)gridDim.x * NT) {
+        const int j = (int)(c / W), i = (int)(c % W);
+        for (int a = 0; a < A; ++a) {
+            const float t = dda_cells(trav, H, W, j, i, dirs[2 * a], dirs[2 * a + 1], rmax);
+            const float f = floorf(__fadd_rn(__fmul_rn(t, inv_step), 0.5f));
+            out[(size_t)a * hw + c] = (uint8_t)(f > 255.0f ? 255.0f : f);
+        }
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(DC) dense_score_kernel(const uint8_t* __restrict__ table,
+                                                         const uint8_t* __restrict__ trav, const T* __restrict__ B,
+                                                         size_t hw, int K, int A, int s, const int* __restrict__ m,
+                                                         const float* __restrict__ zs, int nu, float scale,
+                                                         float* __restrict__ logL, unsigned int* maxL) {
+    extern __shared__ __align__(16) unsigned char dsm[];
+    uint8_t* Ts = dsm;                                            // [2A][DC]
+    int* sm_m = reinterpret_cast<int*>(dsm + (size_t)2 * A * DC);  // [nu]
+    float* sm_z = reinterpret_cast<float*>(sm_m + nu);            // [nu]
+    const int t = threadIdx.x;
+    const size_t c0 = (size_t)blockIdx.x * DC, c = c0 + t;
+    if ((hw & 3) == 0 && c0 + DC <= hw) {
+        // 4 cells per 32-bit load: DC / 4 threads per direction, DC / (DC / 4) directions a pass
+        constexpr int TPD = DC / 4;
+        const int g = t % TPD, a0 = t / TPD;
+        for (int a = a0; a < A; a += DC / TPD) {
+            const uint32_t v = *reinterpret_cast<const uint32_t*>(table + (size_t)a * hw + c0 + 4 * g);
+            *reinterpret_cast<uint32_t*>(Ts + (size_t)a * DC + 4 * g) = v;
+            *reinterpret_cast<uint32_t*>(Ts + (size_t)(a + A) * DC + 4 * g) = v;
+        }
+    } else {
+        for (int a = 0; a < A; ++a) {
+            const uint8_t v = c < hw ? table[(size_t)a * hw + c] : (uint8_t)0;
+            Ts[(size_t)a * DC + t] = v;
+            Ts[(size_t)(a + A) * DC + t] = v;
+        }
+    }
+    for (int u = t; u < nu; u += DC) {
+        sm_m[u] = m[u];
+        sm_z[u] = zs[u];
+    }
+    __syncthreads();
+    const bool in = c < hw, free = in && trav[c] != 0;
+    const int stride = s * DC;
+    float best = -FLT_MAX;
+    for (int k0 = 0; k0 < K; k0 += KC) {
+        float acc[KC];
+#pragma unroll
+        for (int kk = 0; kk < KC; ++kk) acc[kk] = 0.0f;
+        const uint8_t* base = Ts + (size_t)k0 * stride + t;
+        for (int u = 0; u < nu; ++u) {
+            const uint8_t* col = base + (size_t)sm_m[u] * DC;
+            const float zu = sm_z[u];
+#pragma unroll
+            for (int kk = 0; kk < KC; ++kk) {
+                if (k0 + kk < K) {                                 // k s + m_u < 2A
+                    const uint32_t q = col[kk * stride];
+                    const float qf = __uint_as_float(0x4B000000u | q) - 8388608.0f;
+                    const float d = zu - qf;
+                    acc[kk] = fmaf(d, d, acc[kk]);
+                }
+            }
+        }
+#pragma unroll
+        for (int kk = 0; kk < KC; ++kk) {
+            if (k0 + kk < K && in) {
+                const size_t q = (size_t)(k0 + kk) * hw + c;
+                const float l = free ? -acc[kk] * scale : -INFINITY;
+                logL[q] = l;
+                const float x = Store<T>::ld(B + q);
+                if (free && x > 0.0f) best = fmaxf(best, l + logf(x));
+            }
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) best = fmaxf(best, __shfl_down_sync(0xffffffffu, best, o));
+    if ((t & 31) == 0 && best > -FLT_MAX) atomicMax(maxL, f2ord(best));
+}
+
+template <typename T>
+__global__ void __launch_bounds__(NT) dense_apply_kernel(T* __restrict__ B, const float* __restrict__ logL, size_t n,
+                                                         const unsigned int* maxL, float log_mult, uint32_t seed,
+                                                         double* partials, SessionDev* sd) {
+    __shared__ double red[NT / 32];
+    const float c = ord2f(*maxL);                 // max of log L + log X
+    const float off = log_mult - c;
+    KahanF acc;
+    for (size_t q = (size_t)blockIdx.x * NT + threadIdx.x; q < n; q += (size_t)gridDim.x * NT) {
+        const float x = Store<T>::ld(B + q);
+        // x exp(log L + off) <= mult; for a small x the factor alone could overflow, so a large
+        // exponent takes log x in (the multiply keeps x's precision elsewhere)
+        const float e = logL[q] + off;
+        const float v = x > 0.0f ? (e < 80.0f ? x * expf(e) : expf(e + logf(x))) : 0.0f;
+        acc.add(store_out<T>(B + q, v, pcg_hash((uint32_t)q ^ seed)));
+    }
+    const double bt = block_sum<NT>(acc.value(), red);
+    const unsigned int nblocks = gridDim.x;
+    finish_sum<NT>(bt, partials, &sd->counter, nblocks, red, [sd, c, log_mult](double S) {
+        const double Z0 = sd->Z;
+        if (S > 0.0 && isfinite(S)) {
+            // Eq. 9's normaliser: sum(b exp(log L)) = S exp(c) / (mult Z0)
+            sd->Z = S;
+            sd->inv_Z = (float)(1.0 / S);
+            sd->logscale += log(S) - log(Z0) + (double)c - (double)log_mult;
+        } else {
+            if (!isfinite(S)) sd->status |= LOC_DEV_ERR_NONFINITE_Z;
+            sd->Z = 1.0;
+            sd->inv_Z = 1.0f;
+            sd->reinit = 1;
+            sd->n_reinit += 1;
+        }
+    });
+}
+
+}  // namespace
+
+size_t dense_score_smem(int A, int nu) { return (size_t)2 * A * DC + (size_t)nu * 8; }
+
+cudaError_t launch_range_table(const uint8_t* trav, int H, int W, const float* dirs, int A, float rmax,
+                               float inv_step, uint8_t* out, cudaStream_t st) {
+    const size_t hw = (size_t)H * W;
+    size_t nb = (hw + NT - 1) / NT;
+    if (nb > 65535) nb = 65535;
+    range_table_kernel<<<(unsigned int)nb, NT, 0, st>>>(trav, H, W, dirs, A, rmax, inv_step, out);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t score_t(const uint8_t* table, const uint8_t* trav, const void* B, int H, int W, int K, int A,
+                    const int* m, const float* zs, int nu, float scale, float* logL, unsigned int* maxL,
+                    cudaStream_t st) {
+    const size_t hw = (size_t)H * W;
+    const size_t smem = dense_score_smem(A, nu);
+    static size_t attr = 0;                        // the largest size set so far
+    if (smem > 48 * 1024 && smem > attr) {
+        const cudaError_t e = cudaFuncSetAttribute(dense_score_kernel<T>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr = smem;
+    }
+    const unsigned int nb = (unsigned int)((hw + DC - 1) / DC);
+    dense_score_kernel<T><<<nb, DC, smem, st>>>(table, trav, static_cast<const T*>(B), hw, K, A, A / K, m, zs, nu,
+                                                scale, logL, maxL);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dense_score(const uint8_t* table, const uint8_t* trav, const void* B, int storage, int H, int W,
+                               int K, int A, const int* m, const float* zs, int nu, float scale, float* logL,
+                               unsigned int* maxL, cudaStream_t st) {
+    if (A % K != 0) return cudaErrorInvalidValue;
+    switch (storage) {
+        case LOC_F32: return score_t<float>(table, trav, B, H, W, K, A, m, zs, nu, scale, logL, maxL, st);
+        case LOC_BF16: return score_t<__nv_bfloat16>(table, trav, B, H, W, K, A, m, zs, nu, scale, logL, maxL, st);
+        case LOC_F16: return score_t<__half>(table, trav, B, H, W, K, A, m, zs, nu, scale, logL, maxL, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_dense_apply(void* B, int storage, const float* logL, size_t n, const unsigned int* maxL,
+                               float log_mult, uint32_t seed, double* partials, unsigned int nparts,
+                               SessionDev* sd, cudaStream_t st) {
+    size_t nb = (n + NT - 1) / NT;
+    if (nb > nparts) nb = nparts;
+    if (nb > 4096) nb = 4096;
+    if (nb < 1) nb = 1;
+    switch (storage) {
+        case LOC_F32:
+            dense_apply_kernel<float><<<(unsigned int)nb, NT, 0, st>>>((float*)B, logL, n, maxL, log_mult, seed, partials, sd);
+            break;
+        case LOC_BF16:
+            dense_apply_kernel<__nv_bfloat16><<<(unsigned int)nb, NT, 0, st>>>((__nv_bfloat16*)B, logL, n, maxL,
+                                                                               log_mult, seed, partials, sd);
+            break;
+        case LOC_F16:
+            dense_apply_kernel<__half><<<(unsigned int)nb, NT, 0, st>>>((__half*)B, logL, n, maxL, log_mult, seed, partials, sd);
+            break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace loc

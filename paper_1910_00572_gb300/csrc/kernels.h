@@ -18,6 +18,18 @@ unsigned int step_num_blocks(int H, int W);
 // The same with anisotropic motion noise (Eq. 5-6, sigma_x != sigma_y): a.phi0, a.dphi,
 // a.sigma_a, a.sigma_c give channel k's rotated x/y kernel; a.gx is unused.  Same grid and
 // partials as launch_step.
+// Dense scan update (dense.cu): the expected-range table, the score of every state (log L
+// [K][H][W] and the maximum of log L + log X as an ordered uint) and the reweighting.
+cudaError_t launch_range_table(const uint8_t* trav, int H, int W, const float* dirs, int A, float rmax,
+                               float inv_step, uint8_t* out, cudaStream_t st);
+size_t dense_score_smem(int A, int nu);
+cudaError_t launch_dense_score(const uint8_t* table, const uint8_t* trav, const void* B, int storage, int H, int W,
+                               int K, int A, const int* m, const float* zs, int nu, float scale, float* logL,
+                               unsigned int* maxL, cudaStream_t st);
+cudaError_t launch_dense_apply(void* B, int storage, const float* logL, size_t n, const unsigned int* maxL,
+                               float log_mult, uint32_t seed, double* partials, unsigned int nparts,
+                               SessionDev* sd, cudaStream_t st);
+
 // Anisotropic propagation (step_aniso.cu).  `tmap` is the tensor map of B_in built by
 // make_aniso_tmap, or null (plain loads).
 cudaError_t launch_step_aniso(const StepArgs& a, const void* tmap, int storage, cudaStream_t st);

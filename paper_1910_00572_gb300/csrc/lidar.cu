@@ -7,6 +7,7 @@
 // __fdiv_rn, so nothing is contracted into an FMA) in a fixed order.
 #include <cfloat>
 
+#include "dda.cuh"
 #include "kernels.h"
 
 namespace loc {
@@ -293,31 +294,6 @@ __global__ void __launch_bounds__(NT) compact_kernel(const uint8_t* __restrict__
 }
 
 // ------------------------------------------------------------------ ray casting + scoring
-
-// Distance in cells from the centre of free cell (j, i) along (dx, dy) to the first occupied
-// cell or the grid edge, capped at rmax; ties step x first.  Same FP32 operations, in the
-// same order, as the reference walk.
-__device__ float dda_cells(const uint8_t* __restrict__ trav, int H, int W, int j, int i, float dx, float dy,
-                           float rmax) {
-    if (!trav[(size_t)j * W + i]) return 0.0f;
-    const int sx = dx > 0.0f ? 1 : -1, sy = dy > 0.0f ? 1 : -1;
-    const float tdx = dx != 0.0f ? __fdiv_rn(1.0f, fabsf(dx)) : INFINITY;
-    const float tdy = dy != 0.0f ? __fdiv_rn(1.0f, fabsf(dy)) : INFINITY;
-    int nx = 0, ny = 0;
-    // every step crosses one cell boundary and t grows by at least 1/2 cell per two steps
-    const int max_steps = 4 * (int)rmax + 16;
-    for (int s = 0; s < max_steps; ++s) {
-        const float tx = __fmul_rn(__fadd_rn((float)nx, 0.5f), tdx);
-        const float ty = __fmul_rn(__fadd_rn((float)ny, 0.5f), tdy);
-        float t;
-        if (tx <= ty) { i += sx; nx += 1; t = tx; }
-        else          { j += sy; ny += 1; t = ty; }
-        if (t >= rmax) return rmax;
-        if (i < 0 || i >= W || j < 0 || j >= H) return t;
-        if (!trav[(size_t)j * W + i]) return t;
-    }
-    return rmax;
-}
 
 // Ranges for given cells and directions (the loc_ray_ranges entry point).
 __global__ void __launch_bounds__(NT) ray_ranges_kernel(const uint8_t* __restrict__ trav, int H, int W,

@@ -49,6 +49,16 @@ struct loc_session {
     float* z = nullptr;            // used ranges [cap_beams]
     int cap_dirs = 0, cap_beams = 0, cap_dir_of = 0;
     long long n_lidar = 0;
+    // dense scan update (allocated by loc_range_table / the first dense update)
+    uint8_t* table = nullptr;      // expected-range codes [table_A][H][W]
+    int table_A = 0;
+    double table_rmax = 0.0;
+    float* dense_logL = nullptr;   // log-likelihood of every state [K][H][W]
+    int* dense_m = nullptr;        // table offsets of the used beams [cap_dense]
+    float* dense_z = nullptr;      // their ranges over the code step [cap_dense]
+    unsigned int* dense_max = nullptr;
+    int cap_dense = 0, cap_dense_z = 0;
+    long long n_dense = 0;
     bool aniso = false;            // anisotropic motion noise (step_aniso.cu)
     bool aniso_tma = false;        // ... with its input boxes by TMA (tmap holds its maps)
     bool tiled = false;            // use the TMA-tiled kernel
