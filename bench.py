@@ -607,6 +607,154 @@ def run_serve256(args, wl, ws, rank, local):
     print(json.dumps(line), flush=True)
 
 
+def dense_scans(wl, occ, walk, n):
+    """n scans along the walk (poses 1 .. n)."""
+    from synth import scan
+    return [scan.simulate_scan(occ, wl["cell"], walk.poses[1 + t], seed=wl["seed"] * 97 + t,
+                               n_beams=wl["n_beams"], angle_min=wl["angle_min"], angle_inc=wl["angle_inc"],
+                               r_max=wl["r_max"], noise_sigma=wl["scan_noise"], dropout=wl["dropout"],
+                               march=0.25) for t in range(n)]
+
+
+def oracle_dense_rate(wl, occ, walk, budget_s: float, steps: int):
+    """The oracle's dense scan update on a band of map rows (all bins; the band's own table).
+    Returns (state-updates/s, rows, timed steps, seconds per step)."""
+    from oracle import dense as D
+    from oracle import filter as F
+    H, W, K, A = wl["H"], wl["W"], wl["K"], wl["n_angles"]
+    z = dense_scans(wl, occ, walk, 1)[0]
+
+    def timed(rows, n):
+        j0 = (H - rows) // 2
+        band = occ[j0:j0 + rows]
+        table = D.range_table(band, A, wl["r_max"], wl["cell"])
+        b = F.uniform_belief(F.traversability(band), K)
+        ts = []
+        for _ in range(n):
+            t = time.perf_counter()
+            b, _, _, _ = D.dense_update(b, band, table, 0.0, z, wl["angle_min"], wl["angle_inc"], wl["r_max"],
+                                        wl["beam_stride"], wl["sigma_r"])
+            ts.append(time.perf_counter() - t)
+        return ts
+
+    probe = min(H, 8)
+    per_row = statistics.mean(timed(probe, 1)) / probe
+    rows = int(max(4, min(H, budget_s / max(steps, 1) / max(per_row, 1e-9))))
+    ts = timed(rows, steps)
+    per = statistics.mean(ts)
+    return rows * W * K / per, rows, len(ts), per
+
+
+def run_dense(args, wl, occ, walk, ws, rank, local):
+    """One dense scan update per step (timed), with an odometry step between scans (untimed)."""
+    import torch
+
+    import paper_1910_00572_gb300 as loc
+    from paper_1910_00572_gb300 import build
+    build.build()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    storage = wl["storage"]
+    K, A = wl["K"], wl["n_angles"]
+    p = loc.loc_params_default(H=wl["H"], W=wl["W"], K=K, cell_m=wl["cell"], sigma_xy_cells=wl["sigma_xy_cells"],
+                               sigma_theta_bins=wl["sigma_theta_bins"], storage=storage, stream=loc.torch_stream())
+    h = loc.loc_create(occ, p)
+    n_scans = 16
+    scans = dense_scans(wl, occ, walk, n_scans)
+    n_used = statistics.mean(float((z[::wl["beam_stride"]] < wl["r_max"]).sum()) for z in scans)
+    odom = walk.odom
+    n_states = wl["H"] * wl["W"] * K
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    scan_args = (wl["angle_min"], wl["angle_inc"], wl["beam_stride"], wl["sigma_r"])
+    try:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        loc.loc_range_table(h, A, wl["r_max"])
+        table_s = time.perf_counter() - t0
+        for s in range(args.warmup):
+            loc.loc_step(h, *odom[s % len(odom)])
+            loc.loc_lidar_update_dense(h, scans[s % n_scans], *scan_args)
+        torch.cuda.synchronize()
+        barrier(ws)
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        with ClockSampler(None) as clk:
+            for s in range(args.steps):
+                loc.loc_step(h, *odom[(args.warmup + s) % len(odom)])
+                flush.zero_()
+                starts[s].record()
+                loc.loc_lidar_update_dense(h, scans[(args.warmup + s) % n_scans], *scan_args)
+                ends[s].record()
+            torch.cuda.synchronize()
+        barrier(ws)
+        ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
+        total_s = max_over_ranks(sum(ms) / 1e3, ws)
+        per_step_s = total_s / args.steps
+        # end to end: the scan from host memory in, the pose estimate out
+        n_e2e = 0 if args.no_e2e else min(args.steps, 200)
+        e2e_t = 0.0
+        for s in range(n_e2e):
+            loc.loc_step(h, *odom[s % len(odom)])
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            loc.loc_lidar_update_dense(h, scans[s % n_scans], *scan_args)
+            loc.loc_argmax(h)
+            e2e_t += time.perf_counter() - t
+        e2e_t = max_over_ranks(e2e_t, ws)
+    finally:
+        loc.loc_destroy(h)
+    if rank != 0:
+        return
+    flops_state = 3.0 * n_used                    # per used beam: z - q, then (.)^2 accumulated (FMA)
+    achieved = n_states * flops_state / (statistics.mean(ms) / 1e3) / 1e12
+    peak = 152 * 128 * 2 * 2.070e9 / 1e12
+    elem = ELEM[storage]
+    cpu = None
+    if ws == 1 and not args.no_cpu_baseline:
+        rate, rows, n, per = oracle_dense_rate(wl, occ, walk, 15.0, 2)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"FP64 oracle dense_update on a {rows}-row band ({rows} x {wl['W']} x {K} states, "
+                         f"the band's own table), mean of {n} updates, {per:.2f} s each"}
+    line = {
+        "metric": METRIC, "value": n_states * ws / per_step_s, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": per_step_s * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": storage, "data": "synthetic",
+        "config": config_of(wl, args, extra={"n_angles": A, "r_max": wl["r_max"], "n_beams": wl["n_beams"],
+                                             "beam_stride": wl["beam_stride"], "used_beams_mean": n_used,
+                                             "timed": "loc_lidar_update_dense (score + reweight of every state)",
+                                             "table_build_s": table_s}),
+        "p50_step_ms": float(np.percentile(ms, 50)), "p99_step_ms": float(np.percentile(ms, 99)),
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                     "traffic": None, "kernel": "dense_score + dense_apply",
+                     "algorithmic_flops_per_launch": n_states * flops_state,
+                     "hbm_bytes_per_launch": n_states * (A / K + 8 + 3 * elem),
+                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"},
+        "cpu_baseline": cpu,
+        "e2e": {"value": n_states * ws * n_e2e / e2e_t if n_e2e else None, "unit": UNIT,
+                "h2d_bytes_per_step": 4 * wl["n_beams"], "d2h_bytes_per_step": 12, "steps": n_e2e,
+                "path": "loc_lidar_update_dense (ranges from host memory) + loc_argmax, host wall clock"},
+        "gpu_launches": 2 * args.steps,
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_reference_dense(args, wl, occ, walk, ws, rank):
+    if rank != 0:
+        return
+    rate, rows, n, per = oracle_dense_rate(wl, occ, walk, 150.0, args.steps + args.warmup)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": config_of(wl, args, extra={"sample": f"oracle dense update on a {rows}-row band"}),
+        "cpu_baseline": {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"FP64 oracle dense_update on {rows} x {wl['W']} x {wl['K']} states, {n} updates"},
+        "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     ws, rank, local = dist_init(args.gpus)
@@ -625,8 +773,11 @@ def main():
     else:
         occ = workloads.make_map(wl)
         walk = workloads.make_walk(wl, occ, seed_offset=rank)
+        dense = "n_angles" in wl
         if args.impl == "reference":
-            run_reference(args, wl, occ, walk, ws, rank)
+            (run_reference_dense if dense else run_reference)(args, wl, occ, walk, ws, rank)
+        elif dense:
+            run_dense(args, wl, occ, walk, ws, rank, local)
         else:
             run_ours(args, wl, occ, walk, ws, rank, local)
     if ws > 1:

@@ -16,8 +16,9 @@
 //  * range_table_kernel: one thread per cell walks all A directions; the writes of one
 //    direction are consecutive across a warp.
 //  * dense_score_kernel: a CTA of DC = 64 cells stages their table columns in shared memory
-//    twice over (directions 0 .. 2A-1, so k s + m_b needs no wrap); per thread, beams in the
-//    outer loop and KC = 16 bins of accumulators in registers.  The code is turned into a
+//    (16-byte loads, several in flight), regrouped by residue r = a mod s and stored twice
+//    over, so that bins k .. k+15 of a beam are rows DC bytes apart with no wrap; per thread,
+//    beams in the outer loop and KC = 16 bins of accumulators in registers.  The code is turned into a
 //    float by the 2^23 exponent trick (exact for 0 .. 255) and compared with z_b / step.  It
 //    also reads the stored belief for the offset c.
 //  * dense_apply_kernel: X exp(log L - c) mult stored with the storage type's rounding, FP32
@@ -64,48 +65,55 @@ __global__ void __launch_bounds__(DC) dense_score_kernel(const uint8_t* __restri
                                                          size_t hw, int K, int A, int s, const int* __restrict__ m,
                                                          const float* __restrict__ zs, int nu, float scale,
                                                          float* __restrict__ logL, unsigned int* maxL) {
+    // Us[(r 2K + k') DC + t] = code of direction ((k' mod K) s + r) for cell c0 + t: per residue
+    // r the K directions r, s + r, ... twice over, so bins k0 .. k0+15 of a beam with
+    // m = q s + r sit at rows r 2K + q + k0 .. +15, DC bytes apart (compile-time offsets).
     extern __shared__ __align__(16) unsigned char dsm[];
-    uint8_t* Ts = dsm;                                            // [2A][DC]
-    int* sm_m = reinterpret_cast<int*>(dsm + (size_t)2 * A * DC);  // [nu]
-    float* sm_z = reinterpret_cast<float*>(sm_m + nu);            // [nu]
+    uint8_t* Us = dsm;                                            // [s][2K][DC] = [2A][DC]
+    int* sm_o = reinterpret_cast<int*>(dsm + (size_t)2 * A * DC);  // [nu] row offset of each beam
+    float* sm_z = reinterpret_cast<float*>(sm_o + nu);            // [nu]
     const int t = threadIdx.x;
     const size_t c0 = (size_t)blockIdx.x * DC, c = c0 + t;
-    if ((hw & 3) == 0 && c0 + DC <= hw) {
-        // 4 cells per 32-bit load: DC / 4 threads per direction, DC / (DC / 4) directions a pass
-        constexpr int TPD = DC / 4;
+    auto row_of = [&](int a) { return (a % s) * 2 * K + a / s; };   // row of direction a (first copy)
+    if ((hw & 15) == 0 && c0 + DC <= hw) {
+        // 16 cells per 16-byte load: DC / 16 threads per direction, 16 directions a pass, four
+        // passes in flight
+        constexpr int TPD = DC / 16;
         const int g = t % TPD, a0 = t / TPD;
+#pragma unroll 4
         for (int a = a0; a < A; a += DC / TPD) {
-            const uint32_t v = *reinterpret_cast<const uint32_t*>(table + (size_t)a * hw + c0 + 4 * g);
-            *reinterpret_cast<uint32_t*>(Ts + (size_t)a * DC + 4 * g) = v;
-            *reinterpret_cast<uint32_t*>(Ts + (size_t)(a + A) * DC + 4 * g) = v;
+            const uint4 v = *reinterpret_cast<const uint4*>(table + (size_t)a * hw + c0 + 16 * g);
+            const int r0 = row_of(a);
+            *reinterpret_cast<uint4*>(Us + (size_t)r0 * DC + 16 * g) = v;
+            *reinterpret_cast<uint4*>(Us + (size_t)(r0 + K) * DC + 16 * g) = v;
         }
     } else {
         for (int a = 0; a < A; ++a) {
             const uint8_t v = c < hw ? table[(size_t)a * hw + c] : (uint8_t)0;
-            Ts[(size_t)a * DC + t] = v;
-            Ts[(size_t)(a + A) * DC + t] = v;
+            const int r0 = row_of(a);
+            Us[(size_t)r0 * DC + t] = v;
+            Us[(size_t)(r0 + K) * DC + t] = v;
         }
     }
     for (int u = t; u < nu; u += DC) {
-        sm_m[u] = m[u];
+        sm_o[u] = row_of(m[u]) * DC;
         sm_z[u] = zs[u];
     }
     __syncthreads();
     const bool in = c < hw, free = in && trav[c] != 0;
-    const int stride = s * DC;
     float best = -FLT_MAX;
     for (int k0 = 0; k0 < K; k0 += KC) {
         float acc[KC];
 #pragma unroll
         for (int kk = 0; kk < KC; ++kk) acc[kk] = 0.0f;
-        const uint8_t* base = Ts + (size_t)k0 * stride + t;
+        const uint8_t* base = Us + k0 * DC + t;
         for (int u = 0; u < nu; ++u) {
-            const uint8_t* col = base + (size_t)sm_m[u] * DC;
+            const uint8_t* col = base + sm_o[u];
             const float zu = sm_z[u];
 #pragma unroll
             for (int kk = 0; kk < KC; ++kk) {
-                if (k0 + kk < K) {                                 // k s + m_u < 2A
-                    const uint32_t q = col[kk * stride];
+                if (k0 + kk < K) {                                 // rows stay below r 2K + 2K
+                    const uint32_t q = col[kk * DC];
                     const float qf = __uint_as_float(0x4B000000u | q) - 8388608.0f;
                     const float d = zu - qf;
                     acc[kk] = fmaf(d, d, acc[kk]);

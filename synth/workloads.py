@@ -7,6 +7,9 @@ Each workload is a plain dict of sizes and noise settings plus a seed; `make_map
 * ``office512``    512 x 512 cells of 0.05 m, K = 64 bins; office plan; 2000 steps at dt 0.01 s.
 * ``office512_aniso`` the same map, bins and walk with anisotropic motion noise (Eq. 6): sigma
                    1.0 cell along each bin's heading, 0.5 across it.
+* ``office512_dense`` the office512 session with a dense scan update (Eq. 9 on every state):
+                   a 384-direction expected-range table (6 per bin, r_max 10 m) and a 360-beam
+                   scan (every 4th beam scored, sigma 0.1 m) after every step.
 * ``office2048``   2048 x 2048 cells of 0.05 m, K = 72 bins, BF16 storage; a 360-beam scan every
                    10th step; parity on a 256 x 256 crop.
 * ``batch64``      64 sessions, side log-uniform in [128, 1024], K in {36, 48, 64, 72}.
@@ -35,6 +38,10 @@ WORKLOADS = {
     "office512_aniso": dict(COMMON, name="office512_aniso", seed=1, H=512, W=512, K=64, cell=0.05,
                             steps=2000, dt=0.01, storage="f32", plan="office", sigma_xy_cells=1.0,
                             sigma_cross_cells=0.5),
+    "office512_dense": dict(COMMON, name="office512_dense", seed=1, H=512, W=512, K=64, cell=0.05,
+                            steps=2000, dt=0.01, storage="f32", plan="office", n_angles=384,
+                            r_max=10.0, n_beams=360, angle_min=-math.pi, angle_inc=math.pi / 180,
+                            beam_stride=4, sigma_r=0.1, scan_noise=0.05, dropout=0.05),
     "office2048": dict(COMMON, name="office2048", seed=2, H=2048, W=2048, K=72, cell=0.05,
                        steps=1000, dt=0.01, storage="bf16", plan="office", scan_every=10,
                        n_beams=360, angle_inc=math.pi / 180, r_max=10.0, scan_noise=0.05,
