@@ -16,9 +16,10 @@
 //  * range_table_kernel: one thread per cell walks all A directions; the writes of one
 //    direction are consecutive across a warp.
 //  * dense_score_kernel: a CTA of DC = 64 cells stages their table columns in shared memory
-//    (16-byte loads, several in flight), regrouped by residue r = a mod s and stored twice
-//    over, so that bins k .. k+15 of a beam are rows DC bytes apart with no wrap; per thread,
-//    beams in the outer loop and KC = 16 bins of accumulators in registers.  The code is turned into a
+//    (16-byte loads, several in flight), regrouped by residue r = a mod s with the first KC - 1
+//    rows of each group repeated, so that bins k .. k+KC-1 of a beam are rows DC bytes apart
+//    with no wrap; per thread, beams in the outer loop and KC = 32 bins of accumulators in
+//    registers.  The code is turned into a
 //    float by the 2^23 exponent trick (exact for 0 .. 255) and compared with z_b / step.  It
 //    also reads the stored belief for the offset c.
 //  * dense_apply_kernel: X exp(log L - c) mult stored with the storage type's rounding, FP32
@@ -34,7 +35,13 @@ namespace {
 
 constexpr int NT = 256;
 constexpr int DC = 64;            // cells per score CTA (one per thread)
-constexpr int KC = 16;            // bins per register chunk
+constexpr int KC = 32;            // bins per register chunk
+
+// Shared bytes of a score CTA's staged table: s residue blocks of K + min(K, KC - 1) rows of DC
+// cells (at most 2 A DC).
+__host__ __device__ constexpr size_t dense_table_bytes(int A, int K) {
+    return ((size_t)(A / K) * (K + (K < KC - 1 ? K : KC - 1)) * DC + 15) / 16 * 16;
+}
 
 // Order-preserving map of floats to unsigned ints (for atomicMax on floats).
 __device__ __forceinline__ unsigned int f2ord(float f) {
@@ -65,16 +72,23 @@ __global__ void __launch_bounds__(DC) dense_score_kernel(const uint8_t* __restri
                                                          size_t hw, int K, int A, int s, const int* __restrict__ m,
                                                          const float* __restrict__ zs, int nu, float scale,
                                                          float* __restrict__ logL, unsigned int* maxL) {
-    // Us[(r 2K + k') DC + t] = code of direction ((k' mod K) s + r) for cell c0 + t: per residue
-    // r the K directions r, s + r, ... twice over, so bins k0 .. k0+15 of a beam with
-    // m = q s + r sit at rows r 2K + q + k0 .. +15, DC bytes apart (compile-time offsets).
+    // Us[(r RB + k') DC + t] = code of direction ((k' mod K) s + r) for cell c0 + t, k' < RB =
+    // K + min(K, KC - 1): per residue r the K directions r, s + r, ... followed by the first
+    // RB - K of them again, so bins k0 .. k0+KC-1 of a beam with m = q s + r sit at rows
+    // r RB + ((q + k0) mod K) + 0 .. KC-1, DC bytes apart (compile-time offsets).
     extern __shared__ __align__(16) unsigned char dsm[];
-    uint8_t* Us = dsm;                                            // [s][2K][DC] = [2A][DC]
-    int* sm_o = reinterpret_cast<int*>(dsm + (size_t)2 * A * DC);  // [nu] row offset of each beam
-    float* sm_z = reinterpret_cast<float*>(sm_o + nu);            // [nu]
+    const int RB = K + (K < KC - 1 ? K : KC - 1);
+    uint8_t* Us = dsm;                                            // [s][RB][DC]
+    int* sm_r = reinterpret_cast<int*>(dsm + dense_table_bytes(A, K));  // [nu] block row of each beam
+    int* sm_q = sm_r + nu;                                        // [nu] its q
+    float* sm_z = reinterpret_cast<float*>(sm_q + nu);            // [nu]
     const int t = threadIdx.x;
     const size_t c0 = (size_t)blockIdx.x * DC, c = c0 + t;
-    auto row_of = [&](int a) { return (a % s) * 2 * K + a / s; };   // row of direction a (first copy)
+    auto put = [&](int a, auto store) {                           // direction a's row(s)
+        const int r = a % s, k = a / s;
+        store(r * RB + k);
+        if (k < RB - K) store(r * RB + K + k);
+    };
     if ((hw & 15) == 0 && c0 + DC <= hw) {
         // 16 cells per 16-byte load: DC / 16 threads per direction, 16 directions a pass, four
         // passes in flight
@@ -83,20 +97,17 @@ __global__ void __launch_bounds__(DC) dense_score_kernel(const uint8_t* __restri
 #pragma unroll 4
         for (int a = a0; a < A; a += DC / TPD) {
             const uint4 v = *reinterpret_cast<const uint4*>(table + (size_t)a * hw + c0 + 16 * g);
-            const int r0 = row_of(a);
-            *reinterpret_cast<uint4*>(Us + (size_t)r0 * DC + 16 * g) = v;
-            *reinterpret_cast<uint4*>(Us + (size_t)(r0 + K) * DC + 16 * g) = v;
+            put(a, [&](int row) { *reinterpret_cast<uint4*>(Us + (size_t)row * DC + 16 * g) = v; });
         }
     } else {
         for (int a = 0; a < A; ++a) {
             const uint8_t v = c < hw ? table[(size_t)a * hw + c] : (uint8_t)0;
-            const int r0 = row_of(a);
-            Us[(size_t)r0 * DC + t] = v;
-            Us[(size_t)(r0 + K) * DC + t] = v;
+            put(a, [&](int row) { Us[(size_t)row * DC + t] = v; });
         }
     }
     for (int u = t; u < nu; u += DC) {
-        sm_o[u] = row_of(m[u]) * DC;
+        sm_r[u] = (m[u] % s) * RB * DC;
+        sm_q[u] = m[u] / s;
         sm_z[u] = zs[u];
     }
     __syncthreads();
@@ -106,13 +117,14 @@ __global__ void __launch_bounds__(DC) dense_score_kernel(const uint8_t* __restri
         float acc[KC];
 #pragma unroll
         for (int kk = 0; kk < KC; ++kk) acc[kk] = 0.0f;
-        const uint8_t* base = Us + k0 * DC + t;
         for (int u = 0; u < nu; ++u) {
-            const uint8_t* col = base + sm_o[u];
+            int k1 = sm_q[u] + k0;
+            if (k1 >= K) k1 -= K;
+            const uint8_t* col = Us + sm_r[u] + k1 * DC + t;
             const float zu = sm_z[u];
 #pragma unroll
             for (int kk = 0; kk < KC; ++kk) {
-                if (k0 + kk < K) {                                 // rows stay below r 2K + 2K
+                if (k0 + kk < K) {                                 // rows stay below r RB + RB
                     const uint32_t q = col[kk * DC];
                     const float qf = __uint_as_float(0x4B000000u | q) - 8388608.0f;
                     const float d = zu - qf;
@@ -172,7 +184,7 @@ __global__ void __launch_bounds__(NT) dense_apply_kernel(T* __restrict__ B, cons
 
 }  // namespace
 
-size_t dense_score_smem(int A, int nu) { return (size_t)2 * A * DC + (size_t)nu * 8; }
+size_t dense_score_smem(int A, int K, int nu) { return dense_table_bytes(A, K) + (size_t)nu * 12; }
 
 cudaError_t launch_range_table(const uint8_t* trav, int H, int W, const float* dirs, int A, float rmax,
                                float inv_step, uint8_t* out, cudaStream_t st) {
@@ -188,7 +200,7 @@ cudaError_t score_t(const uint8_t* table, const uint8_t* trav, const void* B, in
                     const int* m, const float* zs, int nu, float scale, float* logL, unsigned int* maxL,
                     cudaStream_t st) {
     const size_t hw = (size_t)H * W;
-    const size_t smem = dense_score_smem(A, nu);
+    const size_t smem = dense_score_smem(A, K, nu);
     static size_t attr = 0;                        // the largest size set so far
     if (smem > 48 * 1024 && smem > attr) {
         const cudaError_t e = cudaFuncSetAttribute(dense_score_kernel<T>,

@@ -22,7 +22,7 @@ unsigned int step_num_blocks(int H, int W);
 // [K][H][W] and the maximum of log L + log X as an ordered uint) and the reweighting.
 cudaError_t launch_range_table(const uint8_t* trav, int H, int W, const float* dirs, int A, float rmax,
                                float inv_step, uint8_t* out, cudaStream_t st);
-size_t dense_score_smem(int A, int nu);
+size_t dense_score_smem(int A, int K, int nu);
 cudaError_t launch_dense_score(const uint8_t* table, const uint8_t* trav, const void* B, int storage, int H, int W,
                                int K, int A, const int* m, const float* zs, int nu, float scale, float* logL,
                                unsigned int* maxL, cudaStream_t st);
