@@ -170,6 +170,25 @@ loc_status loc_dither(loc_handle h, const float* m, float fs, uint8_t* sel, int*
 loc_status loc_ray_ranges(loc_handle h, const int32_t* cells, int n_cells, const float* dirs,
                           int n_dirs, double r_max, float* out);
 
+/* The pose estimate and how concentrated the belief is around it (Section III-A.3's belief
+ * map; the multiple hypotheses of Section V).  The estimate is loc_argmax's state (k, j, i):
+ * pose x = (i + 1/2) cell_m, y = (j + 1/2) cell_m, theta = 2 pi k / K + theta_t mod 2 pi,
+ * belief p.  mass_near = the belief of the states whose cell lies within radius_m of (j, i)
+ * (dj^2 + di^2 <= floor(radius_m^2 / cell_m^2 + 1e-9), so a radius of a whole number of cells
+ * includes the cells at that distance) and whose bin is within dk of k (circular).  The second
+ * hypothesis is the largest belief-map value (max over bins) among the cells outside that disk,
+ * the lowest cell index on ties: (second_j, second_i, second_p), or (-1, -1, 0) when no cell
+ * outside holds belief; second_ratio = second_p / p.  Synchronous.
+ * Errors: INVALID_ARG (null out, radius_m negative or not finite, dk < 0), OOM, CUDA, STATE. */
+typedef struct loc_estimate_t {
+    int k, j, i;
+    double x, y, theta, p;
+    double mass_near;
+    int second_j, second_i;
+    double second_p, second_ratio;
+} loc_estimate_t;
+loc_status loc_estimate(loc_handle h, double radius_m, int dk, loc_estimate_t* out);
+
 /* Readbacks (synchronous).  n must equal the element count exactly.
  *   loc_belief:   normalised belief, host float[K][H][W].
  *   loc_marginal: host float[H][W]: LOC_MAP_MAX = max over channels (the paper's belief

@@ -21,7 +21,8 @@ __all__ = [
     "loc_lidar_update_cells", "loc_belief", "loc_marginal", "loc_argmax", "loc_set_belief",
     "loc_stats", "loc_sync", "loc_destroy", "loc_last_error", "torch_stream",
     "use_torch_allocator", "loc_propagate_noalloc", "loc_samples", "loc_dither", "loc_ray_ranges",
-    "loc_range_table", "loc_range_table_read", "loc_lidar_update_dense",
+    "loc_range_table", "loc_range_table_read", "loc_lidar_update_dense", "loc_estimate",
+    "loc_estimate_t",
     "LOC_BATCH_CONFIGS", "Batch", "loc_batch_create", "loc_batch_step", "loc_batch_sync",
     "loc_batch_info", "loc_batch_destroy", "loc_batch_last_error", "loc_session_bytes",
     "LOC_SESSION_PENDING", "LOC_SESSION_ACTIVE", "LOC_SESSION_CLOSED", "LOC_SESSION_FAILED",
@@ -82,6 +83,14 @@ class loc_server_stats_t(ctypes.Structure):
                 ("last_s", ctypes.c_double)]
 
 
+class loc_estimate_t(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int), ("j", ctypes.c_int), ("i", ctypes.c_int),
+                ("x", ctypes.c_double), ("y", ctypes.c_double), ("theta", ctypes.c_double),
+                ("p", ctypes.c_double), ("mass_near", ctypes.c_double),
+                ("second_j", ctypes.c_int), ("second_i", ctypes.c_int),
+                ("second_p", ctypes.c_double), ("second_ratio", ctypes.c_double)]
+
+
 _lib = None
 _P = ctypes.c_void_p
 _ALLOC = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
@@ -114,6 +123,7 @@ _SIGS = {
     "loc_samples": (ctypes.c_int, [_P, _P, ctypes.c_size_t, ctypes.POINTER(ctypes.c_int)]),
     "loc_dither": (ctypes.c_int, [_P, _P, ctypes.c_float, _P, ctypes.POINTER(ctypes.c_int)]),
     "loc_ray_ranges": (ctypes.c_int, [_P, _P, ctypes.c_int, _P, ctypes.c_int, ctypes.c_double, _P]),
+    "loc_estimate": (ctypes.c_int, [_P, ctypes.c_double, ctypes.c_int, ctypes.POINTER(loc_estimate_t)]),
     "loc_range_table": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_double]),
     "loc_range_table_read": (ctypes.c_int, [_P, _P, ctypes.c_size_t]),
     "loc_lidar_update_dense": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_double, ctypes.c_double,
@@ -285,6 +295,13 @@ def loc_ray_ranges(h: Handle, cells: np.ndarray, dirs: np.ndarray, r_max: float)
     _check(h, lib().loc_ray_ranges(h, _ptr(c), int(c.size), _ptr(d), int(d.shape[0]), float(r_max),
                                    _ptr(out)))
     return out
+
+
+def loc_estimate(h: Handle, radius_m: float, dk: int) -> dict:
+    """The pose estimate, the belief near it and the second hypothesis outside its disk."""
+    e = loc_estimate_t()
+    _check(h, lib().loc_estimate(h, float(radius_m), int(dk), ctypes.byref(e)))
+    return {name: getattr(e, name) for name, _ in loc_estimate_t._fields_}
 
 
 def loc_range_table(h: Handle, n_angles: int, r_max: float) -> None:

@@ -816,6 +816,59 @@ LOC_API loc_status loc_argmax(loc_handle h, int* k, int* j, int* i, float* p) {
     return check_status(h, status);
 }
 
+LOC_API loc_status loc_estimate(loc_handle h, double radius_m, int dk, loc_estimate_t* out) {
+    loc_status st = check_live(h);
+    if (st != LOC_OK) return st;
+    if (!out) return fail(h, LOC_ERR_INVALID_ARG, "null output");
+    if (!(radius_m >= 0.0) || !std::isfinite(radius_m) || dk < 0)
+        return fail(h, LOC_ERR_INVALID_ARG, "radius_m must be finite and >= 0, dk >= 0");
+    if (!h->est) {
+        h->est = (EstimateOut*)dev_alloc(h, sizeof(EstimateOut));
+        if (!h->est) return fail(h, LOC_ERR_OOM, "estimate buffer");
+    }
+    const double c = h->p.cell_m;
+    // cells whose centres lie within radius_m; the 1e-9 keeps a whole number of cells inclusive
+    const double r2d = std::floor(radius_m * radius_m / (c * c) + 1e-9);
+    const long long r2 = r2d > 4.0e18 ? (long long)4e18 : (long long)r2d;
+    cudaError_t e = launch_argmax(h->B[h->cur], h->p.storage, h->trav, h->sd, h->inv_uniform, h->p.H, h->p.W, h->p.K,
+                                  h->argmax_scratch, h->argmax_idx, h->argmax_val, h->stream);
+    if (e == cudaSuccess)
+        e = launch_estimate(h->B[h->cur], h->p.storage, h->trav, h->sd, h->inv_uniform, h->p.H, h->p.W, h->p.K,
+                            h->argmax_scratch, h->argmax_idx, r2, dk, h->partials, h->nparts, h->est, h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h->pinned, h->argmax_idx, sizeof(long long) + sizeof(float), cudaMemcpyDeviceToHost,
+                            h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->pinned + 16, &h->sd->status, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h->pinned + 24, h->est, sizeof(EstimateOut), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "loc_estimate");
+    long long idx;
+    float val;
+    int status;
+    EstimateOut eo;
+    std::memcpy(&idx, h->pinned, sizeof(idx));
+    std::memcpy(&val, h->pinned + sizeof(long long), sizeof(val));
+    std::memcpy(&status, h->pinned + 16, sizeof(status));
+    std::memcpy(&eo, h->pinned + 24, sizeof(eo));
+    const long long hw = (long long)h->hw;
+    out->k = (int)(idx / hw);
+    out->j = (int)((idx % hw) / h->p.W);
+    out->i = (int)(idx % h->p.W);
+    out->x = (out->i + 0.5) * c;
+    out->y = (out->j + 0.5) * c;
+    double th = std::fmod(2.0 * M_PI * out->k / h->p.K + h->theta, 2.0 * M_PI);
+    if (th < 0.0) th += 2.0 * M_PI;
+    out->theta = th;
+    out->p = val;
+    out->mass_near = eo.mass_near;
+    out->second_j = eo.second_cell >= 0 ? (int)(eo.second_cell / h->p.W) : -1;
+    out->second_i = eo.second_cell >= 0 ? (int)(eo.second_cell % h->p.W) : -1;
+    out->second_p = eo.second_p;
+    out->second_ratio = val > 0.0f ? (double)eo.second_p / (double)val : 0.0;
+    return check_status(h, status);
+}
+
 LOC_API loc_status loc_set_belief(loc_handle h, const float* b, size_t n) {
     loc_status st = check_live(h);
     if (st != LOC_OK) return st;

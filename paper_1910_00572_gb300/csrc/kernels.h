@@ -114,6 +114,19 @@ cudaError_t launch_read_marginal(const void* B, int storage, const uint8_t* trav
 
 // Argmax of the stored tensor: per-CTA (value, index) pairs then a final pass writing
 // out_idx[0] (linear index) and out_val[0] (normalised value).  `scratch` holds
+// loc_estimate's results (device): the mass near the argmax state and the strongest cell
+// outside its disk (-1 when none holds belief).
+struct EstimateOut {
+    double mass_near;
+    long long second_cell;
+    float second_p;
+    float pad;
+};
+// After launch_argmax on the same stream (its index in arg_idx; its scratch reused).
+cudaError_t launch_estimate(const void* B, int storage, const uint8_t* trav, const SessionDev* sd,
+                            float inv_uniform, int H, int W, int K, void* scratch, const long long* arg_idx,
+                            long long r2, int dk, double* partials, unsigned int nparts, EstimateOut* out,
+                            cudaStream_t st);
 // argmax_scratch_len(n) float + int pairs.
 size_t argmax_scratch_bytes(size_t n);
 cudaError_t launch_argmax(const void* B, int storage, const uint8_t* trav,

@@ -207,6 +207,115 @@ __global__ void __launch_bounds__(NT) argmax_vec_kernel(const T* __restrict__ B,
     }
 }
 
+// loc_estimate: one pass over the belief around the argmax state a (written by the argmax
+// kernel on the same stream).  mass_near sums the states whose cell lies within the disk
+// dj^2 + di^2 <= r2 of a's cell and whose bin is within dk of a's (circular): FP32 Kahan per
+// thread, FP64 per CTA, the last CTA summing the CTA partials in a fixed order.  The second
+// hypothesis is the largest belief among the cells outside the disk, the lowest cell index on
+// ties (threads scan in increasing index order and combine with better()).
+template <typename T>
+__global__ void __launch_bounds__(NT) estimate_kernel(const T* __restrict__ B, const uint8_t* __restrict__ trav,
+                                                      const SessionDev* sd, float inv_uniform, int H, int W, int K,
+                                                      const long long* arg_idx, long long r2, int dk,
+                                                      double* partials, float* pv, long long* pi,
+                                                      unsigned int* counter, EstimateOut* out) {
+    __shared__ double red[NT / 32];
+    __shared__ float sv[NT / 32];
+    __shared__ long long si[NT / 32];
+    const size_t hw = (size_t)H * W, n = hw * K;
+    const long long a = *arg_idx;
+    const int ka = (int)(a / (long long)hw), ja = (int)((a % (long long)hw) / W), ia = (int)(a % W);
+    const int reinit = sd->reinit;
+    const float scale = sd->inv_Z;
+    KahanF mass;
+    float bv = -FLT_MAX;
+    long long bi = LLONG_MAX;
+    for (size_t q = (size_t)blockIdx.x * NT + threadIdx.x; q < n; q += (size_t)gridDim.x * NT) {
+        const int k = (int)(q / hw);
+        const size_t cell = q - (size_t)k * hw;
+        const int j = (int)(cell / W), i = (int)(cell - (size_t)j * W);
+        const float v = belief_at(B, trav, hw, q, reinit, inv_uniform, scale);
+        const long long dj = j - ja, di = i - ia;
+        if (dj * dj + di * di <= r2) {
+            int d = k > ka ? k - ka : ka - k;
+            if (K - d < d) d = K - d;
+            if (d <= dk) mass.add(v);
+        } else if (better(v, (long long)cell, bv, bi)) {
+            bv = v;
+            bi = (long long)cell;
+        }
+    }
+    const double bm = block_sum<NT>(mass.value(), red);
+    for (int o = 16; o > 0; o >>= 1) {
+        const float ov = __shfl_down_sync(0xffffffffu, bv, o);
+        const long long oi = __shfl_down_sync(0xffffffffu, bi, o);
+        if (better(ov, oi, bv, bi)) {
+            bv = ov;
+            bi = oi;
+        }
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) {
+        sv[warp] = bv;
+        si[warp] = bi;
+    }
+    __syncthreads();
+    __shared__ int s_last;
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < NT / 32; ++w)
+            if (better(sv[w], si[w], bv, bi)) {
+                bv = sv[w];
+                bi = si[w];
+            }
+        partials[blockIdx.x] = bm;
+        pv[blockIdx.x] = bv;
+        pi[blockIdx.x] = bi;
+        __threadfence();
+        s_last = atomicAdd(counter, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    double ms = 0.0;
+    bv = -FLT_MAX;
+    bi = LLONG_MAX;
+    for (unsigned int b = threadIdx.x; b < gridDim.x; b += NT) {
+        ms += ((volatile double*)partials)[b];
+        const float v = ((volatile float*)pv)[b];
+        const long long q = ((volatile long long*)pi)[b];
+        if (better(v, q, bv, bi)) {
+            bv = v;
+            bi = q;
+        }
+    }
+    const double mt = block_sum<NT>(ms, red);
+    for (int o = 16; o > 0; o >>= 1) {
+        const float ov = __shfl_down_sync(0xffffffffu, bv, o);
+        const long long oi = __shfl_down_sync(0xffffffffu, bi, o);
+        if (better(ov, oi, bv, bi)) {
+            bv = ov;
+            bi = oi;
+        }
+    }
+    __syncthreads();
+    if (lane == 0) {
+        sv[warp] = bv;
+        si[warp] = bi;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < NT / 32; ++w)
+            if (better(sv[w], si[w], bv, bi)) {
+                bv = sv[w];
+                bi = si[w];
+            }
+        out->mass_near = mt;
+        out->second_p = bv > 0.0f ? bv : 0.0f;
+        out->second_cell = bv > 0.0f ? bi : -1;
+        *counter = 0u;
+    }
+}
+
 __global__ void argmax_final_kernel(const float* __restrict__ pv, const long long* __restrict__ pi,
                                     int nb, const SessionDev* sd, long long* out_idx,
                                     float* out_val) {
@@ -356,6 +465,22 @@ cudaError_t launch_argmax(const void* B, int storage, const uint8_t* trav,
                                   (const T*)B, trav, sd, inv_uniform, hw, n, pv, pi)));
     }
     argmax_final_kernel<<<1, NT, 0, st>>>(pv, pi, (int)nb, sd, out_idx, out_val);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_estimate(const void* B, int storage, const uint8_t* trav, const SessionDev* sd,
+                            float inv_uniform, int H, int W, int K, void* scratch, const long long* arg_idx,
+                            long long r2, int dk, double* partials, unsigned int nparts, EstimateOut* out,
+                            cudaStream_t st) {
+    const size_t n = (size_t)H * W * K;
+    long long* pi = (long long*)scratch;
+    float* pv = (float*)(pi + kArgmaxBlocks);
+    unsigned int* counter = reinterpret_cast<unsigned int*>(pv + kArgmaxBlocks);
+    unsigned int nb = grid_for(n);
+    if (nb > kArgmaxBlocks) nb = kArgmaxBlocks;
+    if (nb > nparts) nb = nparts;
+    LOC_DISPATCH(storage, (estimate_kernel<T><<<nb, NT, 0, st>>>((const T*)B, trav, sd, inv_uniform, H, W, K, arg_idx,
+                                                                 r2, dk, partials, pv, pi, counter, out)));
     return cudaGetLastError();
 }
 

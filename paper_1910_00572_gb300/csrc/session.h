@@ -31,6 +31,7 @@ struct loc_session {
     long long* argmax_idx = nullptr;
     float* argmax_val = nullptr;
     unsigned char* pinned = nullptr;   // 64 bytes of pinned host memory for small readbacks
+    loc::EstimateOut* est = nullptr;   // loc_estimate's device results (allocated on first use)
     // LIDAR sample update scratch (allocated on first use)
     bool lidar_ready = false;
     int cap = 0;                   // capacity of the sample list

@@ -10,6 +10,7 @@ import pytest
 from scipy import signal
 
 from oracle import filter as F
+from oracle import readout as R
 from oracle.odometry import Odometry
 from synth import floorplan
 
@@ -335,3 +336,33 @@ def test_gate_defers_small_motion():
     assert not o.due()
     o.add(0.06, 0.0, 0.0)
     assert o.due()
+
+
+def test_estimate_of_a_point_mass_and_of_two_blobs():
+    """The pose estimate's concentration and second hypothesis on beliefs with known answers:
+    a point mass (all mass near, no second hypothesis); two blobs far apart (the near mass is
+    the first blob's, the second hypothesis the other blob's peak); the disk's edge (a cell
+    exactly radius_m away counts as near); the bin window wrapping around."""
+    K, H, W, c = 8, 30, 40, 0.1
+    b = np.zeros((K, H, W))
+    b[3, 10, 12] = 1.0
+    e = R.estimate(b, c, 0.25, 0.5, 1)
+    assert (e["k"], e["j"], e["i"]) == (3, 10, 12) and e["mass_near"] == 1.0
+    assert (e["second_j"], e["second_i"], e["second_p"]) == (-1, -1, 0.0)
+    assert abs(e["x"] - 1.25) < 1e-12 and abs(e["y"] - 1.05) < 1e-12
+    assert abs(e["theta"] - (2 * np.pi * 3 / 8 + 0.25)) < 1e-12
+    # two blobs: 0.6 at bins 0 and 7 (wrapping) around (5, 5), 0.4 spread at (20, 30)
+    b = np.zeros((K, H, W))
+    b[0, 5, 5], b[7, 5, 6], b[1, 4, 5] = 0.3, 0.2, 0.1
+    b[2, 20, 30], b[2, 21, 30] = 0.25, 0.15
+    e = R.estimate(b, c, 0.0, 0.3, 1)
+    assert (e["k"], e["j"], e["i"]) == (0, 5, 5)
+    assert abs(e["mass_near"] - 0.6) < 1e-15                   # bin 7 is one bin from bin 0
+    assert (e["second_j"], e["second_i"]) == (20, 30) and e["second_p"] == 0.25
+    assert abs(e["second_ratio"] - 0.25 / 0.3) < 1e-15
+    # the disk's edge: (5, 8) is exactly 0.3 m from (5, 5); (5, 9) is not
+    b[0, 5, 8] = 0.01
+    b[0, 5, 9] = 0.29
+    e = R.estimate(b, c, 0.0, 0.3, 0)
+    assert abs(e["mass_near"] - (0.3 + 0.1 * 0 + 0.01)) < 1e-15   # bins 7 and 1 are excluded
+    assert (e["second_j"], e["second_i"]) == (5, 9)
