@@ -125,3 +125,47 @@ class Filter:
         self.f.B, _, _, dl = dense_update(self.f.B, self.occ, self.table, self.f.odo.theta, z,
                                           angle_min, angle_inc, self.r_max, beam_stride, sigma_r)
         self.f.logscale += dl
+
+
+def probe_scan(table: np.ndarray, K: int, cell_index: int, probe_bin: int, beam_step: int):
+    """The noise-free scan of a probe: beams b = 0, 1, ... on table directions
+    probe_bin A/K + b beam_step (mod A), b beam_step < A; each range is the table's code at the
+    probe's cell (in code steps).  Returns the used beams' offsets m_b = b beam_step and codes
+    (code 255, the capped range, is skipped like a dropout)."""
+    A = table.shape[0]
+    s = A // K
+    col = table.reshape(A, -1)[:, cell_index]
+    m, q = [], []
+    for b in range(0, (A + beam_step - 1) // beam_step):
+        off = b * beam_step
+        if off >= A:
+            break
+        code = int(col[(probe_bin * s + off) % A])
+        if code == 255:
+            continue
+        m.append(off)
+        q.append(code)
+    return np.array(m, np.int64), np.array(q, np.int64)
+
+
+def map_difficulty(occ: np.ndarray, table: np.ndarray, K: int, cell: float, r_max: float,
+                   probes: np.ndarray, probe_bin: int, beam_step: int, sigma_r: float, C: float):
+    """Eq. 11 on a set of probe cells: for each probe p, the state that best matches its
+    noise-free scan (the argmax of log L over the states of free cells, the first in [K][H][W]
+    order on ties) gives the location p_hat; e_p = |p - p_hat| between cell centres (m).
+    Returns (e_p for every probe, the number with e_p > C)."""
+    H, W = occ.shape
+    step = float(np.float32(r_max / 255.0))
+    free = np.broadcast_to(occ == 0, (K, H, W))
+    errors = []
+    for p in probes:
+        m, q = probe_scan(table, K, int(p), probe_bin, beam_step)
+        logL = log_likelihood(table, K, m, q.astype(np.float64) * step, r_max, sigma_r)
+        logL = np.where(free, logL, -np.inf)
+        flat = int(np.argmax(logL.reshape(-1)))
+        rem = flat % (H * W)
+        jh, ih = divmod(rem, W)
+        j, i = divmod(int(p), W)
+        errors.append(cell * math.hypot(jh - j, ih - i))
+    e = np.array(errors)
+    return e, int((e > C).sum())

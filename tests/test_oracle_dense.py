@@ -149,3 +149,59 @@ def test_a_clean_scan_on_the_table_grid_scores_the_true_state_highest():
     nb, logL, mx, _ = D.dense_update(f.B, occ, table, 0.0, z, 0.0, ainc, r_max, 1, 0.05)
     assert logL[kt, jt, it] == pytest.approx(0.0, abs=1e-9) and mx == pytest.approx(0.0, abs=1e-9)
     assert nb[kt, jt, it] == nb.max()
+
+
+def test_map_difficulty_of_a_featureless_corridor():
+    """A corridor much longer than r_max: along its middle every cell sees the same scan (the
+    side walls; the beams along the corridor are capped and skipped, like dropouts), so the best
+    match of a probe there is the first cell of its row that agrees with the probe on every used
+    beam, and the error is the distance to it."""
+    H, W, K, A = 7, 80, 4, 16
+    occ = np.zeros((H, W), np.uint8)
+    occ[0, :] = occ[-1, :] = 1
+    cell, r_max = 0.1, 1.0                                   # r_max = 10 cells << 80
+    table = D.range_table(occ, A, r_max, cell)
+    probes = np.array([3 * W + i for i in (20, 30, 40, 50, 60)])
+    e, n = D.map_difficulty(occ, table, K, cell, r_max, probes, 0, 1, 0.1, 1.0)
+    # the probe's used directions (code < 255 in its own column), and the first cell of row 3
+    # (bin 0) whose codes agree on all of them
+    used = [a for a in range(A) if table[a, 3, 40] < 255]
+    first = next(i for i in range(W) if all(table[a, 3, i] == table[a, 3, 40] for a in used))
+    assert 0 < first < 20
+    assert np.allclose(e, [cell * (i - first) for i in (20, 30, 40, 50, 60)])
+    assert n == 5                                            # all farther than 1 m
+
+
+def test_map_difficulty_is_zero_where_every_scan_is_distinct():
+    """Noise-free probes in a room with distinct features: each probe's own state matches
+    exactly (log L = 0) and no other free state within the cap does, so e_p = 0."""
+    rng = np.random.default_rng(2)
+    H, W, K, A = 20, 26, 8, 32
+    occ = np.zeros((H, W), np.uint8)
+    occ[0, :] = occ[-1, :] = occ[:, 0] = occ[:, -1] = 1
+    occ[5:7, 8:10] = 1
+    occ[12, 15:20] = 1
+    occ[3:9, 19] = 1
+    cell, r_max = 0.1, 3.0
+    table = D.range_table(occ, A, r_max, cell)
+    free = np.flatnonzero(occ.reshape(-1) == 0)
+    probes = rng.choice(free, 25, replace=False)
+    e, n = D.map_difficulty(occ, table, K, cell, r_max, probes, 0, 1, 0.1, 1.0)
+    assert n == 0 and e.max() == 0.0
+
+
+def test_map_difficulty_of_two_identical_rooms_finds_the_copy():
+    """Two closed rooms, one a translate of the other: the walk depends only on offsets, so a
+    probe in the second room (the larger index) sees exactly the scan of its copy in the first,
+    and the tie goes to the copy; a probe in the first room matches itself."""
+    H, W, K, A = 12, 40, 8, 32
+    occ = np.zeros((H, W), np.uint8)
+    occ[0, :] = occ[-1, :] = 1
+    occ[:, 0] = occ[:, 19] = occ[:, 20] = occ[:, 39] = 1
+    occ[3, 5] = occ[3, 25] = 1                               # the same feature in both rooms
+    occ[8, 12:15] = occ[8, 32:35] = 1
+    cell, r_max = 0.1, 3.0
+    table = D.range_table(occ, A, r_max, cell)
+    probes = np.array([6 * W + 8, 6 * W + 28])
+    e, n = D.map_difficulty(occ, table, K, cell, r_max, probes, 0, 1, 0.1, 1.0)
+    assert e[0] == 0.0 and abs(e[1] - 2.0) < 1e-12 and n == 1
