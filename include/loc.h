@@ -269,6 +269,20 @@ loc_status loc_range_table_read(loc_handle h, uint8_t* out, size_t n);
 loc_status loc_lidar_update_dense(loc_handle h, const float* ranges, int n_beams, double angle_min,
                                   double angle_inc, int beam_stride, double sigma_r);
 
+/* Map difficulty D_M (Eq. 11) on probe cells through the dense scorer.  For each probe
+ * (a free cell, linear index j W + i), its noise-free scan is read off the range table: beams
+ * on table directions probe_bin n_angles / K + b beam_step (mod n_angles), b beam_step <
+ * n_angles, each range the table's code at the probe (code 255, the capped range, skipped).
+ * Every state is scored against it as in loc_lidar_update_dense (sigma_r), and the best match
+ * is the argmax of log L over the states of free cells (the first in [K][H][W] order on ties);
+ * e_p = cell_m * |p - p_hat| between cell centres.  errors (may be NULL): double[n_probes]
+ * receives e_p; *n_wrong = the number of probes with e_p > c_m, so D_M is estimated as
+ * n_wrong / n_probes.  Needs the range table; leaves the belief unchanged; synchronous.
+ * Errors: INVALID_ARG (no table, probe out of grid or occupied, bad parameters), OOM, CUDA,
+ * STATE. */
+loc_status loc_map_difficulty(loc_handle h, const int32_t* probes, int n_probes, int probe_bin,
+                              int beam_step, double sigma_r, double c_m, double* errors, int* n_wrong);
+
 /* ---- Batched propagation of many sessions (one persistent launch per tick).
  * Alg. 1 lines 3-7 and the Eq. 9 normaliser for every session whose gate opens, over a work
  * list of (session, tile) items that the launch's CTAs take from a device queue; the CTA that

@@ -21,7 +21,7 @@ __all__ = [
     "loc_lidar_update_cells", "loc_belief", "loc_marginal", "loc_argmax", "loc_set_belief",
     "loc_stats", "loc_sync", "loc_destroy", "loc_last_error", "torch_stream",
     "use_torch_allocator", "loc_propagate_noalloc", "loc_samples", "loc_dither", "loc_ray_ranges",
-    "loc_range_table", "loc_range_table_read", "loc_lidar_update_dense", "loc_estimate",
+    "loc_range_table", "loc_range_table_read", "loc_lidar_update_dense", "loc_estimate", "loc_map_difficulty",
     "loc_estimate_t",
     "LOC_BATCH_CONFIGS", "Batch", "loc_batch_create", "loc_batch_step", "loc_batch_sync",
     "loc_batch_info", "loc_batch_destroy", "loc_batch_last_error", "loc_session_bytes",
@@ -124,6 +124,8 @@ _SIGS = {
     "loc_dither": (ctypes.c_int, [_P, _P, ctypes.c_float, _P, ctypes.POINTER(ctypes.c_int)]),
     "loc_ray_ranges": (ctypes.c_int, [_P, _P, ctypes.c_int, _P, ctypes.c_int, ctypes.c_double, _P]),
     "loc_estimate": (ctypes.c_int, [_P, ctypes.c_double, ctypes.c_int, ctypes.POINTER(loc_estimate_t)]),
+    "loc_map_difficulty": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                          ctypes.c_double, _P, ctypes.POINTER(ctypes.c_int)]),
     "loc_range_table": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_double]),
     "loc_range_table_read": (ctypes.c_int, [_P, _P, ctypes.c_size_t]),
     "loc_lidar_update_dense": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_double, ctypes.c_double,
@@ -302,6 +304,17 @@ def loc_estimate(h: Handle, radius_m: float, dk: int) -> dict:
     e = loc_estimate_t()
     _check(h, lib().loc_estimate(h, float(radius_m), int(dk), ctypes.byref(e)))
     return {name: getattr(e, name) for name, _ in loc_estimate_t._fields_}
+
+
+def loc_map_difficulty(h: Handle, probes: np.ndarray, probe_bin: int, beam_step: int, sigma_r: float,
+                       c_m: float):
+    """Eq. 11 on probe cells: (e_p per probe in metres, the number with e_p > c_m)."""
+    p = np.ascontiguousarray(probes, dtype=np.int32)
+    err = np.empty(max(p.size, 1), np.float64)
+    n = ctypes.c_int()
+    _check(h, lib().loc_map_difficulty(h, _ptr(p), int(p.size), int(probe_bin), int(beam_step), float(sigma_r),
+                                       float(c_m), _ptr(err), ctypes.byref(n)))
+    return err[:p.size], n.value
 
 
 def loc_range_table(h: Handle, n_angles: int, r_max: float) -> None:

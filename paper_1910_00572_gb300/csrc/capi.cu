@@ -754,6 +754,105 @@ LOC_API loc_status loc_lidar_update_dense(loc_handle h, const float* ranges, int
     return LOC_OK;
 }
 
+LOC_API loc_status loc_map_difficulty(loc_handle h, const int32_t* probes, int n_probes, int probe_bin,
+                                      int beam_step, double sigma_r, double c_m, double* errors, int* n_wrong) {
+    loc_status st = check_live(h);
+    if (st != LOC_OK) return st;
+    if (!h->table) return fail(h, LOC_ERR_INVALID_ARG, "no range table: call loc_range_table first");
+    if (!probes || n_probes <= 0 || !n_wrong) return fail(h, LOC_ERR_INVALID_ARG, "null argument or n_probes <= 0");
+    const int A = h->table_A, K = h->p.K, s = A / K;
+    if (probe_bin < 0 || probe_bin >= K || beam_step < 1 || !(sigma_r > 0.0) || !std::isfinite(sigma_r) ||
+        !(c_m >= 0.0) || !std::isfinite(c_m))
+        return fail(h, LOC_ERR_INVALID_ARG, "probe_bin in [0, K), beam_step >= 1, sigma_r > 0, c_m >= 0");
+    if ((A + beam_step - 1) / beam_step > LOC_MAX_DENSE_BEAMS)
+        return fail(h, LOC_ERR_INVALID_ARG, "more than LOC_MAX_DENSE_BEAMS probe beams");
+    for (int p = 0; p < n_probes; ++p)
+        if (probes[p] < 0 || (size_t)probes[p] >= h->hw) return fail(h, LOC_ERR_INVALID_ARG, "probe out of grid");
+    // the probes' table columns and map flags
+    int32_t* dp = (int32_t*)dev_alloc(h, sizeof(int32_t) * n_probes);
+    uint8_t* dcol = (uint8_t*)dev_alloc(h, (size_t)n_probes * A);
+    uint8_t* dflag = (uint8_t*)dev_alloc(h, (size_t)n_probes);
+    long long* didx = (long long*)dev_alloc(h, sizeof(long long) * n_probes);
+    void* scratch = dev_alloc(h, argmax_f32_scratch_bytes());
+    auto release = [&]() { for (void* q : {(void*)dp, (void*)dcol, (void*)dflag, (void*)didx, scratch}) dev_release(h, q); };
+    if (!dp || !dcol || !dflag || !didx || !scratch) {
+        release();
+        return fail(h, LOC_ERR_OOM, "map difficulty buffers");
+    }
+    std::vector<uint8_t> col((size_t)n_probes * A), flag(n_probes);
+    cudaError_t e = cudaMemcpyAsync(dp, probes, sizeof(int32_t) * n_probes, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(scratch, 0, argmax_f32_scratch_bytes(), h->stream);
+    if (e == cudaSuccess) e = launch_gather_columns(h->table, h->trav, h->p.H, h->p.W, A, dp, n_probes, dcol, dflag, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(col.data(), dcol, col.size(), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(flag.data(), dflag, flag.size(), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) {
+        release();
+        return cuda_fail(h, e, "loc_map_difficulty gather");
+    }
+    for (int p = 0; p < n_probes; ++p)
+        if (!flag[p]) {
+            release();
+            return fail(h, LOC_ERR_INVALID_ARG, "probe on an occupied cell");
+        }
+    // each probe's noise-free scan: beams on table directions probe_bin s + b beam_step, the
+    // code as the range in code steps; code 255 (capped) skipped
+    std::vector<int> mall;
+    std::vector<float> zall;
+    std::vector<int> off(n_probes + 1, 0);
+    for (int p = 0; p < n_probes; ++p) {
+        for (int o = 0; o < A; o += beam_step) {
+            const uint8_t code = col[(size_t)p * A + (probe_bin * s + o) % A];
+            if (code == 255) continue;
+            mall.push_back(o);
+            zall.push_back((float)code);
+        }
+        off[p + 1] = (int)mall.size();
+    }
+    int* dm = (int*)dev_alloc(h, sizeof(int) * std::max<size_t>(mall.size(), 1));
+    float* dz = (float*)dev_alloc(h, sizeof(float) * std::max<size_t>(zall.size(), 1));
+    if (!h->dense_logL) {
+        h->dense_logL = (float*)dev_alloc(h, sizeof(float) * h->n);
+        h->dense_max = (unsigned int*)dev_alloc(h, 16);
+    }
+    if (!dm || !dz || !h->dense_logL || !h->dense_max) {
+        release();
+        if (dm) dev_release(h, dm);
+        if (dz) dev_release(h, dz);
+        return fail(h, LOC_ERR_OOM, "map difficulty buffers");
+    }
+    if (!mall.empty()) {
+        e = cudaMemcpyAsync(dm, mall.data(), sizeof(int) * mall.size(), cudaMemcpyHostToDevice, h->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dz, zall.data(), sizeof(float) * zall.size(), cudaMemcpyHostToDevice, h->stream);
+    }
+    const double step = (double)(float)(h->table_rmax / 255.0);
+    const float scale = (float)(step * step / (2.0 * sigma_r * sigma_r));
+    for (int p = 0; p < n_probes && e == cudaSuccess; ++p) {
+        const int nu = off[p + 1] - off[p];           // 0: every free state scores 0
+        e = launch_dense_score(h->table, h->trav, h->B[h->cur], h->p.storage, h->p.H, h->p.W, K, A, dm + off[p],
+                               dz + off[p], nu, scale, h->dense_logL, h->dense_max, h->stream);
+        if (e == cudaSuccess) e = launch_argmax_f32(h->dense_logL, h->n, scratch, didx + p, h->stream);
+    }
+    std::vector<long long> idx(n_probes);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(idx.data(), didx, sizeof(long long) * n_probes, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    release();
+    dev_release(h, dm);
+    dev_release(h, dz);
+    if (e != cudaSuccess) return cuda_fail(h, e, "loc_map_difficulty");
+    int wrong = 0;
+    const long long hw = (long long)h->hw, W = h->p.W;
+    for (int p = 0; p < n_probes; ++p) {
+        const long long rem = idx[p] % hw;
+        const double dj = (double)(rem / W - probes[p] / W), di = (double)(rem % W - probes[p] % W);
+        const double ep = h->p.cell_m * std::hypot(dj, di);
+        if (errors) errors[p] = ep;
+        wrong += ep > c_m;
+    }
+    *n_wrong = wrong;
+    return sync_and_check(h);
+}
+
 LOC_API loc_status loc_belief(loc_handle h, float* out, size_t n) {
     loc_status st = check_live(h);
     if (st != LOC_OK) return st;

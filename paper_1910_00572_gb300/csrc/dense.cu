@@ -26,6 +26,7 @@
 //    Kahan partial sums per thread, FP64 per CTA, the last CTA combining them in a fixed
 //    order.
 #include <cfloat>
+#include <climits>
 
 #include "dda.cuh"
 #include "kernels.h"
@@ -182,7 +183,116 @@ __global__ void __launch_bounds__(NT) dense_apply_kernel(T* __restrict__ B, cons
     });
 }
 
+// Probe columns for the map difficulty: out[p A + a] = table[a][probes[p]], flag[p] = M there.
+__global__ void __launch_bounds__(NT) gather_columns_kernel(const uint8_t* __restrict__ table,
+                                                            const uint8_t* __restrict__ trav, size_t hw, int A,
+                                                            const int32_t* __restrict__ probes, int n,
+                                                            uint8_t* __restrict__ out, uint8_t* __restrict__ flag) {
+    const size_t total = (size_t)n * A;
+    for (size_t q = (size_t)blockIdx.x * NT + threadIdx.x; q < total; q += (size_t)gridDim.x * NT) {
+        const int p = (int)(q / A), a = (int)(q % A);
+        out[q] = table[(size_t)a * hw + probes[p]];
+        if (a == 0) flag[p] = trav[probes[p]];
+    }
+}
+
+__device__ __forceinline__ bool better_f(float v, long long i, float bv, long long bi) {
+    return v > bv || (v == bv && i < bi);
+}
+
+// argmax of a float array (the first index among equal values): per-thread scans in
+// increasing index order, warps and CTAs combined with better_f, the last CTA combining the
+// CTA results in a fixed order and writing the index to *out.
+__global__ void __launch_bounds__(NT) argmax_f32_kernel(const float* __restrict__ x, size_t n, float* pv,
+                                                        long long* pi, unsigned int* counter, long long* out) {
+    __shared__ float sv[NT / 32];
+    __shared__ long long si[NT / 32];
+    __shared__ int s_last;
+    float bv = -INFINITY;
+    long long bi = LLONG_MAX;
+    for (size_t q = (size_t)blockIdx.x * NT + threadIdx.x; q < n; q += (size_t)gridDim.x * NT) {
+        const float v = x[q];
+        if (better_f(v, (long long)q, bv, bi)) {
+            bv = v;
+            bi = (long long)q;
+        }
+    }
+    auto reduce = [&]() {
+        for (int o = 16; o > 0; o >>= 1) {
+            const float ov = __shfl_down_sync(0xffffffffu, bv, o);
+            const long long oi = __shfl_down_sync(0xffffffffu, bi, o);
+            if (better_f(ov, oi, bv, bi)) {
+                bv = ov;
+                bi = oi;
+            }
+        }
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        __syncthreads();
+        if (lane == 0) {
+            sv[warp] = bv;
+            si[warp] = bi;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0)
+            for (int w = 1; w < NT / 32; ++w)
+                if (better_f(sv[w], si[w], bv, bi)) {
+                    bv = sv[w];
+                    bi = si[w];
+                }
+    };
+    reduce();
+    if (threadIdx.x == 0) {
+        pv[blockIdx.x] = bv;
+        pi[blockIdx.x] = bi;
+        __threadfence();
+        s_last = atomicAdd(counter, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    bv = -INFINITY;
+    bi = LLONG_MAX;
+    for (unsigned int b = threadIdx.x; b < gridDim.x; b += NT) {
+        const float v = ((volatile float*)pv)[b];
+        const long long q = ((volatile long long*)pi)[b];
+        if (better_f(v, q, bv, bi)) {
+            bv = v;
+            bi = q;
+        }
+    }
+    reduce();
+    if (threadIdx.x == 0) {
+        *out = bi;
+        *counter = 0u;
+    }
+}
+
 }  // namespace
+
+constexpr unsigned int kArgmaxF32Blocks = 512;
+
+size_t argmax_f32_scratch_bytes() { return (size_t)kArgmaxF32Blocks * (sizeof(float) + sizeof(long long)) + 16; }
+
+cudaError_t launch_gather_columns(const uint8_t* table, const uint8_t* trav, int H, int W, int A,
+                                  const int32_t* probes, int n, uint8_t* out, uint8_t* flag, cudaStream_t st) {
+    const size_t total = (size_t)n * A;
+    size_t nb = (total + NT - 1) / NT;
+    if (nb > 4096) nb = 4096;
+    if (nb < 1) nb = 1;
+    gather_columns_kernel<<<(unsigned int)nb, NT, 0, st>>>(table, trav, (size_t)H * W, A, probes, n, out, flag);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_argmax_f32(const float* x, size_t n, void* scratch, long long* out, cudaStream_t st) {
+    long long* pi = (long long*)scratch;
+    float* pv = (float*)(pi + kArgmaxF32Blocks);
+    unsigned int* counter = reinterpret_cast<unsigned int*>(pv + kArgmaxF32Blocks);
+    size_t nb = (n + NT - 1) / NT;
+    if (nb > kArgmaxF32Blocks) nb = kArgmaxF32Blocks;
+    if (nb < 1) nb = 1;
+    argmax_f32_kernel<<<(unsigned int)nb, NT, 0, st>>>(x, n, pv, pi, counter, out);
+    return cudaGetLastError();
+}
 
 size_t dense_score_smem(int A, int K, int nu) { return dense_table_bytes(A, K) + (size_t)nu * 12; }
 

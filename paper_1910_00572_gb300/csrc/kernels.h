@@ -30,6 +30,13 @@ cudaError_t launch_dense_apply(void* B, int storage, const float* logL, size_t n
                                float log_mult, uint32_t seed, double* partials, unsigned int nparts,
                                SessionDev* sd, cudaStream_t st);
 
+// Map difficulty (dense.cu): the probes' table columns and map flags; an argmax of a float
+// array (the first index on ties) with its scratch (the arrival counter must start at 0).
+cudaError_t launch_gather_columns(const uint8_t* table, const uint8_t* trav, int H, int W, int A,
+                                  const int32_t* probes, int n, uint8_t* out, uint8_t* flag, cudaStream_t st);
+size_t argmax_f32_scratch_bytes();
+cudaError_t launch_argmax_f32(const float* x, size_t n, void* scratch, long long* out, cudaStream_t st);
+
 // Anisotropic propagation (step_aniso.cu).  `tmap` is the tensor map of B_in built by
 // make_aniso_tmap, or null (plain loads).
 cudaError_t launch_step_aniso(const StepArgs& a, const void* tmap, int storage, cudaStream_t st);

@@ -203,3 +203,66 @@ def test_arguments_are_checked():
         assert loc.loc_stats(h)["n_propagations"] == 0
     finally:
         loc.loc_destroy(h)
+
+
+def map_cases():
+    H, W = 7, 80                                        # a featureless corridor
+    corridor = np.zeros((H, W), np.uint8)
+    corridor[0, :] = corridor[-1, :] = 1
+    rooms = np.zeros((12, 40), np.uint8)                 # two identical closed rooms
+    rooms[0, :] = rooms[-1, :] = 1
+    rooms[:, 0] = rooms[:, 19] = rooms[:, 20] = rooms[:, 39] = 1
+    rooms[3, 5] = rooms[3, 25] = 1
+    rooms[8, 12:15] = rooms[8, 32:35] = 1
+    plan = floorplan.rooms_map(21, size=48)[:45, :47].copy()
+    return [("corridor", corridor, 4, 16, 1.0, [3 * 80 + i for i in (5, 20, 40, 60, 78)]),
+            ("two rooms", rooms, 8, 32, 3.0, [6 * 40 + 8, 6 * 40 + 28, 2 * 40 + 2, 9 * 40 + 37]),
+            ("rooms plan", plan, 8, 64, 2.0, None)]
+
+
+@pytest.mark.parametrize("case", range(3), ids=["corridor", "two rooms", "rooms plan"])
+@pytest.mark.parametrize("probe_bin,beam_step", [(0, 1), (3, 2)])
+def test_map_difficulty_matches_oracle(case, probe_bin, beam_step):
+    name, occ, K, A, r_max, probes = map_cases()[case]
+    cell = 0.1
+    if probes is None:
+        free = np.flatnonzero(occ.reshape(-1) == 0)
+        probes = np.random.default_rng(4).choice(free, 40, replace=False)
+    probes = np.asarray(probes, np.int32)
+    h = make(occ, K, cell)
+    try:
+        loc.loc_range_table(h, A, r_max)
+        got_e, got_n = loc.loc_map_difficulty(h, probes, probe_bin, beam_step, 0.1, 1.0)
+        b_after = loc.loc_belief(h)
+        assert np.array_equal(b_after, loc.loc_belief(h))
+    finally:
+        loc.loc_destroy(h)
+    table = D.range_table(occ, A, r_max, cell)
+    want_e, want_n = D.map_difficulty(occ, table, K, cell, r_max, probes, probe_bin, beam_step, 0.1, 1.0)
+    assert np.abs(got_e - want_e).max() <= 1e-9, (name, got_e, want_e)
+    assert got_n == want_n
+
+
+def test_map_difficulty_arguments():
+    occ = floorplan.rooms_map(22, size=32)
+    h = make(occ, 8, 0.1)
+    try:
+        free = int(np.flatnonzero(occ.reshape(-1) == 0)[0])
+        wall = int(np.flatnonzero(occ.reshape(-1) != 0)[0])
+        with pytest.raises(loc.LocError):
+            loc.loc_map_difficulty(h, [free], 0, 1, 0.1, 1.0)            # no table
+        loc.loc_range_table(h, 32, 2.0)
+        with pytest.raises(loc.LocError) as e:
+            loc.loc_map_difficulty(h, [free, wall], 0, 1, 0.1, 1.0)      # an occupied probe
+        assert "occupied" in loc.loc_last_error(h)
+        for bad in (dict(probe_bin=8), dict(beam_step=0), dict(sigma_r=0.0), dict(c_m=-1.0)):
+            kw = dict(probe_bin=0, beam_step=1, sigma_r=0.1, c_m=1.0)
+            kw.update(bad)
+            with pytest.raises(loc.LocError):
+                loc.loc_map_difficulty(h, [free], **kw)
+        with pytest.raises(loc.LocError):
+            loc.loc_map_difficulty(h, [32 * 32], 0, 1, 0.1, 1.0)       # out of the grid
+        e, n = loc.loc_map_difficulty(h, [free], 0, 1, 0.1, 1.0)
+        assert e.shape == (1,) and n in (0, 1)
+    finally:
+        loc.loc_destroy(h)
