@@ -714,6 +714,13 @@ def run_dense(args, wl, occ, walk, ws, rank, local):
             loc.loc_argmax(h)
             e2e_t += time.perf_counter() - t
         e2e_t = max_over_ranks(e2e_t, ws)
+        # map difficulty (Eq. 11) on 64 seeded free probe cells, heading bin 0, every 4th direction
+        free = np.flatnonzero(occ.reshape(-1) == 0)
+        probes = np.random.default_rng(wl["seed"] + 5).choice(free, 64, replace=False)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        dm_err, dm_wrong = loc.loc_map_difficulty(h, probes, 0, 4, wl["sigma_r"], 1.0)
+        dm_s = time.perf_counter() - t0
     finally:
         loc.loc_destroy(h)
     if rank != 0:
@@ -748,6 +755,10 @@ def run_dense(args, wl, occ, walk, ws, rank, local):
                 "path": "loc_lidar_update_dense (ranges from host memory) + loc_argmax, host wall clock"},
         "gpu_launches": 2 * args.steps,
         "clocks": clk.summary(),
+        "map_difficulty": {"probes": int(probes.size), "n_wrong": int(dm_wrong),
+                           "D_M": dm_wrong / probes.size, "median_error_m": float(np.median(dm_err)),
+                           "ms_per_probe": dm_s * 1e3 / probes.size,
+                           "note": "Eq. 11 with C = 1 m on seeded free probe cells (noise-free table scans)"},
     }
     print(json.dumps(line), flush=True)
 
