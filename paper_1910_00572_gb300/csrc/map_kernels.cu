@@ -222,7 +222,7 @@ __global__ void __launch_bounds__(NT) estimate_kernel(const T* __restrict__ B, c
     __shared__ double red[NT / 32];
     __shared__ float sv[NT / 32];
     __shared__ long long si[NT / 32];
-    const size_t hw = (size_t)H * W, n = hw * K;
+    const size_t hw = (size_t)H * W;
     const long long a = *arg_idx;
     const int ka = (int)(a / (long long)hw), ja = (int)((a % (long long)hw) / W), ia = (int)(a % W);
     const int reinit = sd->reinit;
@@ -230,18 +230,25 @@ __global__ void __launch_bounds__(NT) estimate_kernel(const T* __restrict__ B, c
     KahanF mass;
     float bv = -FLT_MAX;
     long long bi = LLONG_MAX;
-    for (size_t q = (size_t)blockIdx.x * NT + threadIdx.x; q < n; q += (size_t)gridDim.x * NT) {
-        const int k = (int)(q / hw);
-        const size_t cell = q - (size_t)k * hw;
-        const int j = (int)(cell / W), i = (int)(cell - (size_t)j * W);
-        const float v = belief_at(B, trav, hw, q, reinit, inv_uniform, scale);
+    // one thread per cell (consecutive across a warp), its K bins in turn
+    for (size_t cell = (size_t)blockIdx.x * NT + threadIdx.x; cell < hw; cell += (size_t)gridDim.x * NT) {
+        const int j = (int)(cell / (unsigned int)W), i = (int)(cell - (size_t)j * W);
         const long long dj = j - ja, di = i - ia;
-        if (dj * dj + di * di <= r2) {
-            int d = k > ka ? k - ka : ka - k;
-            if (K - d < d) d = K - d;
-            if (d <= dk) mass.add(v);
-        } else if (better(v, (long long)cell, bv, bi)) {
-            bv = v;
+        const bool inside = dj * dj + di * di <= r2;
+        float m = 0.0f;                                   // the cell's belief-map value
+#pragma unroll 8
+        for (int k = 0; k < K; ++k) {
+            const float v = belief_at(B, trav, hw, (size_t)k * hw + cell, reinit, inv_uniform, scale);
+            if (inside) {
+                int d = k > ka ? k - ka : ka - k;
+                if (K - d < d) d = K - d;
+                if (d <= dk) mass.add(v);
+            } else {
+                m = fmaxf(m, v);
+            }
+        }
+        if (!inside && better(m, (long long)cell, bv, bi)) {
+            bv = m;
             bi = (long long)cell;
         }
     }
@@ -472,11 +479,11 @@ cudaError_t launch_estimate(const void* B, int storage, const uint8_t* trav, con
                             float inv_uniform, int H, int W, int K, void* scratch, const long long* arg_idx,
                             long long r2, int dk, double* partials, unsigned int nparts, EstimateOut* out,
                             cudaStream_t st) {
-    const size_t n = (size_t)H * W * K;
+    const size_t hw = (size_t)H * W;
     long long* pi = (long long*)scratch;
     float* pv = (float*)(pi + kArgmaxBlocks);
     unsigned int* counter = reinterpret_cast<unsigned int*>(pv + kArgmaxBlocks);
-    unsigned int nb = grid_for(n);
+    unsigned int nb = grid_for(hw);
     if (nb > kArgmaxBlocks) nb = kArgmaxBlocks;
     if (nb > nparts) nb = nparts;
     LOC_DISPATCH(storage, (estimate_kernel<T><<<nb, NT, 0, st>>>((const T*)B, trav, sd, inv_uniform, H, W, K, arg_idx,
