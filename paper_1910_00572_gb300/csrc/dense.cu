@@ -27,6 +27,7 @@
 //    order.
 #include <cfloat>
 #include <climits>
+#include <type_traits>
 
 #include "dda.cuh"
 #include "kernels.h"
@@ -118,21 +119,26 @@ __global__ void __launch_bounds__(DC) dense_score_kernel(const uint8_t* __restri
         float acc[KC];
 #pragma unroll
         for (int kk = 0; kk < KC; ++kk) acc[kk] = 0.0f;
-        for (int u = 0; u < nu; ++u) {
-            int k1 = sm_q[u] + k0;
-            if (k1 >= K) k1 -= K;
-            const uint8_t* col = Us + sm_r[u] + k1 * DC + t;
-            const float zu = sm_z[u];
+        // bins k0 .. k0+KC-1 of every used beam; a chunk past K is guarded (rows stay below r RB + RB)
+        auto beams = [&](auto full) {
+            for (int u = 0; u < nu; ++u) {
+                int k1 = sm_q[u] + k0;
+                if (k1 >= K) k1 -= K;
+                const uint8_t* col = Us + sm_r[u] + k1 * DC + t;
+                const float zu = sm_z[u];
 #pragma unroll
-            for (int kk = 0; kk < KC; ++kk) {
-                if (k0 + kk < K) {                                 // rows stay below r RB + RB
-                    const uint32_t q = col[kk * DC];
-                    const float qf = __uint_as_float(0x4B000000u | q) - 8388608.0f;
-                    const float d = zu - qf;
-                    acc[kk] = fmaf(d, d, acc[kk]);
+                for (int kk = 0; kk < KC; ++kk) {
+                    if (decltype(full)::value || k0 + kk < K) {
+                        const uint32_t q = col[kk * DC];
+                        const float qf = __uint_as_float(0x4B000000u | q) - 8388608.0f;
+                        const float d = zu - qf;
+                        acc[kk] = fmaf(d, d, acc[kk]);
+                    }
                 }
             }
-        }
+        };
+        if (k0 + KC <= K) beams(std::true_type{});
+        else beams(std::false_type{});
 #pragma unroll
         for (int kk = 0; kk < KC; ++kk) {
             if (k0 + kk < K && in) {
