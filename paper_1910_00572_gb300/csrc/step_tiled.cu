@@ -129,15 +129,15 @@ struct WsCfg {
 template <typename T, typename C>
 struct SmemWS {
     T raw[C::NSTAGE][raw_stride<T, C>()];
-    float S[C::XR][SW];
+    float S[2][C::XR][SW];                   // S of planes p and p + 1 (the X-pass of p overlaps)
     float X[2][C::XR][XW_PITCH];
     float wrap[NWRAP][C::TH][TW];
     float mk[C::XR][MW];
     unsigned long long tma[C::NSTAGE];
     unsigned long long full[2], empty[2];
-    // failure flags.  Producers write fail_a only before their first named barrier of a plane
-    // and read it right after it, fail_b likewise for the second barrier, so every producer
-    // takes the same decision; consumers (no named barriers) use fail_c.
+    // failure flags (a bounded wait gave up): producers set fail_a (TMA) and fail_b (EMPTY),
+    // consumers fail_c.  A set flag only skips work and further waits; no thread leaves its
+    // loop early, so every producer reaches every named barrier.
     int fail_a, fail_b, fail_c;
     double red[C::NT / 32];
 };
@@ -173,7 +173,7 @@ __global__ void __launch_bounds__(C::NT, C::MINB) step_ws_kernel(const __grid_co
     __syncthreads();
 
     KahanF acc;
-    int p_done = 0, next_issue = 0;         // producer: planes [p_done, next_issue) in flight
+    int waited = 0, next_issue = 0;         // producer: planes [waited, next_issue) maybe in flight
     if (tid < NP) {
         // ------------------------------------------------------------------ producers
         const int t = tid;
@@ -190,8 +190,8 @@ __global__ void __launch_bounds__(C::NT, C::MINB) step_ws_kernel(const __grid_co
                 for (int q = 0; q < next_issue; ++q) issue(q);
         }
         for (int p = 0; p < K; ++p) {
-            p_done = p;
             const int stage = p % NSTAGE;
+            float (*S)[SW] = sm.S[p & 1];
             const Shift s = a.sh[p];
             int x_al, xo;
             box_x<T>(tx0, s, x_al, xo);
@@ -205,21 +205,23 @@ __global__ void __launch_bounds__(C::NT, C::MINB) step_ws_kernel(const __grid_co
                     sm.raw[stage][y * BW + c] = T(v);
                 }
                 producers_sync<NP>();
-            } else if (!bar_wait(&sm.tma[stage], (uint32_t)((p / NSTAGE) & 1))) {
-                sm.fail_a = 1;
+            } else if (!sm.fail_a) {
+                if (bar_wait(&sm.tma[stage], (uint32_t)((p / NSTAGE) & 1))) waited = p + 1;
+                else sm.fail_a = 1;
             }
             if (!sm.fail_a) {
                 const int xb = xo & ~3;
                 switch (xo & 3) {
-                    case 0: s_pass<T, C, 0>(sm.raw[stage], sm.mk, sm.S, t, xb, s.fx, s.fy); break;
-                    case 1: s_pass<T, C, 1>(sm.raw[stage], sm.mk, sm.S, t, xb, s.fx, s.fy); break;
-                    case 2: s_pass<T, C, 2>(sm.raw[stage], sm.mk, sm.S, t, xb, s.fx, s.fy); break;
-                    default: s_pass<T, C, 3>(sm.raw[stage], sm.mk, sm.S, t, xb, s.fx, s.fy); break;
+                    case 0: s_pass<T, C, 0>(sm.raw[stage], sm.mk, S, t, xb, s.fx, s.fy); break;
+                    case 1: s_pass<T, C, 1>(sm.raw[stage], sm.mk, S, t, xb, s.fx, s.fy); break;
+                    case 2: s_pass<T, C, 2>(sm.raw[stage], sm.mk, S, t, xb, s.fx, s.fy); break;
+                    default: s_pass<T, C, 3>(sm.raw[stage], sm.mk, S, t, xb, s.fx, s.fy); break;
                 }
             }
-            producers_sync<NP>();                        // S complete; raw stage free
-            if (sm.fail_a) break;                    // the same decision in every producer
-            if (!reinit && p + NSTAGE < K) {
+            // S of plane p complete and the raw stage free; every producer has also finished the
+            // X-pass of plane p - 1, so S of plane p + 1 (the other buffer's next use) may be written
+            producers_sync<NP>();
+            if (!reinit && p + NSTAGE < K && !sm.fail_a) {
                 if (t == 0) {
                     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                     issue(p + NSTAGE);
@@ -227,13 +229,9 @@ __global__ void __launch_bounds__(C::NT, C::MINB) step_ws_kernel(const __grid_co
                 next_issue = p + NSTAGE + 1;
             }
             const int b = p & 1;
-            if (p >= 2 && !bar_wait(&sm.empty[b], (uint32_t)(((p - 2) >> 1) & 1))) sm.fail_b = 1;
-            producers_sync<NP>();
-            if (sm.fail_b) break;
-            x_pass<C>(sm.S, sm.X[b], t, a.g0, a.g1, a.g2);
+            if (p >= 2 && !sm.fail_b && !bar_wait(&sm.empty[b], (uint32_t)(((p - 2) >> 1) & 1))) sm.fail_b = 1;
+            if (!(sm.fail_a | sm.fail_b)) x_pass<C>(S, sm.X[b], t, a.g0, a.g1, a.g2);
             bar_arrive(&sm.full[b]);                 // X[b] of plane p is ready
-            producers_sync<NP>();                        // the X-pass has read S: S may be rewritten
-            p_done = p + 1;
         }
     } else {
         // ------------------------------------------------------------------ consumers
@@ -290,7 +288,7 @@ __global__ void __launch_bounds__(C::NT, C::MINB) step_ws_kernel(const __grid_co
     if (sm.fail_a | sm.fail_b | sm.fail_c) {
         if (tid == 0) {
             atomicOr(&a.sd->status, LOC_DEV_ERR_TIMEOUT);
-            for (int q = p_done; q < next_issue; ++q) bar_wait(&sm.tma[q % NSTAGE], (uint32_t)((q / NSTAGE) & 1));
+            for (int q = waited; q < next_issue; ++q) bar_wait(&sm.tma[q % NSTAGE], (uint32_t)((q / NSTAGE) & 1));
         }
         __syncthreads();
         return;
