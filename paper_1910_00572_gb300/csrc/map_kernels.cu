@@ -323,6 +323,148 @@ __global__ void __launch_bounds__(NT) estimate_kernel(const T* __restrict__ B, c
     }
 }
 
+// The same pass over the flat tensor in 16-byte groups of V consecutive states (hw a multiple
+// of V and W >= V, so a group stays in one plane): one division to place a thread's first
+// group, then the plane, cell, row and column advance by the grid stride.
+template <typename T, int V>
+__global__ void __launch_bounds__(NT) estimate_vec_kernel(const T* __restrict__ B, const uint8_t* __restrict__ trav,
+                                                          const SessionDev* sd, float inv_uniform, int H, int W,
+                                                          int K, const long long* arg_idx, long long r2, int dk,
+                                                          double* partials, float* pv, long long* pi,
+                                                          unsigned int* counter, EstimateOut* out) {
+    static_assert(V * sizeof(T) == 16, "one 16-byte load");
+    __shared__ double red[NT / 32];
+    __shared__ float sv[NT / 32];
+    __shared__ long long si[NT / 32];
+    const size_t hw = (size_t)H * W, ng = hw * K / V;
+    const long long a = *arg_idx;
+    const int ka = (int)(a / (long long)hw), ja = (int)((a % (long long)hw) / W), ia = (int)(a % W);
+    const int reinit = sd->reinit;
+    const float scale = sd->inv_Z;
+    KahanF mass;
+    float bv = -FLT_MAX;
+    long long bi = LLONG_MAX;
+    const size_t g0 = (size_t)blockIdx.x * NT + threadIdx.x, gs = (size_t)gridDim.x * NT;
+    if (g0 < ng) {
+        size_t q = g0 * V;
+        int k = (int)(q / hw);
+        size_t cell = q - (size_t)k * hw;
+        int j = (int)(cell / (unsigned int)W), i = (int)(cell - (size_t)j * W);
+        const size_t step = gs * V;                       // the grid stride in states
+        const int dkk = (int)(step / hw);
+        const size_t dcell = step - (size_t)dkk * hw;
+        const int dj = (int)(dcell / (unsigned int)W), di = (int)(dcell - (size_t)dj * W);
+        for (size_t g = g0; g < ng; g += gs) {
+            union {
+                uint4 u;
+                T x[V];
+            } raw;
+            if (!reinit) raw.u = __ldg(reinterpret_cast<const uint4*>(B) + g);
+            int je = j, ie = i;
+#pragma unroll
+            for (int e = 0; e < V; ++e) {
+                if (e > 0 && ++ie == W) {
+                    ie = 0;
+                    ++je;
+                }
+                const size_t ce = cell + e;
+                const float v = reinit ? (float)trav[ce] * inv_uniform : Store<T>::ld(&raw.x[e]) * scale;
+                const long long ddj = je - ja, ddi = ie - ia;
+                if (ddj * ddj + ddi * ddi <= r2) {
+                    int d = k > ka ? k - ka : ka - k;
+                    if (K - d < d) d = K - d;
+                    if (d <= dk) mass.add(v);
+                } else if (better(v, (long long)ce, bv, bi)) {
+                    bv = v;
+                    bi = (long long)ce;
+                }
+            }
+            k += dkk;
+            cell += dcell;
+            j += dj;
+            i += di;
+            if (i >= W) {
+                i -= W;
+                ++j;
+            }
+            if (cell >= hw) {
+                cell -= hw;
+                j -= H;
+                ++k;
+            }
+        }
+    }
+    const double bm = block_sum<NT>(mass.value(), red);
+    for (int o = 16; o > 0; o >>= 1) {
+        const float ov = __shfl_down_sync(0xffffffffu, bv, o);
+        const long long oi = __shfl_down_sync(0xffffffffu, bi, o);
+        if (better(ov, oi, bv, bi)) {
+            bv = ov;
+            bi = oi;
+        }
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) {
+        sv[warp] = bv;
+        si[warp] = bi;
+    }
+    __syncthreads();
+    __shared__ int s_last;
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < NT / 32; ++w)
+            if (better(sv[w], si[w], bv, bi)) {
+                bv = sv[w];
+                bi = si[w];
+            }
+        partials[blockIdx.x] = bm;
+        pv[blockIdx.x] = bv;
+        pi[blockIdx.x] = bi;
+        __threadfence();
+        s_last = atomicAdd(counter, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    double ms = 0.0;
+    bv = -FLT_MAX;
+    bi = LLONG_MAX;
+    for (unsigned int b = threadIdx.x; b < gridDim.x; b += NT) {
+        ms += ((volatile double*)partials)[b];
+        const float v = ((volatile float*)pv)[b];
+        const long long q = ((volatile long long*)pi)[b];
+        if (better(v, q, bv, bi)) {
+            bv = v;
+            bi = q;
+        }
+    }
+    const double mt = block_sum<NT>(ms, red);
+    for (int o = 16; o > 0; o >>= 1) {
+        const float ov = __shfl_down_sync(0xffffffffu, bv, o);
+        const long long oi = __shfl_down_sync(0xffffffffu, bi, o);
+        if (better(ov, oi, bv, bi)) {
+            bv = ov;
+            bi = oi;
+        }
+    }
+    __syncthreads();
+    if (lane == 0) {
+        sv[warp] = bv;
+        si[warp] = bi;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < NT / 32; ++w)
+            if (better(sv[w], si[w], bv, bi)) {
+                bv = sv[w];
+                bi = si[w];
+            }
+        out->mass_near = mt;
+        out->second_p = bv > 0.0f ? bv : 0.0f;
+        out->second_cell = bv > 0.0f ? bi : -1;
+        *counter = 0u;
+    }
+}
+
 __global__ void argmax_final_kernel(const float* __restrict__ pv, const long long* __restrict__ pi,
                                     int nb, const SessionDev* sd, long long* out_idx,
                                     float* out_val) {
@@ -483,6 +625,16 @@ cudaError_t launch_estimate(const void* B, int storage, const uint8_t* trav, con
     long long* pi = (long long*)scratch;
     float* pv = (float*)(pi + kArgmaxBlocks);
     unsigned int* counter = reinterpret_cast<unsigned int*>(pv + kArgmaxBlocks);
+    const size_t vec = storage == LOC_F32 ? 4 : 8;
+    if (hw % vec == 0 && (size_t)W >= vec) {
+        unsigned int nb = grid_for(hw * K / vec);
+        if (nb > kArgmaxBlocks) nb = kArgmaxBlocks;
+        if (nb > nparts) nb = nparts;
+        LOC_DISPATCH(storage, (estimate_vec_kernel<T, 16 / sizeof(T)><<<nb, NT, 0, st>>>(
+                                  (const T*)B, trav, sd, inv_uniform, H, W, K, arg_idx, r2, dk, partials, pv, pi,
+                                  counter, out)));
+        return cudaGetLastError();
+    }
     unsigned int nb = grid_for(hw);
     if (nb > kArgmaxBlocks) nb = kArgmaxBlocks;
     if (nb > nparts) nb = nparts;

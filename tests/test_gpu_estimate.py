@@ -1,7 +1,9 @@
 """GPU parity of loc_estimate (the pose estimate, the belief near it and the second hypothesis)
 against ``oracle.readout.estimate``.
 
-The argmax state and the second hypothesis's cell are exact (the belief values are distinct);
+Both passes are covered: one thread per cell (a grid whose H W is not a multiple of the 16-byte
+group) and the flat 16-byte pass.  The argmax state and the second hypothesis's cell are exact
+(the belief values are distinct);
 the near mass agrees to 1e-6 relative; the second value to FP32 rounding of the stored belief.
 """
 import math
@@ -33,13 +35,14 @@ def compare(got, want):
         assert abs(got[key] - want[key]) <= 1e-9, key
 
 
+@pytest.mark.parametrize("H,W", [(50, 61), (48, 64)], ids=["per-cell pass", "16-byte pass"])
 @pytest.mark.parametrize("storage", ["f32", "bf16"])
 @pytest.mark.parametrize("radius,dk", [(0.0, 0), (0.3, 1), (1.0, 3), (50.0, 64)])
-def test_estimate_matches_oracle(storage, radius, dk):
-    occ = floorplan.rooms_map(3, size=64)[:50, :61].copy()
+def test_estimate_matches_oracle(H, W, storage, radius, dk):
+    occ = floorplan.rooms_map(3, size=64)[:H, :W].copy()
     K, cell = 16, 0.1
     b = fields.belief_like(occ, K, seed=7, dtype=np.float32)
-    p = loc.loc_params_default(H=50, W=61, K=K, cell_m=cell, storage=storage)
+    p = loc.loc_params_default(H=H, W=W, K=K, cell_m=cell, storage=storage)
     h = loc.loc_create(occ, p)
     try:
         loc.loc_set_belief(h, b)
