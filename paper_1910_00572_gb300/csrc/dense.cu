@@ -317,12 +317,14 @@ cudaError_t score_t(const uint8_t* table, const uint8_t* trav, const void* B, in
                     cudaStream_t st) {
     const size_t hw = (size_t)H * W;
     const size_t smem = dense_score_smem(A, K, nu);
-    static size_t attr = 0;                        // the largest size set so far
-    if (smem > 48 * 1024 && smem > attr) {
+    static size_t attr[64] = {};                   // per device: the largest size set so far
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (smem > 48 * 1024 && (dev < 0 || dev >= 64 || smem > attr[dev])) {
         const cudaError_t e = cudaFuncSetAttribute(dense_score_kernel<T>,
                                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        attr = smem;
+        if (dev >= 0 && dev < 64) attr[dev] = smem;
     }
     const unsigned int nb = (unsigned int)((hw + DC - 1) / DC);
     dense_score_kernel<T><<<nb, DC, smem, st>>>(table, trav, static_cast<const T*>(B), hw, K, A, A / K, m, zs, nu,

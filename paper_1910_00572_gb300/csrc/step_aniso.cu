@@ -535,12 +535,14 @@ __global__ void __launch_bounds__(NT, 2) step_aniso_kernel(const __grid_constant
 template <typename T, int R>
 cudaError_t launch_r(const StepArgs& a, const void* tmap, cudaStream_t st) {
     const size_t smem = aniso_smem_bytes<T, R>(a.r_th);
-    static bool attr_set = false;                 // the largest size any session can ask for
-    if (!attr_set) {
+    static bool attr_set[64] = {};                // per device: the largest size any session asks for
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64 || !attr_set[dev]) {
         const cudaError_t e = cudaFuncSetAttribute(step_aniso_kernel<T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                    (int)aniso_smem_bytes<T, R>(LOC_MAX_R_THETA));
         if (e != cudaSuccess) return e;
-        attr_set = true;
+        if (dev >= 0 && dev < 64) attr_set[dev] = true;
     }
     CUtensorMap tm;
     memset(&tm, 0, sizeof(tm));
