@@ -112,7 +112,7 @@ void loc_set_allocator(loc_alloc_fn alloc, loc_free_fn release, void* ctx);
 
 /* Create a session on the current CUDA device.  occ: host uint8 [H][W] (copied).
  * The initial belief is uniform over free cells (Section III-A: the initial state is
- * unknown).  Precomputes G(B_0)^-1 of Alg. 1 line 7 / Eq. 8 on the device.
+ * unknown).  Precomputes G(B_0)^-1 of Algorithm 1's edge correction (Eq. 8) on the device.
  * Errors: INVALID_ARG (sizes <= 0, K > LOC_MAX_K, radii above the maxima, cell_m <= 0,
  * no free cell), OOM, CUDA.  On error *out is NULL. */
 loc_status loc_create(const uint8_t* occ, const loc_params* p, loc_handle* out);
@@ -215,7 +215,7 @@ loc_status loc_stats(loc_handle h, double* theta_t, double* last_Z, double* logs
  *   occ_dev    device uint8 [H][W], nonzero = occupied;
  *   b_in_dev   device float [K][H][W], the belief to propagate (used as given);
  *   b_out_dev  device float [K][H][W], receives the propagated, unnormalised tensor
- *              (Alg. 1 lines 3-7 with the edge correction of Eq. 8);
+ *              (Algorithm 1's propagation with the edge correction of Eq. 8);
  *   z_out_dev  device double, receives Z = sum of b_out (the Eq. 9 normaliser);
  *   dx_m, dy_m translation in metres in the frame of bin 0 (bin k moves by R(2 pi k / K)).
  * From p it uses H, W, K, cell_m, the sigmas and radii and stream; storage must be LOC_F32
@@ -284,7 +284,7 @@ loc_status loc_map_difficulty(loc_handle h, const int32_t* probes, int n_probes,
                               int beam_step, double sigma_r, double c_m, double* errors, int* n_wrong);
 
 /* ---- Batched propagation of many sessions (one persistent launch per tick).
- * Alg. 1 lines 3-7 and the Eq. 9 normaliser for every session whose gate opens, over a work
+ * Algorithm 1's propagation and the Eq. 9 normaliser for every session whose gate opens, over a work
  * list of (session, tile) items that the launch's CTAs take from a device queue; the CTA that
  * finishes a session's last tile sums that session's tile partials into Z in the same fixed
  * order as loc_step's tiled kernel with the same tile configuration, so a session's result

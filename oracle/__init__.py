@@ -9,7 +9,7 @@ What is here, each function citing the passage it follows:
 
 * ``odometry``  Section III-A (theta_t = theta_{t-1} + w), Eq. 2 (per-channel motion),
                 Alg. 1 (the |u_{t,k}| >= 1 gate) -- FP64.
-* ``filter``    Eq. 3 (AF shift, bilinear), Alg. 1 lines 3-7 (mask, 3-D Gaussian blur of
+* ``filter``    Eq. 3 (AF shift, bilinear), Algorithm 1's propagation (mask, 3-D Gaussian blur of
                 Eq. 5-7, mask, edge normalisation of Eq. 8), the normaliser eta of Eq. 9 --
                 FP64, direct sums (the 3-D convolution is the plain triple sum with the joint
                 kernel exp(-1/2 d^T Sigma^-1 d), not a separable pass).

@@ -89,7 +89,7 @@ def edge_correction(M: np.ndarray, kernels: list) -> np.ndarray:
 
 
 def propagate(B: np.ndarray, M: np.ndarray, shifts: np.ndarray, kernels: list) -> np.ndarray:
-    """Alg. 1 lines 3-7 with the per-channel kernels (no normalisation)."""
+    """Algorithm 1's propagation with the per-channel kernels (no normalisation)."""
     K = B.shape[0]
     S = np.stack([F.shift_bilinear(B[k], shifts[k, 0], shifts[k, 1]) for k in range(K)])
     S = M[None] * S

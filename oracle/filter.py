@@ -13,9 +13,9 @@ Readings of points the paper leaves open (each also listed in the design notes):
   truncated at radius ceil(3 sigma) per axis unless given, and normalised to sum 1.  With
   sigma_x == sigma_y the rotation R_z of Eq. 6 leaves it unchanged.
 * The 3-D convolution of Eq. 7 is circular in theta and reads zero outside the grid in x/y.
-* G(B_0, k) of Alg. 1 line 7 / Eq. 8 is the same convolution applied to the binary tensor
+* G(B_0, k) of Algorithm 1's edge correction (Eq. 8) is the same convolution applied to the binary tensor
   with ones on free cells; its pixel-wise inverse is taken on free cells only (occupied
-  cells are zero after line 6 anyway).
+  cells are zero after the mask that follows the blur anyway).
 * The normaliser eta of Eq. 9 is applied after every propagation: Z = sum B, B /= Z.  If
   Z == 0 (all mass removed) the belief restarts uniform over free cells.
 """
@@ -87,7 +87,7 @@ def blur3d(S: np.ndarray, g: np.ndarray) -> np.ndarray:
 
 
 def edge_correction(M: np.ndarray, K: int, g: np.ndarray) -> np.ndarray:
-    """Alg. 1 line 7 / Eq. 8: the pixel-wise inverse of G(B_0, k), where B_0 is the binary
+    """Algorithm 1's edge correction (Eq. 8): the pixel-wise inverse of G(B_0, k), where B_0 is the binary
     tensor with ones on free cells; zero on occupied cells.  Shape [K][H][W]."""
     G = blur3d(np.broadcast_to(M, (K,) + M.shape).copy(), g)
     out = np.zeros_like(G)
@@ -104,7 +104,7 @@ def uniform_belief(M: np.ndarray, K: int) -> np.ndarray:
 
 def propagate(B: np.ndarray, M: np.ndarray, corr: np.ndarray, shifts: np.ndarray,
               g: np.ndarray) -> np.ndarray:
-    """Alg. 1 lines 3-7 for every channel k (no normalisation):
+    """Algorithm 1's propagation for every channel k (no normalisation):
     B' = AF(B, u_k); B' = M * B'; B'' = G(B'); B'' = M * B''; B_t = B'' * G(B_0)^-1."""
     K = B.shape[0]
     S = np.stack([shift_bilinear(B[k], shifts[k, 0], shifts[k, 1]) for k in range(K)])
@@ -116,7 +116,7 @@ def propagate(B: np.ndarray, M: np.ndarray, corr: np.ndarray, shifts: np.ndarray
 
 def propagate_at(B: np.ndarray, M: np.ndarray, shifts: np.ndarray, g: np.ndarray,
                  idx) -> np.ndarray:
-    """Alg. 1 lines 3-7 (no normalisation) evaluated at the requested states only, each one
+    """Algorithm 1's propagation (no normalisation) evaluated at the requested states only, each one
     from the definitions: for output (k, j, i) on a free cell,
         T = sum_{dk,dj,di} g[dk][dj][di] * M(j+dj, i+di) * AF(B, s)[(k+dk) mod K](j+dj, i+di)
         G = sum_{dk,dj,di} g[dk][dj][di] * M(j+dj, i+di)           (G(B_0, k), Eq. 8)

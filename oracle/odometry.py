@@ -3,7 +3,7 @@
 Section III-A: a state [i, j, k] means pose (i*dW, j*dH, k*dTheta + theta_t); the internal
 orientation offset advances as theta_t = theta_{t-1} + w for each motion update
 u_t = {u, v, w}.  Eq. 2: the motion of channel k is the odometry translation rotated by that
-channel's orientation.  Alg. 1 (first line): the channels are propagated only when
+channel's orientation.  Alg. 1 (its gate): the channels are propagated only when
 |u_{t,k}| >= 1 (in cells).
 
 Reading used here (the paper leaves the frame of (u, v) implicit): (u, v, w) is the

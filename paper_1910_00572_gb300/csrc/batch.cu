@@ -2,7 +2,7 @@
 //
 // The grid is sized to the GPU (resident CTAs per SM x SMs).  Each CTA repeatedly takes the
 // next (session, tile) item from a device work queue and runs the synchronous tiled pass
-// (Alg. 1 lines 3-7, run_tile) on that session's tile; the CTA that finishes a session's last
+// (Algorithm 1's propagation, run_tile) on that session's tile; the CTA that finishes a session's last
 // tile combines the session's FP64 tile partials into its normaliser Z (Eq. 9) in the same
 // fixed order as a single-session launch, so a session's result does not depend on which
 // other sessions share the launch.

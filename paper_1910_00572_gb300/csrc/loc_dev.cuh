@@ -49,7 +49,7 @@ struct KahanF {
 
 enum { LOC_DEV_ERR_NONFINITE_Z = 1, LOC_DEV_ERR_TIMEOUT = 2 };
 
-// Arguments of one propagation (Alg. 1 lines 3-7 + the Eq. 9 sum) for one session.
+// Arguments of one propagation (Algorithm 1's propagation + the Eq. 9 sum) for one session.
 struct StepArgs {
     const void* B_in;              // stored tensor X_{t-1}, [K][H][W] of the storage type
     void* B_out;                   // X_t

@@ -1,5 +1,5 @@
-// Propagation with anisotropic motion noise (Eq. 5-6 with sigma_x != sigma_y): Algorithm 1
-// lines 3-7 for all channels plus the Eq. 9 normaliser, any kernel radii up to LOC_MAX_R_XY /
+// Propagation with anisotropic motion noise (Eq. 5-6 with sigma_x != sigma_y): Algorithm 1's
+// propagation for all channels plus the Eq. 9 normaliser, any kernel radii up to LOC_MAX_R_XY /
 // LOC_MAX_R_THETA and any storage type.
 //
 // The motion kernel of output channel k is exp(-1/2 [(d . e_k / sigma_x)^2 + (d . n_k /
@@ -7,10 +7,10 @@
 // theta_t and n_k its normal, normalised to sum 1: separable into the theta taps and a
 // rotated, non-separable x/y stencil that differs per channel.  Since every source plane of
 // output channel k is blurred with the same x/y stencil, the theta sum is taken first:
-//   S_c   = M * bilinear(X_{t-1}[c])                          (Eq. 3 + Alg. 1 line 4)
+//   S_c   = M * bilinear(X_{t-1}[c])                          (Eq. 3 + Algorithm 1's first mask)
 //   C_k   = sum_d gt[d] S_{k+d}                               (theta part, circular)
 //   T_k   = g_k (x/y) applied to C_k;  G_k = g_k applied to M  (Eq. 7, Eq. 8 for B_0)
-//   X_t[k] = M * T_k / G_k * (1 / Z_{t-1})                    (Alg. 1 lines 6-7)
+//   X_t[k] = M * T_k / G_k * (1 / Z_{t-1})                    (Algorithm 1's mask + edge correction)
 // Channel k's stencil is computed in the CTA from phi_k (FP32 sin/cos/exp); its normalisation
 // cancels in T_k / G_k.
 //

@@ -1,15 +1,15 @@
-// Generic fused propagation kernel: Algorithm 1 lines 3-7 for all channels plus the Eq. 9
+// Generic fused propagation kernel: Algorithm 1's propagation for all channels plus the Eq. 9
 // normaliser, for any kernel radii up to LOC_MAX_R_XY / LOC_MAX_R_THETA and any storage type.
 //
 // One CTA owns a kGenTH x kGenTW tile of output cells and streams the channels
 // kk = -r_th .. K-1+r_th (channel kk mod K; the first and last r_th planes are computed twice
 // so that the circular theta blur needs no second pass).  For each channel, in shared memory:
 //   raw  = X_{t-1}[c] around the tile, shifted by the channel's integer source offset
-//   S    = M * bilinear(raw)                      (Eq. 3 + Alg. 1 line 4)
+//   S    = M * bilinear(raw)                      (Eq. 3 + Algorithm 1's first mask)
 //   Xb   = x-blur(S); P[ring] = y-blur(Xb)        (Eq. 7, separable for isotropic Sigma)
 // and once the ring holds planes kk-2r_th..kk the output channel o = kk - r_th is
-//   X_t[o] = corr * (1/Z_{t-1}) * sum_d gt[d] P[o + d]  (theta blur, Alg. 1 lines 6-7)
-// The map mask of line 6 is folded into corr (0 on occupied cells).  Every thread keeps an
+//   X_t[o] = corr * (1/Z_{t-1}) * sum_d gt[d] P[o + d]  (theta blur, Algorithm 1's mask + edge correction)
+// The map mask after the blur is folded into corr (0 on occupied cells).  Every thread keeps an
 // FP32 running sum of the values it stores (after rounding to the storage type), added
 // into an FP64 accumulator once per channel; CTA partials are combined in FP64 by the last
 // CTA, which writes Z and advances the log-scale.

@@ -1,15 +1,15 @@
 // Tiled fused propagation kernel for the default motion kernel (x/y radius 2, theta radius 3):
-// Algorithm 1 lines 3-7 for all K channels plus the Eq. 9 normaliser in one pass over HBM.
+// Algorithm 1's propagation for all K channels plus the Eq. 9 normaliser in one pass over HBM.
 //
 // One CTA owns a TH x 64 output tile and streams the planes p = 0 .. K+5:
 //   * raw tile of X_{t-1}[p] around the tile, shifted by the plane's integer source offset,
 //     arrives by TMA (cp.async.bulk.tensor.3d, zero fill off the grid) NSTAGE-1 planes ahead
 //     into a ring of stages guarded by mbarriers;
-//   * S-pass: S = M * bilinear(raw) over the (TH+4) x 68 halo region (Eq. 3, Alg. 1 line 4);
+//   * S-pass: S = M * bilinear(raw) over the (TH+4) x 68 halo region (Eq. 3, Algorithm 1's first mask);
 //   * X-pass: X = x-blur(S) over (TH+4) x 64 (Eq. 7, separable for the isotropic kernel);
 //   * P-pass: each thread owns 2 x MR output cells, applies the y-blur and pushes the result
 //     into a 7-deep register ring over theta; once the ring holds planes p-6 .. p it writes
-//     channel p-3 = corr * scale * sum_d gt[d] P[p-3+d] (theta blur, Alg. 1 lines 6-7,
+//     channel p-3 = corr * scale * sum_d gt[d] P[p-3+d] (theta blur, Algorithm 1's mask + edge correction,
 //     Eq. 8) and adds the stored (rounded) values to its FP32 partial.
 // The circular theta blur needs planes 0..5 again at the end: the P-pass keeps them in
 // shared memory (planes p = K .. K+5 read them back), so every input plane is read from HBM

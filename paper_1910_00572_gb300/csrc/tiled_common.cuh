@@ -323,7 +323,7 @@ __device__ __forceinline__ void p_pass(const float (*X)[XW_PITCH], float (*wrap)
 }
 
 // One tile of the synchronous tiled kernel (every thread of the CTA takes part):
-// Alg. 1 lines 3-7 for all channels of a TH x 64 output tile, adding the stored values to acc.
+// Algorithm 1's propagation for all channels of a TH x 64 output tile, adding the stored values to acc.
 struct TileJob {
     const CUtensorMap* tmap;          // X_{t-1} as [K][H][W]
     const Shift* sh;                  // per-channel source offsets

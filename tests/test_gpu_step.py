@@ -130,7 +130,7 @@ def test_mass_is_conserved_on_a_free_map():
 
 
 def test_uniform_belief_is_a_fixed_point_at_walls():
-    """Alg. 1 line 7 ('wall, not cliff'): zero motion keeps the uniform belief uniform."""
+    """Algorithm 1's edge correction ('wall, not cliff'): zero motion keeps the uniform belief uniform."""
     occ = floorplan.rooms_map(5, size=64)
     h = make(occ, 8, 0.1)
     try:

@@ -131,7 +131,7 @@ def test_edge_correction_straight_wall_closed_form():
 
 
 def test_uniform_belief_stays_uniform_at_walls():
-    """'Cliff vs wall' (Alg. 1 line 7): with zero motion a uniform belief is a fixed point."""
+    """'Cliff vs wall' (Algorithm 1's edge correction): with zero motion a uniform belief is a fixed point."""
     occ = floorplan.rooms_map(5, size=32)
     flt = F.Filter(occ, 8, 0.1, 0.5, 1.0)
     B0 = flt.B.copy()
