@@ -186,7 +186,7 @@ def profiled_traffic(wl, args):
     while the kernel source is the one that was profiled (else None)."""
     import hashlib
     import re
-    if wl["name"] != "office512" or wl["storage"] != "f32" or args.tile not in (0, 6) or args.kernel not in (0, 2):
+    if wl["name"] != "office512" or wl["storage"] != "f32" or args.tile not in (0, 16) or args.kernel not in (0, 2):
         return None
     try:
         text = open(os.path.join(ROOT, "profiles", "step_ws_office512.md")).read()

@@ -15,8 +15,8 @@
 // shared memory (planes p = K .. K+5 read them back), so every input plane is read from HBM
 // once.  CTA partials are combined in FP64 by the last CTA (Z, log-scale).
 //
-// Tile configurations (Cfg1..Cfg3) trade halo overhead against the number of resident CTAs;
-// the session picks one per grid shape.
+// Tile configurations (Cfg1..Cfg16) trade halo overhead against the number of resident CTAs
+// and how the passes are spread over warps; the session picks one per grid shape.
 #include <type_traits>
 
 #include "tiled_pairs.cuh"
@@ -96,11 +96,13 @@ __global__ void __launch_bounds__(C::NT, C::MINB) step_tiled_kernel(const __grid
 }
 
 // ---------------------------------------------------------------------------------------------
-// Warp-specialised variant.  Four producer warps run the S-pass and X-pass of plane p+1 while
-// four consumer warps run the P-pass of plane p; the X plane is double-buffered between them.
-// Hand-offs use mbarriers with bounded waits (FULL[b]: producers arrive after writing X[b];
-// EMPTY[b]: consumers arrive after reading it); producers synchronise among themselves with a
-// 128-thread named barrier that every producer thread reaches on every plane.
+// Warp-specialised variant.  Producer warps run the S-pass and X-pass of plane p+1 while
+// consumer warps run the P-pass of plane p; the X plane is double-buffered between them.
+// Hand-offs use mbarriers with bounded waits (FULL[b]: the X-pass threads arrive after writing
+// X[b]; EMPTY[b]: consumers arrive after reading it); producers synchronise among themselves
+// with a named barrier that every producer thread reaches on every plane.  With SPLIT the
+// producers are two groups: S warps run the S-pass of plane p while X warps run the X-pass of
+// plane p - 1, between the same two producer barriers.
 
 __device__ __forceinline__ void bar_arrive(unsigned long long* b) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(b)) : "memory");
@@ -109,29 +111,45 @@ template <int NP>
 __device__ __forceinline__ void producers_sync() {       // named barrier 1, producer threads only
     asm volatile("bar.sync 1, %0;" ::"n"(NP) : "memory");
 }
+template <int NS>
+__device__ __forceinline__ void s_threads_sync() {       // named barrier 2, S threads of a split
+    asm volatile("bar.sync 2, %0;" ::"n"(NS) : "memory");
+}
 
-// TH tile rows (consumers: TH/4 rows x 2 columns each), SR S-pass rows per item, XW X-pass
-// columns per item, NSTAGE raw stages, MINB CTAs per SM asked of the compiler.
-template <int TH_, int SR_, int XW_, int NSTAGE_, int MINB_, int NP_ = 128, int NC_ = 128>
+// TH tile rows, SR S-pass rows per item, XW X-pass columns per item, NSTAGE raw stages, MINB
+// CTAs per SM asked of the compiler, NP / NC producer / consumer threads, MR consumer rows per
+// thread (2 columns each; 0: TH * 64 / (2 NC)).  The consumers cover CR = MR * NC / 32 >= TH
+// rows; rows TH .. CR-1 are computed from zero X rows and never stored, so TH need not be a
+// multiple of MR.  SPLIT divides the producers into S warps (the first NS threads) and X warps
+// (the other NX): the S-pass of plane p and the X-pass of plane p - 1 then run side by side
+// between two producer barriers instead of one after the other.
+template <int TH_, int SR_, int XW_, int NSTAGE_, int MINB_, int NP_ = 128, int NC_ = 128, int MR_ = 0,
+          bool SPLIT_ = false>
 struct WsCfg {
     static constexpr int TH = TH_, SR = SR_, XW = XW_, NSTAGE = NSTAGE_, MINB = MINB_;
     static constexpr int NP = NP_, NC = NC_, NT = NP + NC;
-    static_assert(NP % 32 == 0, "whole producer warps");
-    static constexpr int MR = TH * TW / (2 * NC);          // consumer rows per thread
-    static constexpr int XR = TH + 2 * R;
+    static constexpr bool SPLIT = SPLIT_;
+    static_assert(NP % 32 == 0 && NC % 32 == 0, "whole producer and consumer warps");
+    static constexpr int MR = MR_ > 0 ? MR_ : TH * TW / (2 * NC);   // consumer rows per thread
+    static constexpr int CR = MR * (NC / 32);                         // rows the consumers cover
+    static constexpr int XR = TH + 2 * R;                             // S and X rows computed
+    static constexpr int XRC = CR + 2 * R;                            // X rows the consumers read
     static constexpr int RAW_H = XR + 1;
+    static constexpr int S_ITEMS = (72 / 4) * (XR / SR), X_ITEMS = (TW / XW) * XR;
+    static constexpr int NS = SPLIT ? (S_ITEMS + 31) / 32 * 32 : NP;  // threads of the S-pass
+    static constexpr int NX = SPLIT ? NP - NS : NP;                   // threads of the X-pass
     static_assert(XR % SR == 0, "S-pass row groups must tile the halo rows");
-    static_assert((72 / 4) * (XR / SR) <= NP, "one S-pass item per producer thread");
-    static_assert((TW / XW) * XR <= NP, "one X-pass item per producer thread");
-    static_assert(MR * 2 * NC == TH * TW && (TH / MR) * 32 == NC, "consumer tiling");
+    static_assert(S_ITEMS <= NS, "one S-pass item per S thread");
+    static_assert(X_ITEMS <= NX, "one X-pass item per X thread");
+    static_assert(CR >= TH && CR - MR < TH, "consumer tiling: every consumer warp has a row in the tile");
 };
 
 template <typename T, typename C>
 struct SmemWS {
     T raw[C::NSTAGE][raw_stride<T, C>()];
     float S[2][C::XR][SW];                   // S of planes p and p + 1 (the X-pass of p overlaps)
-    float X[2][C::XR][XW_PITCH];
-    float wrap[NWRAP][C::TH][TW];
+    float X[2][C::XRC][XW_PITCH];            // rows XR .. XRC-1 stay zero
+    float wrap[NWRAP][C::CR][TW];
     float mk[C::XR][MW];
     unsigned long long tma[C::NSTAGE];
     unsigned long long full[2], empty[2];
@@ -160,10 +178,16 @@ __global__ void __launch_bounds__(C::NT, C::MINB) step_ws_kernel(const __grid_co
         const int gy = ty0 - R + y, gx = tx0 - R + c;
         sm.mk[y][c] = (gy >= 0 && gy < H && gx >= 0 && gx < W && a.trav[(size_t)gy * W + gx]) ? 1.0f : 0.0f;
     }
+    if constexpr (C::XRC > XR) {
+        for (int q = tid; q < 2 * (C::XRC - XR) * XW_PITCH; q += NT) {
+            const int b = q / ((C::XRC - XR) * XW_PITCH), r = q % ((C::XRC - XR) * XW_PITCH);
+            sm.X[b][XR + r / XW_PITCH][r % XW_PITCH] = 0.0f;
+        }
+    }
     if (tid == 0) {
         for (int s = 0; s < NSTAGE; ++s) bar_init(&sm.tma[s], 1);
         for (int b = 0; b < 2; ++b) {
-            bar_init(&sm.full[b], C::NP);
+            bar_init(&sm.full[b], C::NX);
             bar_init(&sm.empty[b], C::NC);
         }
         sm.fail_a = sm.fail_b = sm.fail_c = 0;
@@ -189,7 +213,50 @@ __global__ void __launch_bounds__(C::NT, C::MINB) step_ws_kernel(const __grid_co
             if (t == 0)
                 for (int q = 0; q < next_issue; ++q) issue(q);
         }
-        for (int p = 0; p < K; ++p) {
+        if constexpr (C::SPLIT) {
+            // S threads take plane p, X threads plane p - 1.  S of plane p goes to S[p & 1], which
+            // the X-pass of plane p - 2 finished reading before the previous producer barrier;
+            // the X-pass of plane p - 1 reads S[(p - 1) & 1], complete since that barrier.
+            const bool s_role = t < C::NS;
+            for (int p = 0; p <= K; ++p) {
+                if (s_role) {
+                    if (p < K) {
+                        const int stage = p % NSTAGE;
+                        const Shift s = a.sh[p];
+                        int x_al, xo;
+                        box_x<T>(tx0, s, x_al, xo);
+                        if (reinit) {
+                            const int y0 = ty0 - R + s.oy;
+                            for (int q = t; q < C::RAW_H * BW; q += C::NS) {
+                                const int y = q / BW, c = q % BW;
+                                const int gy = y0 + y, gx = x_al + c;
+                                float v = 0.0f;
+                                if (gy >= 0 && gy < H && gx >= 0 && gx < W) v = (float)a.trav[(size_t)gy * W + gx];
+                                sm.raw[stage][y * BW + c] = T(v);
+                            }
+                            s_threads_sync<C::NS>();
+                        } else if (!sm.fail_a) {
+                            if (bar_wait(&sm.tma[stage], (uint32_t)((p / NSTAGE) & 1))) waited = p + 1;
+                            else sm.fail_a = 1;
+                        }
+                        if (!sm.fail_a) s_pass_any<T, C>(sm.raw[stage], sm.mk, sm.S[p & 1], t, xo, s.fx, s.fy);
+                    }
+                } else if (p >= 1) {
+                    const int q = p - 1, b = q & 1;
+                    if (q >= 2 && !sm.fail_b && !bar_wait(&sm.empty[b], (uint32_t)(((q - 2) >> 1) & 1))) sm.fail_b = 1;
+                    if (!(sm.fail_a | sm.fail_b)) x_pass<C>(sm.S[b], sm.X[b], t - C::NS, a.g0, a.g1, a.g2);
+                    bar_arrive(&sm.full[b]);             // X[b] of plane p - 1 is ready
+                }
+                producers_sync<NP>();
+                if (p < K && !reinit && p + NSTAGE < K && !sm.fail_a) {
+                    if (t == 0) {
+                        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                        issue(p + NSTAGE);
+                    }
+                    next_issue = p + NSTAGE + 1;
+                }
+            }
+        } else for (int p = 0; p < K; ++p) {
             const int stage = p % NSTAGE;
             float (*S)[SW] = sm.S[p & 1];
             const Shift s = a.sh[p];
@@ -209,15 +276,7 @@ __global__ void __launch_bounds__(C::NT, C::MINB) step_ws_kernel(const __grid_co
                 if (bar_wait(&sm.tma[stage], (uint32_t)((p / NSTAGE) & 1))) waited = p + 1;
                 else sm.fail_a = 1;
             }
-            if (!sm.fail_a) {
-                const int xb = xo & ~3;
-                switch (xo & 3) {
-                    case 0: s_pass<T, C, 0>(sm.raw[stage], sm.mk, S, t, xb, s.fx, s.fy); break;
-                    case 1: s_pass<T, C, 1>(sm.raw[stage], sm.mk, S, t, xb, s.fx, s.fy); break;
-                    case 2: s_pass<T, C, 2>(sm.raw[stage], sm.mk, S, t, xb, s.fx, s.fy); break;
-                    default: s_pass<T, C, 3>(sm.raw[stage], sm.mk, S, t, xb, s.fx, s.fy); break;
-                }
-            }
+            if (!sm.fail_a) s_pass_any<T, C>(sm.raw[stage], sm.mk, S, t, xo, s.fx, s.fy);
             // S of plane p complete and the raw stage free; every producer has also finished the
             // X-pass of plane p - 1, so S of plane p + 1 (the other buffer's next use) may be written
             producers_sync<NP>();
@@ -243,7 +302,7 @@ __global__ void __launch_bounds__(C::NT, C::MINB) step_ws_kernel(const __grid_co
         for (int rr = 0; rr < MR; ++rr) {
             const int gy = ty0 + r0 + rr;
             float c0 = 0.0f, c1 = 0.0f;
-            if (gy < H && gxp < W) {
+            if (gy < H && gxp < W && r0 + rr < TH) {
                 c0 = a.corr[(size_t)gy * W + gxp] * in_scale;
                 c1 = a.corr[(size_t)gy * W + gxp + 1] * in_scale;
             }
@@ -330,6 +389,14 @@ using Cfg9 = pairs::PCfg<16, 2, 2, 4, 3, 2>;
 using Cfg10 = pairs::PCfg<32, 4, 2, 8, 2, 2>;
 using Cfg11 = pairs::PCfg<8, 2, 2, 8, 3, 4>;
 using Cfg12 = pairs::PCfg<16, 4, 2, 8, 2, 4>;
+// 13: warp-specialised 14-row tiles (the consumers cover 16 rows, 14 stored); 14-16: split
+// producers (S warps beside X warps): 14: 16-row tiles, 96 + 96 producer threads; 15: 14-row
+// tiles, 64 + 96; 16: 28-row tiles, one CTA of 16 warps per SM (160 + 128 producer threads,
+// 224 consumer threads).
+using Cfg13 = WsCfg<14, 3, 16, 3, 2, 128, 128, 4>;
+using Cfg14 = WsCfg<16, 4, 16, 3, 2, 192, 128, 0, true>;
+using Cfg15 = WsCfg<14, 6, 16, 3, 2, 160, 128, 4, true>;
+using Cfg16 = WsCfg<28, 4, 16, 3, 1, 288, 224, 4, true>;
 
 template <typename T, typename C> size_t smem_bytes() {
     using SM = std::conditional_t<C::PAIRS, pairs::PSmem<T, C>, Smem<T, C>>;
@@ -382,6 +449,10 @@ cudaError_t launch_cfg(int cfg, const FastArgs& a, int W, int H, cudaStream_t st
         case 10: return launch_typed<T, Cfg10>(a, dim3((W + TW - 1) / TW, (H + Cfg10::TH - 1) / Cfg10::TH), st);
         case 11: return launch_typed<T, Cfg11>(a, dim3((W + TW - 1) / TW, (H + Cfg11::TH - 1) / Cfg11::TH), st);
         case 12: return launch_typed<T, Cfg12>(a, dim3((W + TW - 1) / TW, (H + Cfg12::TH - 1) / Cfg12::TH), st);
+        case 13: return launch_ws<T, Cfg13>(a, dim3((W + TW - 1) / TW, (H + Cfg13::TH - 1) / Cfg13::TH), st);
+        case 14: return launch_ws<T, Cfg14>(a, dim3((W + TW - 1) / TW, (H + Cfg14::TH - 1) / Cfg14::TH), st);
+        case 15: return launch_ws<T, Cfg15>(a, dim3((W + TW - 1) / TW, (H + Cfg15::TH - 1) / Cfg15::TH), st);
+        case 16: return launch_ws<T, Cfg16>(a, dim3((W + TW - 1) / TW, (H + Cfg16::TH - 1) / Cfg16::TH), st);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -399,7 +470,11 @@ int cfg_tile_rows(int cfg) {
         case 9: return Cfg9::TH;
         case 10: return Cfg10::TH;
         case 11: return Cfg11::TH;
-        default: return Cfg12::TH;
+        case 12: return Cfg12::TH;
+        case 13: return Cfg13::TH;
+        case 14: return Cfg14::TH;
+        case 15: return Cfg15::TH;
+        default: return Cfg16::TH;
     }
 }
 
@@ -427,20 +502,40 @@ bool step_tiled_eligible(int H, int W, int K, int r_xy, int r_th, int storage) {
     return r_xy == R && r_th == RT && K >= 8 && K <= LOC_MAX_K && W % align == 0 && W >= 8 && H >= 1;
 }
 
-int step_tiled_num_cfgs() { return 12; }
+int step_tiled_num_cfgs() { return 16; }
 
 int step_tiled_default_cfg(int H, int W, int K, int storage) {
     (void)K;
     (void)storage;
-    // measured on GB300 (office plans): with few tiles per SM the warp-specialised pipeline
-    // (6) is fastest; with many tiles the 128-thread synchronous configuration (3)
-    const long long tiles16 = (long long)((W + TW - 1) / TW) * ((H + 15) / 16);
-    return tiles16 >= 8 * 152 ? 3 : 6;
+    int dev = 0, nsm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm <= 0)
+        nsm = 152;
+    // measured on GB300 (office plans): with many tiles per SM the 128-thread synchronous
+    // configuration (3) is fastest
+    const long long cols = (W + TW - 1) / TW;
+    if (cols * ((H + 15) / 16) >= 8LL * nsm) return 3;
+    // with few tiles the warp-specialised pipelines, whose time follows the S/X rows (tile rows
+    // + 4) that the busiest SM computes: 16-row tiles two per SM (6), 14-row tiles two per SM
+    // with split producers (15), 28-row tiles one per SM (16); ties keep the earlier one
+    const int cand[3][2] = {{6, Cfg6::TH}, {15, Cfg15::TH}, {16, Cfg16::TH}};
+    int best = 6;
+    long long best_cost = -1;
+    for (const auto& c : cand) {
+        const long long tiles = cols * ((H + c[1] - 1) / c[1]);
+        const long long cost = (tiles + nsm - 1) / nsm * (c[1] + 2 * R);
+        if (best_cost < 0 || cost < best_cost) {
+            best = c[0];
+            best_cost = cost;
+        }
+    }
+    return best;
 }
 
 cudaError_t make_step_tmap(void* tmap_out, const void* B, int storage, int H, int W, int K, int cfg) {
     if (cfg < 1 || cfg > step_tiled_num_cfgs()) return cudaErrorInvalidValue;
-    const int bw = cfg < 8 ? BW : (storage == LOC_F32 ? pairs::pbw<float>() : pairs::pbw<__half>());
+    const bool paired = cfg >= 8 && cfg <= 12;    // the paired-column passes use a wider box
+    const int bw = !paired ? BW : (storage == LOC_F32 ? pairs::pbw<float>() : pairs::pbw<__half>());
     return make_box_tmap(tmap_out, B, storage, H, W, K, bw, cfg_tile_rows(cfg) + 2 * R + 1);
 }
 

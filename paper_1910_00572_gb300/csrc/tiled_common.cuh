@@ -27,6 +27,7 @@ template <int TH_, int MR_, int SR_, int XW_, int NSTAGE_, int MINB_>
 struct Cfg {
     static constexpr int TH = TH_, MR = MR_, SR = SR_, XW = XW_, NSTAGE = NSTAGE_, MINB = MINB_;
     static constexpr bool PAIRS = false;
+    static constexpr int CR = TH;                  // rows the P-pass threads cover
     static constexpr int NT = (TH / MR) * 32;
     static constexpr int XR = TH + 2 * R;          // rows of S and X
     static constexpr int RAW_H = XR + 1;           // raw rows (bilinear needs one more)
@@ -64,7 +65,7 @@ struct Smem {
     T raw[C::NSTAGE][raw_stride<T, C>()];   // each stage [RAW_H][BW], 128-byte aligned
     float S[C::XR][SW];
     float X[C::XR][XW_PITCH];
-    float wrap[NWRAP][C::TH][TW];
+    float wrap[NWRAP][C::CR][TW];
     float mk[C::XR][MW];                     // 1 free, 0 occupied / off-grid
     unsigned long long bar[C::NSTAGE];
     double red[C::NT / 32];
@@ -235,6 +236,19 @@ __device__ __forceinline__ void x_pass(const float (*S)[SW], float (*X)[XW_PITCH
     }
 }
 
+// The S-pass for the in-box offset xo (its residue mod 4 selects the compile-time variant).
+template <typename T, typename C>
+__device__ __forceinline__ void s_pass_any(const T* raw, const float (*mk)[MW], float (*S)[SW], int t,
+                                           int xo, float fx, float fy) {
+    const int xb = xo & ~3;
+    switch (xo & 3) {
+        case 0: s_pass<T, C, 0>(raw, mk, S, t, xb, fx, fy); break;
+        case 1: s_pass<T, C, 1>(raw, mk, S, t, xb, fx, fy); break;
+        case 2: s_pass<T, C, 2>(raw, mk, S, t, xb, fx, fy); break;
+        default: s_pass<T, C, 3>(raw, mk, S, t, xb, fx, fy); break;
+    }
+}
+
 // Store two neighbouring outputs v = {a, b} (FP32 as is, BF16 stochastically rounded with the
 // 32 random bits h, FP16 round-to-nearest) and add the stored values to sum.
 template <typename T> __device__ __forceinline__ void store2(T* p, f2 v, uint32_t h, f2& sum);
@@ -275,7 +289,7 @@ struct Taps2 {
 // P-pass for plane p with the newest ring slot PH = p mod 7.  The thread's cells are rows
 // r0 .. r0+MR-1 of the tile, columns 2cp and 2cp+1, handled as column pairs.
 template <typename T, typename C, int PH>
-__device__ __forceinline__ void p_pass(const float (*X)[XW_PITCH], float (*wrap)[C::TH][TW],
+__device__ __forceinline__ void p_pass(const float (*X)[XW_PITCH], float (*wrap)[C::CR][TW],
                                        const TileOut& a, const Taps2& tp,
                                        f2 (&ring)[RING][C::MR], const f2 (&cs)[C::MR], int p,
                                        int r0, int cp, int ty0, int gx, KahanF& acc) {
@@ -303,7 +317,8 @@ __device__ __forceinline__ void p_pass(const float (*X)[XW_PITCH], float (*wrap)
         const size_t base = ((size_t)o * a.H + (ty0 + r0)) * a.W + gx;
         T* out = static_cast<T*>(a.B_out) + base;
         const uint32_t h = sizeof(T) == 2 ? pcg_hash((uint32_t)base ^ a.seed) : 0u;
-        const int rows = a.H - (ty0 + r0);             // rows of this thread inside the grid
+        int rows = a.H - (ty0 + r0);                   // rows of this thread inside the grid
+        if constexpr (C::CR > C::TH) rows = min(rows, C::TH - r0);   // ... and inside the tile
         const bool full = rows >= MR && gx < a.W;
         f2 part = 0ull;
 #pragma unroll
@@ -422,13 +437,7 @@ __device__ __forceinline__ bool run_tile(Smem<T, C>& sm, const TileJob& j, unsig
                 failed = 1;
             }
             if (!failed) {
-                const int xb = xo & ~3;
-                switch (xo & 3) {
-                    case 0: s_pass<T, C, 0>(sm.raw[stage], sm.mk, sm.S, tid, xb, s.fx, s.fy); break;
-                    case 1: s_pass<T, C, 1>(sm.raw[stage], sm.mk, sm.S, tid, xb, s.fx, s.fy); break;
-                    case 2: s_pass<T, C, 2>(sm.raw[stage], sm.mk, sm.S, tid, xb, s.fx, s.fy); break;
-                    default: s_pass<T, C, 3>(sm.raw[stage], sm.mk, sm.S, tid, xb, s.fx, s.fy); break;
-                }
+                s_pass_any<T, C>(sm.raw[stage], sm.mk, sm.S, tid, xo, s.fx, s.fy);
             }
             if (__syncthreads_or(failed)) {
                 failed = 1;
