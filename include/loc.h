@@ -200,7 +200,10 @@ loc_status loc_estimate(loc_handle h, double radius_m, int dk, loc_estimate_t* o
  *   loc_marginal: host float[H][W]: LOC_MAP_MAX = max over channels (the paper's belief
  *                 map, Section III-A.3), LOC_MAP_SUM = sum over channels (marginal).
  *   loc_argmax:   the most probable state (k, j, i) and its probability; ties go to the
- *                 lowest linear index in [K][H][W] order. */
+ *                 lowest linear index in [K][H][W] order.  After a loc_step through a
+ *                 warp-specialised tile configuration (6, 7, 13-16) the step kernel has
+ *                 already combined this argmax, and the call only reads it back; otherwise
+ *                 it makes one pass over the tensor. */
 loc_status loc_belief(loc_handle h, float* out, size_t n);
 loc_status loc_marginal(loc_handle h, float* out, size_t n, int mode);
 loc_status loc_argmax(loc_handle h, int* k, int* j, int* i, float* p);

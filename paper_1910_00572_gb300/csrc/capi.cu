@@ -142,7 +142,7 @@ LOC_API loc_status loc_session_bytes(const loc_params* p, size_t* bytes) {
     size_t nparts = step_num_blocks(p->H, p->W);
     if (nparts < 4096) nparts = 4096;
     size_t b = 2 * r(n * elem) + r(hw) + r(hw * 4) + r(sizeof(SessionDev)) + r(nparts * 8) +
-               r(argmax_scratch_bytes(n)) + r(16);
+               r(nparts * 12) + r(argmax_scratch_bytes(n)) + r(16);
     // LIDAR scratch (allocated by the first scan update); the scan tables are sized for a
     // 1080-beam scan
     size_t cap = 2 * (size_t)p->n_samples + 4 * (H + W) + 1024;
@@ -223,9 +223,11 @@ LOC_API loc_status loc_create(const uint8_t* occ, const loc_params* p, loc_handl
     s->corr = (float*)dev_alloc(s, hw * sizeof(float));
     s->sd = (SessionDev*)dev_alloc(s, sizeof(SessionDev));
     s->partials = (double*)dev_alloc(s, s->nparts * sizeof(double));
+    s->am_pi = (long long*)dev_alloc(s, s->nparts * (sizeof(long long) + sizeof(float)));
+    s->am_pv = s->am_pi ? (float*)(s->am_pi + s->nparts) : nullptr;
     s->argmax_scratch = dev_alloc(s, argmax_scratch_bytes(s->n));
     s->argmax_idx = (long long*)dev_alloc(s, sizeof(long long) + sizeof(float));
-    if (!s->B[0] || !s->B[1] || !s->trav || !s->corr || !s->sd || !s->partials ||
+    if (!s->B[0] || !s->B[1] || !s->trav || !s->corr || !s->sd || !s->partials || !s->am_pi ||
         !s->argmax_scratch || !s->argmax_idx) {
         release_all(s);
         delete s;
@@ -321,11 +323,13 @@ void shift_table(const loc_session* h, Shift* sh) {
 // Key of the stochastic rounding of propagation number n_prop.
 uint32_t step_seed(const loc_session* h) { return pcg_hash((uint32_t)h->n_prop * 0x9E3779B9u + 0x632BE5ABu); }
 
-// After a propagation was enqueued: the output buffer becomes current.
+// After a propagation was enqueued: the output buffer becomes current.  A fused argmax
+// result, if any, is for the previous tensor (loc_step marks a fresh one afterwards).
 void step_done(loc_session* h) {
     h->cur = 1 - h->cur;
     h->px = h->py = 0.0;
     h->n_prop += 1;
+    h->am_valid = false;
 }
 
 }  // namespace loc
@@ -344,6 +348,10 @@ LOC_API loc_status loc_step(loc_handle h, double u, double v, double w) {
     a.corr = h->corr;
     a.sd = h->sd;
     a.partials = h->partials;
+    a.am_pv = h->am_pv;
+    a.am_pi = h->am_pi;
+    a.am_idx = h->argmax_idx;
+    a.am_val = h->argmax_val;
     a.inv_uniform = h->inv_uniform;
     a.out_mult = storage_mult(h->p.storage);
     a.log_out_mult = std::log((double)a.out_mult);
@@ -372,6 +380,8 @@ LOC_API loc_status loc_step(loc_handle h, double u, double v, double w) {
     }
     if (e != cudaSuccess) return cuda_fail(h, e, "step launch");
     step_done(h);
+    // the warp-specialised tiled kernels write the argmax of the new tensor
+    h->am_valid = !h->aniso && h->tiled && step_tiled_fuses_argmax(h->tile_cfg);
     return LOC_OK;
 }
 
@@ -508,6 +518,7 @@ loc_status check_scan(loc_session* h, const float* ranges, int n_beams, double a
 // Scores the sample list on the device (h->samples, count in h->dscal[0]) and reweights.
 loc_status score_and_reweight(loc_session* h, int n_used, int n_dirs, double r_max, double sigma_r) {
     if (n_used == 0 || n_dirs == 0) return LOC_OK;        // nothing to score
+    h->am_valid = false;
     const double cell = h->p.cell_m;
     const uint32_t seed = pcg_hash((uint32_t)h->n_lidar * 0x85EBCA6Bu + 0x27D4EB2Fu);
     cudaError_t e = launch_score_reweight(
@@ -521,6 +532,7 @@ loc_status score_and_reweight(loc_session* h, int n_used, int n_dirs, double r_m
 }
 
 loc_status materialize(loc_session* h) {
+    h->am_valid = false;
     cudaError_t e = launch_materialize(h->B[h->cur], h->p.storage, h->trav, h->sd,
                                        h->inv_uniform * storage_mult(h->p.storage), h->hw, h->p.K, h->partials,
                                        h->nparts, h->stream);
@@ -744,6 +756,7 @@ LOC_API loc_status loc_lidar_update_dense(loc_handle h, const float* ranges, int
         e = launch_dense_score(h->table, h->trav, h->B[h->cur], h->p.storage, h->p.H, h->p.W, K, A, h->dense_m,
                                h->dense_z, nu, (float)(step * step / (2.0 * sigma_r * sigma_r)), h->dense_logL,
                                h->dense_max, h->stream);
+    h->am_valid = false;
     if (e == cudaSuccess)
         e = launch_dense_apply(h->B[h->cur], h->p.storage, h->dense_logL, h->n, h->dense_max,
                                (float)std::log((double)storage_mult(h->p.storage)),
@@ -890,23 +903,33 @@ LOC_API loc_status loc_argmax(loc_handle h, int* k, int* j, int* i, float* p) {
     loc_status st = check_live(h);
     if (st != LOC_OK) return st;
     if (!k || !j || !i || !p) return fail(h, LOC_ERR_INVALID_ARG, "null output");
-    cudaError_t e = launch_argmax(h->B[h->cur], h->p.storage, h->trav, h->sd, h->inv_uniform,
-                                  h->p.H, h->p.W, h->p.K, h->argmax_scratch, h->argmax_idx,
-                                  h->argmax_val, h->stream);
-    // the result and the device status in one round trip, through pinned memory
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(h->pinned, h->argmax_idx, sizeof(long long) + sizeof(float), cudaMemcpyDeviceToHost,
-                            h->stream);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(h->pinned + 16, &h->sd->status, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-    if (e != cudaSuccess) return cuda_fail(h, e, "loc_argmax");
-    long long idx;
-    float val;
-    int status;
-    std::memcpy(&idx, h->pinned, sizeof(idx));
-    std::memcpy(&val, h->pinned + sizeof(long long), sizeof(val));
-    std::memcpy(&status, h->pinned + 16, sizeof(status));
+    long long idx = -1;
+    float val = 0.0f;
+    int status = 0;
+    // after a tiled propagation the step itself left the argmax of the new tensor (or -1 when
+    // it restarted); otherwise, or then, one pass over the stored tensor
+    for (int pass = h->am_valid ? 0 : 1; pass < 2 && idx < 0; ++pass) {
+        cudaError_t e = cudaSuccess;
+        if (pass == 1)
+            e = launch_argmax(h->B[h->cur], h->p.storage, h->trav, h->sd, h->inv_uniform, h->p.H, h->p.W, h->p.K,
+                              h->argmax_scratch, h->argmax_idx, h->argmax_val, h->stream);
+        // the result and the device status in one round trip, through pinned memory
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(h->pinned, h->argmax_idx, sizeof(long long) + sizeof(float),
+                                cudaMemcpyDeviceToHost, h->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(h->pinned + 16, &h->sd->status, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "loc_argmax");
+        std::memcpy(&idx, h->pinned, sizeof(idx));
+        std::memcpy(&val, h->pinned + sizeof(long long), sizeof(val));
+        std::memcpy(&status, h->pinned + 16, sizeof(status));
+        if (status != 0) break;
+    }
+    const loc_status cs = check_status(h, status);
+    if (cs != LOC_OK) return cs;
+    if (idx < 0) return fail(h, LOC_ERR_CUDA, "loc_argmax: no result");
+    h->am_valid = true;                    // the buffer holds the argmax of the current tensor
     const long long hw = (long long)h->hw;
     *k = (int)(idx / hw);
     *j = (int)((idx % hw) / h->p.W);
@@ -981,6 +1004,7 @@ LOC_API loc_status loc_set_belief(loc_handle h, const float* b, size_t n) {
     if (!(sum > 0.0)) return fail(h, LOC_ERR_INVALID_ARG, "belief sums to 0");
     float* tmp = (float*)dev_alloc(h, n * sizeof(float));
     if (!tmp) return fail(h, LOC_ERR_OOM, "upload buffer");
+    h->am_valid = false;
     cudaError_t e = cudaMemcpyAsync(tmp, b, n * sizeof(float), cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess)
         e = launch_set_belief(tmp, h->B[h->cur], h->p.storage, n, h->sd, h->partials, h->nparts, h->stream);

@@ -49,6 +49,8 @@ cudaError_t make_aniso_tmap(void* tmap_out, const void* B, int storage, int H, i
 bool step_tiled_eligible(int H, int W, int K, int r_xy, int r_th, int storage);
 int step_tiled_num_cfgs();
 int step_tiled_default_cfg(int H, int W, int K, int storage);
+// Whether tile configuration cfg also writes the argmax of the new tensor (StepArgs::am_idx).
+bool step_tiled_fuses_argmax(int cfg);
 size_t step_tmap_bytes();
 cudaError_t make_step_tmap(void* tmap_out, const void* B, int storage, int H, int W, int K, int cfg);
 // Tensor map of a [K][H][W] belief buffer loaded in boxes of box_w x box_h cells of one plane.

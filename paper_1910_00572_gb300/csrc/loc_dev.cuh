@@ -57,6 +57,12 @@ struct StepArgs {
     const float* corr;             // G(B_0)^-1 on free cells, 0 on occupied, [H][W]
     SessionDev* sd;
     double* partials;              // one FP64 partial sum per CTA
+    // the fused argmax of the tiled kernels: per-CTA candidates (value, index) and the result
+    // (index of X_t's largest stored value, lowest on ties, or -1; its normalised belief)
+    float* am_pv;
+    long long* am_pi;
+    long long* am_idx;
+    float* am_val;
     float inv_uniform;             // 1 / (K * n_free): the uniform belief value
     float out_mult;                // storage multiplier of the outputs (FP16: 2^14, else 1)
     double log_out_mult;           // log(out_mult), removed from the log-scale

@@ -27,6 +27,12 @@ struct loc_session {
     loc::SessionDev* sd = nullptr;
     double* partials = nullptr;
     unsigned int nparts = 0;
+    // the argmax fused into the tiled propagation: per-CTA candidates, and whether the result
+    // in argmax_idx / argmax_val belongs to the current tensor (set by loc_step, cleared by
+    // every other change of the tensor)
+    float* am_pv = nullptr;
+    long long* am_pi = nullptr;
+    bool am_valid = false;
     void* argmax_scratch = nullptr;
     long long* argmax_idx = nullptr;
     float* argmax_val = nullptr;

@@ -26,6 +26,24 @@ namespace {
 
 using namespace tiled;
 
+// The last CTA's update of the session scalars from the new normaliser Z (Eq. 9): Z, 1/Z and
+// the log-scale, or the uniform restart when no mass is left.
+__device__ __forceinline__ void finish_step(SessionDev* sd, double Z, double log_mult) {
+    sd->n_prop += 1;
+    if (Z > 0.0 && isfinite(Z)) {
+        sd->Z = Z;
+        sd->inv_Z = (float)(1.0 / Z);
+        sd->logscale += log(Z) - log_mult;
+        sd->reinit = 0;
+    } else {
+        if (!isfinite(Z)) sd->status |= LOC_DEV_ERR_NONFINITE_Z;
+        sd->Z = 1.0;
+        sd->inv_Z = 1.0f;
+        sd->reinit = 1;
+        sd->n_reinit += 1;
+    }
+}
+
 template <typename T, typename C>
 __global__ void __launch_bounds__(C::NT, C::MINB) step_tiled_kernel(const __grid_constant__ FastArgs a) {
     constexpr int NT = C::NT, NSTAGE = C::NSTAGE;
@@ -78,21 +96,8 @@ __global__ void __launch_bounds__(C::NT, C::MINB) step_tiled_kernel(const __grid
     const double bt = block_sum<NT>(acc.value(), sm.red);
     SessionDev* sd = a.sd;
     const double log_mult = a.log_out_mult;
-    finish_sum<NT>(bt, a.partials, &sd->counter, gridDim.x * gridDim.y, sm.red, [sd, log_mult](double Z) {
-        sd->n_prop += 1;
-        if (Z > 0.0 && isfinite(Z)) {
-            sd->Z = Z;
-            sd->inv_Z = (float)(1.0 / Z);
-            sd->logscale += log(Z) - log_mult;
-            sd->reinit = 0;
-        } else {
-            if (!isfinite(Z)) sd->status |= LOC_DEV_ERR_NONFINITE_Z;
-            sd->Z = 1.0;
-            sd->inv_Z = 1.0f;
-            sd->reinit = 1;
-            sd->n_reinit += 1;
-        }
-    });
+    finish_sum<NT>(bt, a.partials, &sd->counter, gridDim.x * gridDim.y, sm.red,
+                   [sd, log_mult](double Z) { finish_step(sd, Z, log_mult); });
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -102,7 +107,9 @@ __global__ void __launch_bounds__(C::NT, C::MINB) step_tiled_kernel(const __grid
 // X[b]; EMPTY[b]: consumers arrive after reading it); producers synchronise among themselves
 // with a named barrier that every producer thread reaches on every plane.  With SPLIT the
 // producers are two groups: S warps run the S-pass of plane p while X warps run the X-pass of
-// plane p - 1, between the same two producer barriers.
+// plane p - 1, between the same two producer barriers.  The consumers, which wait on the
+// producers, also keep the running argmax of the values they store; the last CTA combines it
+// with the normaliser, so a pose read after the step needs no pass over the tensor.
 
 __device__ __forceinline__ void bar_arrive(unsigned long long* b) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(b)) : "memory");
@@ -197,6 +204,7 @@ __global__ void __launch_bounds__(C::NT, C::MINB) step_ws_kernel(const __grid_co
     __syncthreads();
 
     KahanF acc;
+    ArgBest am;                             // consumers: the argmax of the values they store
     int waited = 0, next_issue = 0;         // producer: planes [waited, next_issue) maybe in flight
     if (tid < NP) {
         // ------------------------------------------------------------------ producers
@@ -332,13 +340,13 @@ __global__ void __launch_bounds__(C::NT, C::MINB) step_ws_kernel(const __grid_co
                 break;
             }
             switch (p % RING) {
-                case 0: p_pass<T, C, 0>(sm.X[b], sm.wrap, o, tp, ring, cs, p, r0, cp, ty0, gxp, acc); break;
-                case 1: p_pass<T, C, 1>(sm.X[b], sm.wrap, o, tp, ring, cs, p, r0, cp, ty0, gxp, acc); break;
-                case 2: p_pass<T, C, 2>(sm.X[b], sm.wrap, o, tp, ring, cs, p, r0, cp, ty0, gxp, acc); break;
-                case 3: p_pass<T, C, 3>(sm.X[b], sm.wrap, o, tp, ring, cs, p, r0, cp, ty0, gxp, acc); break;
-                case 4: p_pass<T, C, 4>(sm.X[b], sm.wrap, o, tp, ring, cs, p, r0, cp, ty0, gxp, acc); break;
-                case 5: p_pass<T, C, 5>(sm.X[b], sm.wrap, o, tp, ring, cs, p, r0, cp, ty0, gxp, acc); break;
-                default: p_pass<T, C, 6>(sm.X[b], sm.wrap, o, tp, ring, cs, p, r0, cp, ty0, gxp, acc); break;
+                case 0: p_pass<T, C, 0, true>(sm.X[b], sm.wrap, o, tp, ring, cs, p, r0, cp, ty0, gxp, acc, &am); break;
+                case 1: p_pass<T, C, 1, true>(sm.X[b], sm.wrap, o, tp, ring, cs, p, r0, cp, ty0, gxp, acc, &am); break;
+                case 2: p_pass<T, C, 2, true>(sm.X[b], sm.wrap, o, tp, ring, cs, p, r0, cp, ty0, gxp, acc, &am); break;
+                case 3: p_pass<T, C, 3, true>(sm.X[b], sm.wrap, o, tp, ring, cs, p, r0, cp, ty0, gxp, acc, &am); break;
+                case 4: p_pass<T, C, 4, true>(sm.X[b], sm.wrap, o, tp, ring, cs, p, r0, cp, ty0, gxp, acc, &am); break;
+                case 5: p_pass<T, C, 5, true>(sm.X[b], sm.wrap, o, tp, ring, cs, p, r0, cp, ty0, gxp, acc, &am); break;
+                default: p_pass<T, C, 6, true>(sm.X[b], sm.wrap, o, tp, ring, cs, p, r0, cp, ty0, gxp, acc, &am); break;
             }
             if (p + 2 < K) bar_arrive(&sm.empty[b]);  // a producer waits for this release
         }
@@ -355,21 +363,8 @@ __global__ void __launch_bounds__(C::NT, C::MINB) step_ws_kernel(const __grid_co
     const double bt = block_sum<NT>(acc.value(), sm.red);
     SessionDev* sd = a.sd;
     const double log_mult = a.log_out_mult;
-    finish_sum<NT>(bt, a.partials, &sd->counter, gridDim.x * gridDim.y, sm.red, [sd, log_mult](double Z) {
-        sd->n_prop += 1;
-        if (Z > 0.0 && isfinite(Z)) {
-            sd->Z = Z;
-            sd->inv_Z = (float)(1.0 / Z);
-            sd->logscale += log(Z) - log_mult;
-            sd->reinit = 0;
-        } else {
-            if (!isfinite(Z)) sd->status |= LOC_DEV_ERR_NONFINITE_Z;
-            sd->Z = 1.0;
-            sd->inv_Z = 1.0f;
-            sd->reinit = 1;
-            sd->n_reinit += 1;
-        }
-    });
+    finish_sum_am<NT>(bt, am, a.partials, a.am_pv, a.am_pi, &sd->counter, gridDim.x * gridDim.y, sm.red, a.am_idx,
+                      a.am_val, [sd, log_mult](double Z) { finish_step(sd, Z, log_mult); });
 }
 
 // The tile configurations.  1: 32-row tiles (large grids); 2: 16-row tiles with 2-row
@@ -504,6 +499,8 @@ bool step_tiled_eligible(int H, int W, int K, int r_xy, int r_th, int storage) {
 
 int step_tiled_num_cfgs() { return 16; }
 
+bool step_tiled_fuses_argmax(int cfg) { return cfg == 6 || cfg == 7 || (cfg >= 13 && cfg <= 16); }
+
 int step_tiled_default_cfg(int H, int W, int K, int storage) {
     (void)K;
     (void)storage;
@@ -562,6 +559,10 @@ cudaError_t launch_step_tiled(const StepArgs& g, const void* tmap, int storage, 
     FastArgs a;
     memcpy(&a.tmap, tmap, sizeof(CUtensorMap));
     a.B_out = g.B_out;
+    a.am_pv = g.am_pv;
+    a.am_pi = g.am_pi;
+    a.am_idx = g.am_idx;
+    a.am_val = g.am_val;
     a.trav = g.trav;
     a.corr = g.corr;
     a.sd = g.sd;

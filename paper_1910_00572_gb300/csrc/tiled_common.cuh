@@ -5,6 +5,9 @@
 #pragma once
 #include <cuda.h>
 
+#include <cfloat>
+#include <climits>
+
 #include "kernels.h"
 
 namespace loc {
@@ -43,6 +46,10 @@ struct FastArgs {
     const float* corr;
     SessionDev* sd;
     double* partials;
+    float* am_pv;                      // per-CTA argmax candidates: value ...
+    long long* am_pi;                  // ... and linear index
+    long long* am_idx;                 // the argmax of X_t (-1: not produced) ...
+    float* am_val;                     // ... and its normalised belief
     float inv_uniform;
     float out_mult;
     double log_out_mult;
@@ -250,13 +257,16 @@ __device__ __forceinline__ void s_pass_any(const T* raw, const float (*mk)[MW], 
 }
 
 // Store two neighbouring outputs v = {a, b} (FP32 as is, BF16 stochastically rounded with the
-// 32 random bits h, FP16 round-to-nearest) and add the stored values to sum.
-template <typename T> __device__ __forceinline__ void store2(T* p, f2 v, uint32_t h, f2& sum);
-template <> __device__ __forceinline__ void store2<float>(float* p, f2 v, uint32_t, f2& sum) {
+// 32 random bits h, FP16 round-to-nearest), add them to sum, and return the stored values as
+// FP32 in st.
+template <typename T> __device__ __forceinline__ void store2(T* p, f2 v, uint32_t h, f2& sum, f2& st);
+template <> __device__ __forceinline__ void store2<float>(float* p, f2 v, uint32_t, f2& sum, f2& st) {
     *reinterpret_cast<f2*>(p) = v;
     sum = fadd2(sum, v);
+    st = v;
 }
-template <> __device__ __forceinline__ void store2<__nv_bfloat16>(__nv_bfloat16* p, f2 v, uint32_t h, f2& sum) {
+template <> __device__ __forceinline__ void store2<__nv_bfloat16>(__nv_bfloat16* p, f2 v, uint32_t h, f2& sum,
+                                                                  f2& st) {
     float a, b;
     upk(v, a, b);
     const uint32_t ua = __float_as_uint(a) + (h & 0xFFFFu);
@@ -264,13 +274,102 @@ template <> __device__ __forceinline__ void store2<__nv_bfloat16>(__nv_bfloat16*
     *reinterpret_cast<uint32_t*>(p) = __byte_perm(ua, ub, 0x7632);   // high halves: {a, b}
     // the stochastic rounding is unbiased: Z takes the unrounded values (within ~1e-7)
     sum = fadd2(sum, v);
+    st = pk(__uint_as_float(ua & 0xFFFF0000u), __uint_as_float(ub & 0xFFFF0000u));
 }
-template <> __device__ __forceinline__ void store2<__half>(__half* p, f2 v, uint32_t, f2& sum) {
+template <> __device__ __forceinline__ void store2<__half>(__half* p, f2 v, uint32_t, f2& sum, f2& st) {
     float a, b;
     upk(v, a, b);
     const __half2 hv = __floats2half2_rn(a, b);
     *reinterpret_cast<__half2*>(p) = hv;
-    sum = fadd2(sum, pk(__low2float(hv), __high2float(hv)));
+    st = pk(__low2float(hv), __high2float(hv));
+    sum = fadd2(sum, st);
+}
+
+// Running argmax of the stored values: the larger value, then the lower linear index (the
+// order of the argmax pass over the stored tensor).
+struct ArgBest {
+    float v = -FLT_MAX;
+    long long i = LLONG_MAX;
+};
+__device__ __forceinline__ bool am_better(float v, long long i, float bv, long long bi) {
+    return v > bv || (v == bv && i < bi);
+}
+
+// The CTA's best (value, index) by a fixed shuffle tree and warp order; valid in thread 0.
+// sv / si hold NT/32 entries.
+template <int NT>
+__device__ __forceinline__ ArgBest am_block(ArgBest b, float* sv, long long* si) {
+    for (int o = 16; o > 0; o >>= 1) {
+        const float ov = __shfl_down_sync(0xffffffffu, b.v, o);
+        const long long oi = __shfl_down_sync(0xffffffffu, b.i, o);
+        if (am_better(ov, oi, b.v, b.i)) {
+            b.v = ov;
+            b.i = oi;
+        }
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();                    // an earlier call may still read sv / si
+    if (lane == 0) {
+        sv[warp] = b.v;
+        si[warp] = b.i;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int w = 1; w < NT / 32; ++w)
+            if (am_better(sv[w], si[w], b.v, b.i)) {
+                b.v = sv[w];
+                b.i = si[w];
+            }
+    return b;
+}
+
+// finish_sum for the normaliser, together with the argmax of the stored tensor: every CTA
+// also stores its best (value, index); the CTA that arrives last combines the candidates in a
+// fixed order and writes the index and the normalised value (value / Z) to out_idx / out_val,
+// the results of the argmax pass over X_t.  When Z is not positive and finite the session
+// restarts (its belief reads as uniform over free cells) and out_idx gets -1: no result.
+template <int NT, typename Fin>
+__device__ __forceinline__ void finish_sum_am(double block_total, ArgBest best, double* partials, float* apv,
+                                              long long* api, unsigned int* counter, unsigned int nblocks,
+                                              double* red, long long* out_idx, float* out_val, Fin fin) {
+    __shared__ int s_last;
+    __shared__ float s_v[NT / 32];
+    __shared__ long long s_i[NT / 32];
+    best = am_block<NT>(best, s_v, s_i);
+    if (threadIdx.x == 0) {
+        const unsigned int b = blockIdx.x + gridDim.x * blockIdx.y;
+        partials[b] = block_total;
+        apv[b] = best.v;
+        api[b] = best.i;
+        __threadfence();
+        s_last = atomicAdd(counter, 1u) == nblocks - 1;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    double s = 0.0;
+    ArgBest g;
+    for (unsigned int b = threadIdx.x; b < nblocks; b += NT) {
+        s += ((volatile double*)partials)[b];
+        const float v = ((volatile float*)apv)[b];
+        const long long i = ((volatile long long*)api)[b];
+        if (am_better(v, i, g.v, g.i)) {
+            g.v = v;
+            g.i = i;
+        }
+    }
+    const double tot = block_sum<NT>(s, red);
+    g = am_block<NT>(g, s_v, s_i);
+    if (threadIdx.x == 0) {
+        *counter = 0u;
+        fin(tot);
+        if (tot > 0.0 && isfinite(tot)) {
+            *out_idx = g.i;
+            *out_val = (float)((double)g.v / tot);
+        } else {
+            *out_idx = -1;
+        }
+    }
 }
 
 // Where the P-pass writes: the output tensor, the rounding key and the grid.
@@ -288,11 +387,12 @@ struct Taps2 {
 
 // P-pass for plane p with the newest ring slot PH = p mod 7.  The thread's cells are rows
 // r0 .. r0+MR-1 of the tile, columns 2cp and 2cp+1, handled as column pairs.
-template <typename T, typename C, int PH>
+// With AM the thread also keeps the running argmax of the values it stores in *am.
+template <typename T, typename C, int PH, bool AM = false>
 __device__ __forceinline__ void p_pass(const float (*X)[XW_PITCH], float (*wrap)[C::CR][TW],
                                        const TileOut& a, const Taps2& tp,
                                        f2 (&ring)[RING][C::MR], const f2 (&cs)[C::MR], int p,
-                                       int r0, int cp, int ty0, int gx, KahanF& acc) {
+                                       int r0, int cp, int ty0, int gx, KahanF& acc, ArgBest* am = nullptr) {
     constexpr int MR = C::MR;
     const int K = a.K;
     if (p < K) {
@@ -321,6 +421,7 @@ __device__ __forceinline__ void p_pass(const float (*X)[XW_PITCH], float (*wrap)
         if constexpr (C::CR > C::TH) rows = min(rows, C::TH - r0);   // ... and inside the tile
         const bool full = rows >= MR && gx < a.W;
         f2 part = 0ull;
+        f2 stv[MR];                                    // stored values (-FLT_MAX: not stored)
 #pragma unroll
         for (int rr = 0; rr < MR; ++rr) {
             f2 t = fmul2(tp.gt[0], ring[(PH + 1) % RING][rr]);
@@ -329,11 +430,35 @@ __device__ __forceinline__ void p_pass(const float (*X)[XW_PITCH], float (*wrap)
             const f2 v = fmul2(cs[rr], t);
             // 32 random bits per row: the thread's hash with a per-row odd constant mixed in
             const uint32_t hr = h ^ (0x9E3779B9u * (uint32_t)(2 * rr + 1));
-            if (full || (rr < rows && gx < a.W)) store2<T>(out + (size_t)rr * a.W, v, hr, part);
+            stv[rr] = pk(-FLT_MAX, -FLT_MAX);
+            if (full || (rr < rows && gx < a.W)) store2<T>(out + (size_t)rr * a.W, v, hr, part, stv[rr]);
         }
         float p0, p1;
         upk(part, p0, p1);
         acc.add(p0 + p1);
+        if constexpr (AM) {
+            float m = -FLT_MAX;
+#pragma unroll
+            for (int rr = 0; rr < MR; ++rr) {
+                float lo, hi;
+                upk(stv[rr], lo, hi);
+                m = fmaxf(m, fmaxf(lo, hi));
+            }
+            if (m >= am->v && m > -FLT_MAX) {          // rare: the lowest index holding m
+                long long idx = LLONG_MAX;
+#pragma unroll
+                for (int rr = 0; rr < MR; ++rr) {
+                    float lo, hi;
+                    upk(stv[rr], lo, hi);
+                    if (idx == LLONG_MAX && lo == m) idx = (long long)(base + (size_t)rr * a.W);
+                    if (idx == LLONG_MAX && hi == m) idx = (long long)(base + (size_t)rr * a.W + 1);
+                }
+                if (am_better(m, idx, am->v, am->i)) {
+                    am->v = m;
+                    am->i = idx;
+                }
+            }
+        }
     }
 }
 

@@ -194,3 +194,71 @@ def test_split_producers_are_bit_identical(packed, scalar, storage):
     finally:
         loc.loc_destroy(hp)
         loc.loc_destroy(hs)
+
+
+FUSED = [6, 7, 13, 14, 15, 16]                  # the warp-specialised configurations
+UNFUSED = [1, 3, 8]                             # synchronous and paired: the pass after the step
+
+
+def full_pass_argmax(h):
+    """The argmax pass over the stored tensor (loc_estimate runs it before its own pass)."""
+    e = loc.loc_estimate(h, 0.0, 0)
+    return (e["k"], e["j"], e["i"]), e["p"]
+
+
+@pytest.mark.parametrize("storage", ["f32", "bf16", "f16"])
+@pytest.mark.parametrize("tile", FUSED + UNFUSED)
+def test_fused_argmax_equals_the_argmax_pass(tile, storage):
+    """After a warp-specialised propagation loc_argmax reads the argmax the step kernel itself
+    combined (per-thread running maxima of the stored values, lowest index on ties): the same
+    state and value as the separate pass over the stored tensor, step after step.  The other
+    configurations take the pass, with the same results."""
+    H, W, K = 75, 200, 20
+    rng = np.random.default_rng(100 + tile)
+    occ = (rng.random((H, W)) < 0.15).astype(np.uint8)
+    b = fields.belief_like(occ, K, seed=tile, dtype=np.float32)
+    h = make(occ, K, 0.05, tile=tile, storage=storage)
+    try:
+        loc.loc_set_belief(h, b)
+        for (u, v, w) in [(0.013, -0.041, 0.05), (0.07, 0.02, -0.1), (-0.11, 0.09, 0.0), (0.0, 0.0, 0.0)]:
+            loc.loc_step(h, u, v, w)
+            got = loc.loc_argmax(h)
+            want, p = full_pass_argmax(h)
+            assert got[:3] == want
+            assert abs(got[3] - p) <= 1e-6 * p
+            assert loc.loc_argmax(h) == got            # a second read: the same result
+    finally:
+        loc.loc_destroy(h)
+
+
+@pytest.mark.parametrize("storage", ["f32", "bf16"])
+@pytest.mark.parametrize("tile", [3, 6, 14, 15, 16])
+def test_fused_argmax_ties_and_restart(tile, storage):
+    """Exact ties: a uniform belief on a free map stepped without motion leaves every interior
+    cell with the bit-identical value, so the lowest [K][H][W] index among the maxima must win.
+    A step that removes all mass restarts the session; loc_argmax then falls back to the pass
+    over the uniform restart state (the first free cell of bin 0)."""
+    H, W, K = 60, 128, 12
+    occ = np.zeros((H, W), np.uint8)
+    h = make(occ, K, 0.1, tile=tile, storage=storage)
+    try:
+        loc.loc_set_belief(h, np.ones((K, H, W), np.float32))
+        loc.loc_step(h, 0.0, 0.0, 0.0)
+        got = loc.loc_argmax(h)
+        want, p = full_pass_argmax(h)
+        assert got[:3] == want and abs(got[3] - p) <= 1e-6 * p
+        flat = loc.loc_belief(h).reshape(-1)
+        assert (flat == flat.max()).sum() > 1               # ties exist
+    finally:
+        loc.loc_destroy(h)
+    occ = np.ones((40, 64), np.uint8)
+    occ[18:22, 30:34] = 0
+    h = make(occ, 8, 1.0, tile=tile, storage=storage)
+    try:
+        loc.loc_step(h, 12.0, 0.0, 0.0)                 # everything walks into walls
+        assert loc.loc_stats(h)["n_reinit"] == 1
+        k, j, i, p = loc.loc_argmax(h)
+        assert (k, j, i) == (0, 18, 30)
+        assert abs(p - 1.0 / (8 * 16)) <= 1e-6 / (8 * 16)
+    finally:
+        loc.loc_destroy(h)
