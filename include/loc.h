@@ -223,9 +223,10 @@ loc_status loc_stats(loc_handle h, double* theta_t, double* last_Z, double* logs
  * and hosts whose allocator belongs to another runtime.  The caller owns every buffer:
  *   occ_dev    device uint8 [H][W], nonzero = occupied;
  *   b_in_dev   device float [K][H][W], the belief to propagate (used as given);
- *   b_out_dev  device float [K][H][W], receives the propagated, unnormalised tensor
- *              (Algorithm 1's propagation with the edge correction of Eq. 8);
- *   z_out_dev  device double, receives Z = sum of b_out (the Eq. 9 normaliser);
+ *   b_out_dev  device float [K][H][W], receives the propagated, unnormalised tensor: the
+ *              same shift, map mask, motion blur and edge correction as loc_step, without
+ *              the division by Z;
+ *   z_out_dev  device double, receives Z = the sum of b_out;
  *   dx_m, dy_m translation in metres in the frame of bin 0 (bin k moves by R(2 pi k / K)).
  * From p it uses H, W, K, cell_m, the sigmas and radii and stream; storage must be LOC_F32
  * and the noise isotropic (sigma_cross_cells 0 or equal to sigma_xy_cells).
@@ -379,6 +380,24 @@ typedef struct {
                                       opened the gate) to the end of its propagation */
     double scan_p50_ms, scan_p99_ms, scan_max_ms;   /* scan arrival to the end of its update */
     double first_s, last_s;        /* server clock of the first arrival and last completion */
+    /* Where the time goes.  Device time is measured between CUDA events recorded where each
+     * piece of work could begin (after its ordering waits) and where it ends, so work that
+     * overlaps on the device is counted once per piece. */
+    double batch_device_ms;        /* sum over batched launches (table copy + kernel) */
+    double batch_alg_bytes;        /* their algorithmic HBM bytes: 2 x storage bytes per
+                                      cell-update plus 5 bytes of map fields per map cell */
+    long long n_batches;
+    double scan_device_ms;         /* sum over scan updates (belief map, dithering, ray casts,
+                                      scoring and reweighting) */
+    long long n_scans_timed;
+    double plain_device_ms;        /* sum over plain-path propagations (one loc_step each) */
+    double plain_alg_bytes;
+    long long n_plain;
+    double host_gather_ms;         /* worker thread: taking work from the queues (gate included) */
+    double host_batch_ms;          /* worker thread: preparing and launching the batched tick */
+    double host_scan_ms;           /* worker thread: the scan phase of the ticks (host work and
+                                      launches of the scan updates, up to the last one issued) */
+    double host_plain_ms;          /* worker thread: the plain-path loc_step calls */
 } loc_server_stats_t;
 
 void loc_server_params_default(loc_server_params* p);

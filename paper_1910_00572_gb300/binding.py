@@ -80,7 +80,13 @@ class loc_server_stats_t(ctypes.Structure):
                 ("step_p99_ms", ctypes.c_double), ("step_max_ms", ctypes.c_double),
                 ("scan_p50_ms", ctypes.c_double), ("scan_p99_ms", ctypes.c_double),
                 ("scan_max_ms", ctypes.c_double), ("first_s", ctypes.c_double),
-                ("last_s", ctypes.c_double)]
+                ("last_s", ctypes.c_double), ("batch_device_ms", ctypes.c_double),
+                ("batch_alg_bytes", ctypes.c_double), ("n_batches", ctypes.c_longlong),
+                ("scan_device_ms", ctypes.c_double), ("n_scans_timed", ctypes.c_longlong),
+                ("plain_device_ms", ctypes.c_double), ("plain_alg_bytes", ctypes.c_double),
+                ("n_plain", ctypes.c_longlong), ("host_gather_ms", ctypes.c_double),
+                ("host_batch_ms", ctypes.c_double), ("host_scan_ms", ctypes.c_double),
+                ("host_plain_ms", ctypes.c_double)]
 
 
 class loc_estimate_t(ctypes.Structure):

@@ -1,6 +1,7 @@
 // C-ABI of the localizer: session state on the host, device buffers, odometry bookkeeping
 // (Section III-A, Eq. 2, the Alg. 1 gate) and the launches of the device kernels.
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -76,8 +77,12 @@ void taps(double sigma, int r, float* out) {
     for (int d = 0; d <= 2 * r; ++d) out[d] = (float)(g[d] / sum);
 }
 
+// Kernel radius: the given one, else ceil(3 sigma).  A sigma that is not finite, or whose
+// radius would exceed every supported maximum, gives INT_MAX (rejected by the callers' radius
+// checks) without converting an out-of-range double to int.
 int radius(double sigma, int given) {
     if (given >= 0) return given;
+    if (std::isnan(sigma) || !(3.0 * sigma <= 1024.0)) return INT_MAX;
     return sigma <= 0.0 ? 0 : (int)std::ceil(3.0 * sigma);
 }
 

@@ -186,13 +186,18 @@ LOC_API loc_status loc_propagate_noalloc(const loc_params* p, const uint8_t* occ
     if (p->storage != LOC_F32) return noalloc_fail(LOC_ERR_INVALID_ARG, "storage must be LOC_F32");
     if (!(p->cell_m > 0.0) || !std::isfinite(p->cell_m) || !std::isfinite(dx_m) || !std::isfinite(dy_m))
         return noalloc_fail(LOC_ERR_INVALID_ARG, "cell_m and the translation must be finite, cell_m > 0");
-    if (!(p->sigma_xy_cells >= 0.0) || !(p->sigma_theta_bins >= 0.0))
-        return noalloc_fail(LOC_ERR_INVALID_ARG, "sigmas must be >= 0");
+    if (!(p->sigma_xy_cells >= 0.0) || !(p->sigma_theta_bins >= 0.0) || !std::isfinite(p->sigma_xy_cells) ||
+        !std::isfinite(p->sigma_theta_bins) || !std::isfinite(p->sigma_cross_cells))
+        return noalloc_fail(LOC_ERR_INVALID_ARG, "sigmas must be finite and >= 0");
     if (p->sigma_cross_cells != 0.0 && p->sigma_cross_cells != p->sigma_xy_cells)
         return noalloc_fail(LOC_ERR_INVALID_ARG, "anisotropic noise (sigma_cross_cells) needs a session (loc_create)");
+    // the default radius ceil(3 sigma) is checked against the maxima before any conversion to int
+    if ((p->r_xy < 0 && 3.0 * p->sigma_xy_cells > LOC_MAX_R_XY) ||
+        (p->r_theta < 0 && 3.0 * p->sigma_theta_bins > LOC_MAX_R_THETA))
+        return noalloc_fail(LOC_ERR_INVALID_ARG, "kernel radius above LOC_MAX_R_XY / LOC_MAX_R_THETA");
     const int rxy = p->r_xy >= 0 ? p->r_xy : (p->sigma_xy_cells <= 0.0 ? 0 : (int)std::ceil(3.0 * p->sigma_xy_cells));
     const int rth = p->r_theta >= 0 ? p->r_theta : (p->sigma_theta_bins <= 0.0 ? 0 : (int)std::ceil(3.0 * p->sigma_theta_bins));
-    if (rxy > LOC_MAX_R_XY || rth > LOC_MAX_R_THETA)
+    if (rxy < 0 || rth < 0 || rxy > LOC_MAX_R_XY || rth > LOC_MAX_R_THETA)
         return noalloc_fail(LOC_ERR_INVALID_ARG, "kernel radius above LOC_MAX_R_XY / LOC_MAX_R_THETA");
     const unsigned int gx = (unsigned int)((p->W + TW - 1) / TW), gy = (unsigned int)((p->H + TH - 1) / TH);
     if ((unsigned long long)gx * gy > kNoAllocMaxBlocks)

@@ -67,10 +67,16 @@ struct SrvSession {
     bool scan_pending = false;         // a scan update was launched since its last propagation
 };
 
+// Categories of timed device work: the batched launch, a scan update, a plain loc_step.
+enum { WORK_BATCH = 0, WORK_SCAN = 1, WORK_PLAIN = 2 };
+
 struct Inflight {
     cudaEvent_t ev;
     int kind;
     std::vector<double> t_arr;
+    cudaEvent_t ev0 = nullptr;         // timing start (recorded where the work could begin)
+    int work = WORK_BATCH;
+    double bytes = 0.0;                // algorithmic HBM bytes of the work (propagations)
 };
 
 constexpr int kRing = 64;              // batch events kept for scan ordering
@@ -119,6 +125,10 @@ struct loc_server_s {
     std::vector<double> lat_step, lat_scan;
     long long n_ticks = 0, n_msgs = 0, n_props = 0, n_scans = 0, n_batched = 0, n_in_batches = 0;
     double cells = 0.0, first_s = -1.0, last_s = 0.0;
+    // device time per category of work (event pairs) and the worker's host time per tick phase
+    double dev_ms[3] = {0.0, 0.0, 0.0}, dev_bytes[3] = {0.0, 0.0, 0.0};
+    long long dev_n[3] = {0, 0, 0};
+    double host_gather_ms = 0.0, host_batch_ms = 0.0, host_scan_ms = 0.0, host_plain_ms = 0.0;
 
     double now() const {
         return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -155,13 +165,22 @@ cudaEvent_t get_event(loc_server s) {
         }
     }
     cudaEvent_t e = nullptr;
-    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;   // timing enabled: ends of timed work
     return e;
 }
 
-void push_inflight(loc_server s, cudaEvent_t ev, int kind, std::vector<double>&& t_arr) {
+void push_inflight(loc_server s, cudaEvent_t ev, int kind, std::vector<double>&& t_arr, cudaEvent_t ev0 = nullptr,
+                   int work = WORK_BATCH, double bytes = 0.0) {
     std::lock_guard<std::mutex> lk(s->mu_inf);
-    s->inflight.push_back(Inflight{ev, kind, std::move(t_arr)});
+    Inflight f{ev, kind, std::move(t_arr)};
+    f.ev0 = ev0;
+    f.work = work;
+    f.bytes = bytes;
+    s->inflight.push_back(std::move(f));
+}
+
+double ms_since(std::chrono::steady_clock::time_point t) {
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t).count();
 }
 
 void note_arrival(loc_server s, double t) {
@@ -188,6 +207,11 @@ void completer_main(loc_server s) {
                     cudaGetLastError();
                     failure = std::string("device work failed: ") + cudaGetErrorString(q);
                 }
+                float dms = -1.0f;
+                if (it->ev0 && q == cudaSuccess && cudaEventElapsedTime(&dms, it->ev0, it->ev) != cudaSuccess) {
+                    cudaGetLastError();
+                    dms = -1.0f;
+                }
                 {
                     std::lock_guard<std::mutex> ls(s->mu_st);
                     for (double a : it->t_arr) {
@@ -195,7 +219,13 @@ void completer_main(loc_server s) {
                         s->n_msgs += 1;
                     }
                     s->last_s = std::max(s->last_s, t);
+                    if (dms >= 0.0f) {
+                        s->dev_ms[it->work] += dms;
+                        s->dev_bytes[it->work] += it->bytes;
+                        s->dev_n[it->work] += 1;
+                    }
                 }
+                if (it->ev0) s->ev_free.push_back(it->ev0);
                 s->ev_free.push_back(it->ev);
                 it = s->inflight.erase(it);
                 any = true;
@@ -378,12 +408,13 @@ bool launch(loc_server s, TickWork& t) {
                 e = cudaStreamWaitEvent(s->core.bs, pr.first->scan_ev, 0);
                 pr.first->scan_pending = false;
             }
+        const auto tb = std::chrono::steady_clock::now();
         BatchTick* ht = nullptr;
         Shift* hs = nullptr;
         if (e == cudaSuccess) e = batch_begin(&s->core, &ht, &hs);
         std::vector<char> active(s->core.sess.size(), 0);
         std::vector<double> arr;
-        double cells = 0.0;
+        double cells = 0.0, bytes = 0.0;
         if (e == cudaSuccess) {
             for (auto& pr : t.props) {
                 loc_session* h = pr.first->h;
@@ -392,11 +423,15 @@ bool launch(loc_server s, TickWork& t) {
                 shift_table(h, batch_shift_slot(&s->core, hs, ci));
                 active[(size_t)ci] = 1;
                 arr.push_back(pr.second);
-                cells += (double)h->p.H * h->p.W * h->p.K;
+                const double hw = (double)h->p.H * h->p.W;
+                cells += hw * h->p.K;
+                bytes += hw * h->p.K * 2.0 * (double)h->elem + hw * 5.0;   // read + write X, map fields
             }
         }
+        cudaEvent_t ev0 = e == cudaSuccess ? get_event(s) : nullptr;
         cudaEvent_t ev = e == cudaSuccess ? get_event(s) : nullptr;
-        if (e == cudaSuccess && !ev) e = cudaErrorMemoryAllocation;
+        if (e == cudaSuccess && (!ev || !ev0)) e = cudaErrorMemoryAllocation;
+        if (e == cudaSuccess) e = cudaEventRecord(ev0, s->core.bs);
         if (e == cudaSuccess) e = batch_launch(&s->core, active, ev, false);
         if (e == cudaSuccess) e = cudaEventRecord(s->ring[s->tick % kRing], s->core.bs);
         if (e != cudaSuccess) {
@@ -413,11 +448,18 @@ bool launch(loc_server s, TickWork& t) {
             s->n_batched += 1;
             s->n_in_batches += (long long)t.props.size();
             s->cells += cells;
+            s->host_batch_ms += ms_since(tb);
         }
-        push_inflight(s, ev, MSG_ODO, std::move(arr));
+        push_inflight(s, ev, MSG_ODO, std::move(arr), ev0, WORK_BATCH, bytes);
     }
+    const auto tp = std::chrono::steady_clock::now();
     for (auto& pm : t.plain) {                        // the plain path: one loc_step each
         SrvSession* ss = pm.first;
+        cudaEvent_t ev0 = get_event(s);
+        if (!ev0 || cudaEventRecord(ev0, s->pool[(size_t)ss->stream_idx]) != cudaSuccess) {
+            set_failed(s, "event record failed");
+            return false;
+        }
         const loc_status st = loc_step(ss->h, pm.second.u, pm.second.v, pm.second.w);
         if (st < 0) {
             set_failed(s, std::string("loc_step: ") + loc_last_error(ss->h));
@@ -429,16 +471,26 @@ bool launch(loc_server s, TickWork& t) {
                 set_failed(s, "event record failed");
                 return false;
             }
+            const double hw = (double)ss->p.H * ss->p.W;
             {
                 std::lock_guard<std::mutex> ls(s->mu_st);
                 s->n_props += 1;
-                s->cells += (double)ss->p.H * ss->p.W * ss->p.K;
+                s->cells += hw * ss->p.K;
             }
-            push_inflight(s, ev, MSG_ODO, std::vector<double>{pm.second.t_arr});
+            push_inflight(s, ev, MSG_ODO, std::vector<double>{pm.second.t_arr}, ev0, WORK_PLAIN,
+                          hw * ss->p.K * 2.0 * (double)ss->h->elem + hw * 5.0);
         } else {
-            std::lock_guard<std::mutex> ls(s->mu_st);
-            s->n_msgs += 1;
+            {
+                std::lock_guard<std::mutex> ls(s->mu_st);
+                s->n_msgs += 1;
+            }
+            std::lock_guard<std::mutex> li(s->mu_inf);
+            s->ev_free.push_back(ev0);                // nothing to time: the gate held the message
         }
+    }
+    if (!t.plain.empty()) {
+        std::lock_guard<std::mutex> ls(s->mu_st);
+        s->host_plain_ms += ms_since(tp);
     }
     // Scan updates: distinct sessions on their own streams.  Their host work (direction tables,
     // uploads, launches) runs on up to kScanThreads threads.
@@ -455,6 +507,8 @@ bool launch(loc_server s, TickWork& t) {
             cudaError_t we = cudaSuccess;
             if (s->prm.batching && ss->last_prop_tick >= 0)
                 we = cudaStreamWaitEvent(ps, s->ring[ss->last_prop_tick % kRing], 0);
+            cudaEvent_t ev0 = we == cudaSuccess ? get_event(s) : nullptr;
+            if (we == cudaSuccess) we = ev0 ? cudaEventRecord(ev0, ps) : cudaErrorMemoryAllocation;
             if (we != cudaSuccess) {
                 set_failed(s, std::string("scan ordering: ") + cudaGetErrorString(we));
                 bad = true;
@@ -481,17 +535,20 @@ bool launch(loc_server s, TickWork& t) {
                 std::lock_guard<std::mutex> ls(s->mu_st);
                 s->n_scans += 1;
             }
-            push_inflight(s, ev, MSG_SCAN, std::vector<double>{t.scans[(size_t)i].second.t_arr});
+            push_inflight(s, ev, MSG_SCAN, std::vector<double>{t.scans[(size_t)i].second.t_arr}, ev0, WORK_SCAN);
         }
     };
     const int nthreads = (int)std::min<size_t>(kScanThreads, t.scans.size());
     if (nthreads > 0) {
+        const auto ts = std::chrono::steady_clock::now();
         std::vector<std::thread> helpers;
         for (int k = 1; k < nthreads; ++k) helpers.emplace_back(scan_worker);
         scan_worker();
         for (std::thread& th : helpers) th.join();
         for (auto& pm : t.scans) delete pm.second.scan;     // left over after a failure
         if (bad.load()) return false;
+        std::lock_guard<std::mutex> ls(s->mu_st);
+        s->host_scan_ms += ms_since(ts);
     }
     {
         std::lock_guard<std::mutex> ls(s->mu_st);
@@ -513,7 +570,12 @@ void worker_main(loc_server s) {
         TickWork t;
         {
             std::unique_lock<std::mutex> lk(s->mu);
+            const auto tg = std::chrono::steady_clock::now();
             gather(s, t);
+            if (!t.empty()) {
+                std::lock_guard<std::mutex> ls(s->mu_st);
+                s->host_gather_ms += ms_since(tg);
+            }
             if (t.empty()) {
                 s->busy = false;
                 s->cv_done.notify_all();
@@ -771,6 +833,18 @@ LOC_API loc_status loc_server_stats(loc_server s, loc_server_stats_t* o) {
         o->mean_batch = s->n_batched ? (double)s->n_in_batches / (double)s->n_batched : 0.0;
         o->first_s = s->first_s;
         o->last_s = s->last_s;
+        o->batch_device_ms = s->dev_ms[WORK_BATCH];
+        o->batch_alg_bytes = s->dev_bytes[WORK_BATCH];
+        o->n_batches = s->dev_n[WORK_BATCH];
+        o->scan_device_ms = s->dev_ms[WORK_SCAN];
+        o->n_scans_timed = s->dev_n[WORK_SCAN];
+        o->plain_device_ms = s->dev_ms[WORK_PLAIN];
+        o->plain_alg_bytes = s->dev_bytes[WORK_PLAIN];
+        o->n_plain = s->dev_n[WORK_PLAIN];
+        o->host_gather_ms = s->host_gather_ms;
+        o->host_batch_ms = s->host_batch_ms;
+        o->host_scan_ms = s->host_scan_ms;
+        o->host_plain_ms = s->host_plain_ms;
         a = s->lat_step;
         b = s->lat_scan;
     }
@@ -792,6 +866,11 @@ LOC_API loc_status loc_server_reset_stats(loc_server s) {
     s->cells = 0.0;
     s->first_s = -1.0;
     s->last_s = 0.0;
+    for (int w = 0; w < 3; ++w) {
+        s->dev_ms[w] = s->dev_bytes[w] = 0.0;
+        s->dev_n[w] = 0;
+    }
+    s->host_gather_ms = s->host_batch_ms = s->host_scan_ms = s->host_plain_ms = 0.0;
     return LOC_OK;
 }
 

@@ -110,3 +110,23 @@ def test_anisotropic_arguments_fail_without_gpu_work(libloc):
     with pytest.raises(loc.LocError) as e:
         loc.loc_propagate_noalloc(p, 256, 256, 256, 256, 0.0, 0.0)
     assert e.value.status == loc.LOC_ERR_INVALID_ARG and "anisotropic" in loc.loc_last_error()
+
+
+def test_huge_or_infinite_sigmas_are_rejected_before_any_conversion(libloc):
+    """A default radius ceil(3 sigma) beyond every maximum (or an infinite sigma) is refused
+    with INVALID_ARG by the session and the allocation-free call alike, before the pointers
+    are touched and without converting an out-of-range double to int."""
+    import math
+    import paper_1910_00572_gb300 as loc
+    import numpy as np
+    occ = np.zeros((8, 8), np.uint8)
+    for field in ("sigma_xy_cells", "sigma_theta_bins"):
+        for bad in (1e12, 1e300, math.inf, 2.0):
+            p = loc.loc_params_default(H=8, W=8, K=4, cell_m=0.1, **{field: bad})
+            with pytest.raises(loc.LocError) as e:
+                loc.loc_create(occ, p)
+            assert e.value.status == loc.LOC_ERR_INVALID_ARG
+            with pytest.raises(loc.LocError) as e:
+                loc.loc_propagate_noalloc(p, 256, 256, 256, 256, 0.0, 0.0)
+            assert e.value.status == loc.LOC_ERR_INVALID_ARG
+            assert "radius" in loc.loc_last_error() or "finite" in loc.loc_last_error()

@@ -22,13 +22,35 @@ def built():
     loc.lib()
 
 
-def test_noalloc_matches_session_step_twice():
+def _occ(H, W, seed):
+    """An office-plan crop of H x W cells (a larger plan when the crop needs it)."""
+    side = max(256, 1 << (max(H, W) - 1).bit_length())
+    big = floorplan.office_map(seed, size=side)
+    return floorplan.crop(big, (side - H) // 2, (side - W) // 2, H, W)
+
+
+# (H, W, K, sigma_xy_cells, sigma_theta_bins): the office crop of the first version; ragged H
+# and W (multiples of neither the 16-row nor the 32-column tile); no x/y blur (radius 0);
+# K = 4 with a theta radius of 4 (the ring of 9 planes wraps the 4 bins more than once); and
+# 2048 x 2048 cells, exactly the 8192 tiles the scratch array holds.
+CASES = [
+    (96, 112, 12, 0.5, 1.0),
+    (101, 75, 12, 0.5, 1.0),
+    (96, 112, 12, 0.0, 1.0),
+    (80, 72, 4, 0.5, 1.2),
+    (2048, 2048, 2, 0.5, 1.0),
+]
+
+
+@pytest.mark.parametrize("H,W,K,sxy,sth", CASES, ids=[f"{c[0]}x{c[1]}x{c[2]}_s{c[3]}_{c[4]}" for c in CASES])
+def test_noalloc_matches_session_step_twice(H, W, K, sxy, sth):
     import torch
-    occ = floorplan.crop(floorplan.office_map(7, size=256), 40, 30, 96, 112)
-    H, W, K, cell = occ.shape[0], occ.shape[1], 12, 0.05
+    occ = _occ(H, W, 7)
+    cell = 0.05
     b = fields.belief_like(occ, K, seed=3, dtype=np.float32)
     dev = torch.device("cuda", 0)
-    p = loc.loc_params_default(H=H, W=W, K=K, cell_m=cell, stream=loc.torch_stream())
+    p = loc.loc_params_default(H=H, W=W, K=K, cell_m=cell, sigma_xy_cells=sxy, sigma_theta_bins=sth,
+                               stream=loc.torch_stream())
     occ_d = torch.from_numpy(occ).to(dev)
     cur = torch.from_numpy(b).to(dev)
     out = torch.empty_like(cur)
