@@ -13,6 +13,9 @@ What is here, each function citing the passage it follows:
                 Eq. 5-7, mask, edge normalisation of Eq. 8), the normaliser eta of Eq. 9 --
                 FP64, direct sums (the 3-D convolution is the plain triple sum with the joint
                 kernel exp(-1/2 d^T Sigma^-1 d), not a separable pass).
+* ``cprop``     the propagation of ``filter`` restated in plain C (``prop.c``): the same
+                direct sums in the same order, bit-identical, with the channels spread over
+                OpenMP threads, for long trajectories and the all-cores CPU baseline.
 * ``aniso``     Eq. 5-6 with sigma_x != sigma_y: the motion kernel rotated to each output
                 channel's heading, the per-channel 3-D convolution and edge correction --
                 FP64, direct sums.

@@ -12,7 +12,7 @@ from scipy import signal
 from oracle import filter as F
 from oracle import readout as R
 from oracle.odometry import Odometry
-from synth import floorplan
+from synth import fields, floorplan
 
 
 def gauss1d(sigma, r):
@@ -366,3 +366,46 @@ def test_estimate_of_a_point_mass_and_of_two_blobs():
     e = R.estimate(b, c, 0.0, 0.3, 0)
     assert abs(e["mass_near"] - (0.3 + 0.1 * 0 + 0.01)) < 1e-15   # bins 7 and 1 are excluded
     assert (e["second_j"], e["second_i"]) == (5, 9)
+
+
+# ------------------------------------------------------------------ the C restatement
+
+@pytest.mark.parametrize("H,W,K,sxy,sth,shift", [
+    (23, 31, 8, 0.5, 1.0, (0.37, -1.61)),      # ragged grid, sub-cell shift
+    (16, 16, 3, 0.5, 1.2, (2.0, 0.0)),         # K below the theta ring (radius 4), integer shift
+    (12, 40, 5, 0.0, 1.0, (-0.5, 0.25)),       # no x/y blur (radius 0)
+    (9, 7, 4, 1.3, 0.0, (5.2, -7.9)),          # x/y radius 4 on a grid smaller than the window; no theta blur
+])
+def test_c_propagation_is_bit_identical_to_the_numpy_definition(H, W, K, sxy, sth, shift):
+    """oracle.cprop restates Algorithm 1's propagation in C with the same double operations in
+    the same order: every value equals the numpy definition's bit for bit, on any thread
+    count (the threads split the channels, not the sums)."""
+    from oracle import cprop
+    rng = np.random.default_rng(H * W + K)
+    occ = (rng.random((H, W)) < 0.2).astype(np.uint8)
+    occ[0, 0] = 0
+    M = F.traversability(occ)
+    g = F.motion_kernel(sxy, sth)
+    corr = F.edge_correction(M, K, g)
+    B = fields.belief_like(occ, K, seed=H)
+    sh = np.array([[shift[0] * math.cos(0.7 * k) - shift[1] * math.sin(0.7 * k),
+                    shift[0] * math.sin(0.7 * k) + shift[1] * math.cos(0.7 * k)] for k in range(K)])
+    want = F.propagate(B, M, corr, sh, g)
+    for threads in (1, 3):
+        got = cprop.propagate(B, M, corr, sh, g, threads)
+        assert np.array_equal(got, want)
+
+
+def test_c_filter_follows_the_numpy_filter():
+    """The Filter on the C propagation follows the numpy Filter's trajectory bit for bit (the
+    normalisation is the same numpy code)."""
+    from oracle import cprop
+    occ = floorplan.rooms_map(0, size=32)
+    a = F.Filter(occ, 8, 0.1)
+    b = cprop.Filter(occ, 8, 0.1, threads=2)
+    rng = np.random.default_rng(0)
+    for _ in range(5):
+        u, v, w = rng.normal(0, 0.07, 3)
+        a.step(u, v, w)
+        b.step(u, v, w)
+    assert np.array_equal(a.B, b.B) and a.logscale == b.logscale and a.last_Z == b.last_Z
