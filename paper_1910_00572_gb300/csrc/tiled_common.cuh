@@ -269,12 +269,29 @@ template <> __device__ __forceinline__ void store2<__nv_bfloat16>(__nv_bfloat16*
                                                                   f2& st) {
     float a, b;
     upk(v, a, b);
-    const uint32_t ua = __float_as_uint(a) + (h & 0xFFFFu);
-    const uint32_t ub = __float_as_uint(b) + (h >> 16);
-    *reinterpret_cast<uint32_t*>(p) = __byte_perm(ua, ub, 0x7632);   // high halves: {a, b}
+    // one stochastically rounded pair (cvt.rs): a value rounds up iff its 16 discarded mantissa
+    // bits plus 16 random bits carry into the kept ones -- b takes the high half of h, a the low
+    // half -- so each rounds up with probability equal to its discarded fraction (unbiased)
+    uint32_t d;
+    asm("cvt.rs.bf16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(b), "f"(a), "r"(h));
+    *reinterpret_cast<uint32_t*>(p) = d;               // {a, b} in memory order
     // the stochastic rounding is unbiased: Z takes the unrounded values (within ~1e-7)
     sum = fadd2(sum, v);
-    st = pk(__uint_as_float(ua & 0xFFFF0000u), __uint_as_float(ub & 0xFFFF0000u));
+    st = pk(__uint_as_float(d << 16), __uint_as_float(d & 0xFFFF0000u));
+}
+
+// Stratified random bits for the stochastic rounding of a thread's cells.  The thread draws one
+// uniform 16-bit number u per plane; cell i of its group of eight (row rr: cell 2 rr in the low
+// half of the word, 2 rr + 1 in the high half) uses u with its top three bits XOR-ed by i in
+// bit-reversed order.  Each cell's number is still uniform, so each rounding stays unbiased, but
+// the eight numbers fall one in each eighth of [0, 2^16): the group's round-ups are spread
+// evenly instead of independently, which keeps the rounding error of the group's (and of a
+// pair's) sum small.  That is the error that random-walks the mass between hypotheses when
+// the belief is concentrated.  sr_word(h) puts u = the low 16 bits of h in both halves.
+__device__ __forceinline__ uint32_t sr_word(uint32_t h) { return __byte_perm(h, 0u, 0x1010); }
+__device__ __forceinline__ uint32_t sr_row_bits(uint32_t w, int rr) {
+    constexpr uint32_t kRev[8] = {0, 4, 2, 6, 1, 5, 3, 7};   // 3-bit bit reversal
+    return w ^ ((kRev[(2 * rr + 1) & 7] << 29) | (kRev[(2 * rr) & 7] << 13));
 }
 template <> __device__ __forceinline__ void store2<__half>(__half* p, f2 v, uint32_t, f2& sum, f2& st) {
     float a, b;
@@ -416,7 +433,7 @@ __device__ __forceinline__ void p_pass(const float (*X)[XW_PITCH], float (*wrap)
         if (o >= K) o -= K;
         const size_t base = ((size_t)o * a.H + (ty0 + r0)) * a.W + gx;
         T* out = static_cast<T*>(a.B_out) + base;
-        const uint32_t h = sizeof(T) == 2 ? pcg_hash((uint32_t)base ^ a.seed) : 0u;
+        const uint32_t h = sizeof(T) == 2 ? sr_word(pcg_hash((uint32_t)base ^ a.seed)) : 0u;
         int rows = a.H - (ty0 + r0);                   // rows of this thread inside the grid
         if constexpr (C::CR > C::TH) rows = min(rows, C::TH - r0);   // ... and inside the tile
         const bool full = rows >= MR && gx < a.W;
@@ -429,7 +446,7 @@ __device__ __forceinline__ void p_pass(const float (*X)[XW_PITCH], float (*wrap)
             for (int d = 1; d < RING; ++d) t = ffma2(tp.gt[d], ring[(PH + 1 + d) % RING][rr], t);
             const f2 v = fmul2(cs[rr], t);
             // 32 random bits per row: the thread's hash with a per-row odd constant mixed in
-            const uint32_t hr = h ^ (0x9E3779B9u * (uint32_t)(2 * rr + 1));
+            const uint32_t hr = sr_row_bits(h, rr);
             stv[rr] = pk(-FLT_MAX, -FLT_MAX);
             if (full || (rr < rows && gx < a.W)) store2<T>(out + (size_t)rr * a.W, v, hr, part, stv[rr]);
         }

@@ -209,7 +209,7 @@ __device__ __forceinline__ void p_pass(const float (*X)[XPW], float (*wrap)[C::T
         int o = p - RT;
         if (o >= K) o -= K;
         T* out = out_tile + (size_t)o * plane;
-        const uint32_t h = sizeof(T) == 2 ? pcg_hash((h_tile + (uint32_t)o * (uint32_t)plane) ^ a.seed) : 0u;
+        const uint32_t h = sizeof(T) == 2 ? sr_word(pcg_hash((h_tile + (uint32_t)o * (uint32_t)plane) ^ a.seed)) : 0u;
         f2 part = 0ull;
 #pragma unroll
         for (int rr = 0; rr < MR; ++rr) {
@@ -217,7 +217,7 @@ __device__ __forceinline__ void p_pass(const float (*X)[XPW], float (*wrap)[C::T
 #pragma unroll
             for (int d = 1; d < RING; ++d) t = ffma2(tp.gt[d], ring[(PH + 1 + d) % RING][rr], t);
             const f2 v = fmul2(cs[rr], t);
-            const uint32_t hr = h ^ (0x9E3779B9u * (uint32_t)(2 * rr + 1));
+            const uint32_t hr = sr_row_bits(h, rr);
             const bool in = rr < rows;
             store_pair<T>(out + (size_t)rr * a.W, v, hr, in && ok0, in && ok1, part);
         }

@@ -10,6 +10,7 @@ import math
 import numpy as np
 import pytest
 
+import bounds
 import paper_1910_00572_gb300 as loc
 from oracle import filter as F
 from oracle import readout as R
@@ -185,8 +186,13 @@ def test_all_mass_removed_restarts_uniform():
     h = make(occ, 2, 1.0, sigma_xy_cells=0.0, sigma_theta_bins=0.0)
     try:
         loc.loc_step(h, 6.0, 0.0, 0.0)                 # every hypothesis walks into a wall
+        assert loc.loc_sync(h) == loc.LOC_WARN_REINIT   # reported once ...
+        assert loc.loc_sync(h) == loc.LOC_OK            # ... per new restart
         st = loc.loc_stats(h)
         b = loc.loc_belief(h)
+        loc.loc_step(h, 6.0, 0.0, 0.0)                 # the uniform restart walks into the walls again
+        assert loc.loc_sync(h) == loc.LOC_WARN_REINIT
+        assert loc.loc_stats(h)["n_reinit"] == 2
     finally:
         loc.loc_destroy(h)
     assert st["n_reinit"] == 1 and st["last_Z"] == 0.0
@@ -272,6 +278,49 @@ def test_office512_one_step_replay_sampled():
     assert err.max() <= ABS_TOL and err.max() <= REL_TOL * b_in.max(), err.max()
     # Z is the FP64 sum of the stored tensor (a property at any size)
     assert abs(got.astype(np.float64).sum() - 1.0) < 1e-5
+
+
+@pytest.mark.slow
+def test_office2048_bf16_one_step_replay_sampled():
+    """The 2048 x 2048 x 72 BF16 office workload at full size (302 M states), one step through
+    the tile configuration the benchmark times (the session default): 3000 random states, the
+    neighbourhoods of the ten largest input values, and the GPU's argmax state, each recomputed
+    from the definitions by the oracle from the same stored input.  Every state is within one
+    BF16 stochastic-rounding step of its own exact value plus the FP32 error (tests/bounds.py),
+    the argmax state holds at least every checked state's value, and the tensor sums to 1."""
+    wl = workloads.get("office2048")
+    occ = workloads.make_map(wl)
+    K, cell = wl["K"], wl["cell"]
+    H, W = occ.shape
+    h = make(occ, K, cell, storage="bf16")
+    u, v, w = 0.0137, -0.0061, 0.003
+    try:
+        loc.loc_set_belief(h, fields.belief_like(occ, K, seed=21, dtype=np.float32))
+        before = loc.loc_belief(h)                      # the stored BF16 input, normalised
+        loc.loc_step(h, u, v, w)
+        got = loc.loc_belief(h)
+        Z = loc.loc_stats(h)["last_Z"]
+        ak, aj, ai, _ = loc.loc_argmax(h)
+    finally:
+        loc.loc_destroy(h)
+    odo = Odometry(K, cell)
+    odo.add(u, v, w)
+    M = F.traversability(occ)
+    g = F.motion_kernel(wl["sigma_xy_cells"], wl["sigma_theta_bins"])
+    rng = np.random.default_rng(8)
+    idx = [(int(rng.integers(K)), int(rng.integers(H)), int(rng.integers(W))) for _ in range(3000)]
+    for q in np.argpartition(before.reshape(-1), -10)[-10:]:
+        k, rem = divmod(int(q), H * W)
+        j, i = rem // W, rem % W
+        idx += [(k, jj, ii) for jj in range(max(0, j - 2), min(H, j + 3)) for ii in range(max(0, i - 2), min(W, i + 3))]
+    idx.append((ak, aj, ai))
+    T = F.propagate_at(before.astype(np.float64), M, odo.shifts(), g, idx)
+    gotT = np.array([got[k, j, i] for (k, j, i) in idx], np.float64) * Z
+    bound = bounds.bf16_step_bound(T)
+    bad = np.flatnonzero(np.abs(gotT - T) > bound)
+    assert bad.size == 0, [(idx[b], gotT[b], T[b], bound[b]) for b in bad[:5]]
+    assert T[-1] >= T.max() - 2.0 * bounds.bf16_step_bound(T.max())
+    assert abs(got.astype(np.float64).sum() - 1.0) < 1e-4
 
 
 @pytest.mark.parametrize("storage", ["f32", "bf16", "f16"])
