@@ -49,6 +49,10 @@ typedef enum {
     LOC_OK = 0,
     LOC_OK_DEFERRED = 1,       /* loc_step: the Alg. 1 gate was not reached; only theta_t
                                   and the accumulated translation changed */
+    LOC_WARN_REINIT = 2,       /* success; since the last report a propagation removed all mass
+                                  (Z == 0) and the belief restarted uniform over free cells.
+                                  Returned once per new restart count by the calls that
+                                  synchronise with the device (loc_sync and the readbacks) */
     LOC_ERR_INVALID_ARG = -1,  /* bad pointer, size, non-finite value, or n mismatch */
     LOC_ERR_OOM = -2,          /* device allocation failed */
     LOC_ERR_CUDA = -3,         /* a CUDA runtime call failed */
@@ -439,6 +443,18 @@ loc_status loc_server_session(loc_server s, int id, int* state, loc_handle* h);
  * and free every session.  s may be NULL. */
 loc_status loc_server_destroy(loc_server s);
 const char* loc_server_last_error(loc_server s);
+
+/* ---- Test hook of the bounded device waits (no paper counterpart).
+ * Every device-side wait of the library gives up after a limit, records LOC_DEV_ERR_TIMEOUT in
+ * the session's status and returns, so a stalled hand-off surfaces as LOC_ERR_TIMEOUT (after
+ * which the handle fails with LOC_ERR_STATE) while the CUDA context stays usable.  This hook
+ * exercises that path on the Floyd-Steinberg block hand-offs of the scan update, whose waits
+ * poll a progress flag in global memory: with stall != 0 every hand-off waits on a flag that
+ * nothing sets, so each wait runs for wait_limit_s and gives up; the sample list of that scan is
+ * empty.  stall = 0, wait_limit_s = 0.2 restore the defaults.  Applies to the current device,
+ * process-wide; not for use while other threads run scan updates.
+ * Errors: INVALID_ARG (wait_limit_s outside (0, 10]), CUDA. */
+loc_status loc_debug_fs_stall(int stall, double wait_limit_s);
 
 /* Wait for all enqueued work of the handle; returns the first device-side error if any. */
 loc_status loc_sync(loc_handle h);

@@ -14,13 +14,13 @@ import os
 import numpy as np
 
 __all__ = [
-    "LOC_OK", "LOC_OK_DEFERRED", "LOC_ERR_INVALID_ARG", "LOC_ERR_OOM", "LOC_ERR_CUDA",
+    "LOC_OK", "LOC_OK_DEFERRED", "LOC_WARN_REINIT", "LOC_ERR_INVALID_ARG", "LOC_ERR_OOM", "LOC_ERR_CUDA",
     "LOC_ERR_TIMEOUT", "LOC_ERR_STATE", "LOC_F32", "LOC_BF16", "LOC_F16", "LOC_MAP_SUM",
     "LOC_MAP_MAX", "LOC_KERNEL_AUTO", "LOC_KERNEL_GENERIC", "LOC_KERNEL_TILED", "LocError", "loc_params", "Handle", "library_path", "lib",
     "loc_params_default", "loc_set_allocator", "loc_create", "loc_step", "loc_lidar_update",
     "loc_lidar_update_cells", "loc_belief", "loc_marginal", "loc_argmax", "loc_set_belief",
     "loc_stats", "loc_sync", "loc_destroy", "loc_last_error", "torch_stream",
-    "use_torch_allocator", "loc_propagate_noalloc", "loc_samples", "loc_dither", "loc_ray_ranges",
+    "use_torch_allocator", "loc_propagate_noalloc", "loc_debug_fs_stall", "loc_samples", "loc_dither", "loc_ray_ranges",
     "loc_range_table", "loc_range_table_read", "loc_lidar_update_dense", "loc_estimate", "loc_map_difficulty",
     "loc_estimate_t",
     "LOC_BATCH_CONFIGS", "Batch", "loc_batch_create", "loc_batch_step", "loc_batch_sync",
@@ -32,7 +32,7 @@ __all__ = [
     "loc_server_reset_stats", "loc_server_session", "loc_server_destroy", "loc_server_last_error",
 ]
 
-LOC_OK, LOC_OK_DEFERRED = 0, 1
+LOC_OK, LOC_OK_DEFERRED, LOC_WARN_REINIT = 0, 1, 2
 LOC_ERR_INVALID_ARG, LOC_ERR_OOM, LOC_ERR_CUDA, LOC_ERR_TIMEOUT, LOC_ERR_STATE = -1, -2, -3, -4, -5
 LOC_F32, LOC_BF16, LOC_F16 = 0, 1, 2
 LOC_MAP_SUM, LOC_MAP_MAX = 0, 1
@@ -124,6 +124,7 @@ _SIGS = {
     "loc_sync": (ctypes.c_int, [_P]),
     "loc_destroy": (ctypes.c_int, [_P]),
     "loc_last_error": (ctypes.c_char_p, [_P]),
+    "loc_debug_fs_stall": (ctypes.c_int, [ctypes.c_int, ctypes.c_double]),
     "loc_propagate_noalloc": (ctypes.c_int, [ctypes.POINTER(loc_params), _P, _P, _P, _P,
                                              ctypes.c_double, ctypes.c_double]),
     "loc_samples": (ctypes.c_int, [_P, _P, ctypes.c_size_t, ctypes.POINTER(ctypes.c_int)]),
@@ -379,8 +380,9 @@ def loc_stats(h: Handle) -> dict:
                 n_reinit=nre.value)
 
 
-def loc_sync(h: Handle) -> None:
-    _check(h, lib().loc_sync(h))
+def loc_sync(h: Handle) -> int:
+    """Wait for the handle's work; LOC_OK, or LOC_WARN_REINIT once after new restarts."""
+    return _check(h, lib().loc_sync(h))
 
 
 def loc_destroy(h: Handle) -> None:
@@ -392,6 +394,11 @@ def loc_destroy(h: Handle) -> None:
 def loc_last_error(h: Handle | None = None) -> str:
     m = lib().loc_last_error(h.ptr if h is not None else None)
     return m.decode() if m else ""
+
+
+def loc_debug_fs_stall(stall: bool, wait_limit_s: float = 0.2) -> None:
+    """Test hook: make the dithering's bounded block hand-offs wait on a flag nothing sets."""
+    _check(None, lib().loc_debug_fs_stall(1 if stall else 0, float(wait_limit_s)))
 
 
 def loc_propagate_noalloc(params: loc_params, occ_dev: int, b_in_dev: int, b_out_dev: int,

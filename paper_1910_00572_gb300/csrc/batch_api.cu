@@ -393,7 +393,7 @@ LOC_API loc_status loc_batch_sync(loc_batch b) {
     if (e != cudaSuccess) return bfail(b, LOC_ERR_CUDA, std::string("loc_batch_sync: ") + cudaGetErrorString(e));
     for (loc_session* h : b->core.sess) {
         const loc_status s = sync_and_check(h);
-        if (s != LOC_OK) return bfail(b, s, "a session of the batch failed: " + h->err);
+        if (s < 0) return bfail(b, s, "a session of the batch failed: " + h->err);
     }
     if (ctl.status & LOC_DEV_ERR_TIMEOUT) return bfail(b, LOC_ERR_TIMEOUT, "device wait timed out");
     return LOC_OK;

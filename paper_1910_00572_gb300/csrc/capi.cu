@@ -2,6 +2,7 @@
 // (Section III-A, Eq. 2, the Alg. 1 gate) and the launches of the device kernels.
 #include <algorithm>
 #include <climits>
+#include <cstddef>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -57,6 +58,15 @@ void* dev_alloc(loc_session* s, size_t bytes) {
 void release_all(loc_session* s) {
     if (s->pinned) cudaFreeHost(s->pinned);
     s->pinned = nullptr;
+    for (int k = 0; k < 2; ++k) {
+        if (s->scan_pin_ev[k]) {
+            cudaEventSynchronize(s->scan_pin_ev[k]);
+            cudaEventDestroy(s->scan_pin_ev[k]);
+        }
+        if (s->scan_pin[k]) cudaFreeHost(s->scan_pin[k]);
+        s->scan_pin[k] = nullptr;
+        s->scan_pin_ev[k] = nullptr;
+    }
     for (void* p : s->owned) {
         if (g_free) g_free(p, (void*)s->stream, g_alloc_ctx);
         else cudaFree(p);
@@ -95,10 +105,21 @@ loc_status check_live(loc_session* h) {
 loc_status sync_and_check(loc_session* h) {
     cudaError_t e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamSynchronize");
-    int status = 0;
-    e = cudaMemcpy(&status, &h->sd->status, sizeof(int), cudaMemcpyDeviceToHost);
+    // the device status and the restart count are adjacent in SessionDev: one copy
+    struct {
+        int status, pad;
+        unsigned long long n_reinit;
+    } d{};
+    static_assert(offsetof(SessionDev, n_reinit) == offsetof(SessionDev, status) + 8, "SessionDev layout");
+    e = cudaMemcpy(&d, &h->sd->status, sizeof(d), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemcpy(status)");
-    return check_status(h, status);
+    const loc_status st = check_status(h, d.status);
+    if (st != LOC_OK) return st;
+    if (d.n_reinit > h->reinit_reported) {         // restarts since the last report
+        h->reinit_reported = d.n_reinit;
+        return LOC_WARN_REINIT;
+    }
+    return LOC_OK;
 }
 
 loc_status check_status(loc_session* h, int status) {
@@ -443,31 +464,83 @@ bool grow(loc_session* h, P*& ptr, int& capn, int n, size_t elem) {
 // Scoring inputs for one scan: the used beams (b % stride == 0, range < r_max), their
 // ranges, the distinct FP32 map-frame directions of every (bin, used beam) pair and the
 // direction index of each pair.  The angle of bin k and beam b is
-// (2 pi / K) k + theta_t + (angle_min + angle_inc b), evaluated in FP64 in that order.
+// (2 pi / K) k + theta_t + (angle_min + angle_inc b), evaluated in FP64 in that order; its
+// cosine and sine are rounded to FP32.  Pairs with the same FP64 angle share one sincos
+// (most of the K x used-beam pairs repeat an angle), and the tables go to the device through
+// pinned staging, so the copies are asynchronous.
 loc_status upload_scan(loc_session* h, const float* ranges, int n_beams, double angle_min, double angle_inc,
                        double r_max, int stride, int* n_used_out, int* n_dirs_out) {
     const int K = h->p.K;
+    int nu = 0;
+    for (int b = 0; b < n_beams; b += stride) nu += ranges[b] < r_max;
+    const size_t npairs = (size_t)K * std::max(nu, 1);
+    // staging slot: [dirs: 2 * npairs floats][z: nu floats][dir_of: npairs ints]
+    const size_t bytes = sizeof(float) * 2 * npairs + sizeof(float) * std::max(nu, 1) + sizeof(int32_t) * npairs;
+    const int slot = h->scan_slot;
+    h->scan_slot ^= 1;
+    if (h->scan_pin_ev[slot]) {
+        cudaError_t e = cudaEventSynchronize(h->scan_pin_ev[slot]);   // its copies have run
+        if (e != cudaSuccess) return cuda_fail(h, e, "scan staging");
+    } else if (cudaEventCreateWithFlags(&h->scan_pin_ev[slot], cudaEventDisableTiming) != cudaSuccess) {
+        h->scan_pin_ev[slot] = nullptr;
+        return fail(h, LOC_ERR_OOM, "scan staging event");
+    }
+    if (h->scan_pin_cap[slot] < bytes) {
+        if (h->scan_pin[slot]) cudaFreeHost(h->scan_pin[slot]);
+        h->scan_pin[slot] = nullptr;
+        h->scan_pin_cap[slot] = 0;
+        const size_t want = std::max(bytes, (size_t)K * 512 * 16);       // room for 512 used beams
+        void* q = nullptr;
+        if (cudaMallocHost(&q, want) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(h, LOC_ERR_OOM, "scan staging (pinned)");
+        }
+        h->scan_pin[slot] = static_cast<unsigned char*>(q);
+        h->scan_pin_cap[slot] = want;
+    }
+    float* dirs = reinterpret_cast<float*>(h->scan_pin[slot]);
+    float* zu = dirs + 2 * npairs;
+    int32_t* dir_of = reinterpret_cast<int32_t*>(zu + std::max(nu, 1));
     std::vector<int> used;
-    std::vector<float> zu;
-    for (int b = 0; b < n_beams; b += stride)
+    used.reserve((size_t)nu);
+    for (int b = 0, u = 0; b < n_beams; b += stride)
         if (ranges[b] < r_max) {
             used.push_back(b);
-            zu.push_back(ranges[b]);
+            zu[u++] = ranges[b];
         }
-    const int nu = (int)used.size();
-    std::vector<float> dirs;
-    std::vector<int32_t> dir_of((size_t)K * std::max(nu, 1));
-    // distinct FP32 direction pairs through an open-addressing table (keys are the bit
-    // patterns of (cos, sin); a zero key marks an empty slot, so that pattern is kept aside)
+    // open-addressing tables: FP64 angle bits -> (cos, sin) as FP32, and the distinct FP32
+    // direction pairs (keys are the bit patterns of (cos, sin); a zero key marks an empty slot,
+    // so that pattern is kept aside)
     size_t cap = 64;
-    while (cap < 2 * (size_t)K * std::max(nu, 1)) cap <<= 1;
+    while (cap < 2 * npairs) cap <<= 1;
+    std::vector<unsigned long long> akeys(cap, 0ull);
+    std::vector<float> acs(2 * cap);
     std::vector<unsigned long long> keys(cap, 0ull);
     std::vector<int> ids(cap, -1);
-    int zero_id = -1;
-    for (int k = 0; k < K; ++k)
+    int zero_id = -1, nd = 0;
+    const double beam0 = angle_min;
+    for (int k = 0; k < K; ++k) {
+        const double ak = (2.0 * M_PI / K) * k + h->theta;
         for (int u = 0; u < nu; ++u) {
-            const double a = (2.0 * M_PI / K) * k + h->theta + (angle_min + angle_inc * used[u]);
-            const float c = (float)std::cos(a), sn = (float)std::sin(a);
+            const double a = ak + (beam0 + angle_inc * used[u]);
+            unsigned long long abits;
+            std::memcpy(&abits, &a, 8);
+            float c, sn;
+            {
+                const unsigned long long akey = abits ? abits : 1ull;   // 0 bits (angle +0.0): key 1, never a double's bits here otherwise
+                size_t slot_a = (size_t)((akey * 0x9E3779B97F4A7C15ull) >> 40) & (cap - 1);
+                while (akeys[slot_a] != 0ull && akeys[slot_a] != akey) slot_a = (slot_a + 1) & (cap - 1);
+                if (akeys[slot_a] == akey) {
+                    c = acs[2 * slot_a];
+                    sn = acs[2 * slot_a + 1];
+                } else {
+                    c = (float)std::cos(a);
+                    sn = (float)std::sin(a);
+                    akeys[slot_a] = akey;
+                    acs[2 * slot_a] = c;
+                    acs[2 * slot_a + 1] = sn;
+                }
+            }
             unsigned int bc, bs;
             std::memcpy(&bc, &c, 4);
             std::memcpy(&bs, &sn, 4);
@@ -476,32 +549,34 @@ loc_status upload_scan(loc_session* h, const float* ranges, int n_beams, double 
             if (key == 0ull) {
                 id = zero_id;
             } else {
-                size_t slot = (size_t)((key * 0x9E3779B97F4A7C15ull) >> 40) & (cap - 1);
-                while (keys[slot] != 0ull && keys[slot] != key) slot = (slot + 1) & (cap - 1);
-                if (keys[slot] == key) id = ids[slot];
-                else keys[slot] = key;
-                if (id < 0) ids[slot] = (int)(dirs.size() / 2);
+                size_t sl = (size_t)((key * 0x9E3779B97F4A7C15ull) >> 40) & (cap - 1);
+                while (keys[sl] != 0ull && keys[sl] != key) sl = (sl + 1) & (cap - 1);
+                if (keys[sl] == key) id = ids[sl];
+                else keys[sl] = key;
+                if (id < 0) ids[sl] = nd;
             }
             if (id < 0) {
-                id = (int)(dirs.size() / 2);
+                id = nd++;
                 if (key == 0ull) zero_id = id;
-                dirs.push_back(c);
-                dirs.push_back(sn);
+                dirs[2 * id] = c;
+                dirs[2 * id + 1] = sn;
             }
             dir_of[(size_t)k * nu + u] = id;
         }
-    const int nd = (int)(dirs.size() / 2);
-    if (!grow(h, h->dirs, h->cap_dirs, nd, 2 * sizeof(float)) ||
-        !grow(h, h->z, h->cap_beams, nu, sizeof(float)) ||
-        !grow(h, h->dir_of, h->cap_dir_of, K * nu, sizeof(int32_t)))
+    }
+    // device tables sized once for this staging capacity, so steady-state scans allocate nothing
+    const int cap_pairs = (int)std::min<size_t>(h->scan_pin_cap[slot] / 16, (size_t)INT_MAX / 2);
+    if (!grow(h, h->dirs, h->cap_dirs, std::max(nd, cap_pairs), 2 * sizeof(float)) ||
+        !grow(h, h->z, h->cap_beams, std::max(nu, cap_pairs / K), sizeof(float)) ||
+        !grow(h, h->dir_of, h->cap_dir_of, std::max(K * nu, cap_pairs), sizeof(int32_t)))
         return fail(h, LOC_ERR_OOM, "scan buffers");
     cudaError_t e = cudaSuccess;
-    if (nd) e = cudaMemcpyAsync(h->dirs, dirs.data(), sizeof(float) * dirs.size(), cudaMemcpyHostToDevice, h->stream);
+    if (nd) e = cudaMemcpyAsync(h->dirs, dirs, sizeof(float) * 2 * (size_t)nd, cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess && nu)
-        e = cudaMemcpyAsync(h->z, zu.data(), sizeof(float) * nu, cudaMemcpyHostToDevice, h->stream);
+        e = cudaMemcpyAsync(h->z, zu, sizeof(float) * nu, cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess && nu)
-        e = cudaMemcpyAsync(h->dir_of, dir_of.data(), sizeof(int32_t) * (size_t)K * nu, cudaMemcpyHostToDevice,
-                            h->stream);
+        e = cudaMemcpyAsync(h->dir_of, dir_of, sizeof(int32_t) * (size_t)K * nu, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(h->scan_pin_ev[slot], h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "scan upload");
     *n_used_out = nu;
     *n_dirs_out = nd;
@@ -545,6 +620,14 @@ loc_status materialize(loc_session* h) {
 }
 
 }  // namespace
+
+LOC_API loc_status loc_debug_fs_stall(int stall, double wait_limit_s) {
+    if (!(wait_limit_s > 0.0) || !(wait_limit_s <= 10.0))
+        return fail(nullptr, LOC_ERR_INVALID_ARG, "wait_limit_s must be in (0, 10]");
+    const cudaError_t e = set_fs_wait(wait_limit_s, stall != 0);
+    if (e != cudaSuccess) return fail(nullptr, LOC_ERR_CUDA, std::string("loc_debug_fs_stall: ") + cudaGetErrorString(e));
+    return LOC_OK;
+}
 
 LOC_API loc_status loc_lidar_update(loc_handle h, const float* ranges, int n_beams, double angle_min,
                                     double angle_inc, double r_max, int beam_stride, double sigma_r) {

@@ -172,6 +172,10 @@ cudaError_t launch_score_reweight(void* B, int storage, const uint8_t* trav, int
 cudaError_t launch_materialize(void* B, int storage, const uint8_t* trav, SessionDev* sd, float value,
                                size_t hw, int K, double* partials, unsigned int nparts, cudaStream_t st);
 
+// The bounded-wait limit of the Floyd-Steinberg block hand-offs on the current device, and the
+// test hook that makes every hand-off wait on a flag nothing sets (stall != 0).
+cudaError_t set_fs_wait(double seconds, int stall);
+
 // Sets the calling thread's error message returned by loc_last_error(NULL).
 void set_thread_error(const char* msg);
 

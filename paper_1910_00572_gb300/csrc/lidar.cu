@@ -16,6 +16,12 @@ namespace {
 constexpr int NT = 256;
 constexpr unsigned long long kSpinNs = 200ull * 1000 * 1000;
 
+// Limit of the bounded waits of the Floyd-Steinberg block hand-offs, and the test hook that
+// makes them wait on a flag nothing sets (so that the limit runs out and the kernel returns
+// with LOC_DEV_ERR_TIMEOUT).  Set by set_fs_wait (loc_debug_fs_stall).
+__device__ unsigned long long g_fs_wait_ns = kSpinNs;
+__device__ int g_fs_stall = 0;
+
 __device__ __forceinline__ unsigned long long gtime() {
     unsigned long long t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -121,6 +127,8 @@ __global__ void __launch_bounds__(kFsWarps * 32) fs_kernel(const float* __restri
     float* ring = fs_ring_all + (size_t)warp * 32 * kFsPitch;
     float* own = ring + lane * kFsPitch;                       // this lane's row
     const float fs = *fs_ptr;
+    const unsigned long long wait_ns = g_fs_wait_ns;
+    const int stall = g_fs_stall;
     const int nrb = (H + 31) / 32, nch = (W + 31) / 32;
     const int vec = (W & 3) == 0 ? 4 : 1;
     const float w7 = 0.4375f, w3 = 0.1875f, w5 = 0.3125f, w1 = 0.0625f;
@@ -186,8 +194,8 @@ __global__ void __launch_bounds__(kFsWarps * 32) fs_kernel(const float* __restri
                 if (lane == 0) {
                     const unsigned long long g0 = gtime();
                     unsigned int it = 0;
-                    while (((volatile int*)prog)[rb] < need) {
-                        if (++it > (1u << 26) || gtime() - g0 > kSpinNs) {
+                    while (stall || ((volatile int*)prog)[rb] < need) {
+                        if (++it > (1u << 26) || gtime() - g0 > wait_ns) {
                             ok = 0;
                             break;
                         }
@@ -254,7 +262,11 @@ __global__ void __launch_bounds__(kFsWarps * 32) fs_kernel(const float* __restri
 
 // Exclusive prefix of the per-row counts (one CTA); total -> *count.
 __global__ void __launch_bounds__(1024) row_scan_kernel(const int* __restrict__ rowcnt, int H,
-                                                        int* __restrict__ rowoff, int* count) {
+                                                        int* __restrict__ rowoff, int* count, const int* status) {
+    if (*(volatile const int*)status & LOC_DEV_ERR_TIMEOUT) {   // the dithering gave up: no samples
+        if (threadIdx.x == 0) *count = 0;
+        return;
+    }
     __shared__ int part[1024];
     const int per = (H + 1023) / 1024;
     const int j0 = threadIdx.x * per;
@@ -278,7 +290,9 @@ __global__ void __launch_bounds__(1024) row_scan_kernel(const int* __restrict__ 
 
 // Linear indices of the selected cells in raster order (one warp per row), at most cap.
 __global__ void __launch_bounds__(NT) compact_kernel(const uint8_t* __restrict__ sel, const int* __restrict__ rowoff,
-                                                     int H, int W, int cap, int32_t* __restrict__ out) {
+                                                     int H, int W, int cap, int32_t* __restrict__ out,
+                                                     const int* status) {
+    if (*(volatile const int*)status & LOC_DEV_ERR_TIMEOUT) return;   // no row offsets were made
     const int lane = threadIdx.x & 31;
     for (int j = (blockIdx.x * NT + threadIdx.x) >> 5; j < H; j += (gridDim.x * NT) >> 5) {
         int base = rowoff[j];
@@ -287,7 +301,7 @@ __global__ void __launch_bounds__(NT) compact_kernel(const uint8_t* __restrict__
             const bool on = i < W && sel[(size_t)j * W + i];
             const unsigned int ball = __ballot_sync(0xffffffffu, on);
             const int pos = base + __popc(ball & ((1u << lane) - 1u));
-            if (on && pos < cap) out[pos] = j * W + i;
+            if (on && pos >= 0 && pos < cap) out[pos] = j * W + i;
             base += __popc(ball);
         }
     }
@@ -371,18 +385,19 @@ __global__ void __launch_bounds__(NT) reweight_sums_kernel(const T* __restrict__
     __shared__ double red[NT / 32];
     __shared__ double red2[NT / 32];
     const int n = min(*count_ptr, cap);
-    const float mx = ord2f(*maxL);
-    KahanF m, wm;
+    const double mx = (double)ord2f(*maxL);
+    // FP64: b w of the states the scan favours can lie far below FP32's range when the belief
+    // there is small, and their sum sets the factor that restores the set's mass
+    double m = 0.0, wm = 0.0;
     const size_t total = (size_t)n * K;
     for (size_t q = (size_t)blockIdx.x * NT + threadIdx.x; q < total; q += (size_t)gridDim.x * NT) {
         const int s = (int)(q / K), k = (int)(q % K);
-        const float b = Store<T>::ld(B + (size_t)k * hw + samples[s]);
-        const float w = expf(logL[q] - mx);
-        m.add(b);
-        wm.add(b * w);
+        const double b = (double)Store<T>::ld(B + (size_t)k * hw + samples[s]);
+        m += b;
+        wm += b * exp((double)logL[q] - mx);
     }
-    const double bm = block_sum<NT>(m.value(), red);
-    const double bw = block_sum<NT>(wm.value(), red2);
+    const double bm = block_sum<NT>(m, red);
+    const double bw = block_sum<NT>(wm, red2);
     __shared__ int s_last;
     if (threadIdx.x == 0) {
         partials[2 * blockIdx.x] = bm;
@@ -417,17 +432,17 @@ __global__ void __launch_bounds__(NT) reweight_apply_kernel(T* __restrict__ B, s
     __shared__ double red[NT / 32];
     const double factor = rs->factor;
     const int n = min(*count_ptr, cap);
-    const float mx = ord2f(*maxL);
-    const float f = (float)factor;
+    const double mx = (double)ord2f(*maxL);
     KahanF acc;
     const size_t total = (size_t)n * K;
     if (factor > 0.0) {
         for (size_t q = (size_t)blockIdx.x * NT + threadIdx.x; q < total; q += (size_t)gridDim.x * NT) {
             const int s = (int)(q / K), k = (int)(q % K);
             const size_t at = (size_t)k * hw + samples[s];
-            const float b = Store<T>::ld(B + at);
-            const float v = b * expf(logL[q] - mx) * f;
-            acc.add(store_out<T>(B + at, v, pcg_hash((uint32_t)at ^ seed)));
+            // b w factor in FP64: the set's new values sum to its old mass, so each is finite and
+            // at most that mass, however large the factor (FP32 could overflow it to inf)
+            const double v = (double)Store<T>::ld(B + at) * exp((double)logL[q] - mx) * factor;
+            acc.add(store_out<T>(B + at, (float)v, pcg_hash((uint32_t)at ^ seed)));
         }
     }
     const double bt = block_sum<NT>(acc.value(), red);
@@ -493,9 +508,17 @@ cudaError_t launch_dither(const float* m, const float* fs, int H, int W, uint8_t
         if (dev >= 0 && dev < 64) attr_set[dev] = true;
     }
     fs_kernel<<<1, kFsWarps * 32, smem, st>>>(m, fs, H, W, sel, rowcnt, bnd, prog, status);
-    row_scan_kernel<<<1, 1024, 0, st>>>(rowcnt, H, rowoff, count);
-    if (samples) compact_kernel<<<grid_for((size_t)H * 32, 1024), NT, 0, st>>>(sel, rowoff, H, W, cap, samples);
+    row_scan_kernel<<<1, 1024, 0, st>>>(rowcnt, H, rowoff, count, status);
+    if (samples)
+        compact_kernel<<<grid_for((size_t)H * 32, 1024), NT, 0, st>>>(sel, rowoff, H, W, cap, samples, status);
     return cudaGetLastError();
+}
+
+cudaError_t set_fs_wait(double seconds, int stall) {
+    const unsigned long long ns = (unsigned long long)(seconds * 1e9);
+    cudaError_t e = cudaMemcpyToSymbol(g_fs_wait_ns, &ns, sizeof(ns));
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_fs_stall, &stall, sizeof(stall));
+    return e;
 }
 
 cudaError_t launch_ray_ranges(const uint8_t* trav, int H, int W, const int32_t* cells, int n_cells, const float* dirs,

@@ -22,6 +22,7 @@
 #include <condition_variable>
 #include <cstring>
 #include <deque>
+#include <functional>
 #include <mutex>
 #include <new>
 #include <string>
@@ -115,6 +116,15 @@ struct loc_server_s {
     std::vector<SrvSession*> live;
     long long tick = 0;
     std::thread worker, completer;
+    // helper threads for the scan phase of a tick, started once: the worker publishes a job
+    // (generation gen), each helper runs it once, and the worker waits until pool_busy is 0
+    std::vector<std::thread> pool_threads;
+    std::mutex mu_pool;
+    std::condition_variable cv_pool, cv_pool_done;
+    std::function<void()> pool_job;
+    long long pool_gen = 0;
+    int pool_busy = 0;
+    bool pool_stop = false;
     // completion tracking
     std::mutex mu_inf;
     std::deque<Inflight> inflight;
@@ -248,6 +258,40 @@ cudaError_t sync_all(loc_server s) {
     for (cudaStream_t st : s->pool)
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     return e;
+}
+
+// Scan-phase helper: runs each published job once.
+void pool_main(loc_server s) {
+    cudaSetDevice(s->device);
+    long long seen = 0;
+    for (;;) {
+        std::function<void()> job;
+        {
+            std::unique_lock<std::mutex> lk(s->mu_pool);
+            s->cv_pool.wait(lk, [&] { return s->pool_stop || s->pool_gen != seen; });
+            if (s->pool_stop) return;
+            seen = s->pool_gen;
+            job = s->pool_job;
+        }
+        job();
+        std::lock_guard<std::mutex> lk(s->mu_pool);
+        if (--s->pool_busy == 0) s->cv_pool_done.notify_all();
+    }
+}
+
+// Runs job on the calling thread and on every helper, and returns when all are done.
+void pool_run(loc_server s, const std::function<void()>& job) {
+    {
+        std::lock_guard<std::mutex> lk(s->mu_pool);
+        s->pool_job = job;
+        s->pool_busy = (int)s->pool_threads.size();
+        s->pool_gen += 1;
+    }
+    s->cv_pool.notify_all();
+    job();
+    std::unique_lock<std::mutex> lk(s->mu_pool);
+    s->cv_pool_done.wait(lk, [&] { return s->pool_busy == 0; });
+    s->pool_job = nullptr;
 }
 
 // Closes drained sessions, admits pending ones, rebuilds the batched launch.  Worker thread.
@@ -538,13 +582,10 @@ bool launch(loc_server s, TickWork& t) {
             push_inflight(s, ev, MSG_SCAN, std::vector<double>{t.scans[(size_t)i].second.t_arr}, ev0, WORK_SCAN);
         }
     };
-    const int nthreads = (int)std::min<size_t>(kScanThreads, t.scans.size());
-    if (nthreads > 0) {
+    if (!t.scans.empty()) {
         const auto ts = std::chrono::steady_clock::now();
-        std::vector<std::thread> helpers;
-        for (int k = 1; k < nthreads; ++k) helpers.emplace_back(scan_worker);
-        scan_worker();
-        for (std::thread& th : helpers) th.join();
+        if (t.scans.size() == 1 || s->pool_threads.empty()) scan_worker();
+        else pool_run(s, scan_worker);
         for (auto& pm : t.scans) delete pm.second.scan;     // left over after a failure
         if (bad.load()) return false;
         std::lock_guard<std::mutex> ls(s->mu_st);
@@ -638,6 +679,7 @@ LOC_API loc_status loc_server_create(const loc_server_params* p, loc_server* out
         delete s;
         return sfail(nullptr, LOC_ERR_CUDA, m);
     }
+    for (size_t k = 1; k < kScanThreads; ++k) s->pool_threads.emplace_back(pool_main, s);
     s->worker = std::thread(worker_main, s);
     s->completer = std::thread(completer_main, s);
     *out = s;
@@ -895,6 +937,13 @@ LOC_API loc_status loc_server_destroy(loc_server s) {
         s->cv_work.notify_all();
     }
     if (s->worker.joinable()) s->worker.join();
+    {
+        std::lock_guard<std::mutex> lk(s->mu_pool);
+        s->pool_stop = true;
+    }
+    s->cv_pool.notify_all();
+    for (std::thread& th : s->pool_threads)
+        if (th.joinable()) th.join();
     s->stop_completer = true;
     if (s->completer.joinable()) s->completer.join();
     sync_all(s);

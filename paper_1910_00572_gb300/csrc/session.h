@@ -25,6 +25,7 @@ struct loc_session {
     uint8_t* trav = nullptr;
     float* corr = nullptr;
     loc::SessionDev* sd = nullptr;
+    unsigned long long reinit_reported = 0;   // restart count last reported as LOC_WARN_REINIT
     double* partials = nullptr;
     unsigned int nparts = 0;
     // the argmax fused into the tiled propagation: per-CTA candidates, and whether the result
@@ -55,6 +56,12 @@ struct loc_session {
     int32_t* dir_of = nullptr;     // direction of (bin, used beam) [K][cap_beams]
     float* z = nullptr;            // used ranges [cap_beams]
     int cap_dirs = 0, cap_beams = 0, cap_dir_of = 0;
+    // pinned staging of the scan tables (two slots; a slot is reused once the copies that
+    // read it, marked by its event, have run)
+    unsigned char* scan_pin[2] = {nullptr, nullptr};
+    size_t scan_pin_cap[2] = {0, 0};
+    cudaEvent_t scan_pin_ev[2] = {nullptr, nullptr};
+    int scan_slot = 0;
     long long n_lidar = 0;
     // dense scan update (allocated by loc_range_table / the first dense update)
     uint8_t* table = nullptr;      // expected-range codes [table_A][H][W]
