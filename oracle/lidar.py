@@ -18,7 +18,7 @@ Readings of what the paper leaves open:
   channel k points at k*dTheta + theta_t + angle_min + b*angle_inc.
 * Eq. 9's eta is applied within the sampled set: the set keeps its total mass, so
   unsampled states keep their value and the tensor still sums to 1.  Weights are
-  exp(log L - max log L) over the set.
+  proportional to L b over the set, normalised in the log domain.
 """
 from __future__ import annotations
 
@@ -147,19 +147,25 @@ def log_likelihood(ranges: np.ndarray, z: np.ndarray, r_max: float, beam_stride:
 
 def reweight(b: np.ndarray, cells: np.ndarray, logL: np.ndarray) -> np.ndarray:
     """Eq. 9 on the sampled states (all channels of each sampled cell), keeping the set's
-    total mass: b(c,k) <- b(c,k) w(c,k) * sum_set b / sum_set b w, w = exp(logL - max)."""
+    total mass A = sum_set b: b(c,k) <- A L(c,k) b(c,k) / sum_set L b.  The products L b are
+    formed as exp(log L + log b - c) with c their largest logarithm, the same values as
+    b exp(log L - max log L) * A / sum(b exp(log L - max log L)) but without underflow when the
+    scan's likelihood peaks on states of tiny or zero belief.  States with b = 0 stay 0; a set
+    without mass is left as it is."""
     K, H, W = b.shape
     out = b.copy()
     if cells.size == 0:
         return out
     flat = out.reshape(K, H * W)
     sub = flat[:, cells].T                          # (n_cells, K)
-    w = np.exp(logL - logL.max())
     mass = sub.sum()
-    wmass = (sub * w).sum()
-    if not wmass > 0.0:
+    if not mass > 0.0:
         return out
-    flat[:, cells] = (sub * w * (mass / wmass)).T
+    pos = sub > 0.0
+    lw = np.full(sub.shape, -np.inf)
+    lw[pos] = logL[pos] + np.log(sub[pos])
+    w = np.where(pos, np.exp(lw - lw.max()), 0.0)
+    flat[:, cells] = (w * (mass / w.sum())).T
     return out
 
 

@@ -142,6 +142,28 @@ def test_reweight_keeps_set_mass_and_leaves_others():
     assert np.allclose(np.log(r / r.max()), logL - logL.max(), atol=1e-9)
 
 
+def test_reweight_is_the_plain_formula_and_shift_invariant():
+    """Eq. 9 normalises L b over the set, so adding a constant to every log-likelihood changes
+    nothing.  For moderate values the result equals b w A / sum(b w) with w = exp(log L -
+    max log L) written out directly; shifted by -1000 (where that direct form underflows to
+    0 / 0) and with the likelihood peaking on zero-belief states, the result is the same."""
+    rng = np.random.default_rng(12)
+    b = rng.random((5, 9, 11))
+    b[:, 2, 3] = 0.0                                 # a sampled cell without belief
+    b /= b.sum()
+    cells = np.array([5, 2 * 11 + 3, 60, 71], np.int32)
+    logL = rng.normal(0, 20, (4, 5))
+    logL[1, :] += 60.0                               # the likelihood peaks on the empty cell
+    sub = b.reshape(5, -1)[:, cells].T
+    w = np.exp(logL - logL.max())
+    want = sub * w * (sub.sum() / (sub * w).sum())
+    got = L.reweight(b, cells, logL).reshape(5, -1)[:, cells].T
+    assert np.allclose(got, want, rtol=1e-12, atol=0.0)
+    shifted = L.reweight(b, cells, logL - 1000.0).reshape(5, -1)[:, cells].T
+    assert np.allclose(shifted, want, rtol=1e-12, atol=0.0)
+    assert np.all(np.isfinite(shifted)) and np.all(shifted[1] == 0.0)
+
+
 def test_true_pose_scores_best_with_clean_scan():
     """Eq. 10: a noise-free scan from the true state scores at least as high as any other."""
     occ = floorplan.rooms_map(3, size=48)
