@@ -339,10 +339,9 @@ __global__ void __launch_bounds__(NT) score_kernel(const uint8_t* __restrict__ t
                                                    const float* __restrict__ dirs, int n_dirs,
                                                    const int32_t* __restrict__ dir_of, const float* __restrict__ z,
                                                    int n_used, float rmax, float cell_m, float inv2s2,
-                                                   float* __restrict__ logL, unsigned int* maxL) {
+                                                   float* __restrict__ logL) {
     extern __shared__ float rh[];                 // n_dirs expected ranges (metres)
     const int n = min(*count_ptr, cap);
-    float best = -FLT_MAX;
     for (int s = blockIdx.x; s < n; s += gridDim.x) {
         const int cell = samples[s];
         const int j = cell / W, i = cell % W;
@@ -358,12 +357,9 @@ __global__ void __launch_bounds__(NT) score_kernel(const uint8_t* __restrict__ t
             }
             const float l = -acc * inv2s2;
             logL[(size_t)s * K + k] = l;
-            best = fmaxf(best, l);
         }
         __syncthreads();
     }
-    for (int o = 16; o > 0; o >>= 1) best = fmaxf(best, __shfl_down_sync(0xffffffffu, best, o));
-    if ((threadIdx.x & 31) == 0 && best > -FLT_MAX) atomicMax(maxL, f2ord(best));
 }
 
 // ------------------------------------------------------------------ Eq. 9 on the sampled set
@@ -374,8 +370,30 @@ struct ReweightScalars {
     int pad;
 };
 
-// Sums over the sampled states (stored units): mass = sum b, wmass = sum b w,
-// w = exp(logL - max logL); the last CTA writes factor = mass / wmass (0: leave as is).
+// Eq. 9 on the sampled set keeps its mass A = sum b and gives b' = A b L / sum(b L).  It is
+// evaluated in the log domain against the offset c = max over the set of (log L + log b), so
+// every weight w = exp(log L + log b - c) lies in (0, 1] with the largest equal to 1 and the
+// normaliser sum w is at least 1: a scan whose likelihood peaks on states of tiny or zero
+// belief cannot underflow the normaliser or overflow the factor.  States with b = 0 stay 0.
+// reweight_max writes c (as an ordered uint; untouched when no state of the set holds mass).
+template <typename T>
+__global__ void __launch_bounds__(NT) reweight_max_kernel(const T* __restrict__ B, size_t hw, int K,
+                                                          const int32_t* __restrict__ samples, const int* count_ptr,
+                                                          int cap, const float* __restrict__ logL, unsigned int* maxL) {
+    const int n = min(*count_ptr, cap);
+    float best = -FLT_MAX;
+    const size_t total = (size_t)n * K;
+    for (size_t q = (size_t)blockIdx.x * NT + threadIdx.x; q < total; q += (size_t)gridDim.x * NT) {
+        const int s = (int)(q / K), k = (int)(q % K);
+        const float b = Store<T>::ld(B + (size_t)k * hw + samples[s]);
+        if (b > 0.0f) best = fmaxf(best, logL[q] + logf(b));
+    }
+    for (int o = 16; o > 0; o >>= 1) best = fmaxf(best, __shfl_down_sync(0xffffffffu, best, o));
+    if ((threadIdx.x & 31) == 0 && best > -FLT_MAX) atomicMax(maxL, f2ord(best));
+}
+
+// Sums over the sampled states (stored units): mass = sum b, wmass = sum w (the weights above);
+// the last CTA writes factor = mass / wmass (0: leave the set as it is).
 template <typename T>
 __global__ void __launch_bounds__(NT) reweight_sums_kernel(const T* __restrict__ B, size_t hw, int K,
                                                            const int32_t* __restrict__ samples, const int* count_ptr,
@@ -386,15 +404,14 @@ __global__ void __launch_bounds__(NT) reweight_sums_kernel(const T* __restrict__
     __shared__ double red2[NT / 32];
     const int n = min(*count_ptr, cap);
     const double mx = (double)ord2f(*maxL);
-    // FP64: b w of the states the scan favours can lie far below FP32's range when the belief
-    // there is small, and their sum sets the factor that restores the set's mass
+    const bool any = isfinite(mx);                // some state of the set holds mass
     double m = 0.0, wm = 0.0;
     const size_t total = (size_t)n * K;
-    for (size_t q = (size_t)blockIdx.x * NT + threadIdx.x; q < total; q += (size_t)gridDim.x * NT) {
+    for (size_t q = (size_t)blockIdx.x * NT + threadIdx.x; q < total && any; q += (size_t)gridDim.x * NT) {
         const int s = (int)(q / K), k = (int)(q % K);
         const double b = (double)Store<T>::ld(B + (size_t)k * hw + samples[s]);
         m += b;
-        wm += b * exp((double)logL[q] - mx);
+        if (b > 0.0) wm += exp((double)logL[q] + log(b) - mx);
     }
     const double bm = block_sum<NT>(m, red);
     const double bw = block_sum<NT>(wm, red2);
@@ -439,9 +456,9 @@ __global__ void __launch_bounds__(NT) reweight_apply_kernel(T* __restrict__ B, s
         for (size_t q = (size_t)blockIdx.x * NT + threadIdx.x; q < total; q += (size_t)gridDim.x * NT) {
             const int s = (int)(q / K), k = (int)(q % K);
             const size_t at = (size_t)k * hw + samples[s];
-            // b w factor in FP64: the set's new values sum to its old mass, so each is finite and
-            // at most that mass, however large the factor (FP32 could overflow it to inf)
-            const double v = (double)Store<T>::ld(B + at) * exp((double)logL[q] - mx) * factor;
+            // the new values sum to the set's old mass, so each is finite and at most that mass
+            const double b = (double)Store<T>::ld(B + at);
+            const double v = b > 0.0 ? factor * exp((double)logL[q] + log(b) - mx) : 0.0;
             acc.add(store_out<T>(B + at, (float)v, pcg_hash((uint32_t)at ^ seed)));
         }
     }
@@ -542,11 +559,13 @@ cudaError_t launch_score_reweight(void* B, int storage, const uint8_t* trav, int
     }
     const unsigned int ns = (unsigned int)(cap < 8192 ? (cap > 0 ? cap : 1) : 8192);
     score_kernel<<<ns, NT, smem, st>>>(trav, H, W, K, samples, count, cap, dirs, n_dirs, dir_of, z, n_used,
-                                       rmax_cells, cell_m, inv2s2, logL, maxL);
+                                       rmax_cells, cell_m, inv2s2, logL);
     const size_t hw = (size_t)H * W;
     const unsigned int half = nparts / 2 < 1024 ? nparts / 2 : 1024;
     const unsigned int nb = grid_for((size_t)cap * K, half > 0 ? half : 1);
     ReweightScalars* r = static_cast<ReweightScalars*>(rs);
+    LOC_DISPATCH(storage, (reweight_max_kernel<T><<<nb, NT, 0, st>>>((const T*)B, hw, K, samples, count, cap, logL,
+                                                                       maxL)));
     LOC_DISPATCH(storage, (reweight_sums_kernel<T><<<nb, NT, 0, st>>>((const T*)B, hw, K, samples, count, cap, logL,
                                                                         maxL, partials, r)));
     LOC_DISPATCH(storage, (reweight_apply_kernel<T><<<nb, NT, 0, st>>>((T*)B, hw, K, samples, count, cap, logL, maxL,

@@ -132,6 +132,52 @@ def test_reweight_with_given_cells_matches_oracle(seed):
     assert abs(got.astype(np.float64).sum() - 1.0) < 1e-5
 
 
+@pytest.mark.parametrize("storage", ["f32", "bf16"])
+def test_reweight_when_the_scan_disagrees_with_the_belief(storage):
+    """A scan taken far from where the belief lies: the sampled set holds cells of the scan's
+    pose (zero belief, where the likelihood peaks) and cells of the belief (log-likelihoods
+    about 9500 below the maximum).  Eq. 9 still moves the set's mass onto its best states with
+    belief, finite, as the oracle does; before the weights were normalised in the log domain
+    their sum underflowed (a served session's normaliser became non-finite).  The device sums
+    each log-likelihood in FP32, good to about 1e-3 absolute at these magnitudes, so the
+    result is checked by L1 and the argmax state rather than element by element."""
+    occ = floorplan.office_map(6, size=256)[40:200, 30:210].copy()
+    occ[0, :] = occ[-1, :] = 1
+    occ[:, 0] = occ[:, -1] = 1
+    H, W = occ.shape
+    K, cell, theta = 16, 0.05, 0.0
+    free = np.argwhere(occ == 0)
+    rng = np.random.default_rng(4)
+    a = free[np.argmin(np.abs(free[:, 0] - 20) + np.abs(free[:, 1] - 20))]     # belief here
+    c = free[np.argmin(np.abs(free[:, 0] - 140) + np.abs(free[:, 1] - 160))]   # scan from here
+    b = np.zeros((K, H, W), np.float32)
+    b[:, max(0, a[0] - 3):a[0] + 4, max(0, a[1] - 3):a[1] + 4] = rng.random((K, 7, 7)).astype(np.float32)
+    b[:, occ != 0] = 0.0
+    b /= b.sum()
+    z = scan.simulate_scan(occ, cell, ((c[1] + 0.5) * cell, (c[0] + 0.5) * cell, 0.0), seed=3, n_beams=360,
+                           r_max=10.0, noise_sigma=0.02)
+    near_a = [(j, i) for j in range(a[0] - 3, a[0] + 4) for i in range(a[1] - 3, a[1] + 4)
+              if 0 <= j < H and 0 <= i < W and occ[j, i] == 0]
+    near_c = [(j, i) for j in range(c[0] - 2, c[0] + 3) for i in range(c[1] - 2, c[1] + 3)
+              if 0 <= j < H and 0 <= i < W and occ[j, i] == 0]
+    cells = np.array(sorted(j * W + i for j, i in near_a + near_c), np.int32)
+    h = make(occ, K, cell, storage=storage, sigma_xy_cells=0.0, sigma_theta_bins=0.0)
+    try:
+        loc.loc_set_belief(h, b)
+        before = loc.loc_belief(h).astype(np.float64)
+        loc.loc_lidar_update_cells(h, cells, z, 0.0, math.pi / 180, 10.0, 4, 0.1)
+        loc.loc_sync(h)
+        got = loc.loc_belief(h).astype(np.float64)
+    finally:
+        loc.loc_destroy(h)
+    assert np.all(np.isfinite(got))
+    want, _ = OL.lidar_update(before, occ, theta, z, cell, 0.0, math.pi / 180, 10.0, 4, 0.1, 0, cells=cells)
+    assert abs(got.sum() - 1.0) < 1e-4
+    # the set's mass left the scan's pose for the belief's states, as the oracle's does
+    assert np.abs(got - want).sum() <= 1e-2
+    assert np.unravel_index(np.argmax(got), got.shape) == np.unravel_index(np.argmax(want), want.shape)
+
+
 def test_lidar_update_properties_with_device_dithering():
     occ, cell, theta, z, b, (k_true, j_true, i_true) = lidar_case(4, n_samples=600)
     K = b.shape[0]
