@@ -61,3 +61,22 @@ def test_reference_arm_under_torchrun_prints_once():
     line = lines[0]
     assert line["impl"] == "reference" and line["n_gpus"] == 2 and line["value"] > 0
     assert line["cpu_baseline"]["kind"] == "oracle"
+
+
+@pytest.mark.slow
+def test_default_reference_arm_under_torchrun_prints_once():
+    """The default workload's oracle arm (served workload, session 0 of the mix) under torchrun
+    with two ranks: rank 0 alone times the oracle and prints one line, with the served line's
+    config."""
+    env = dict(os.environ, CUDA_VISIBLE_DEVICES="")
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
+           "--master-addr", "127.0.0.1", "--master-port", str(free_port()), "bench.py", "--gpus", "2",
+           "--impl", "reference", "--steps", "2", "--warmup", "1", "--ref-budget-s", "3"]
+    r = subprocess.run(cmd, cwd=ROOT, env=env, capture_output=True, text=True, timeout=900)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [json.loads(x) for x in r.stdout.splitlines() if x.startswith("{")]
+    assert len(lines) == 1
+    line = lines[0]
+    assert line["impl"] == "reference" and line["config"]["workload"] == "serve256" and line["value"] > 0
+    assert line["steps"] == 2 and line["warmup"] == 1
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
