@@ -75,7 +75,7 @@ batch_kernel(const BatchStatic* __restrict__ ss, const BatchTick* __restrict__ t
         j.tx0 = (tile % S.ntx) * TW;
         if (tid == 0)   // the tensor map lives in global memory, written by a copy before the launch
             asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(tmap) : "memory");
-        KahanF acc;
+        KahanF2 acc;
         int p_stop = 0, next_issue = 0;
         if (!run_tile<T, C>(sm, j, gp, acc, p_stop, next_issue)) {
             // a TMA wait gave up: flag the launch and the session, let the copies in flight land

@@ -78,7 +78,7 @@ __global__ void __launch_bounds__(C::NT, C::MINB) step_tiled_kernel(const __grid
     j.g2 = a.g2;
     j.ty0 = blockIdx.y * C::TH;
     j.tx0 = blockIdx.x * TW;
-    KahanF acc;
+    std::conditional_t<PAIRS, KahanF, KahanF2> acc;
     int p_stop = 0, next_issue = 0;
     bool ok;
     if constexpr (PAIRS) ok = pairs::run_tile<T, C>(sm, j, 0u, acc, p_stop, next_issue);
@@ -203,12 +203,15 @@ __global__ void __launch_bounds__(C::NT, C::MINB) step_ws_kernel(const __grid_co
     }
     __syncthreads();
 
-    KahanF acc;
+    KahanF2 acc;
     ArgBest am;                             // consumers: the argmax of the values they store
     int waited = 0, next_issue = 0;         // producer: planes [waited, next_issue) maybe in flight
     if (tid < NP) {
         // ------------------------------------------------------------------ producers
         const int t = tid;
+        // items: in a split, the S threads are the first NS and the X threads the rest
+        const SItem si = s_item<C>(t);
+        const XItem xi = x_item<C>(C::SPLIT ? t - C::NS : t);
         auto issue = [&](int q) {
             const Shift s = a.sh[q];
             int x_al, xo;
@@ -247,12 +250,12 @@ __global__ void __launch_bounds__(C::NT, C::MINB) step_ws_kernel(const __grid_co
                             if (bar_wait(&sm.tma[stage], (uint32_t)((p / NSTAGE) & 1))) waited = p + 1;
                             else sm.fail_a = 1;
                         }
-                        if (!sm.fail_a) s_pass_any<T, C>(sm.raw[stage], sm.mk, sm.S[p & 1], t, xo, s.fx, s.fy);
+                        if (!sm.fail_a) s_pass_any<T, C>(sm.raw[stage], &sm.mk[0][0], &sm.S[p & 1][0][0], si, xo, s.fx, s.fy);
                     }
                 } else if (p >= 1) {
                     const int q = p - 1, b = q & 1;
                     if (q >= 2 && !sm.fail_b && !bar_wait(&sm.empty[b], (uint32_t)(((q - 2) >> 1) & 1))) sm.fail_b = 1;
-                    if (!(sm.fail_a | sm.fail_b)) x_pass<C>(sm.S[b], sm.X[b], t - C::NS, a.g0, a.g1, a.g2);
+                    if (!(sm.fail_a | sm.fail_b)) x_pass<C>(&sm.S[b][0][0], &sm.X[b][0][0], xi, a.g0, a.g1, a.g2);
                     bar_arrive(&sm.full[b]);             // X[b] of plane p - 1 is ready
                 }
                 producers_sync<NP>();
@@ -284,7 +287,7 @@ __global__ void __launch_bounds__(C::NT, C::MINB) step_ws_kernel(const __grid_co
                 if (bar_wait(&sm.tma[stage], (uint32_t)((p / NSTAGE) & 1))) waited = p + 1;
                 else sm.fail_a = 1;
             }
-            if (!sm.fail_a) s_pass_any<T, C>(sm.raw[stage], sm.mk, S, t, xo, s.fx, s.fy);
+            if (!sm.fail_a) s_pass_any<T, C>(sm.raw[stage], &sm.mk[0][0], &S[0][0], si, xo, s.fx, s.fy);
             // S of plane p complete and the raw stage free; every producer has also finished the
             // X-pass of plane p - 1, so S of plane p + 1 (the other buffer's next use) may be written
             producers_sync<NP>();
@@ -297,7 +300,7 @@ __global__ void __launch_bounds__(C::NT, C::MINB) step_ws_kernel(const __grid_co
             }
             const int b = p & 1;
             if (p >= 2 && !sm.fail_b && !bar_wait(&sm.empty[b], (uint32_t)(((p - 2) >> 1) & 1))) sm.fail_b = 1;
-            if (!(sm.fail_a | sm.fail_b)) x_pass<C>(S, sm.X[b], t, a.g0, a.g1, a.g2);
+            if (!(sm.fail_a | sm.fail_b)) x_pass<C>(&S[0][0], &sm.X[b][0][0], xi, a.g0, a.g1, a.g2);
             bar_arrive(&sm.full[b]);                 // X[b] of plane p is ready
         }
     } else {
@@ -333,20 +336,21 @@ __global__ void __launch_bounds__(C::NT, C::MINB) step_ws_kernel(const __grid_co
         o.H = H;
         o.W = W;
         o.K = K;
-        for (int p = 0; p < K + NWRAP; ++p) {
+        const PCtx<T> pc = p_ctx<T, C>(o, r0, ty0, gxp);
+        for (int p = 0, ph = 0; p < K + NWRAP; ++p, ph = ph == RING - 1 ? 0 : ph + 1) {
             const int b = p & 1;
             if (p < K && !bar_wait(&sm.full[b], (uint32_t)((p >> 1) & 1))) {
                 sm.fail_c = 1;
                 break;
             }
-            switch (p % RING) {
-                case 0: p_pass<T, C, 0, true>(sm.X[b], sm.wrap, o, tp, ring, cs, p, r0, cp, ty0, gxp, acc, &am); break;
-                case 1: p_pass<T, C, 1, true>(sm.X[b], sm.wrap, o, tp, ring, cs, p, r0, cp, ty0, gxp, acc, &am); break;
-                case 2: p_pass<T, C, 2, true>(sm.X[b], sm.wrap, o, tp, ring, cs, p, r0, cp, ty0, gxp, acc, &am); break;
-                case 3: p_pass<T, C, 3, true>(sm.X[b], sm.wrap, o, tp, ring, cs, p, r0, cp, ty0, gxp, acc, &am); break;
-                case 4: p_pass<T, C, 4, true>(sm.X[b], sm.wrap, o, tp, ring, cs, p, r0, cp, ty0, gxp, acc, &am); break;
-                case 5: p_pass<T, C, 5, true>(sm.X[b], sm.wrap, o, tp, ring, cs, p, r0, cp, ty0, gxp, acc, &am); break;
-                default: p_pass<T, C, 6, true>(sm.X[b], sm.wrap, o, tp, ring, cs, p, r0, cp, ty0, gxp, acc, &am); break;
+            switch (ph) {
+                case 0: p_pass<T, C, 0, true>(sm.X[b], sm.wrap, pc, K, tp, ring, cs, p, r0, cp, acc, &am); break;
+                case 1: p_pass<T, C, 1, true>(sm.X[b], sm.wrap, pc, K, tp, ring, cs, p, r0, cp, acc, &am); break;
+                case 2: p_pass<T, C, 2, true>(sm.X[b], sm.wrap, pc, K, tp, ring, cs, p, r0, cp, acc, &am); break;
+                case 3: p_pass<T, C, 3, true>(sm.X[b], sm.wrap, pc, K, tp, ring, cs, p, r0, cp, acc, &am); break;
+                case 4: p_pass<T, C, 4, true>(sm.X[b], sm.wrap, pc, K, tp, ring, cs, p, r0, cp, acc, &am); break;
+                case 5: p_pass<T, C, 5, true>(sm.X[b], sm.wrap, pc, K, tp, ring, cs, p, r0, cp, acc, &am); break;
+                default: p_pass<T, C, 6, true>(sm.X[b], sm.wrap, pc, K, tp, ring, cs, p, r0, cp, acc, &am); break;
             }
             if (p + 2 < K) bar_arrive(&sm.empty[b]);  // a producer waits for this release
         }

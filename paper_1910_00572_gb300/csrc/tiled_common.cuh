@@ -145,6 +145,29 @@ __device__ __forceinline__ f2 ffma2(f2 a, f2 b, f2 c) {
     asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
     return d;
 }
+__device__ __forceinline__ f2 fsub2(f2 a, f2 b) {
+    f2 d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+// Compensated (Kahan) FP32 running sums of the two lanes of a packed pair, four packed
+// operations per addition; value() widens both to FP64.
+struct KahanF2 {
+    f2 s = 0ull, c = 0ull;
+    __device__ __forceinline__ void add(f2 x) {
+        const f2 y = fsub2(x, c);
+        const f2 t = fadd2(s, y);
+        c = fsub2(fsub2(t, s), y);
+        s = t;
+    }
+    __device__ __forceinline__ double value() const {
+        float s0, s1, c0, c1;
+        upk(s, s0, s1);
+        upk(c, c0, c1);
+        return ((double)s0 - (double)c0) + ((double)s1 - (double)c1);
+    }
+};
 
 // Eight consecutive raw values starting at a 4-element boundary, as FP32.
 template <typename T> __device__ __forceinline__ void load8(const T* p, float (&v)[8]);
@@ -182,77 +205,119 @@ __device__ __forceinline__ void box_x(int tx0, const Shift& s, int& x_al, int& x
     xo = x - x_al;
 }
 
-// S-pass: S[y][c] for y in [0, XR), c in [0, 72) (tile col c - 2); one item per thread: 4
-// columns x SR rows, the x-lerp of the shared raw row carried down.  XO is xo mod 4; the
-// runtime part xo - XO (0, or 4 for 16-bit types) moves the base address.
-template <typename T, typename C, int XO>
-__device__ __forceinline__ void s_pass(const T* raw, const float (*mk)[MW], float (*S)[SW], int t,
-                                       int xbase, float fx, float fy) {
+// A thread's S-pass item (4 columns x SR rows of S) and X-pass item (XW columns of one row),
+// fixed for the kernel: element offsets into a raw stage, the mask, S and X.
+struct SItem {
+    int on, raw, mk, s;
+};
+struct XItem {
+    int on, s, x;
+};
+template <typename C>
+__device__ __forceinline__ SItem s_item(int t) {
     constexpr int UNITS = 72 / 4;              // 18 items of 4 columns cover tile cols -2 .. 69
     constexpr int ITEMS = UNITS * (C::XR / C::SR);
-    const int q = t;
-    if (q >= ITEMS) return;
-    const int u = q % UNITS, y0 = (q / UNITS) * C::SR;
-    const int c0 = 4 * u;
+    SItem it;
+    it.on = t < ITEMS;
+    const int u = t % UNITS, y0 = (t / UNITS) * C::SR, c0 = 4 * u;
+    it.raw = y0 * BW + c0;
+    it.mk = y0 * MW + c0;
+    it.s = y0 * SW + c0;
+    return it;
+}
+template <typename C>
+__device__ __forceinline__ XItem x_item(int t) {
+    constexpr int UNITS = TW / C::XW;
+    XItem it;
+    it.on = t < UNITS * C::XR;
+    const int y = t % C::XR, c0 = C::XW * (t / C::XR);   // consecutive threads take consecutive rows
+    it.s = y * SW + c0;
+    it.x = y * XW_PITCH + c0;
+    return it;
+}
+
+// S-pass: S[y][c] for y in [0, XR), c in [0, 72) (tile col c - 2); one item per thread: 4
+// columns x SR rows, the x-lerp of the shared raw row carried down.  XO is xo mod 4; the
+// runtime part xo - XO (0, or 4 for 16-bit types) moves the base address.  Column pairs run
+// on the packed FP32 pipe with the scalar operation order: xl = fx (v1 - v0) + v0, then
+// S = m (fy xl + (1 - fy) prev).
+template <typename T, typename C, int XO>
+__device__ __forceinline__ void s_pass(const T* raw, const float* mk, float* S, const SItem& it, int xbase,
+                                       float fx, float fy) {
+    if (!it.on) return;
+    const f2 fx2 = pk(fx, fx), fy2 = pk(fy, fy);
     const float gy0 = 1.0f - fy;
-    float prev[4];
+    const f2 gy2 = pk(gy0, gy0);
+    const T* rp = raw + it.raw + xbase;
+    const float* mp = mk + it.mk;
+    float* sp = S + it.s;
+    f2 prev[2];
 #pragma unroll
     for (int r = 0; r <= C::SR; ++r) {
         float v[8];
-        load8<T>(&raw[(y0 + r) * BW + c0 + xbase], v);
-        float xl[4];
+        load8<T>(rp + r * BW, v);
+        f2 xl[2];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) xl[k] = fmaf(fx, v[XO + k + 1] - v[XO + k], v[XO + k]);
-        if (r > 0) {
-            const float4 m = *reinterpret_cast<const float4*>(&mk[y0 + r - 1][c0]);
-            const float mm[4] = {m.x, m.y, m.z, m.w};
-            float4 o;
-            float* op = &o.x;
-#pragma unroll
-            for (int k = 0; k < 4; ++k) op[k] = mm[k] * fmaf(fy, xl[k], gy0 * prev[k]);
-            *reinterpret_cast<float4*>(&S[y0 + r - 1][c0]) = o;
+        for (int k = 0; k < 2; ++k) {
+            const f2 d = pk(v[XO + 2 * k + 1] - v[XO + 2 * k], v[XO + 2 * k + 2] - v[XO + 2 * k + 1]);
+            xl[k] = ffma2(fx2, d, pk(v[XO + 2 * k], v[XO + 2 * k + 1]));
         }
-#pragma unroll
-        for (int k = 0; k < 4; ++k) prev[k] = xl[k];
+        if (r > 0) {
+            const f2* m2 = reinterpret_cast<const f2*>(mp + (r - 1) * MW);
+            f2* o2 = reinterpret_cast<f2*>(sp + (r - 1) * SW);
+            const f2 o0 = fmul2(m2[0], ffma2(fy2, xl[0], fmul2(gy2, prev[0])));
+            const f2 o1 = fmul2(m2[1], ffma2(fy2, xl[1], fmul2(gy2, prev[1])));
+            float a, b, c, d;
+            upk(o0, a, b);
+            upk(o1, c, d);
+            *reinterpret_cast<float4*>(o2) = make_float4(a, b, c, d);
+        }
+        prev[0] = xl[0];
+        prev[1] = xl[1];
     }
 }
 
-// X-pass: X[y][c0..c0+XW) = x-blur of S, one item (XW columns of one row) per thread.
+// X-pass: X[y][c0..c0+XW) = x-blur of S, one item (XW columns of one row) per thread, column
+// pairs on the packed pipe with the scalar order g2 (s0 + s4) + (g1 (s1 + s3) + g0 s2).
 template <typename C>
-__device__ __forceinline__ void x_pass(const float (*S)[SW], float (*X)[XW_PITCH], int t, float g0,
-                                       float g1, float g2) {
-    constexpr int UNITS = TW / C::XW;
-    const int q = t;
-    if (q >= UNITS * C::XR) return;
-    const int y = q % C::XR, u = q / C::XR;    // consecutive threads take consecutive rows
-    const int c0 = C::XW * u;
+__device__ __forceinline__ void x_pass(const float* S, float* X, const XItem& it, float g0, float g1, float g2) {
+    if (!it.on) return;
+    const f2 g02 = pk(g0, g0), g12 = pk(g1, g1), g22 = pk(g2, g2);
+    const float* sp = S + it.s;
+    float* xp = X + it.x;
     float s[C::XW + 4];
 #pragma unroll
     for (int k = 0; k < C::XW + 4; k += 4) {
-        const float4 a = *reinterpret_cast<const float4*>(&S[y][c0 + k]);
+        const float4 a = *reinterpret_cast<const float4*>(sp + k);
         s[k] = a.x; s[k + 1] = a.y; s[k + 2] = a.z; s[k + 3] = a.w;
     }
 #pragma unroll
     for (int k = 0; k < C::XW; k += 4) {
-        float4 o;
-        float* op = &o.x;
+        f2 o[2];
 #pragma unroll
-        for (int j = 0; j < 4; ++j)
-            op[j] = fmaf(g2, s[k + j] + s[k + j + 4], fmaf(g1, s[k + j + 1] + s[k + j + 3], g0 * s[k + j + 2]));
-        *reinterpret_cast<float4*>(&X[y][c0 + k]) = o;
+        for (int j = 0; j < 4; j += 2) {
+            const f2 a = fadd2(pk(s[k + j], s[k + j + 1]), pk(s[k + j + 4], s[k + j + 5]));
+            const f2 b = pk(s[k + j + 1] + s[k + j + 3], s[k + j + 2] + s[k + j + 4]);
+            const f2 c = pk(s[k + j + 2], s[k + j + 3]);
+            o[j / 2] = ffma2(g22, a, ffma2(g12, b, fmul2(g02, c)));
+        }
+        float a0, a1, b0, b1;
+        upk(o[0], a0, a1);
+        upk(o[1], b0, b1);
+        *reinterpret_cast<float4*>(xp + k) = make_float4(a0, a1, b0, b1);
     }
 }
 
 // The S-pass for the in-box offset xo (its residue mod 4 selects the compile-time variant).
 template <typename T, typename C>
-__device__ __forceinline__ void s_pass_any(const T* raw, const float (*mk)[MW], float (*S)[SW], int t,
-                                           int xo, float fx, float fy) {
+__device__ __forceinline__ void s_pass_any(const T* raw, const float* mk, float* S, const SItem& it, int xo,
+                                           float fx, float fy) {
     const int xb = xo & ~3;
     switch (xo & 3) {
-        case 0: s_pass<T, C, 0>(raw, mk, S, t, xb, fx, fy); break;
-        case 1: s_pass<T, C, 1>(raw, mk, S, t, xb, fx, fy); break;
-        case 2: s_pass<T, C, 2>(raw, mk, S, t, xb, fx, fy); break;
-        default: s_pass<T, C, 3>(raw, mk, S, t, xb, fx, fy); break;
+        case 0: s_pass<T, C, 0>(raw, mk, S, it, xb, fx, fy); break;
+        case 1: s_pass<T, C, 1>(raw, mk, S, it, xb, fx, fy); break;
+        case 2: s_pass<T, C, 2>(raw, mk, S, it, xb, fx, fy); break;
+        default: s_pass<T, C, 3>(raw, mk, S, it, xb, fx, fy); break;
     }
 }
 
@@ -402,16 +467,53 @@ struct Taps2 {
     f2 gt[RING];                       // theta taps {g, g}
 };
 
+// A P-pass thread's output geometry, fixed for a tile: its first cell's address in plane 0,
+// the plane and row strides, the rows inside the grid (and tile), its rounding hash.
+template <typename T>
+struct PCtx {
+    T* out0;                           // the thread's first cell (row ty0 + r0, column gx) of plane 0
+    size_t plane;                      // H * W elements
+    long long base0;                   // linear index of out0 (argmax indices)
+    int W;
+    int rows;                          // rows of the thread inside the grid and the tile
+    bool col_ok;                       // gx < W (both columns: W is even)
+    bool full;                         // all MR rows and the columns inside
+    uint32_t h;                        // the thread's hash for this tile and propagation
+};
+
+template <typename T, typename C>
+__device__ __forceinline__ PCtx<T> p_ctx(const TileOut& a, int r0, int ty0, int gx) {
+    PCtx<T> c;
+    const long long base = (long long)(ty0 + r0) * a.W + gx;
+    c.out0 = static_cast<T*>(a.B_out) + base;
+    c.plane = (size_t)a.H * a.W;
+    c.base0 = base;
+    c.W = a.W;
+    int rows = a.H - (ty0 + r0);                       // rows of this thread inside the grid
+    if constexpr (C::CR > C::TH) rows = min(rows, C::TH - r0);   // ... and inside the tile
+    c.rows = rows;
+    c.col_ok = gx < a.W;
+    c.full = rows >= C::MR && c.col_ok;
+    c.h = pcg_hash((uint32_t)base ^ a.seed);
+    return c;
+}
+
+// The 16-bit uniform number of output plane o of a thread (both halves of the word, for
+// sr_row_bits): the thread's tile hash mixed with the plane by one multiply, high half.
+__device__ __forceinline__ uint32_t sr_plane_word(uint32_t h, int o) {
+    const uint32_t x = (h ^ ((uint32_t)o * 0x9E3779B9u)) * 0x85EBCA6Bu;
+    return __byte_perm(x, 0u, 0x3232);
+}
+
 // P-pass for plane p with the newest ring slot PH = p mod 7.  The thread's cells are rows
 // r0 .. r0+MR-1 of the tile, columns 2cp and 2cp+1, handled as column pairs.
 // With AM the thread also keeps the running argmax of the values it stores in *am.
 template <typename T, typename C, int PH, bool AM = false>
 __device__ __forceinline__ void p_pass(const float (*X)[XW_PITCH], float (*wrap)[C::CR][TW],
-                                       const TileOut& a, const Taps2& tp,
+                                       const PCtx<T>& pc, int K, const Taps2& tp,
                                        f2 (&ring)[RING][C::MR], const f2 (&cs)[C::MR], int p,
-                                       int r0, int cp, int ty0, int gx, KahanF& acc, ArgBest* am = nullptr) {
+                                       int r0, int cp, KahanF2& acc, ArgBest* am = nullptr) {
     constexpr int MR = C::MR;
-    const int K = a.K;
     if (p < K) {
         f2 x[MR + 4];
 #pragma unroll
@@ -431,28 +533,30 @@ __device__ __forceinline__ void p_pass(const float (*X)[XW_PITCH], float (*wrap)
     if (p >= 2 * RT) {
         int o = p - RT;
         if (o >= K) o -= K;
-        const size_t base = ((size_t)o * a.H + (ty0 + r0)) * a.W + gx;
-        T* out = static_cast<T*>(a.B_out) + base;
-        const uint32_t h = sizeof(T) == 2 ? sr_word(pcg_hash((uint32_t)base ^ a.seed)) : 0u;
-        int rows = a.H - (ty0 + r0);                   // rows of this thread inside the grid
-        if constexpr (C::CR > C::TH) rows = min(rows, C::TH - r0);   // ... and inside the tile
-        const bool full = rows >= MR && gx < a.W;
+        T* out = pc.out0 + (size_t)o * pc.plane;
+        const uint32_t h = sizeof(T) == 2 ? sr_plane_word(pc.h, o) : 0u;
         f2 part = 0ull;
         f2 stv[MR];                                    // stored values (-FLT_MAX: not stored)
+        if (pc.full) {
 #pragma unroll
-        for (int rr = 0; rr < MR; ++rr) {
-            f2 t = fmul2(tp.gt[0], ring[(PH + 1) % RING][rr]);
+            for (int rr = 0; rr < MR; ++rr) {
+                f2 t = fmul2(tp.gt[0], ring[(PH + 1) % RING][rr]);
 #pragma unroll
-            for (int d = 1; d < RING; ++d) t = ffma2(tp.gt[d], ring[(PH + 1 + d) % RING][rr], t);
-            const f2 v = fmul2(cs[rr], t);
-            // 32 random bits per row: the thread's hash with a per-row odd constant mixed in
-            const uint32_t hr = sr_row_bits(h, rr);
-            stv[rr] = pk(-FLT_MAX, -FLT_MAX);
-            if (full || (rr < rows && gx < a.W)) store2<T>(out + (size_t)rr * a.W, v, hr, part, stv[rr]);
+                for (int d = 1; d < RING; ++d) t = ffma2(tp.gt[d], ring[(PH + 1 + d) % RING][rr], t);
+                store2<T>(out + (size_t)rr * pc.W, fmul2(cs[rr], t), sr_row_bits(h, rr), part, stv[rr]);
+            }
+        } else {
+#pragma unroll
+            for (int rr = 0; rr < MR; ++rr) {
+                f2 t = fmul2(tp.gt[0], ring[(PH + 1) % RING][rr]);
+#pragma unroll
+                for (int d = 1; d < RING; ++d) t = ffma2(tp.gt[d], ring[(PH + 1 + d) % RING][rr], t);
+                stv[rr] = pk(-FLT_MAX, -FLT_MAX);
+                if (rr < pc.rows && pc.col_ok)
+                    store2<T>(out + (size_t)rr * pc.W, fmul2(cs[rr], t), sr_row_bits(h, rr), part, stv[rr]);
+            }
         }
-        float p0, p1;
-        upk(part, p0, p1);
-        acc.add(p0 + p1);
+        acc.add(part);
         if constexpr (AM) {
             float m = -FLT_MAX;
 #pragma unroll
@@ -462,13 +566,14 @@ __device__ __forceinline__ void p_pass(const float (*X)[XW_PITCH], float (*wrap)
                 m = fmaxf(m, fmaxf(lo, hi));
             }
             if (m >= am->v && m > -FLT_MAX) {          // rare: the lowest index holding m
+                const long long base = pc.base0 + (long long)o * (long long)pc.plane;
                 long long idx = LLONG_MAX;
 #pragma unroll
                 for (int rr = 0; rr < MR; ++rr) {
                     float lo, hi;
                     upk(stv[rr], lo, hi);
-                    if (idx == LLONG_MAX && lo == m) idx = (long long)(base + (size_t)rr * a.W);
-                    if (idx == LLONG_MAX && hi == m) idx = (long long)(base + (size_t)rr * a.W + 1);
+                    if (idx == LLONG_MAX && lo == m) idx = base + (long long)rr * pc.W;
+                    if (idx == LLONG_MAX && hi == m) idx = base + (long long)rr * pc.W + 1;
                 }
                 if (am_better(m, idx, am->v, am->i)) {
                     am->v = m;
@@ -498,7 +603,7 @@ struct TileJob {
 // Returns false when a bounded wait gave up; p_stop / next_issue then bound the copies that
 // may still be in flight.
 template <typename T, typename C>
-__device__ __forceinline__ bool run_tile(Smem<T, C>& sm, const TileJob& j, unsigned int gp0, KahanF& acc,
+__device__ __forceinline__ bool run_tile(Smem<T, C>& sm, const TileJob& j, unsigned int gp0, KahanF2& acc,
                                          int& p_stop, int& next_issue) {
     constexpr int NT = C::NT, MR = C::MR, NSTAGE = C::NSTAGE, XR = C::XR;
     constexpr uint32_t kBoxBytes = C::RAW_H * BW * sizeof(T);
@@ -555,9 +660,12 @@ __device__ __forceinline__ bool run_tile(Smem<T, C>& sm, const TileJob& j, unsig
     for (int d = 0; d < RING; ++d)
 #pragma unroll
         for (int k = 0; k < MR; ++k) ring[d][k] = 0ull;
+    const PCtx<T> pc = p_ctx<T, C>(j.o, r0, ty0, gxp);
+    const SItem si = s_item<C>(tid);
+    const XItem xi = x_item<C>(tid);
     int failed = 0;
-    int p = 0;
-    for (; p < K + NWRAP; ++p) {
+    int p = 0, ph = 0;                                  // ph = p mod RING
+    for (; p < K + NWRAP; ++p, ph = ph == RING - 1 ? 0 : ph + 1) {
         if (p < K) {
             const unsigned int g = gp0 + (unsigned int)p;
             const int stage = g % NSTAGE;
@@ -579,7 +687,7 @@ __device__ __forceinline__ bool run_tile(Smem<T, C>& sm, const TileJob& j, unsig
                 failed = 1;
             }
             if (!failed) {
-                s_pass_any<T, C>(sm.raw[stage], sm.mk, sm.S, tid, xo, s.fx, s.fy);
+                s_pass_any<T, C>(sm.raw[stage], &sm.mk[0][0], &sm.S[0][0], si, xo, s.fx, s.fy);
             }
             if (__syncthreads_or(failed)) {
                 failed = 1;
@@ -592,17 +700,17 @@ __device__ __forceinline__ bool run_tile(Smem<T, C>& sm, const TileJob& j, unsig
                 }
                 next_issue = p + NSTAGE + 1;
             }
-            x_pass<C>(sm.S, sm.X, tid, j.g0, j.g1, j.g2);
+            x_pass<C>(&sm.S[0][0], &sm.X[0][0], xi, j.g0, j.g1, j.g2);
             __syncthreads();
         }
-        switch (p % RING) {
-            case 0: p_pass<T, C, 0>(sm.X, sm.wrap, j.o, tp, ring, cs, p, r0, cp, ty0, gxp, acc); break;
-            case 1: p_pass<T, C, 1>(sm.X, sm.wrap, j.o, tp, ring, cs, p, r0, cp, ty0, gxp, acc); break;
-            case 2: p_pass<T, C, 2>(sm.X, sm.wrap, j.o, tp, ring, cs, p, r0, cp, ty0, gxp, acc); break;
-            case 3: p_pass<T, C, 3>(sm.X, sm.wrap, j.o, tp, ring, cs, p, r0, cp, ty0, gxp, acc); break;
-            case 4: p_pass<T, C, 4>(sm.X, sm.wrap, j.o, tp, ring, cs, p, r0, cp, ty0, gxp, acc); break;
-            case 5: p_pass<T, C, 5>(sm.X, sm.wrap, j.o, tp, ring, cs, p, r0, cp, ty0, gxp, acc); break;
-            default: p_pass<T, C, 6>(sm.X, sm.wrap, j.o, tp, ring, cs, p, r0, cp, ty0, gxp, acc); break;
+        switch (ph) {
+            case 0: p_pass<T, C, 0>(sm.X, sm.wrap, pc, K, tp, ring, cs, p, r0, cp, acc); break;
+            case 1: p_pass<T, C, 1>(sm.X, sm.wrap, pc, K, tp, ring, cs, p, r0, cp, acc); break;
+            case 2: p_pass<T, C, 2>(sm.X, sm.wrap, pc, K, tp, ring, cs, p, r0, cp, acc); break;
+            case 3: p_pass<T, C, 3>(sm.X, sm.wrap, pc, K, tp, ring, cs, p, r0, cp, acc); break;
+            case 4: p_pass<T, C, 4>(sm.X, sm.wrap, pc, K, tp, ring, cs, p, r0, cp, acc); break;
+            case 5: p_pass<T, C, 5>(sm.X, sm.wrap, pc, K, tp, ring, cs, p, r0, cp, acc); break;
+            default: p_pass<T, C, 6>(sm.X, sm.wrap, pc, K, tp, ring, cs, p, r0, cp, acc); break;
         }
     }
     p_stop = p;
