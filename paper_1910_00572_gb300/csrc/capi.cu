@@ -175,7 +175,8 @@ LOC_API loc_status loc_session_bytes(const loc_params* p, size_t* bytes) {
     if (cap > hw) cap = hw;
     const size_t nrb = (H + 31) / 32;
     b += r(hw * 4) + r(hw) + 2 * r(H * 4) + r((nrb + 1) * W * 4) + r((nrb + 2) * 4) + r(cap * 4) +
-         r(cap * K * 4) + r(64) + r(reweight_scalars_bytes()) + r(K * 1080 * 8) + r(1080 * 4) + r(K * 1080 * 4);
+         r(cap * K * 4) + r(64) + r(reweight_scalars_bytes()) + r(K * 1080 * 8) + r(1080 * 4) + r(K * 1080 * 4) +
+         r(H * ((W + 31) / 32) * 4);
     *bytes = b;
     return LOC_OK;
 }
@@ -422,6 +423,7 @@ loc_status lidar_setup(loc_session* h) {
     h->cap = (int)cap;
     const int nrb = (H + 31) / 32;
     h->m = (float*)dev_alloc(h, sizeof(float) * hw);
+    h->travbits = (uint32_t*)dev_alloc(h, sizeof(uint32_t) * (size_t)H * ((W + 31) / 32));
     h->sel = (uint8_t*)dev_alloc(h, hw);
     h->rowcnt = (int*)dev_alloc(h, sizeof(int) * H);
     h->rowoff = (int*)dev_alloc(h, sizeof(int) * H);
@@ -432,9 +434,10 @@ loc_status lidar_setup(loc_session* h) {
     h->dscal = (int*)dev_alloc(h, 64);
     h->rs = dev_alloc(h, reweight_scalars_bytes());
     if (!h->m || !h->sel || !h->rowcnt || !h->rowoff || !h->bnd || !h->prog || !h->samples || !h->logL ||
-        !h->dscal || !h->rs)
+        !h->dscal || !h->rs || !h->travbits)
         return fail(h, LOC_ERR_OOM, "LIDAR scratch allocation failed");
     cudaError_t e = cudaMemsetAsync(h->dscal, 0, 64, h->stream);
+    if (e == cudaSuccess) e = launch_pack_bits(h->trav, H, W, h->travbits, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->rs, 0, reweight_scalars_bytes(), h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "LIDAR scratch init");
     h->lidar_ready = true;
@@ -602,7 +605,7 @@ loc_status score_and_reweight(loc_session* h, int n_used, int n_dirs, double r_m
     const double cell = h->p.cell_m;
     const uint32_t seed = pcg_hash((uint32_t)h->n_lidar * 0x85EBCA6Bu + 0x27D4EB2Fu);
     cudaError_t e = launch_score_reweight(
-        h->B[h->cur], h->p.storage, h->trav, h->p.H, h->p.W, h->p.K, h->samples, h->dscal, h->cap, h->dirs,
+        h->B[h->cur], h->p.storage, h->trav, h->travbits, h->p.H, h->p.W, h->p.K, h->samples, h->dscal, h->cap, h->dirs,
         n_dirs, h->dir_of, h->z, n_used, (float)(r_max / cell), (float)cell, (float)(1.0 / (2.0 * sigma_r * sigma_r)),
         h->logL, reinterpret_cast<unsigned int*>(h->dscal + 1), h->rs, h->partials, h->nparts, seed, h->sd,
         h->stream);

@@ -8,10 +8,11 @@ namespace loc {
 
 // Distance in cells from the centre of free cell (j, i) along (dx, dy) to the first occupied
 // cell or the grid edge, capped at rmax; ties step x first.  Same FP32 operations, in the
-// same order, as the reference walk.
-__device__ __forceinline__ float dda_cells(const uint8_t* __restrict__ trav, int H, int W, int j, int i, float dx, float dy,
-                           float rmax) {
-    if (!trav[(size_t)j * W + i]) return 0.0f;
+// same order, as the reference walk.  free_at(j, i) tells whether an in-grid cell is free.
+template <typename FreeAt>
+__device__ __forceinline__ float dda_walk(const FreeAt& free_at, int H, int W, int j, int i, float dx, float dy,
+                                          float rmax) {
+    if (!free_at(j, i)) return 0.0f;
     const int sx = dx > 0.0f ? 1 : -1, sy = dy > 0.0f ? 1 : -1;
     const float tdx = dx != 0.0f ? __fdiv_rn(1.0f, fabsf(dx)) : INFINITY;
     const float tdy = dy != 0.0f ? __fdiv_rn(1.0f, fabsf(dy)) : INFINITY;
@@ -26,9 +27,15 @@ __device__ __forceinline__ float dda_cells(const uint8_t* __restrict__ trav, int
         else          { j += sy; ny += 1; t = ty; }
         if (t >= rmax) return rmax;
         if (i < 0 || i >= W || j < 0 || j >= H) return t;
-        if (!trav[(size_t)j * W + i]) return t;
+        if (!free_at(j, i)) return t;
     }
     return rmax;
+}
+
+// The walk on the byte map (1 = free).
+__device__ __forceinline__ float dda_cells(const uint8_t* __restrict__ trav, int H, int W, int j, int i, float dx, float dy,
+                                           float rmax) {
+    return dda_walk([trav, W](int jj, int ii) { return trav[(size_t)jj * W + ii] != 0; }, H, W, j, i, dx, dy, rmax);
 }
 
 }  // namespace loc

@@ -163,7 +163,10 @@ cudaError_t launch_ray_ranges(const uint8_t* trav, int H, int W, const int32_t* 
                               int n_dirs, float rmax_cells, float cell_m, float* out, cudaStream_t st);
 size_t reweight_scalars_bytes();
 // Score the samples against the scan and reweight them (Eq. 9 on the sampled set).
-cudaError_t launch_score_reweight(void* B, int storage, const uint8_t* trav, int H, int W, int K,
+// The map as bits (row j: ceil(W / 32) words, bit b of word w = cell (j, 32 w + b) is free).
+cudaError_t launch_pack_bits(const uint8_t* trav, int H, int W, uint32_t* bits, cudaStream_t st);
+// bits (from launch_pack_bits, or null) lets the ray casts read a shared-memory window of the map.
+cudaError_t launch_score_reweight(void* B, int storage, const uint8_t* trav, const uint32_t* bits, int H, int W, int K,
                                   const int32_t* samples, const int* count, int cap, const float* dirs, int n_dirs,
                                   const int32_t* dir_of, const float* z, int n_used, float rmax_cells, float cell_m,
                                   float inv2s2, float* logL, unsigned int* maxL, void* rs, double* partials,

@@ -5,6 +5,7 @@
 // The two steps whose results are integers decided by floating point -- the dithering and
 // the ray walk -- use FP32 with every operation explicitly rounded (__fadd_rn / __fmul_rn /
 // __fdiv_rn, so nothing is contracted into an FMA) in a fixed order.
+#include <algorithm>
 #include <cfloat>
 
 #include "dda.cuh"
@@ -116,6 +117,7 @@ __global__ void __launch_bounds__(NT) belief_map_vec_kernel(const T* __restrict_
 // its place.  Terms of the error sum whose source lies outside the grid are zero (their errors
 // were never produced), so the sum always takes the same four terms in the same order; only
 // the right neighbour above is masked at the last column.
+constexpr size_t kScoreWindowBytes = 96 * 1024;   // shared memory for the score kernel's map window
 constexpr int kFsWarps = 16;
 constexpr int kFsPitch = 97;              // 3 x 32 columns + 1: lane accesses hit distinct banks
 
@@ -332,21 +334,59 @@ __device__ __forceinline__ float ord2f(unsigned int u) {
     return __uint_as_float((u & 0x80000000u) ? (u & 0x7FFFFFFFu) : ~u);
 }
 
+// The map as bits: bit b of word w of row j is 1 when cell (j, 32 w + b) is free (words per row
+// wb = ceil(W / 32); bits past W are 0).
+__global__ void __launch_bounds__(NT) pack_bits_kernel(const uint8_t* __restrict__ trav, int H, int W, int wb,
+                                                       uint32_t* __restrict__ bits) {
+    const size_t n = (size_t)H * wb;
+    for (size_t q = (size_t)blockIdx.x * NT + threadIdx.x; q < n; q += (size_t)gridDim.x * NT) {
+        const int j = (int)(q / wb), w = (int)(q % wb);
+        uint32_t v = 0;
+        for (int b = 0; b < 32; ++b) {
+            const int i = 32 * w + b;
+            if (i < W && trav[(size_t)j * W + i]) v |= 1u << b;
+        }
+        bits[q] = v;
+    }
+}
+
 // One CTA per sampled cell (grid-stride): cast the n_dirs distinct rays once, then for every
 // bin k: logL[s][k] = -sum_b (z_b - r(dir_of[k][b]))^2 / (2 sigma^2) over the used beams.
-__global__ void __launch_bounds__(NT) score_kernel(const uint8_t* __restrict__ trav, int H, int W, int K,
+// With WIN the CTA first copies the map bits within R = ceil(rmax) + 2 cells of the sampled
+// cell into shared memory (every cell a walk capped at rmax can look at), so each step of the
+// walk reads shared memory instead of global memory; the walk itself is the same.
+template <bool WIN>
+__global__ void __launch_bounds__(NT) score_kernel(const uint8_t* __restrict__ trav, const uint32_t* __restrict__ bits,
+                                                   int wb, int R, int wwin, int H, int W, int K,
                                                    const int32_t* __restrict__ samples, const int* count_ptr, int cap,
                                                    const float* __restrict__ dirs, int n_dirs,
                                                    const int32_t* __restrict__ dir_of, const float* __restrict__ z,
                                                    int n_used, float rmax, float cell_m, float inv2s2,
                                                    float* __restrict__ logL) {
-    extern __shared__ float rh[];                 // n_dirs expected ranges (metres)
+    extern __shared__ float rh[];                 // n_dirs expected ranges (metres), then the window
+    uint32_t* win = reinterpret_cast<uint32_t*>(rh + ((n_dirs + 3) & ~3));
     const int n = min(*count_ptr, cap);
     for (int s = blockIdx.x; s < n; s += gridDim.x) {
         const int cell = samples[s];
         const int j = cell / W, i = cell % W;
-        for (int d = threadIdx.x; d < n_dirs; d += NT)
-            rh[d] = __fmul_rn(dda_cells(trav, H, W, j, i, dirs[2 * d], dirs[2 * d + 1], rmax), cell_m);
+        if constexpr (WIN) {
+            const int j0 = max(0, j - R), j1 = min(H - 1, j + R);
+            const int w0 = max(0, i - R) >> 5, w1 = min(W - 1, i + R) >> 5;
+            const int rows = j1 - j0 + 1, words = w1 - w0 + 1;
+            for (int q = threadIdx.x; q < rows * words; q += NT) {
+                const int r = q / words, c = q % words;
+                win[r * wwin + c] = bits[(size_t)(j0 + r) * wb + w0 + c];
+            }
+            __syncthreads();
+            const auto free_at = [win, j0, w0, wwin](int jj, int ii) {
+                return ((win[(jj - j0) * wwin + ((ii >> 5) - w0)] >> (ii & 31)) & 1u) != 0u;
+            };
+            for (int d = threadIdx.x; d < n_dirs; d += NT)
+                rh[d] = __fmul_rn(dda_walk(free_at, H, W, j, i, dirs[2 * d], dirs[2 * d + 1], rmax), cell_m);
+        } else {
+            for (int d = threadIdx.x; d < n_dirs; d += NT)
+                rh[d] = __fmul_rn(dda_cells(trav, H, W, j, i, dirs[2 * d], dirs[2 * d + 1], rmax), cell_m);
+        }
         __syncthreads();
         for (int k = threadIdx.x; k < K; k += NT) {
             float acc = 0.0f;
@@ -545,21 +585,43 @@ cudaError_t launch_ray_ranges(const uint8_t* trav, int H, int W, const int32_t* 
     return cudaGetLastError();
 }
 
-cudaError_t launch_score_reweight(void* B, int storage, const uint8_t* trav, int H, int W, int K,
+cudaError_t launch_pack_bits(const uint8_t* trav, int H, int W, uint32_t* bits, cudaStream_t st) {
+    const int wb = (W + 31) / 32;
+    pack_bits_kernel<<<grid_for((size_t)H * wb, 4096), NT, 0, st>>>(trav, H, W, wb, bits);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_score_reweight(void* B, int storage, const uint8_t* trav, const uint32_t* bits, int H, int W, int K,
                                   const int32_t* samples, const int* count, int cap, const float* dirs, int n_dirs,
                                   const int32_t* dir_of, const float* z, int n_used, float rmax_cells, float cell_m,
                                   float inv2s2, float* logL, unsigned int* maxL, void* rs, double* partials,
                                   unsigned int nparts, uint32_t seed, SessionDev* sd, cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(maxL, 0, sizeof(unsigned int), st);
     if (e != cudaSuccess) return e;
-    const size_t smem = sizeof(float) * (size_t)n_dirs;
-    if (smem > 48 * 1024) {
-        e = cudaFuncSetAttribute(score_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-    }
+    // the map window (R cells around the sampled cell) in shared memory when it fits
+    const int R = (int)ceilf(rmax_cells) + 2;
+    const int wwin = (2 * R + 1 + 31) / 32 + 1;
+    const size_t rh_bytes = sizeof(float) * (size_t)((n_dirs + 3) & ~3);
+    const size_t win_bytes = sizeof(uint32_t) * (size_t)(2 * R + 1) * wwin;
+    const bool use_win = bits != nullptr && R < 4096 && rh_bytes + win_bytes <= kScoreWindowBytes;
+    const size_t smem = rh_bytes + (use_win ? win_bytes : 0);
     const unsigned int ns = (unsigned int)(cap < 8192 ? (cap > 0 ? cap : 1) : 8192);
-    score_kernel<<<ns, NT, smem, st>>>(trav, H, W, K, samples, count, cap, dirs, n_dirs, dir_of, z, n_used,
-                                       rmax_cells, cell_m, inv2s2, logL);
+    const int wb = (W + 31) / 32;
+    if (use_win) {
+        if (smem > 48 * 1024) {
+            e = cudaFuncSetAttribute(score_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+        }
+        score_kernel<true><<<ns, NT, smem, st>>>(trav, bits, wb, R, wwin, H, W, K, samples, count, cap, dirs, n_dirs,
+                                                 dir_of, z, n_used, rmax_cells, cell_m, inv2s2, logL);
+    } else {
+        if (smem > 48 * 1024) {
+            e = cudaFuncSetAttribute(score_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+        }
+        score_kernel<false><<<ns, NT, smem, st>>>(trav, bits, wb, R, wwin, H, W, K, samples, count, cap, dirs, n_dirs,
+                                                  dir_of, z, n_used, rmax_cells, cell_m, inv2s2, logL);
+    }
     const size_t hw = (size_t)H * W;
     const unsigned int half = nparts / 2 < 1024 ? nparts / 2 : 1024;
     const unsigned int nb = grid_for((size_t)cap * K, half > 0 ? half : 1);

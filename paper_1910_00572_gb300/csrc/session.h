@@ -43,6 +43,7 @@ struct loc_session {
     bool lidar_ready = false;
     int cap = 0;                   // capacity of the sample list
     float* m = nullptr;            // belief map [H][W]
+    uint32_t* travbits = nullptr;  // the map as bits [H][ceil(W / 32)] (the ray casts' window)
     uint8_t* sel = nullptr;        // selection mask [H][W]
     int* rowcnt = nullptr;         // per-row selections [H]
     int* rowoff = nullptr;         // exclusive prefix [H]

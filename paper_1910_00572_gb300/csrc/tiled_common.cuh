@@ -263,10 +263,11 @@ __device__ __forceinline__ void s_pass(const T* raw, const float* mk, float* S, 
             xl[k] = ffma2(fx2, d, pk(v[XO + 2 * k], v[XO + 2 * k + 1]));
         }
         if (r > 0) {
-            const f2* m2 = reinterpret_cast<const f2*>(mp + (r - 1) * MW);
+            // one 16-byte mask load (two 8-byte loads 16 bytes apart would conflict 2-way)
+            const float4 m = *reinterpret_cast<const float4*>(mp + (r - 1) * MW);
             f2* o2 = reinterpret_cast<f2*>(sp + (r - 1) * SW);
-            const f2 o0 = fmul2(m2[0], ffma2(fy2, xl[0], fmul2(gy2, prev[0])));
-            const f2 o1 = fmul2(m2[1], ffma2(fy2, xl[1], fmul2(gy2, prev[1])));
+            const f2 o0 = fmul2(pk(m.x, m.y), ffma2(fy2, xl[0], fmul2(gy2, prev[0])));
+            const f2 o1 = fmul2(pk(m.z, m.w), ffma2(fy2, xl[1], fmul2(gy2, prev[1])));
             float a, b, c, d;
             upk(o0, a, b);
             upk(o1, c, d);

@@ -42,8 +42,10 @@ def make(occ, K, cell, **kw):
 # ------------------------------------------------------------------ Floyd-Steinberg
 
 @pytest.mark.parametrize("H,W,n_s", [(5, 7, 6), (64, 64, 300), (100, 37, 500), (300, 257, 4096),
-                                     (97, 1100, 2000), (2048, 2048, 4096)])
+                                     (97, 1100, 2000), (2048, 2048, 4096), (4200, 96, 3000)])
 def test_dithering_is_bit_exact(H, W, n_s):
+    """Bit-exact against the oracle's FP32 C code, from a handful of cells to 2048 x 2048 and
+    4200 rows (132 row blocks, so each of the 16 warps takes eight or nine blocks)."""
     m = fields.map_like(H, W, seed=H + W)
     fs = float(OL.fs_factor(m, n_s))
     h = make(np.zeros((H, W), np.uint8), 8, 0.05)
