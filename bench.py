@@ -580,14 +580,17 @@ def serve_run(loc, wl, sess, streams, storage, batching, realtime, warm_windows,
         bytes_in = {"odometry": 0, "scans": 0}
 
         def submit(j0, j1, sc0, sc1, t0):
-            """Messages [j0, j1) and scans [sc0, sc1), in arrival order; t0 None: all at once."""
+            """Messages [j0, j1) and scans [sc0, sc1), in arrival order; t0 None: all at once,
+            else each when its time (t0 + its offset) has come.  The server stamps a message's
+            arrival when it is submitted, so the latencies are the server's own, from receipt
+            to the end of the message's device work."""
             j, sc = j0, sc0
 
             def odometry_upto(k):
                 nonlocal j
                 if k > j:
                     loc.loc_server_odometry(srv, ids_a[odo_s[j:k]], u[j:k], v[j:k], w[j:k],
-                                            t0 + odo_t[j:k] - t_split if t0 is not None else None)
+                                            None)
                     bytes_in["odometry"] += (k - j) * (4 + 3 * 8)      # id + (u, v, w)
                     j = k
             while j < j1 or sc < sc1:
@@ -597,7 +600,7 @@ def serve_run(loc, wl, sess, streams, storage, batching, realtime, warm_windows,
                     odometry_upto(min(j1, int(np.searchsorted(odo_t, ts, side="right"))))
                     z = pool[q][min(3, 4 * i // per_session)]
                     loc.loc_server_scan(srv, ids[q], z, 0.0, wl["angle_inc"], wl["r_max"], wl["beam_stride"],
-                                        wl["sigma_r"], t0 + ts - t_split if t0 is not None else -1.0)
+                                        wl["sigma_r"], -1.0)
                     bytes_in["scans"] += z.size * 4
                     sc += 1
                 odometry_upto(min(j1, int(np.searchsorted(odo_t, now, side="right"))) if t0 is not None else j1)

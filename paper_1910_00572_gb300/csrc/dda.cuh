@@ -7,8 +7,9 @@
 namespace loc {
 
 // Distance in cells from the centre of free cell (j, i) along (dx, dy) to the first occupied
-// cell or the grid edge, capped at rmax; ties step x first.  Same FP32 operations, in the
-// same order, as the reference walk.  free_at(j, i) tells whether an in-grid cell is free.
+// cell or the grid edge, capped at rmax; ties step x first.  Every crossing time is the FP32
+// value the reference walk computes, t = fl(fl(n + 1/2) * fl(1 / |d|)), so the decisions and the
+// result are the same bit for bit.  free_at(j, i) tells whether an in-grid cell is free.
 template <typename FreeAt>
 __device__ __forceinline__ float dda_walk(const FreeAt& free_at, int H, int W, int j, int i, float dx, float dy,
                                           float rmax) {
@@ -16,17 +17,28 @@ __device__ __forceinline__ float dda_walk(const FreeAt& free_at, int H, int W, i
     const int sx = dx > 0.0f ? 1 : -1, sy = dy > 0.0f ? 1 : -1;
     const float tdx = dx != 0.0f ? __fdiv_rn(1.0f, fabsf(dx)) : INFINITY;
     const float tdy = dy != 0.0f ? __fdiv_rn(1.0f, fabsf(dy)) : INFINITY;
-    int nx = 0, ny = 0;
+    // the next crossings: t_x = (n_x + 1/2) * tdx, t_y likewise, n the cells stepped so far;
+    // n + 1/2 is kept as a float (exact: an integer plus one half, far below 2^23) and only the
+    // crossing that was taken is recomputed, so every value equals the per-step formula
+    float ax = 0.5f, ay = 0.5f;
+    float tx = __fmul_rn(ax, tdx), ty = __fmul_rn(ay, tdy);
     // every step crosses one cell boundary and t grows by at least 1/2 cell per two steps
     const int max_steps = 4 * (int)rmax + 16;
     for (int s = 0; s < max_steps; ++s) {
-        const float tx = __fmul_rn(__fadd_rn((float)nx, 0.5f), tdx);
-        const float ty = __fmul_rn(__fadd_rn((float)ny, 0.5f), tdy);
         float t;
-        if (tx <= ty) { i += sx; nx += 1; t = tx; }
-        else          { j += sy; ny += 1; t = ty; }
+        if (tx <= ty) {
+            i += sx;
+            t = tx;
+            ax = __fadd_rn(ax, 1.0f);
+            tx = __fmul_rn(ax, tdx);
+        } else {
+            j += sy;
+            t = ty;
+            ay = __fadd_rn(ay, 1.0f);
+            ty = __fmul_rn(ay, tdy);
+        }
         if (t >= rmax) return rmax;
-        if (i < 0 || i >= W || j < 0 || j >= H) return t;
+        if ((unsigned)i >= (unsigned)W || (unsigned)j >= (unsigned)H) return t;
         if (!free_at(j, i)) return t;
     }
     return rmax;

@@ -118,6 +118,7 @@ __global__ void __launch_bounds__(NT) belief_map_vec_kernel(const T* __restrict_
 // were never produced), so the sum always takes the same four terms in the same order; only
 // the right neighbour above is masked at the last column.
 constexpr size_t kScoreWindowBytes = 96 * 1024;   // shared memory for the score kernel's map window
+constexpr int kScoreNT = 384;                      // score kernel threads: 360 beam directions in one round
 constexpr int kFsWarps = 16;
 constexpr int kFsPitch = 97;              // 3 x 32 columns + 1: lane accesses hit distinct banks
 
@@ -356,7 +357,7 @@ __global__ void __launch_bounds__(NT) pack_bits_kernel(const uint8_t* __restrict
 // cell into shared memory (every cell a walk capped at rmax can look at), so each step of the
 // walk reads shared memory instead of global memory; the walk itself is the same.
 template <bool WIN>
-__global__ void __launch_bounds__(NT) score_kernel(const uint8_t* __restrict__ trav, const uint32_t* __restrict__ bits,
+__global__ void __launch_bounds__(kScoreNT) score_kernel(const uint8_t* __restrict__ trav, const uint32_t* __restrict__ bits,
                                                    int wb, int R, int wwin, int H, int W, int K,
                                                    const int32_t* __restrict__ samples, const int* count_ptr, int cap,
                                                    const float* __restrict__ dirs, int n_dirs,
@@ -373,7 +374,7 @@ __global__ void __launch_bounds__(NT) score_kernel(const uint8_t* __restrict__ t
             const int j0 = max(0, j - R), j1 = min(H - 1, j + R);
             const int w0 = max(0, i - R) >> 5, w1 = min(W - 1, i + R) >> 5;
             const int rows = j1 - j0 + 1, words = w1 - w0 + 1;
-            for (int q = threadIdx.x; q < rows * words; q += NT) {
+            for (int q = threadIdx.x; q < rows * words; q += kScoreNT) {
                 const int r = q / words, c = q % words;
                 win[r * wwin + c] = bits[(size_t)(j0 + r) * wb + w0 + c];
             }
@@ -381,22 +382,25 @@ __global__ void __launch_bounds__(NT) score_kernel(const uint8_t* __restrict__ t
             const auto free_at = [win, j0, w0, wwin](int jj, int ii) {
                 return ((win[(jj - j0) * wwin + ((ii >> 5) - w0)] >> (ii & 31)) & 1u) != 0u;
             };
-            for (int d = threadIdx.x; d < n_dirs; d += NT)
+            for (int d = threadIdx.x; d < n_dirs; d += kScoreNT)
                 rh[d] = __fmul_rn(dda_walk(free_at, H, W, j, i, dirs[2 * d], dirs[2 * d + 1], rmax), cell_m);
         } else {
-            for (int d = threadIdx.x; d < n_dirs; d += NT)
+            for (int d = threadIdx.x; d < n_dirs; d += kScoreNT)
                 rh[d] = __fmul_rn(dda_cells(trav, H, W, j, i, dirs[2 * d], dirs[2 * d + 1], rmax), cell_m);
         }
         __syncthreads();
-        for (int k = threadIdx.x; k < K; k += NT) {
-            float acc = 0.0f;
+        // one warp per bin: lane l sums the beams b = l, l + 32, ... in order, then a fixed
+        // shuffle tree adds the lanes
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        for (int k = warp; k < K; k += kScoreNT / 32) {
             const int32_t* row = dir_of + (size_t)k * n_used;
-            for (int b = 0; b < n_used; ++b) {
+            float acc = 0.0f;
+            for (int b = lane; b < n_used; b += 32) {
                 const float e = z[b] - rh[row[b]];
                 acc = fmaf(e, e, acc);
             }
-            const float l = -acc * inv2s2;
-            logL[(size_t)s * K + k] = l;
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+            if (lane == 0) logL[(size_t)s * K + k] = -acc * inv2s2;
         }
         __syncthreads();
     }
@@ -605,21 +609,22 @@ cudaError_t launch_score_reweight(void* B, int storage, const uint8_t* trav, con
     const size_t win_bytes = sizeof(uint32_t) * (size_t)(2 * R + 1) * wwin;
     const bool use_win = bits != nullptr && R < 4096 && rh_bytes + win_bytes <= kScoreWindowBytes;
     const size_t smem = rh_bytes + (use_win ? win_bytes : 0);
-    const unsigned int ns = (unsigned int)(cap < 8192 ? (cap > 0 ? cap : 1) : 8192);
+    // a grid-stride over the samples: CTAs past the count exit at once, but each still costs a launch
+    const unsigned int ns = (unsigned int)(cap < 2048 ? (cap > 0 ? cap : 1) : 2048);
     const int wb = (W + 31) / 32;
     if (use_win) {
         if (smem > 48 * 1024) {
             e = cudaFuncSetAttribute(score_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e != cudaSuccess) return e;
         }
-        score_kernel<true><<<ns, NT, smem, st>>>(trav, bits, wb, R, wwin, H, W, K, samples, count, cap, dirs, n_dirs,
+        score_kernel<true><<<ns, kScoreNT, smem, st>>>(trav, bits, wb, R, wwin, H, W, K, samples, count, cap, dirs, n_dirs,
                                                  dir_of, z, n_used, rmax_cells, cell_m, inv2s2, logL);
     } else {
         if (smem > 48 * 1024) {
             e = cudaFuncSetAttribute(score_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e != cudaSuccess) return e;
         }
-        score_kernel<false><<<ns, NT, smem, st>>>(trav, bits, wb, R, wwin, H, W, K, samples, count, cap, dirs, n_dirs,
+        score_kernel<false><<<ns, kScoreNT, smem, st>>>(trav, bits, wb, R, wwin, H, W, K, samples, count, cap, dirs, n_dirs,
                                                   dir_of, z, n_used, rmax_cells, cell_m, inv2s2, logL);
     }
     const size_t hw = (size_t)H * W;
