@@ -535,9 +535,11 @@ __global__ void materialize_kernel(T* __restrict__ B, const uint8_t* __restrict_
 
 cudaError_t launch_materialize(void* B, int storage, const uint8_t* trav, SessionDev* sd, float value,
                                size_t hw, int K, double* partials, unsigned int nparts, cudaStream_t st) {
+    // grid-stride over the tensor with a small grid: almost every call finds the restart flag
+    // clear and every CTA returns at once, so the launch should cost little
     unsigned int nb = (unsigned int)((hw * K + NT - 1) / NT);
     if (nb > nparts) nb = nparts;
-    if (nb > 4096) nb = 4096;
+    if (nb > 304) nb = 304;
     switch (storage) {
         case LOC_F32: materialize_kernel<float><<<nb, NT, 0, st>>>((float*)B, trav, sd, value, hw, K, partials); break;
         case LOC_BF16: materialize_kernel<__nv_bfloat16><<<nb, NT, 0, st>>>((__nv_bfloat16*)B, trav, sd, value, hw, K, partials); break;
