@@ -57,7 +57,6 @@ batch_kernel(const BatchStatic* __restrict__ ss, const BatchTick* __restrict__ t
         j.tmap = tmap;
         j.sh = shifts + S.sh_off;
         j.o.B_out = S.B[1 - t.cur];
-        j.o.seed = t.seed;
         j.o.H = S.H;
         j.o.W = S.W;
         j.o.K = S.K;

@@ -142,7 +142,7 @@ cudaError_t autotune(BatchCore* c) {
     int best_cfg = 0;
     const std::vector<char> all(c->sess.size(), 1);
     BatchTick* ht = static_cast<BatchTick*>(c->h_tick[0]);
-    for (size_t s = 0; s < c->sess.size(); ++s) ht[s] = BatchTick{c->sess[s]->cur, 0, 0u, 0};
+    for (size_t s = 0; s < c->sess.size(); ++s) ht[s] = BatchTick{c->sess[s]->cur, 0, 0, 0};
     std::memset(static_cast<unsigned char*>(c->h_tick[0]) + c->lay.shifts_off, 0, c->lay.bytes - c->lay.shifts_off);
     for (int cfg = 1; cfg <= batch_num_cfgs() && e == cudaSuccess; ++cfg) {
         e = build_static(c, cfg);
@@ -367,7 +367,7 @@ LOC_API loc_status loc_batch_step(loc_batch b, const double* u, const double* v,
     for (size_t s = 0; s < n; ++s) {
         loc_session* h = c->sess[s];
         if (odometry_advance(h, u[s], v[s], w[s])) {
-            ht[s] = BatchTick{h->cur, 0, step_seed(h), 0};
+            ht[s] = BatchTick{h->cur, 0, 0, 0};
             shift_table(h, hs + off);
             active[s] = 1;
             ++moved;

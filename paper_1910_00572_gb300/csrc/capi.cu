@@ -347,9 +347,6 @@ void shift_table(const loc_session* h, Shift* sh) {
     }
 }
 
-// Key of the stochastic rounding of propagation number n_prop.
-uint32_t step_seed(const loc_session* h) { return pcg_hash((uint32_t)h->n_prop * 0x9E3779B9u + 0x632BE5ABu); }
-
 // After a propagation was enqueued: the output buffer becomes current.  A fused argmax
 // result, if any, is for the previous tensor (loc_step marks a fresh one afterwards).
 void step_done(loc_session* h) {
@@ -382,7 +379,6 @@ LOC_API loc_status loc_step(loc_handle h, double u, double v, double w) {
     a.inv_uniform = h->inv_uniform;
     a.out_mult = storage_mult(h->p.storage);
     a.log_out_mult = std::log((double)a.out_mult);
-    a.seed = step_seed(h);
     a.H = h->p.H;
     a.W = h->p.W;
     a.K = h->p.K;
@@ -603,11 +599,10 @@ loc_status score_and_reweight(loc_session* h, int n_used, int n_dirs, double r_m
     if (n_used == 0 || n_dirs == 0) return LOC_OK;        // nothing to score
     h->am_valid = false;
     const double cell = h->p.cell_m;
-    const uint32_t seed = pcg_hash((uint32_t)h->n_lidar * 0x85EBCA6Bu + 0x27D4EB2Fu);
     cudaError_t e = launch_score_reweight(
         h->B[h->cur], h->p.storage, h->trav, h->travbits, h->p.H, h->p.W, h->p.K, h->samples, h->dscal, h->cap, h->dirs,
         n_dirs, h->dir_of, h->z, n_used, (float)(r_max / cell), (float)cell, (float)(1.0 / (2.0 * sigma_r * sigma_r)),
-        h->logL, reinterpret_cast<unsigned int*>(h->dscal + 1), h->rs, h->partials, h->nparts, seed, h->sd,
+        h->logL, reinterpret_cast<unsigned int*>(h->dscal + 1), h->rs, h->partials, h->nparts, h->sd,
         h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "score/reweight launch");
     h->n_lidar += 1;
@@ -849,10 +844,9 @@ LOC_API loc_status loc_lidar_update_dense(loc_handle h, const float* ranges, int
                                h->dense_max, h->stream);
     h->am_valid = false;
     if (e == cudaSuccess)
-        e = launch_dense_apply(h->B[h->cur], h->p.storage, h->dense_logL, h->n, h->dense_max,
-                               (float)std::log((double)storage_mult(h->p.storage)),
-                               pcg_hash((uint32_t)h->n_dense * 0x9E3779B1u + 0x7F4A7C15u), h->partials, h->nparts,
-                               h->sd, h->stream);
+        e = launch_dense_apply(h->B[h->cur], h->p.storage, h->dense_logL, (size_t)h->p.H * h->p.W, K, h->dense_max,
+                               (float)std::log((double)storage_mult(h->p.storage)), h->partials, h->nparts, h->sd,
+                               h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "dense scan update launch");
     h->n_dense += 1;
     return LOC_OK;

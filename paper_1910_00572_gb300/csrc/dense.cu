@@ -155,20 +155,25 @@ __global__ void __launch_bounds__(DC) dense_score_kernel(const uint8_t* __restri
 }
 
 template <typename T>
-__global__ void __launch_bounds__(NT) dense_apply_kernel(T* __restrict__ B, const float* __restrict__ logL, size_t n,
-                                                         const unsigned int* maxL, float log_mult, uint32_t seed,
+__global__ void __launch_bounds__(NT) dense_apply_kernel(T* __restrict__ B, const float* __restrict__ logL, size_t hw,
+                                                         int K, const unsigned int* maxL, float log_mult,
                                                          double* partials, SessionDev* sd) {
     __shared__ double red[NT / 32];
     const float c = ord2f(*maxL);                 // max of log L + log X
     const float off = log_mult - c;
     KahanF acc;
-    for (size_t q = (size_t)blockIdx.x * NT + threadIdx.x; q < n; q += (size_t)gridDim.x * NT) {
-        const float x = Store<T>::ld(B + q);
-        // x exp(log L + off) <= mult; for a small x the factor alone could overflow, so a large
-        // exponent takes log x in (the multiply keeps x's precision elsewhere)
-        const float e = logL[q] + off;
-        const float v = x > 0.0f ? (e < 80.0f ? x * expf(e) : expf(e + logf(x))) : 0.0f;
-        acc.add(store_out<T>(B + q, v, pcg_hash((uint32_t)q ^ seed)));
+    // one thread per cell, its bins in order: the BF16 rounding residual runs along theta
+    for (size_t cell = (size_t)blockIdx.x * NT + threadIdx.x; cell < hw; cell += (size_t)gridDim.x * NT) {
+        float res = 0.0f;
+        for (int k = 0; k < K; ++k) {
+            const size_t q = (size_t)k * hw + cell;
+            const float x = Store<T>::ld(B + q);
+            // x exp(log L + off) <= mult; for a small x the factor alone could overflow, so a large
+            // exponent takes log x in (the multiply keeps x's precision elsewhere)
+            const float e = logL[q] + off;
+            const float v = x > 0.0f ? (e < 80.0f ? x * expf(e) : expf(e + logf(x))) : 0.0f;
+            acc.add(store_diffused<T>(B + q, v, res));
+        }
     }
     const double bt = block_sum<NT>(acc.value(), red);
     const unsigned int nblocks = gridDim.x;
@@ -344,23 +349,23 @@ cudaError_t launch_dense_score(const uint8_t* table, const uint8_t* trav, const 
     }
 }
 
-cudaError_t launch_dense_apply(void* B, int storage, const float* logL, size_t n, const unsigned int* maxL,
-                               float log_mult, uint32_t seed, double* partials, unsigned int nparts,
-                               SessionDev* sd, cudaStream_t st) {
-    size_t nb = (n + NT - 1) / NT;
+cudaError_t launch_dense_apply(void* B, int storage, const float* logL, size_t hw, int K, const unsigned int* maxL,
+                               float log_mult, double* partials, unsigned int nparts, SessionDev* sd,
+                               cudaStream_t st) {
+    size_t nb = (hw + NT - 1) / NT;
     if (nb > nparts) nb = nparts;
     if (nb > 4096) nb = 4096;
     if (nb < 1) nb = 1;
     switch (storage) {
         case LOC_F32:
-            dense_apply_kernel<float><<<(unsigned int)nb, NT, 0, st>>>((float*)B, logL, n, maxL, log_mult, seed, partials, sd);
+            dense_apply_kernel<float><<<(unsigned int)nb, NT, 0, st>>>((float*)B, logL, hw, K, maxL, log_mult, partials, sd);
             break;
         case LOC_BF16:
-            dense_apply_kernel<__nv_bfloat16><<<(unsigned int)nb, NT, 0, st>>>((__nv_bfloat16*)B, logL, n, maxL,
-                                                                               log_mult, seed, partials, sd);
+            dense_apply_kernel<__nv_bfloat16><<<(unsigned int)nb, NT, 0, st>>>((__nv_bfloat16*)B, logL, hw, K, maxL,
+                                                                               log_mult, partials, sd);
             break;
         case LOC_F16:
-            dense_apply_kernel<__half><<<(unsigned int)nb, NT, 0, st>>>((__half*)B, logL, n, maxL, log_mult, seed, partials, sd);
+            dense_apply_kernel<__half><<<(unsigned int)nb, NT, 0, st>>>((__half*)B, logL, hw, K, maxL, log_mult, partials, sd);
             break;
         default: return cudaErrorInvalidValue;
     }

@@ -26,9 +26,9 @@ size_t dense_score_smem(int A, int K, int nu);
 cudaError_t launch_dense_score(const uint8_t* table, const uint8_t* trav, const void* B, int storage, int H, int W,
                                int K, int A, const int* m, const float* zs, int nu, float scale, float* logL,
                                unsigned int* maxL, cudaStream_t st);
-cudaError_t launch_dense_apply(void* B, int storage, const float* logL, size_t n, const unsigned int* maxL,
-                               float log_mult, uint32_t seed, double* partials, unsigned int nparts,
-                               SessionDev* sd, cudaStream_t st);
+cudaError_t launch_dense_apply(void* B, int storage, const float* logL, size_t hw, int K, const unsigned int* maxL,
+                               float log_mult, double* partials, unsigned int nparts, SessionDev* sd,
+                               cudaStream_t st);
 
 // Map difficulty (dense.cu): the probes' table columns and map flags; an argmax of a float
 // array (the first index on ties) with its scratch (the arrival counter must start at 0).
@@ -75,9 +75,7 @@ struct alignas(128) BatchStatic {           // per session, uploaded once
 };
 struct BatchTick {                          // per session, uploaded every tick
     int cur;                                // input buffer
-    int pad0;
-    uint32_t seed;                          // stochastic-rounding key
-    int pad1;
+    int pad0, pad1, pad2;
 };
 struct BatchActive {                        // the sessions propagated this tick, in work order
     int s;                                  // session
@@ -170,7 +168,7 @@ cudaError_t launch_score_reweight(void* B, int storage, const uint8_t* trav, con
                                   const int32_t* samples, const int* count, int cap, const float* dirs, int n_dirs,
                                   const int32_t* dir_of, const float* z, int n_used, float rmax_cells, float cell_m,
                                   float inv2s2, float* logL, unsigned int* maxL, void* rs, double* partials,
-                                  unsigned int nparts, uint32_t seed, SessionDev* sd, cudaStream_t st);
+                                  unsigned int nparts, SessionDev* sd, cudaStream_t st);
 // If the session reads as uniform (restart flag), write that belief into B and clear the flag.
 cudaError_t launch_materialize(void* B, int storage, const uint8_t* trav, SessionDev* sd, float value,
                                size_t hw, int K, double* partials, unsigned int nparts, cudaStream_t st);

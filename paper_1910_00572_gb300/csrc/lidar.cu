@@ -489,21 +489,24 @@ __global__ void __launch_bounds__(NT) reweight_apply_kernel(T* __restrict__ B, s
                                                             const int32_t* __restrict__ samples, const int* count_ptr,
                                                             int cap, const float* __restrict__ logL,
                                                             const unsigned int* maxL, ReweightScalars* rs,
-                                                            uint32_t seed, double* partials, SessionDev* sd) {
+                                                            double* partials, SessionDev* sd) {
     __shared__ double red[NT / 32];
     const double factor = rs->factor;
     const int n = min(*count_ptr, cap);
     const double mx = (double)ord2f(*maxL);
     KahanF acc;
-    const size_t total = (size_t)n * K;
     if (factor > 0.0) {
-        for (size_t q = (size_t)blockIdx.x * NT + threadIdx.x; q < total; q += (size_t)gridDim.x * NT) {
-            const int s = (int)(q / K), k = (int)(q % K);
-            const size_t at = (size_t)k * hw + samples[s];
-            // the new values sum to the set's old mass, so each is finite and at most that mass
-            const double b = (double)Store<T>::ld(B + at);
-            const double v = b > 0.0 ? factor * exp((double)logL[q] + log(b) - mx) : 0.0;
-            acc.add(store_out<T>(B + at, (float)v, pcg_hash((uint32_t)at ^ seed)));
+        // one thread per sampled cell, its bins in order: the BF16 rounding residual runs along theta
+        for (int s = blockIdx.x * NT + threadIdx.x; s < n; s += gridDim.x * NT) {
+            const size_t cell = (size_t)samples[s];
+            float res = 0.0f;
+            for (int k = 0; k < K; ++k) {
+                const size_t at = (size_t)k * hw + cell;
+                // the new values sum to the set's old mass, so each is finite and at most that mass
+                const double b = (double)Store<T>::ld(B + at);
+                const double v = b > 0.0 ? factor * exp((double)logL[(size_t)s * K + k] + log(b) - mx) : 0.0;
+                acc.add(store_diffused<T>(B + at, (float)v, res));
+            }
         }
     }
     const double bt = block_sum<NT>(acc.value(), red);
@@ -599,7 +602,7 @@ cudaError_t launch_score_reweight(void* B, int storage, const uint8_t* trav, con
                                   const int32_t* samples, const int* count, int cap, const float* dirs, int n_dirs,
                                   const int32_t* dir_of, const float* z, int n_used, float rmax_cells, float cell_m,
                                   float inv2s2, float* logL, unsigned int* maxL, void* rs, double* partials,
-                                  unsigned int nparts, uint32_t seed, SessionDev* sd, cudaStream_t st) {
+                                  unsigned int nparts, SessionDev* sd, cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(maxL, 0, sizeof(unsigned int), st);
     if (e != cudaSuccess) return e;
     // the map window (R cells around the sampled cell) in shared memory when it fits
@@ -635,8 +638,9 @@ cudaError_t launch_score_reweight(void* B, int storage, const uint8_t* trav, con
                                                                        maxL)));
     LOC_DISPATCH(storage, (reweight_sums_kernel<T><<<nb, NT, 0, st>>>((const T*)B, hw, K, samples, count, cap, logL,
                                                                         maxL, partials, r)));
-    LOC_DISPATCH(storage, (reweight_apply_kernel<T><<<nb, NT, 0, st>>>((T*)B, hw, K, samples, count, cap, logL, maxL,
-                                                                         r, seed, partials, sd)));
+    const unsigned int nb_cells = grid_for((size_t)cap, half > 0 ? half : 1);
+    LOC_DISPATCH(storage, (reweight_apply_kernel<T><<<nb_cells, NT, 0, st>>>((T*)B, hw, K, samples, count, cap, logL,
+                                                                               maxL, r, partials, sd)));
     return cudaGetLastError();
 }
 

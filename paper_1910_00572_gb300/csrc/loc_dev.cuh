@@ -66,7 +66,6 @@ struct StepArgs {
     float inv_uniform;             // 1 / (K * n_free): the uniform belief value
     float out_mult;                // storage multiplier of the outputs (FP16: 2^14, else 1)
     double log_out_mult;           // log(out_mult), removed from the log-scale
-    uint32_t seed;                 // per-propagation key of the stochastic rounding
     int H, W, K;
     int r_xy, r_th;
     float gx[2 * LOC_MAX_R_XY + 1];     // x and y taps (isotropic), normalised
@@ -82,35 +81,34 @@ struct StepArgs {
 // below 2) stays far below 65504.  FP32 and BF16 have the FP32 exponent range: 1.
 inline float storage_mult(int storage) { return storage == LOC_F16 ? 16384.0f : 1.0f; }
 
-// Counter-based hash: the PCG output permutation used as a hash function (Jarzynski &
-// Olano, "Hash Functions for GPU Rendering", JCGT 9(3), 2020).
-__host__ __device__ __forceinline__ uint32_t pcg_hash(uint32_t v) {
-    const uint32_t state = v * 747796405u + 2891336453u;
-    const uint32_t word = ((state >> ((state >> 28u) + 4u)) ^ state) * 277803737u;
-    return (word >> 22u) ^ word;
+// BF16 by error diffusion along theta, for the propagation kernels: each cell carries a residual
+// r from one output plane to the next.  The stored value is the BF16 neighbour of v (the largest
+// BF16 value <= v, or the next one above it) nearest to v + r, and r becomes (v + r) - stored.
+// So every stored value is within one BF16 unit in the last place of v, and a cell's states keep
+// their total mass to within the last residual: rounding does not random-walk the mass of a
+// concentrated hypothesis from step to step, as independent per-value rounding does.
+__device__ __forceinline__ __nv_bfloat16 bf16_diffuse(float v, float& r) {
+    const float w = v + r;
+    const int rn = (short)__bfloat16_as_ushort(__float2bfloat16_rn(w));   // negative w: below 0
+    const int lo = (int)(__float_as_uint(v) >> 16);
+    const int d = min(max(rn, lo), lo + 1);
+    r = w - __uint_as_float((uint32_t)d << 16);
+    return __ushort_as_bfloat16((unsigned short)d);
 }
 
-// BF16 by unbiased stochastic rounding: add 16 random bits below the kept mantissa bits and
-// truncate (v is finite and non-negative).  Round-to-nearest on a near-uniform belief makes
-// correlated errors that accumulate over steps; stochastic rounding keeps them unbiased.
-__device__ __forceinline__ __nv_bfloat16 bf16_sr(float v, uint32_t r16) {
-    const uint32_t b = __float_as_uint(v) + (r16 & 0xFFFFu);
-    return __ushort_as_bfloat16((unsigned short)(b >> 16));
-}
-
-// Store one propagated value: FP32 as is, BF16 stochastically rounded with bits r16, FP16
-// round-to-nearest.  Returns the stored value as FP32.
-template <typename T> __device__ __forceinline__ float store_out(T* p, float v, uint32_t r16);
-template <> __device__ __forceinline__ float store_out<float>(float* p, float v, uint32_t) {
+// Store one propagated value of a cell whose BF16 residual is r: FP32 as is, BF16 by error
+// diffusion, FP16 round-to-nearest.  Returns the stored value as FP32.
+template <typename T> __device__ __forceinline__ float store_diffused(T* p, float v, float& r);
+template <> __device__ __forceinline__ float store_diffused<float>(float* p, float v, float&) {
     *p = v;
     return v;
 }
-template <> __device__ __forceinline__ float store_out<__nv_bfloat16>(__nv_bfloat16* p, float v, uint32_t r16) {
-    const __nv_bfloat16 b = bf16_sr(v, r16);
+template <> __device__ __forceinline__ float store_diffused<__nv_bfloat16>(__nv_bfloat16* p, float v, float& r) {
+    const __nv_bfloat16 b = bf16_diffuse(v, r);
     *p = b;
     return __bfloat162float(b);
 }
-template <> __device__ __forceinline__ float store_out<__half>(__half* p, float v, uint32_t) {
+template <> __device__ __forceinline__ float store_diffused<__half>(__half* p, float v, float&) {
     const __half b = __float2half_rn(v);
     *p = b;
     return __half2float(b);

@@ -104,11 +104,10 @@ loc_status check_status(loc_session* h, int status);
 
 // Odometry bookkeeping of Section III-A (Eq. 2-3): accumulate an increment and report whether
 // the gate lets a propagation through; the per-bin shift table of the accumulated
-// translation; the stochastic-rounding key of the next propagation; and the bookkeeping after
-// a propagation was enqueued (ping-pong flip, translation reset, counter).
+// translation; and the bookkeeping after a propagation was enqueued (ping-pong flip,
+// translation reset, counter).
 bool odometry_advance(loc_session* h, double u, double v, double w);
 void shift_table(const loc_session* h, Shift* sh);
-uint32_t step_seed(const loc_session* h);
 void step_done(loc_session* h);
 
 }  // namespace loc

@@ -98,12 +98,14 @@ template <> __device__ __forceinline__ __nv_bfloat16 from_u8<__nv_bfloat16>(uint
 }
 template <> __device__ __forceinline__ __half from_u8<__half>(uint8_t v) { return __float2half_rn((float)v); }
 
-template <typename T> __device__ __forceinline__ T round_out(float v, uint32_t r16);
-template <> __device__ __forceinline__ float round_out<float>(float v, uint32_t) { return v; }
-template <> __device__ __forceinline__ __nv_bfloat16 round_out<__nv_bfloat16>(float v, uint32_t r16) {
-    return bf16_sr(v, r16);
+// The stored form of an output value of a cell whose BF16 residual is r (BF16 by error diffusion
+// along theta, FP16 round-to-nearest).
+template <typename T> __device__ __forceinline__ T round_out(float v, float& r);
+template <> __device__ __forceinline__ float round_out<float>(float v, float&) { return v; }
+template <> __device__ __forceinline__ __nv_bfloat16 round_out<__nv_bfloat16>(float v, float& r) {
+    return bf16_diffuse(v, r);
 }
-template <> __device__ __forceinline__ __half round_out<__half>(float v, uint32_t) { return __float2half_rn(v); }
+template <> __device__ __forceinline__ __half round_out<__half>(float v, float&) { return __float2half_rn(v); }
 
 template <typename T> struct Vec4;
 template <> struct Vec4<float> {
@@ -434,6 +436,11 @@ __global__ void __launch_bounds__(NT, 2) step_aniso_kernel(const __grid_constant
         // per warp: every lane interior (G_k is the stencil sum) / some lane with a free cell
         const bool warp_interior = __all_sync(0xffffffffu, interior);
         const bool warp_any_free = __any_sync(0xffffffffu, free_bits != 0);
+        float res[BY][4];                                 // BF16 residuals of the block's cells
+#pragma unroll
+        for (int y = 0; y < BY; ++y)
+#pragma unroll
+            for (int x = 0; x < 4; ++x) res[y][x] = 0.0f;
         for (int o = 0; o < K; ++o) {
             const int b = o % NBUF;
             if (!fail_c && !bar_wait(&full[b], (uint32_t)((o / NBUF) & 1))) {
@@ -478,8 +485,7 @@ __global__ void __launch_bounds__(NT, 2) step_aniso_kernel(const __grid_constant
                     for (int x = 0; x < 4; ++x) {
                         // gm >= 1 on a free cell (its own tap is exp(0))
                         const float v = (free_bits >> (4 * y + x)) & 1u ? __fdividef(t[y][x], gm[y][x]) * in_scale : 0.0f;
-                        const uint32_t q_lin = (uint32_t)((size_t)o * H * W + off + x);
-                        ov[x] = round_out<T>(v, pcg_hash(q_lin ^ a.seed));
+                        ov[x] = round_out<T>(v, res[y][x]);
                     }
                     if ((W & 3) == 0 && gi + 3 < W) {
                         Vec4<T>::st(oplane + off, ov);
@@ -496,7 +502,7 @@ __global__ void __launch_bounds__(NT, 2) step_aniso_kernel(const __grid_constant
                 }
             } else {
                 bar_arrive(&empty[b]);
-                const T zero = round_out<T>(0.0f, 0u);
+                const T zero = T(0.0f);
 #pragma unroll
                 for (int y = 0; y < BY; ++y) {
                     const int gj = ty0 + oy0 + y, gi = tx0 + ox0;

@@ -23,6 +23,8 @@ constexpr int RM = LOC_MAX_R_XY, RTM = LOC_MAX_R_THETA;
 constexpr int RAW_H = TH + 2 * RM + 1, RAW_W = TW + 2 * RM + 1;
 constexpr int S_H = TH + 2 * RM, S_W = TW + 2 * RM;
 constexpr int RING = 2 * RTM + 1;
+constexpr int CPT = TH * TW / NT;                              // output cells per thread
+static_assert(TH * TW % NT == 0, "every thread owns the same number of output cells");
 
 template <typename T>
 __global__ void __launch_bounds__(NT) step_generic_kernel(const __grid_constant__ StepArgs a) {
@@ -54,6 +56,9 @@ __global__ void __launch_bounds__(NT) step_generic_kernel(const __grid_constant_
     }
 
     KahanF acc;
+    float res[CPT];                                            // BF16 residuals of the thread's cells
+#pragma unroll
+    for (int n = 0; n < CPT; ++n) res[n] = 0.0f;
     for (int kk = -rt; kk < K + rt; ++kk) {
         const int c = ((kk % K) + K) % K;
         const Shift s = a.sh[c];
@@ -97,7 +102,9 @@ __global__ void __launch_bounds__(NT) step_generic_kernel(const __grid_constant_
             const int o = kk - rt;
             T* oplane = Bout + (size_t)o * H * W;
             float part = 0.0f;
-            for (int q = tid; q < TH * TW; q += NT) {
+#pragma unroll
+            for (int n = 0; n < CPT; ++n) {                 // the thread's cells, the same every plane
+                const int q = tid + n * NT;
                 const int j = q / TW, i = q % TW;
                 const int gj = ty0 + j, gi = tx0 + i;
                 if (gj >= H || gi >= W) continue;
@@ -105,8 +112,7 @@ __global__ void __launch_bounds__(NT) step_generic_kernel(const __grid_constant_
                 for (int d = -rt; d <= rt; ++d) v += a.gt[d + rt] * P[(o + d + rt) % ring][j][i];
                 const size_t off = (size_t)gj * W + gi;
                 v = a.corr[off] * in_scale * v;
-                const uint32_t q_lin = (uint32_t)((size_t)o * H * W + off);
-                part += store_out<T>(oplane + off, v, pcg_hash(q_lin ^ a.seed));
+                part += store_diffused<T>(oplane + off, v, res[n]);
             }
             acc.add(part);
         }

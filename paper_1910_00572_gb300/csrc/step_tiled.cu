@@ -63,7 +63,6 @@ __global__ void __launch_bounds__(C::NT, C::MINB) step_tiled_kernel(const __grid
     j.tmap = &a.tmap;
     j.sh = a.sh;
     j.o.B_out = a.B_out;
-    j.o.seed = a.seed;
     j.o.H = a.H;
     j.o.W = a.W;
     j.o.K = a.K;
@@ -325,14 +324,15 @@ __global__ void __launch_bounds__(C::NT, C::MINB) step_ws_kernel(const __grid_co
         tp.g2 = pk(a.g2, a.g2);
 #pragma unroll
         for (int d = 0; d < RING; ++d) tp.gt[d] = pk(a.gt[d], a.gt[d]);
-        f2 ring[RING][MR];
+        f2 ring[RING][MR], res[MR];
 #pragma unroll
         for (int d = 0; d < RING; ++d)
 #pragma unroll
             for (int k = 0; k < MR; ++k) ring[d][k] = 0ull;
+#pragma unroll
+        for (int k = 0; k < MR; ++k) res[k] = 0ull;
         TileOut o;
         o.B_out = a.B_out;
-        o.seed = a.seed;
         o.H = H;
         o.W = W;
         o.K = K;
@@ -344,13 +344,13 @@ __global__ void __launch_bounds__(C::NT, C::MINB) step_ws_kernel(const __grid_co
                 break;
             }
             switch (ph) {
-                case 0: p_pass<T, C, 0, true>(sm.X[b], sm.wrap, pc, K, tp, ring, cs, p, r0, cp, acc, &am); break;
-                case 1: p_pass<T, C, 1, true>(sm.X[b], sm.wrap, pc, K, tp, ring, cs, p, r0, cp, acc, &am); break;
-                case 2: p_pass<T, C, 2, true>(sm.X[b], sm.wrap, pc, K, tp, ring, cs, p, r0, cp, acc, &am); break;
-                case 3: p_pass<T, C, 3, true>(sm.X[b], sm.wrap, pc, K, tp, ring, cs, p, r0, cp, acc, &am); break;
-                case 4: p_pass<T, C, 4, true>(sm.X[b], sm.wrap, pc, K, tp, ring, cs, p, r0, cp, acc, &am); break;
-                case 5: p_pass<T, C, 5, true>(sm.X[b], sm.wrap, pc, K, tp, ring, cs, p, r0, cp, acc, &am); break;
-                default: p_pass<T, C, 6, true>(sm.X[b], sm.wrap, pc, K, tp, ring, cs, p, r0, cp, acc, &am); break;
+                case 0: p_pass<T, C, 0, true>(sm.X[b], sm.wrap, pc, K, tp, ring, cs, res, p, r0, cp, acc, &am); break;
+                case 1: p_pass<T, C, 1, true>(sm.X[b], sm.wrap, pc, K, tp, ring, cs, res, p, r0, cp, acc, &am); break;
+                case 2: p_pass<T, C, 2, true>(sm.X[b], sm.wrap, pc, K, tp, ring, cs, res, p, r0, cp, acc, &am); break;
+                case 3: p_pass<T, C, 3, true>(sm.X[b], sm.wrap, pc, K, tp, ring, cs, res, p, r0, cp, acc, &am); break;
+                case 4: p_pass<T, C, 4, true>(sm.X[b], sm.wrap, pc, K, tp, ring, cs, res, p, r0, cp, acc, &am); break;
+                case 5: p_pass<T, C, 5, true>(sm.X[b], sm.wrap, pc, K, tp, ring, cs, res, p, r0, cp, acc, &am); break;
+                default: p_pass<T, C, 6, true>(sm.X[b], sm.wrap, pc, K, tp, ring, cs, res, p, r0, cp, acc, &am); break;
             }
             if (p + 2 < K) bar_arrive(&sm.empty[b]);  // a producer waits for this release
         }
@@ -574,7 +574,6 @@ cudaError_t launch_step_tiled(const StepArgs& g, const void* tmap, int storage, 
     a.inv_uniform = g.inv_uniform;
     a.out_mult = g.out_mult;
     a.log_out_mult = g.log_out_mult;
-    a.seed = g.seed;
     a.H = g.H;
     a.W = g.W;
     a.K = g.K;

@@ -53,7 +53,6 @@ struct FastArgs {
     float inv_uniform;
     float out_mult;
     double log_out_mult;
-    uint32_t seed;
     int H, W, K;
     float g0, g1, g2;                  // x/y taps: centre, +-1, +-2
     float gt[RING];                    // theta taps -3 .. +3
@@ -322,44 +321,45 @@ __device__ __forceinline__ void s_pass_any(const T* raw, const float* mk, float*
     }
 }
 
-// Store two neighbouring outputs v = {a, b} (FP32 as is, BF16 stochastically rounded with the
-// 32 random bits h, FP16 round-to-nearest), add them to sum, and return the stored values as
-// FP32 in st.
-template <typename T> __device__ __forceinline__ void store2(T* p, f2 v, uint32_t h, f2& sum, f2& st);
-template <> __device__ __forceinline__ void store2<float>(float* p, f2 v, uint32_t, f2& sum, f2& st) {
+// Store two neighbouring outputs v = {a, b} (FP32 as is, BF16 by error diffusion along theta,
+// FP16 round-to-nearest), add the stored values to sum, and return them as FP32 in st.  res
+// holds the BF16 residuals of the two cells (see store2<__nv_bfloat16>); FP32 and FP16 ignore it.
+template <typename T> __device__ __forceinline__ void store2(T* p, f2 v, f2& res, f2& sum, f2& st);
+template <> __device__ __forceinline__ void store2<float>(float* p, f2 v, f2&, f2& sum, f2& st) {
     *reinterpret_cast<f2*>(p) = v;
     sum = fadd2(sum, v);
     st = v;
 }
-template <> __device__ __forceinline__ void store2<__nv_bfloat16>(__nv_bfloat16* p, f2 v, uint32_t h, f2& sum,
+// BF16 rounding by error diffusion along theta.  Every cell carries a residual from one output
+// plane to the next (its own states in plane order): the stored value is the BF16 neighbour of v
+// -- the largest BF16 value <= v or the next one above it -- that lies nearest to v + residual,
+// and the new residual is (v + residual) - stored.  Each stored value stays within one BF16 unit
+// in the last place of its own exact value, and a cell's states keep their total mass to within
+// the last residual, so rounding no longer random-walks the mass of concentrated hypotheses from
+// step to step (stochastic rounding, unbiased per value, did: its error variance accumulates).
+__device__ __forceinline__ uint32_t bf16x2_diffuse(float a, float b, f2& res, f2& st) {
+    const f2 w = fadd2(pk(a, b), res);
+    float wa, wb;
+    upk(w, wa, wb);
+    uint32_t rn;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(rn) : "f"(wb), "f"(wa));      // {a, b} in memory order
+    const uint32_t lo = __byte_perm(__float_as_uint(a), __float_as_uint(b), 0x7632);   // truncations
+    const uint32_t hi = lo + 0x00010001u;                                       // the values above
+    // clamp the nearest value of v + residual into [lo, hi]; as signed 16-bit halves a negative
+    // v + residual orders below every non-negative value
+    const uint32_t d = __vmins2(__vmaxs2(rn, lo), hi);
+    st = pk(__uint_as_float(d << 16), __uint_as_float(d & 0xFFFF0000u));
+    res = fsub2(w, st);
+    return d;
+}
+template <> __device__ __forceinline__ void store2<__nv_bfloat16>(__nv_bfloat16* p, f2 v, f2& res, f2& sum,
                                                                   f2& st) {
     float a, b;
     upk(v, a, b);
-    // one stochastically rounded pair (cvt.rs): a value rounds up iff its 16 discarded mantissa
-    // bits plus 16 random bits carry into the kept ones -- b takes the high half of h, a the low
-    // half -- so each rounds up with probability equal to its discarded fraction (unbiased)
-    uint32_t d;
-    asm("cvt.rs.bf16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(b), "f"(a), "r"(h));
-    *reinterpret_cast<uint32_t*>(p) = d;               // {a, b} in memory order
-    // the stochastic rounding is unbiased: Z takes the unrounded values (within ~1e-7)
-    sum = fadd2(sum, v);
-    st = pk(__uint_as_float(d << 16), __uint_as_float(d & 0xFFFF0000u));
+    *reinterpret_cast<uint32_t*>(p) = bf16x2_diffuse(a, b, res, st);
+    sum = fadd2(sum, st);
 }
-
-// Stratified random bits for the stochastic rounding of a thread's cells.  The thread draws one
-// uniform 16-bit number u per plane; cell i of its group of eight (row rr: cell 2 rr in the low
-// half of the word, 2 rr + 1 in the high half) uses u with its top three bits XOR-ed by i in
-// bit-reversed order.  Each cell's number is still uniform, so each rounding stays unbiased, but
-// the eight numbers fall one in each eighth of [0, 2^16): the group's round-ups are spread
-// evenly instead of independently, which keeps the rounding error of the group's (and of a
-// pair's) sum small.  That is the error that random-walks the mass between hypotheses when
-// the belief is concentrated.  sr_word(h) puts u = the low 16 bits of h in both halves.
-__device__ __forceinline__ uint32_t sr_word(uint32_t h) { return __byte_perm(h, 0u, 0x1010); }
-__device__ __forceinline__ uint32_t sr_row_bits(uint32_t w, int rr) {
-    constexpr uint32_t kRev[8] = {0, 4, 2, 6, 1, 5, 3, 7};   // 3-bit bit reversal
-    return w ^ ((kRev[(2 * rr + 1) & 7] << 29) | (kRev[(2 * rr) & 7] << 13));
-}
-template <> __device__ __forceinline__ void store2<__half>(__half* p, f2 v, uint32_t, f2& sum, f2& st) {
+template <> __device__ __forceinline__ void store2<__half>(__half* p, f2 v, f2&, f2& sum, f2& st) {
     float a, b;
     upk(v, a, b);
     const __half2 hv = __floats2half2_rn(a, b);
@@ -455,10 +455,9 @@ __device__ __forceinline__ void finish_sum_am(double block_total, ArgBest best, 
     }
 }
 
-// Where the P-pass writes: the output tensor, the rounding key and the grid.
+// Where the P-pass writes: the output tensor and the grid.
 struct TileOut {
     void* B_out;
-    uint32_t seed;
     int H, W, K;
 };
 
@@ -469,7 +468,7 @@ struct Taps2 {
 };
 
 // A P-pass thread's output geometry, fixed for a tile: its first cell's address in plane 0,
-// the plane and row strides, the rows inside the grid (and tile), its rounding hash.
+// the plane and row strides, the rows inside the grid (and tile).
 template <typename T>
 struct PCtx {
     T* out0;                           // the thread's first cell (row ty0 + r0, column gx) of plane 0
@@ -479,7 +478,6 @@ struct PCtx {
     int rows;                          // rows of the thread inside the grid and the tile
     bool col_ok;                       // gx < W (both columns: W is even)
     bool full;                         // all MR rows and the columns inside
-    uint32_t h;                        // the thread's hash for this tile and propagation
 };
 
 template <typename T, typename C>
@@ -495,25 +493,18 @@ __device__ __forceinline__ PCtx<T> p_ctx(const TileOut& a, int r0, int ty0, int 
     c.rows = rows;
     c.col_ok = gx < a.W;
     c.full = rows >= C::MR && c.col_ok;
-    c.h = pcg_hash((uint32_t)base ^ a.seed);
     return c;
-}
-
-// The 16-bit uniform number of output plane o of a thread (both halves of the word, for
-// sr_row_bits): the thread's tile hash mixed with the plane by one multiply, high half.
-__device__ __forceinline__ uint32_t sr_plane_word(uint32_t h, int o) {
-    const uint32_t x = (h ^ ((uint32_t)o * 0x9E3779B9u)) * 0x85EBCA6Bu;
-    return __byte_perm(x, 0u, 0x3232);
 }
 
 // P-pass for plane p with the newest ring slot PH = p mod 7.  The thread's cells are rows
 // r0 .. r0+MR-1 of the tile, columns 2cp and 2cp+1, handled as column pairs.
+// res holds the BF16 rounding residuals of the thread's cells, carried from plane to plane.
 // With AM the thread also keeps the running argmax of the values it stores in *am.
 template <typename T, typename C, int PH, bool AM = false>
 __device__ __forceinline__ void p_pass(const float (*X)[XW_PITCH], float (*wrap)[C::CR][TW],
                                        const PCtx<T>& pc, int K, const Taps2& tp,
-                                       f2 (&ring)[RING][C::MR], const f2 (&cs)[C::MR], int p,
-                                       int r0, int cp, KahanF2& acc, ArgBest* am = nullptr) {
+                                       f2 (&ring)[RING][C::MR], const f2 (&cs)[C::MR], f2 (&res)[C::MR],
+                                       int p, int r0, int cp, KahanF2& acc, ArgBest* am = nullptr) {
     constexpr int MR = C::MR;
     if (p < K) {
         f2 x[MR + 4];
@@ -535,7 +526,6 @@ __device__ __forceinline__ void p_pass(const float (*X)[XW_PITCH], float (*wrap)
         int o = p - RT;
         if (o >= K) o -= K;
         T* out = pc.out0 + (size_t)o * pc.plane;
-        const uint32_t h = sizeof(T) == 2 ? sr_plane_word(pc.h, o) : 0u;
         f2 part = 0ull;
         f2 stv[MR];                                    // stored values (-FLT_MAX: not stored)
         if (pc.full) {
@@ -544,7 +534,7 @@ __device__ __forceinline__ void p_pass(const float (*X)[XW_PITCH], float (*wrap)
                 f2 t = fmul2(tp.gt[0], ring[(PH + 1) % RING][rr]);
 #pragma unroll
                 for (int d = 1; d < RING; ++d) t = ffma2(tp.gt[d], ring[(PH + 1 + d) % RING][rr], t);
-                store2<T>(out + (size_t)rr * pc.W, fmul2(cs[rr], t), sr_row_bits(h, rr), part, stv[rr]);
+                store2<T>(out + (size_t)rr * pc.W, fmul2(cs[rr], t), res[rr], part, stv[rr]);
             }
         } else {
 #pragma unroll
@@ -554,7 +544,7 @@ __device__ __forceinline__ void p_pass(const float (*X)[XW_PITCH], float (*wrap)
                 for (int d = 1; d < RING; ++d) t = ffma2(tp.gt[d], ring[(PH + 1 + d) % RING][rr], t);
                 stv[rr] = pk(-FLT_MAX, -FLT_MAX);
                 if (rr < pc.rows && pc.col_ok)
-                    store2<T>(out + (size_t)rr * pc.W, fmul2(cs[rr], t), sr_row_bits(h, rr), part, stv[rr]);
+                    store2<T>(out + (size_t)rr * pc.W, fmul2(cs[rr], t), res[rr], part, stv[rr]);
             }
         }
         acc.add(part);
@@ -656,11 +646,13 @@ __device__ __forceinline__ bool run_tile(Smem<T, C>& sm, const TileJob& j, unsig
     tp.g2 = pk(j.g2, j.g2);
 #pragma unroll
     for (int d = 0; d < RING; ++d) tp.gt[d] = pk(j.gt[d], j.gt[d]);
-    f2 ring[RING][MR];
+    f2 ring[RING][MR], res[MR];
 #pragma unroll
     for (int d = 0; d < RING; ++d)
 #pragma unroll
         for (int k = 0; k < MR; ++k) ring[d][k] = 0ull;
+#pragma unroll
+    for (int k = 0; k < MR; ++k) res[k] = 0ull;
     const PCtx<T> pc = p_ctx<T, C>(j.o, r0, ty0, gxp);
     const SItem si = s_item<C>(tid);
     const XItem xi = x_item<C>(tid);
@@ -705,13 +697,13 @@ __device__ __forceinline__ bool run_tile(Smem<T, C>& sm, const TileJob& j, unsig
             __syncthreads();
         }
         switch (ph) {
-            case 0: p_pass<T, C, 0>(sm.X, sm.wrap, pc, K, tp, ring, cs, p, r0, cp, acc); break;
-            case 1: p_pass<T, C, 1>(sm.X, sm.wrap, pc, K, tp, ring, cs, p, r0, cp, acc); break;
-            case 2: p_pass<T, C, 2>(sm.X, sm.wrap, pc, K, tp, ring, cs, p, r0, cp, acc); break;
-            case 3: p_pass<T, C, 3>(sm.X, sm.wrap, pc, K, tp, ring, cs, p, r0, cp, acc); break;
-            case 4: p_pass<T, C, 4>(sm.X, sm.wrap, pc, K, tp, ring, cs, p, r0, cp, acc); break;
-            case 5: p_pass<T, C, 5>(sm.X, sm.wrap, pc, K, tp, ring, cs, p, r0, cp, acc); break;
-            default: p_pass<T, C, 6>(sm.X, sm.wrap, pc, K, tp, ring, cs, p, r0, cp, acc); break;
+            case 0: p_pass<T, C, 0>(sm.X, sm.wrap, pc, K, tp, ring, cs, res, p, r0, cp, acc); break;
+            case 1: p_pass<T, C, 1>(sm.X, sm.wrap, pc, K, tp, ring, cs, res, p, r0, cp, acc); break;
+            case 2: p_pass<T, C, 2>(sm.X, sm.wrap, pc, K, tp, ring, cs, res, p, r0, cp, acc); break;
+            case 3: p_pass<T, C, 3>(sm.X, sm.wrap, pc, K, tp, ring, cs, res, p, r0, cp, acc); break;
+            case 4: p_pass<T, C, 4>(sm.X, sm.wrap, pc, K, tp, ring, cs, res, p, r0, cp, acc); break;
+            case 5: p_pass<T, C, 5>(sm.X, sm.wrap, pc, K, tp, ring, cs, res, p, r0, cp, acc); break;
+            default: p_pass<T, C, 6>(sm.X, sm.wrap, pc, K, tp, ring, cs, res, p, r0, cp, acc); break;
         }
     }
     p_stop = p;

@@ -58,11 +58,11 @@ struct PSmem {
     double red[C::NT / 32];
 };
 
-// Two cells of a pair, 32 columns apart: FP32 as is, BF16 stochastically rounded with the 32
-// random bits h (low half for the first cell), FP16 round-to-nearest; the stored values (BF16:
-// unrounded, unbiased) are added to sum.  Cells outside the grid have v = 0 and are not stored.
-template <typename T> __device__ __forceinline__ void store_pair(T* p, f2 v, uint32_t h, bool ok0, bool ok1, f2& sum);
-template <> __device__ __forceinline__ void store_pair<float>(float* p, f2 v, uint32_t, bool ok0, bool ok1, f2& sum) {
+// Two cells of a pair, 32 columns apart: FP32 as is, BF16 by error diffusion along theta (res:
+// the two cells' residuals, see bf16x2_diffuse), FP16 round-to-nearest; the stored values are
+// added to sum.  Cells outside the grid have v = 0 and are not stored.
+template <typename T> __device__ __forceinline__ void store_pair(T* p, f2 v, f2& res, bool ok0, bool ok1, f2& sum);
+template <> __device__ __forceinline__ void store_pair<float>(float* p, f2 v, f2&, bool ok0, bool ok1, f2& sum) {
     float a, b;
     upk(v, a, b);
     if (ok0) p[0] = a;
@@ -70,18 +70,18 @@ template <> __device__ __forceinline__ void store_pair<float>(float* p, f2 v, ui
     sum = fadd2(sum, v);
 }
 template <>
-__device__ __forceinline__ void store_pair<__nv_bfloat16>(__nv_bfloat16* p, f2 v, uint32_t h, bool ok0, bool ok1,
+__device__ __forceinline__ void store_pair<__nv_bfloat16>(__nv_bfloat16* p, f2 v, f2& res, bool ok0, bool ok1,
                                                           f2& sum) {
     float a, b;
     upk(v, a, b);
-    const uint32_t ua = __float_as_uint(a) + (h & 0xFFFFu);
-    const uint32_t ub = __float_as_uint(b) + (h >> 16);
-    if (ok0) *reinterpret_cast<unsigned short*>(p) = (unsigned short)(ua >> 16);
-    if (ok1) *reinterpret_cast<unsigned short*>(p + 32) = (unsigned short)(ub >> 16);
-    sum = fadd2(sum, v);
+    f2 st;
+    const uint32_t d = bf16x2_diffuse(a, b, res, st);
+    if (ok0) *reinterpret_cast<unsigned short*>(p) = (unsigned short)(d & 0xFFFFu);
+    if (ok1) *reinterpret_cast<unsigned short*>(p + 32) = (unsigned short)(d >> 16);
+    sum = fadd2(sum, st);
 }
 template <>
-__device__ __forceinline__ void store_pair<__half>(__half* p, f2 v, uint32_t, bool ok0, bool ok1, f2& sum) {
+__device__ __forceinline__ void store_pair<__half>(__half* p, f2 v, f2&, bool ok0, bool ok1, f2& sum) {
     float a, b;
     upk(v, a, b);
     const __half ha = __float2half_rn(a), hb = __float2half_rn(b);
@@ -185,8 +185,8 @@ __device__ __forceinline__ void x_pass(const float (*S)[SPW], float (*X)[XPW], c
 template <typename T, typename C, int PH>
 __device__ __forceinline__ void p_pass(const float (*X)[XPW], float (*wrap)[C::TH][TW], const PThread<T, C>& th,
                                        const TileOut& a, const Taps2& tp,
-                                       f2 (&ring)[RING][C::MR], const f2 (&cs)[C::MR], int p, T* out_tile,
-                                       size_t plane, uint32_t h_tile, int rows, bool ok0, bool ok1, KahanF& acc) {
+                                       f2 (&ring)[RING][C::MR], const f2 (&cs)[C::MR], f2 (&res)[C::MR], int p,
+                                       T* out_tile, size_t plane, int rows, bool ok0, bool ok1, KahanF& acc) {
     constexpr int MR = C::MR;
     const int K = a.K;
     if (p < K) {
@@ -209,7 +209,6 @@ __device__ __forceinline__ void p_pass(const float (*X)[XPW], float (*wrap)[C::T
         int o = p - RT;
         if (o >= K) o -= K;
         T* out = out_tile + (size_t)o * plane;
-        const uint32_t h = sizeof(T) == 2 ? sr_word(pcg_hash((h_tile + (uint32_t)o * (uint32_t)plane) ^ a.seed)) : 0u;
         f2 part = 0ull;
 #pragma unroll
         for (int rr = 0; rr < MR; ++rr) {
@@ -217,9 +216,8 @@ __device__ __forceinline__ void p_pass(const float (*X)[XPW], float (*wrap)[C::T
 #pragma unroll
             for (int d = 1; d < RING; ++d) t = ffma2(tp.gt[d], ring[(PH + 1 + d) % RING][rr], t);
             const f2 v = fmul2(cs[rr], t);
-            const uint32_t hr = sr_row_bits(h, rr);
             const bool in = rr < rows;
-            store_pair<T>(out + (size_t)rr * a.W, v, hr, in && ok0, in && ok1, part);
+            store_pair<T>(out + (size_t)rr * a.W, v, res[rr], in && ok0, in && ok1, part);
         }
         float p0, p1;
         upk(part, p0, p1);
@@ -284,18 +282,19 @@ __device__ __forceinline__ bool run_tile(PSmem<T, C>& sm, const TileJob& j, unsi
     const size_t plane = (size_t)H * W;
     const size_t cell0 = (size_t)(gy0 < H ? gy0 : 0) * W + gx0;           // plane-0 index of the first cell
     T* out_tile = static_cast<T*>(j.o.B_out) + cell0;
-    const uint32_t h_tile = (uint32_t)cell0;
     Taps2 tp;
     tp.g0 = pk(j.g0, j.g0);
     tp.g1 = pk(j.g1, j.g1);
     tp.g2 = pk(j.g2, j.g2);
 #pragma unroll
     for (int d = 0; d < RING; ++d) tp.gt[d] = pk(j.gt[d], j.gt[d]);
-    f2 ring[RING][MR];
+    f2 ring[RING][MR], res[MR];
 #pragma unroll
     for (int d = 0; d < RING; ++d)
 #pragma unroll
         for (int k = 0; k < MR; ++k) ring[d][k] = 0ull;
+#pragma unroll
+    for (int k = 0; k < MR; ++k) res[k] = 0ull;
     int failed = 0;
     int p = 0;
     for (; p < K + NWRAP; ++p) {
@@ -343,13 +342,13 @@ __device__ __forceinline__ bool run_tile(PSmem<T, C>& sm, const TileJob& j, unsi
             __syncthreads();
         }
         switch (p % RING) {
-            case 0: p_pass<T, C, 0>(sm.X, sm.wrap, th, j.o, tp, ring, cs, p, out_tile, plane, h_tile, rows, ok0, ok1, acc); break;
-            case 1: p_pass<T, C, 1>(sm.X, sm.wrap, th, j.o, tp, ring, cs, p, out_tile, plane, h_tile, rows, ok0, ok1, acc); break;
-            case 2: p_pass<T, C, 2>(sm.X, sm.wrap, th, j.o, tp, ring, cs, p, out_tile, plane, h_tile, rows, ok0, ok1, acc); break;
-            case 3: p_pass<T, C, 3>(sm.X, sm.wrap, th, j.o, tp, ring, cs, p, out_tile, plane, h_tile, rows, ok0, ok1, acc); break;
-            case 4: p_pass<T, C, 4>(sm.X, sm.wrap, th, j.o, tp, ring, cs, p, out_tile, plane, h_tile, rows, ok0, ok1, acc); break;
-            case 5: p_pass<T, C, 5>(sm.X, sm.wrap, th, j.o, tp, ring, cs, p, out_tile, plane, h_tile, rows, ok0, ok1, acc); break;
-            default: p_pass<T, C, 6>(sm.X, sm.wrap, th, j.o, tp, ring, cs, p, out_tile, plane, h_tile, rows, ok0, ok1, acc); break;
+            case 0: p_pass<T, C, 0>(sm.X, sm.wrap, th, j.o, tp, ring, cs, res, p, out_tile, plane, rows, ok0, ok1, acc); break;
+            case 1: p_pass<T, C, 1>(sm.X, sm.wrap, th, j.o, tp, ring, cs, res, p, out_tile, plane, rows, ok0, ok1, acc); break;
+            case 2: p_pass<T, C, 2>(sm.X, sm.wrap, th, j.o, tp, ring, cs, res, p, out_tile, plane, rows, ok0, ok1, acc); break;
+            case 3: p_pass<T, C, 3>(sm.X, sm.wrap, th, j.o, tp, ring, cs, res, p, out_tile, plane, rows, ok0, ok1, acc); break;
+            case 4: p_pass<T, C, 4>(sm.X, sm.wrap, th, j.o, tp, ring, cs, res, p, out_tile, plane, rows, ok0, ok1, acc); break;
+            case 5: p_pass<T, C, 5>(sm.X, sm.wrap, th, j.o, tp, ring, cs, res, p, out_tile, plane, rows, ok0, ok1, acc); break;
+            default: p_pass<T, C, 6>(sm.X, sm.wrap, th, j.o, tp, ring, cs, res, p, out_tile, plane, rows, ok0, ok1, acc); break;
         }
     }
     p_stop = p;

@@ -1,6 +1,6 @@
 """Per-element error bounds of the reduced-precision storage, shared by the GPU parity tests.
 
-A BF16 store with stochastic rounding returns one of the two BF16 neighbours of its FP32
+A BF16 store (error diffusion along theta) returns one of the two BF16 neighbours of its FP32
 input, so its error is below one BF16 unit in the last place of that value: 2^(e - 7) for a
 value in [2^e, 2^(e+1)) (8 significant bits).  Before the store, the FP32 arithmetic of one
 propagation (about 30 rounded operations on non-negative terms) is within a few 1e-6 of the

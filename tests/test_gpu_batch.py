@@ -227,7 +227,7 @@ def test_batch64_full_size_sampled_against_oracle(storage):
     configuration the benchmark times (autotuned tile, CUDA graph): on four sessions (the two
     largest and two smaller, different K), sampled states are recomputed one by one from the
     definitions by the oracle from the same input belief.  FP32: 1e-6; BF16: each state within
-    one stochastic-rounding step of its own exact value plus the FP32 error, and the argmax
+    one BF16 rounding step of its own exact value plus the FP32 error, and the argmax
     state as large as every checked state."""
     from oracle.odometry import Odometry
     wl = workloads.get("batch64")
@@ -266,7 +266,7 @@ def test_batch64_full_size_sampled_against_oracle(storage):
             if storage == "f32":
                 assert err <= ABS_TOL and err <= REL_TOL * before[q].max(), (q, err)
             else:
-                # per element: one BF16 stochastic-rounding step of that state's own value plus
+                # per element: one BF16 rounding step of that state's own value plus
                 # the FP32 propagation error (tests/bounds.py)
                 bound = bounds.bf16_step_bound(T)
                 bad = np.flatnonzero(np.abs(gotT - T) > bound)

@@ -278,14 +278,13 @@ def test_f16_crop_trajectory_with_scans_meets_the_l1_bar():
 
 @pytest.mark.slow
 def test_bf16_crop_trajectory_with_scans_l1_and_argmax():
-    """BF16 storage on the same trajectory.  L1 stays about 2-5e-3, but it can pass 1e-2 at a few
-    checkpoints when two concentrated hypotheses coexist.  The stored values keep 8 significant
-    bits, and every unbiased rounding of a value v has error variance F(1 - F) ulp(v)^2 (F its
-    discarded fraction).  A hypothesis whose mass sits in a few states therefore random-walks
-    its mass by about 2^-8 sqrt(t / (6 n_eff)) relative after t steps, and a scan that weighs
-    two such hypotheses turns their relative error into L1.  Measured over 1000 steps on three
-    seeds: maxima 0.8-1.5e-2, means 3-5e-3.  The bar here is therefore L1 <= 1e-2 at 95 % of
-    the checkpoints and <= 2e-2 at all of them, besides the argmax."""
+    """BF16 storage on the same trajectory: L1 <= 1e-2 at every one of the 100 checkpoints,
+    besides the argmax.  The stored values keep 8 significant bits.  Rounded independently
+    (stochastic rounding, unbiased per value), a hypothesis whose mass sits in a few states
+    random-walks that mass by about 2^-8 sqrt(t / (6 n_eff)) relative after t steps, and a scan
+    that weighs two such hypotheses turns the difference into L1: on this run it passed 1e-2 at
+    15 checkpoints.  The kernels round by error diffusion along theta instead (each cell's
+    residual carried from bin to bin), which keeps every cell's mass over its bins to within
+    half a unit in the last place, step after step, so the mass no longer random-walks."""
     l1 = crop_trajectory_l1("bf16")
-    assert (l1 <= 1e-2).mean() >= 0.95, (l1 > 1e-2).sum()
-    assert l1.max() <= 2e-2, l1.max()
+    assert l1.max() <= 1e-2, (l1.max(), int(np.argmax(l1)))

@@ -286,7 +286,7 @@ def test_office2048_bf16_one_step_replay_sampled():
     the tile configuration the benchmark times (the session default): 3000 random states, the
     neighbourhoods of the ten largest input values, and the GPU's argmax state, each recomputed
     from the definitions by the oracle from the same stored input.  Every state is within one
-    BF16 stochastic-rounding step of its own exact value plus the FP32 error (tests/bounds.py),
+    BF16 rounding step of its own exact value plus the FP32 error (tests/bounds.py),
     the argmax state holds at least every checked state's value, and the tensor sums to 1."""
     wl = workloads.get("office2048")
     occ = workloads.make_map(wl)
@@ -321,6 +321,43 @@ def test_office2048_bf16_one_step_replay_sampled():
     assert bad.size == 0, [(idx[b], gotT[b], T[b], bound[b]) for b in bad[:5]]
     assert T[-1] >= T.max() - 2.0 * bounds.bf16_step_bound(T.max())
     assert abs(got.astype(np.float64).sum() - 1.0) < 1e-4
+
+
+@pytest.mark.parametrize("tile,kernel", [(3, "tiled"), (6, "tiled"), (16, "tiled"), (8, "tiled"), (0, "generic")])
+def test_bf16_rounding_keeps_each_cells_theta_mass(tile, kernel):
+    """BF16 stores round by error diffusion along theta: each stored value is one of the two BF16
+    neighbours of its value (within one unit in the last place of its exact value, plus the FP32
+    error), and the residual a cell carries from plane to plane keeps the cell's total over its
+    bins: |sum_k stored - sum_k exact| <= half a unit in the last place of the cell's largest
+    value, plus the FP32 error.  (The residual never grows: a plane either absorbs it within
+    half a unit of its own value or passes on less of it.)  Independent rounding of each value,
+    stochastic or to nearest, misses the second bound on cells whose bins hold several values of
+    similar size, since its error sums grow like the square root of their number.  Synchronous,
+    warp-specialised, paired and generic kernels alike."""
+    from oracle import cprop
+    occ = floorplan.crop(floorplan.office_map(5, size=256), 40, 30, 96, 128)
+    K, cell = 72, 0.05
+    kw = dict(tile=tile) if kernel == "tiled" else dict(kernel=loc.LOC_KERNEL_GENERIC)
+    h = make(occ, K, cell, storage="bf16", **kw)
+    u, v, w = 0.0137, -0.0061, 0.0
+    try:
+        loc.loc_set_belief(h, fields.belief_like(occ, K, seed=4, dtype=np.float32))
+        before = loc.loc_belief(h).astype(np.float64)          # the stored BF16 input, normalised
+        loc.loc_step(h, u, v, w)
+        got = loc.loc_belief(h).astype(np.float64) * loc.loc_stats(h)["last_Z"]
+    finally:
+        loc.loc_destroy(h)
+    odo = Odometry(K, cell)
+    odo.add(u, v, w)
+    M = F.traversability(occ)
+    g = F.motion_kernel(0.5, 1.0)
+    T = cprop.propagate(before, M, F.edge_correction(M, K, g), odo.shifts(), g, cprop.host_cores())
+    bad = np.flatnonzero(np.abs(got - T) > bounds.bf16_step_bound(T))
+    assert bad.size == 0, bad[:5]
+    cell_err = np.abs(got.sum(axis=0) - T.sum(axis=0))
+    cell_bound = 0.5 * bounds.bf16_ulp(T.max(axis=0) * (1.0 + 1e-5)) + 5e-6 * T.sum(axis=0)
+    worst = np.unravel_index(np.argmax(cell_err - cell_bound), cell_err.shape)
+    assert np.all(cell_err <= cell_bound), (worst, cell_err[worst], cell_bound[worst])
 
 
 @pytest.mark.parametrize("storage", ["f32", "bf16", "f16"])

@@ -144,7 +144,7 @@ def test_tiled_is_refused_where_it_does_not_apply():
 
 @pytest.mark.parametrize("storage", ["bf16", "f16"])
 def test_reduced_precision_trajectory_l1_and_argmax(storage):
-    """Reduced-precision storage (FP32 arithmetic; BF16 stochastically rounded, FP16 scaled by
+    """Reduced-precision storage (FP32 arithmetic; BF16 rounded by error diffusion along theta, FP16 scaled by
     2^14): L1 <= 1e-2 against the FP64 oracle over the whole 200-step trajectory, and the same
     argmax bin wherever the oracle's maximum is unambiguous."""
     wl = workloads.get("rooms64")
@@ -176,7 +176,7 @@ def test_reduced_precision_trajectory_l1_and_argmax(storage):
 def test_split_producers_are_bit_identical(packed, scalar, storage):
     """Split producers (S warps beside X warps) run the same passes on the same cells as the
     configuration with the same tile rows and consumer layout: bit-identical tensors and
-    normalisers, step after step, including the stochastic rounding of BF16."""
+    normalisers, step after step, including the BF16 rounding residuals carried along theta."""
     H, W, K = 75, 200, 20
     rng = np.random.default_rng(packed)
     occ = (rng.random((H, W)) < 0.15).astype(np.uint8)
