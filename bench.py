@@ -37,6 +37,9 @@ import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
+# the serving loop runs scan updates on up to 32 streams at once; CUDA maps streams onto this
+# many hardware work queues (its default is 8), fixed when the process creates its context
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
 
 from synth import workloads  # noqa: E402
 
@@ -834,7 +837,8 @@ def headline_config(wl, sess, ws):
             "min_shift_cells": wl["min_shift_cells"], "n_samples": wl["n_samples"],
             "cells_all_sessions": sum(s["H"] * s["W"] * s["K"] for s in sess),
             "global_batch": len(sess), "parallelism": f"replicas{ws}" if ws > 1 else "single",
-            "l2": "inputs larger than L2 (98 GB of resident belief tensors)"}
+            "l2": "inputs larger than L2 (98 GB of resident belief tensors)",
+            "cuda_device_max_connections": os.environ.get("CUDA_DEVICE_MAX_CONNECTIONS")}
 
 
 def run_headline(args, wl, ws, rank, local):

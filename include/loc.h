@@ -349,10 +349,11 @@ loc_status loc_session_bytes(const loc_params* p, size_t* bytes);
  * Sessions are opened against a device-memory budget (loc_session_bytes each) and admitted
  * first come, first served as memory frees up.  Odometry and scan messages may be submitted
  * from any thread; each session's messages are applied in submission order.  A worker thread
- * forms a tick from whatever sessions have work: a session's odometry messages run through its
- * Alg. 1 gate one by one until one opens it (that propagation joins the tick's batched launch)
- * or a scan message comes next (the scan runs in that tick if the session was not propagated,
- * on a stream of its own, overlapping the batched launch).  So the propagation points and every
+ * forms a tick from whatever sessions have work.  Per session, in message order: odometry
+ * messages run through its Alg. 1 gate one by one; at most one scan message runs in the tick
+ * (on the session's stream, before the tick's batched launch, which waits for it); the first
+ * odometry message that opens the gate joins the tick's batched launch and ends the session's
+ * share of the tick (a scan after it waits for the next tick).  So the propagation points and every
  * result depend only on the session's own message stream, never on the load: a session gives
  * the same belief served alone or in any mix (with the same tile configuration).  A completion
  * thread timestamps finished work for the latency statistics. */
@@ -369,7 +370,12 @@ typedef struct {
     int tile;                      /* batch tile configuration; 0 = autotune on the first batch
                                       and keep it */
     int use_graph;                 /* capture each tick in a CUDA graph (default 1) */
-    int n_streams;                 /* streams for scan updates and plain steps (default 16) */
+    int n_streams;                 /* streams for scan updates and plain steps (default 32);
+                                      each tick hands them out in turn, a session's work on a
+                                      new stream waiting for its work on the previous one.  The
+                                      device runs at most CUDA_DEVICE_MAX_CONNECTIONS streams at
+                                      once (CUDA's default is 8; set it to 32 in the environment
+                                      before the process's first CUDA call) */
 } loc_server_params;
 
 typedef struct {

@@ -5,14 +5,14 @@
 // iteration it (1) closes sessions whose queues ran empty and admits pending sessions, first
 // come first served, while their device bytes fit the budget (rebuilding the batched launch
 // when the set changes), (2) takes work from each admitted session's queue -- odometry
-// messages run through the session's Alg. 1 gate one by one until one opens it, or a scan
-// message comes next -- and (3) launches it: all propagations of the tick in one persistent
-// batched launch, each scan update on the session's own stream where it overlaps the batch.
+// messages run through the session's Alg. 1 gate one by one until one opens it, with at most
+// one scan message before that -- and (3) launches it: each scan update on the session's own
+// stream, then all propagations of the tick in one persistent batched launch.
 // A completion thread polls the events recorded after each piece of work and timestamps it.
 //
 // Ordering.  A session's work runs in message order: a batch waits for the scan updates
-// of its sessions launched since their last batch, and a scan update waits for the batch that last
-// propagated its session.  Because a session is propagated at most once per tick and its
+// of its sessions launched since their last batch (this tick's included), and a scan update
+// waits for the batch that last propagated its session.  Because a session is propagated at most once per tick and its
 // gate only sees its own messages, the propagation points, the rounding keys and therefore the
 // results do not depend on the load or on the other sessions.
 #include <algorithm>
@@ -50,6 +50,7 @@ struct SrvMsg {
     double u = 0, v = 0, w = 0;
     double t_arr = 0;
     SrvScan* scan = nullptr;           // owned while queued
+    double theta = 0;                  // scan taken into a tick: the session's heading then
 };
 
 struct SrvSession {
@@ -65,6 +66,12 @@ struct SrvSession {
     int ci = -1;                       // index in the batched launch
     long long last_prop_tick = -1;
     cudaEvent_t scan_ev = nullptr;     // recorded after the session's latest scan update
+    // The pool stream a session's scans and plain steps run on changes from tick to tick, so
+    // that each tick's work spreads over every stream; tail_ev (recorded after the session's
+    // latest work on a pool stream) orders the next stream after the previous one.
+    cudaEvent_t tail_ev = nullptr;
+    bool tail_valid = false;
+    long long scan_tick = -1;          // tick of the session's latest scan
     bool scan_pending = false;         // a scan update was launched since its last propagation
 };
 
@@ -115,6 +122,7 @@ struct loc_server_s {
     size_t tuned_at = 0;               // live sessions when the tile was last autotuned
     std::vector<SrvSession*> live;
     long long tick = 0;
+    size_t scan_rr = 0, plain_rr = 0;  // next pool stream for a scan / a session's plain steps
     std::thread worker, completer;
     // helper threads for the scan phase of a tick, started once: the worker publishes a job
     // (generation gen), each helper runs it once, and the worker waits until pool_busy is 0
@@ -346,8 +354,15 @@ bool membership(loc_server s) {
             ss->q.clear();
             continue;
         }
-        if (!ss->scan_ev && cudaEventCreateWithFlags(&ss->scan_ev, cudaEventDisableTiming) != cudaSuccess) {
-            ss->scan_ev = nullptr;
+        bool ev_ok = true;
+        for (cudaEvent_t* pe : {&ss->scan_ev, &ss->tail_ev})
+            if (!*pe && cudaEventCreateWithFlags(pe, cudaEventDisableTiming) != cudaSuccess) {
+                *pe = nullptr;
+                ev_ok = false;
+            }
+        // the session's set-up ran on its first stream: later streams wait for it
+        if (ev_ok) ev_ok = cudaEventRecord(ss->tail_ev, s->pool[(size_t)ss->stream_idx]) == cudaSuccess;
+        if (!ev_ok) {
             loc_destroy(h);
             ss->state = LOC_SESSION_FAILED;
             for (SrvMsg& m : ss->q) delete m.scan;
@@ -355,6 +370,7 @@ bool membership(loc_server s) {
             continue;
         }
         ss->h = h;
+        ss->tail_valid = true;
         ss->state = LOC_SESSION_ACTIVE;
         s->used_bytes += ss->bytes;
     }
@@ -410,18 +426,24 @@ struct TickWork {
     bool empty() const { return props.empty() && scans.empty() && plain.empty() && absorbed == 0; }
 };
 
-// Takes this tick's work from the queues (under the lock).  Worker thread.
+// Takes this tick's work from the queues (under the lock).  Worker thread.  Per session, in
+// message order: odometry the gate absorbs, at most one scan, then odometry up to the first
+// propagation.  A scan that follows the tick's propagation waits for the next tick, so the
+// tick's scans can run before its propagations (launch).
 void gather(loc_server s, TickWork& t) {
     for (SrvSession* ss : s->live) {
-        bool prop = false;
+        bool prop = false, scanned = false;
         while (!ss->q.empty()) {
             SrvMsg& m = ss->q.front();
             if (m.kind == MSG_SCAN) {
-                if (!prop) {
-                    t.scans.emplace_back(ss, m);
-                    ss->q.pop_front();
-                }
-                break;
+                if (prop || scanned) break;
+                // the tick's later odometry reaches the gate (and the heading) before the scan
+                // is launched: the scan keeps the heading its own position in the stream gives
+                if (ss->h) m.theta = ss->h->theta;
+                t.scans.emplace_back(ss, m);
+                ss->q.pop_front();
+                scanned = true;
+                continue;
             }
             if (!s->prm.batching) {                  // loc_step applies the gate itself
                 t.plain.emplace_back(ss, m);
@@ -443,7 +465,87 @@ void gather(loc_server s, TickWork& t) {
     }
 }
 
-bool launch(loc_server s, TickWork& t) {
+// Moves a session's pool-stream work to stream k, after its work on the previous stream.
+cudaError_t bind_stream(loc_server s, SrvSession* ss, int k) {
+    if (ss->stream_idx == k) return cudaSuccess;
+    cudaError_t e = cudaSuccess;
+    if (ss->tail_valid) e = cudaStreamWaitEvent(s->pool[(size_t)k], ss->tail_ev, 0);
+    ss->stream_idx = k;
+    ss->h->stream = s->pool[(size_t)k];
+    return e;
+}
+
+// The tick's scan updates: distinct sessions, spread over the pool streams in turn, each after
+// the batch that last propagated its session.  Their host work (direction tables, uploads,
+// launches) runs on up to kScanThreads threads.
+bool launch_scans(loc_server s, TickWork& t) {
+    std::atomic<int> next{0};
+    std::atomic<bool> bad{false};
+    auto scan_worker = [&]() {
+        cudaSetDevice(s->device);
+        for (;;) {
+            const int i = next.fetch_add(1);
+            if (i >= (int)t.scans.size() || bad.load()) return;
+            SrvSession* ss = t.scans[(size_t)i].first;
+            SrvScan* sc = t.scans[(size_t)i].second.scan;
+            // the tick's scans take the streams in turn
+            cudaError_t we = bind_stream(s, ss, (int)((s->scan_rr + (size_t)i) % s->pool.size()));
+            cudaStream_t ps = s->pool[(size_t)ss->stream_idx];
+            ss->scan_tick = s->tick;
+            if (we == cudaSuccess && s->prm.batching && ss->last_prop_tick >= 0)
+                we = cudaStreamWaitEvent(ps, s->ring[ss->last_prop_tick % kRing], 0);
+            cudaEvent_t ev0 = we == cudaSuccess ? get_event(s) : nullptr;
+            if (we == cudaSuccess) we = ev0 ? cudaEventRecord(ev0, ps) : cudaErrorMemoryAllocation;
+            if (we != cudaSuccess) {
+                set_failed(s, std::string("scan ordering: ") + cudaGetErrorString(we));
+                bad = true;
+                return;
+            }
+            // the heading when the scan arrived; the session belongs to this helper until the
+            // scan phase ends, and no other work of the tick reads its heading before then
+            const double theta_now = ss->h->theta;
+            ss->h->theta = t.scans[(size_t)i].second.theta;
+            const loc_status st = loc_lidar_update(ss->h, sc->ranges.data(), (int)sc->ranges.size(), sc->angle_min,
+                                                   sc->angle_inc, sc->r_max, sc->stride, sc->sigma_r);
+            ss->h->theta = theta_now;
+            delete sc;
+            t.scans[(size_t)i].second.scan = nullptr;
+            if (st < 0) {
+                set_failed(s, std::string("loc_lidar_update: ") + loc_last_error(ss->h));
+                bad = true;
+                return;
+            }
+            cudaEvent_t ev = get_event(s);
+            if (!ev || cudaEventRecord(ev, ps) != cudaSuccess || cudaEventRecord(ss->tail_ev, ps) != cudaSuccess ||
+                (s->prm.batching && cudaEventRecord(ss->scan_ev, ps) != cudaSuccess)) {
+                set_failed(s, "event record failed");
+                bad = true;
+                return;
+            }
+            ss->scan_pending = true;
+            ss->tail_valid = true;
+            {
+                std::lock_guard<std::mutex> ls(s->mu_st);
+                s->n_scans += 1;
+            }
+            push_inflight(s, ev, MSG_SCAN, std::vector<double>{t.scans[(size_t)i].second.t_arr}, ev0, WORK_SCAN);
+        }
+    };
+    if (!t.scans.empty()) {
+        const auto ts = std::chrono::steady_clock::now();
+        if (t.scans.size() == 1 || s->pool_threads.empty()) scan_worker();
+        else pool_run(s, scan_worker);
+        for (auto& pm : t.scans) delete pm.second.scan;     // left over after a failure
+        if (bad.load()) return false;
+        s->scan_rr += t.scans.size();
+        std::lock_guard<std::mutex> ls(s->mu_st);
+        s->host_scan_ms += ms_since(ts);
+    }
+    return true;
+}
+
+// The tick's propagations in one batched launch, after the scan updates of their sessions.
+bool launch_batch(loc_server s, TickWork& t) {
     cudaError_t e = cudaSuccess;
     if (!t.props.empty()) {
         // the batch follows the scan updates of its sessions launched since their last batch
@@ -463,7 +565,7 @@ bool launch(loc_server s, TickWork& t) {
             for (auto& pr : t.props) {
                 loc_session* h = pr.first->h;
                 const int ci = pr.first->ci;
-                ht[ci] = BatchTick{h->cur, 0, step_seed(h), 0};
+                ht[ci] = BatchTick{h->cur, 0, 0, 0};
                 shift_table(h, batch_shift_slot(&s->core, hs, ci));
                 active[(size_t)ci] = 1;
                 arr.push_back(pr.second);
@@ -496,9 +598,25 @@ bool launch(loc_server s, TickWork& t) {
         }
         push_inflight(s, ev, MSG_ODO, std::move(arr), ev0, WORK_BATCH, bytes);
     }
+    return true;
+}
+
+// The plain path: one loc_step per odometry message; a session's messages of the tick run on one
+// pool stream (the next in turn, or the one its scan of the tick took).
+bool launch_plain(loc_server s, TickWork& t) {
     const auto tp = std::chrono::steady_clock::now();
+    SrvSession* prev = nullptr;
     for (auto& pm : t.plain) {                        // the plain path: one loc_step each
         SrvSession* ss = pm.first;
+        if (ss != prev && ss->scan_tick != s->tick) {
+            // a session's first message of the tick: the next stream in turn, unless the
+            // session's scan of this tick already chose one (its steps follow the scan there)
+            if (bind_stream(s, ss, (int)(s->plain_rr++ % s->pool.size())) != cudaSuccess) {
+                set_failed(s, "stream ordering failed");
+                return false;
+            }
+        }
+        prev = ss;
         cudaEvent_t ev0 = get_event(s);
         if (!ev0 || cudaEventRecord(ev0, s->pool[(size_t)ss->stream_idx]) != cudaSuccess) {
             set_failed(s, "event record failed");
@@ -515,6 +633,11 @@ bool launch(loc_server s, TickWork& t) {
                 set_failed(s, "event record failed");
                 return false;
             }
+            if (cudaEventRecord(ss->tail_ev, s->pool[(size_t)ss->stream_idx]) != cudaSuccess) {
+                set_failed(s, "event record failed");
+                return false;
+            }
+            ss->tail_valid = true;
             const double hw = (double)ss->p.H * ss->p.W;
             {
                 std::lock_guard<std::mutex> ls(s->mu_st);
@@ -536,61 +659,12 @@ bool launch(loc_server s, TickWork& t) {
         std::lock_guard<std::mutex> ls(s->mu_st);
         s->host_plain_ms += ms_since(tp);
     }
-    // Scan updates: distinct sessions on their own streams.  Their host work (direction tables,
-    // uploads, launches) runs on up to kScanThreads threads.
-    std::atomic<int> next{0};
-    std::atomic<bool> bad{false};
-    auto scan_worker = [&]() {
-        cudaSetDevice(s->device);
-        for (;;) {
-            const int i = next.fetch_add(1);
-            if (i >= (int)t.scans.size() || bad.load()) return;
-            SrvSession* ss = t.scans[(size_t)i].first;
-            SrvScan* sc = t.scans[(size_t)i].second.scan;
-            cudaStream_t ps = s->pool[(size_t)ss->stream_idx];
-            cudaError_t we = cudaSuccess;
-            if (s->prm.batching && ss->last_prop_tick >= 0)
-                we = cudaStreamWaitEvent(ps, s->ring[ss->last_prop_tick % kRing], 0);
-            cudaEvent_t ev0 = we == cudaSuccess ? get_event(s) : nullptr;
-            if (we == cudaSuccess) we = ev0 ? cudaEventRecord(ev0, ps) : cudaErrorMemoryAllocation;
-            if (we != cudaSuccess) {
-                set_failed(s, std::string("scan ordering: ") + cudaGetErrorString(we));
-                bad = true;
-                return;
-            }
-            const loc_status st = loc_lidar_update(ss->h, sc->ranges.data(), (int)sc->ranges.size(), sc->angle_min,
-                                                   sc->angle_inc, sc->r_max, sc->stride, sc->sigma_r);
-            delete sc;
-            t.scans[(size_t)i].second.scan = nullptr;
-            if (st < 0) {
-                set_failed(s, std::string("loc_lidar_update: ") + loc_last_error(ss->h));
-                bad = true;
-                return;
-            }
-            cudaEvent_t ev = get_event(s);
-            if (!ev || cudaEventRecord(ev, ps) != cudaSuccess ||
-                (s->prm.batching && cudaEventRecord(ss->scan_ev, ps) != cudaSuccess)) {
-                set_failed(s, "event record failed");
-                bad = true;
-                return;
-            }
-            ss->scan_pending = true;
-            {
-                std::lock_guard<std::mutex> ls(s->mu_st);
-                s->n_scans += 1;
-            }
-            push_inflight(s, ev, MSG_SCAN, std::vector<double>{t.scans[(size_t)i].second.t_arr}, ev0, WORK_SCAN);
-        }
-    };
-    if (!t.scans.empty()) {
-        const auto ts = std::chrono::steady_clock::now();
-        if (t.scans.size() == 1 || s->pool_threads.empty()) scan_worker();
-        else pool_run(s, scan_worker);
-        for (auto& pm : t.scans) delete pm.second.scan;     // left over after a failure
-        if (bad.load()) return false;
-        std::lock_guard<std::mutex> ls(s->mu_st);
-        s->host_scan_ms += ms_since(ts);
-    }
+    return true;
+}
+
+// Scans first: a session's scan in this tick comes before its propagation in message order.
+bool launch(loc_server s, TickWork& t) {
+    if (!launch_scans(s, t) || !launch_batch(s, t) || !launch_plain(s, t)) return false;
     {
         std::lock_guard<std::mutex> ls(s->mu_st);
         s->n_msgs += t.absorbed;
@@ -646,7 +720,7 @@ LOC_API void loc_server_params_default(loc_server_params* p) {
     p->batching = 1;
     p->tile = 0;
     p->use_graph = 1;
-    p->n_streams = 16;
+    p->n_streams = 32;
 }
 
 LOC_API loc_status loc_server_create(const loc_server_params* p, loc_server* out) {
@@ -952,6 +1026,7 @@ LOC_API loc_status loc_server_destroy(loc_server s) {
         for (SrvMsg& m : ss->q) delete m.scan;
         if (ss->h) loc_destroy(ss->h);
         if (ss->scan_ev) cudaEventDestroy(ss->scan_ev);
+        if (ss->tail_ev) cudaEventDestroy(ss->tail_ev);
         delete ss;
     }
     for (cudaEvent_t ev : s->ev_free) cudaEventDestroy(ev);
