@@ -139,11 +139,18 @@ __global__ void __launch_bounds__(kFsWarps * 32) fs_kernel(const float* __restri
         const int j0 = 32 * rb, j = j0 + lane;
         const bool row_ok = j < H;
         float pre[32];                                         // column 32 c + lane of rows j0 ..
+        const bool interior = j0 + 31 < H;                     // every row of the block in the grid
         auto load_chunk = [&](int c) {
             const int col = 32 * c + lane;
+            if (interior && col < W) {
+                const float* src = m + (size_t)j0 * W + col;
 #pragma unroll
-            for (int r = 0; r < 32; ++r)
-                pre[r] = (j0 + r < H && col < W) ? m[(size_t)(j0 + r) * W + col] : 0.0f;
+                for (int r = 0; r < 32; ++r) pre[r] = src[(size_t)r * W];
+            } else {
+#pragma unroll
+                for (int r = 0; r < 32; ++r)
+                    pre[r] = (j0 + r < H && col < W) ? m[(size_t)(j0 + r) * W + col] : 0.0f;
+            }
         };
         auto store_chunk = [&](int c) {
             float* dst = ring + (c % 3) * 32 + lane;
@@ -185,6 +192,8 @@ __global__ void __launch_bounds__(kFsWarps * 32) fs_kernel(const float* __restri
         float e_prev = 0.0f, last = 0.0f;                      // own error at i-1; newest error
         float chunk = 0.0f;                                    // lane L: bnd[rb][t0 + 1 + L]
         bool failed = false;
+        const bool publish = lane == 31 && rb + 1 < nrb;       // the next block reads this row
+        float* bnd_next = publish ? bnd + (size_t)(rb + 1) * W : bnd;
         const int steps = W + 62;
         const int nwin = (steps + 31) / 32;
         int ri = (96 - 2 * lane) % 96;                         // (t - 2 lane) mod 96
@@ -223,6 +232,39 @@ __global__ void __launch_bounds__(kFsWarps * 32) fs_kernel(const float* __restri
                 store_chunk(T);
                 __syncwarp();
                 if (T + 1 < nch) load_chunk(T + 1);
+            }
+            if (interior && t0 >= 62 && t0 + 31 <= W - 2) {
+                // Every lane's column lies in [0, W - 2] for the whole window and every row of the
+                // block is in the grid: no column or row guards, the right neighbour above always
+                // exists, and lane 31 publishes its progress once, after the window.  The same
+                // operations in the same order as the general steps below (0 + x == x exactly,
+                // and chunk is 0 when there is no row above).
+#pragma unroll
+                for (int s = 0; s < 32; ++s) {
+                    const float from_above = __shfl_sync(0xffffffffu, chunk, s);
+                    const float from_left = __shfl_up_sync(0xffffffffu, last, 1);
+                    up_old = up_mid;
+                    up_mid = up_new;
+                    up_new = lane == 0 ? from_above : from_left;
+                    const float v = own[ri];
+                    float E = __fmul_rn(up_old, w1);
+                    E = __fadd_rn(E, __fmul_rn(up_mid, w5));
+                    E = __fadd_rn(E, __fmul_rn(up_new, w3));
+                    E = __fadd_rn(E, __fmul_rn(e_prev, w7));
+                    const float val = __fadd_rn(v, E);
+                    const bool on = val >= 0.5f;
+                    const float err = on ? __fsub_rn(val, 1.0f) : val;
+                    own[ri] = __uint_as_float(on ? 1u : 0u);
+                    e_prev = err;
+                    last = err;
+                    if (publish) bnd_next[t0 + s - 62] = err;
+                    ri = ri == 95 ? 0 : ri + 1;
+                }
+                if (publish) {
+                    __threadfence_block();
+                    ((volatile int*)prog)[rb + 1] = t0 - 30;      // columns 0 .. t0 - 31 written
+                }
+                continue;
             }
 #pragma unroll
             for (int s = 0; s < 32; ++s) {
