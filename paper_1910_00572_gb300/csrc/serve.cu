@@ -533,6 +533,10 @@ bool launch_scans(loc_server s, TickWork& t) {
     };
     if (!t.scans.empty()) {
         const auto ts = std::chrono::steady_clock::now();
+        // the largest maps first, on distinct streams: their dithering chains are the longest
+        std::stable_sort(t.scans.begin(), t.scans.end(), [](const auto& a, const auto& b) {
+            return (size_t)a.first->p.H * a.first->p.W > (size_t)b.first->p.H * b.first->p.W;
+        });
         if (t.scans.size() == 1 || s->pool_threads.empty()) scan_worker();
         else pool_run(s, scan_worker);
         for (auto& pm : t.scans) delete pm.second.scan;     // left over after a failure
