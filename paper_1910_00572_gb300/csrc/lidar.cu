@@ -525,30 +525,45 @@ __global__ void __launch_bounds__(NT) reweight_sums_kernel(const T* __restrict__
     }
 }
 
-// b <- b w factor on the sampled states; the last CTA updates Z by the change of the set's sum.
+// The new values b w factor of the sampled states, all (sample, bin) pairs in parallel: FP64
+// exp and log, rounded to FP32 and written over logL (which they replace for the store below).
+template <typename T>
+__global__ void __launch_bounds__(NT) reweight_values_kernel(const T* __restrict__ B, size_t hw, int K,
+                                                             const int32_t* __restrict__ samples,
+                                                             const int* count_ptr, int cap, float* __restrict__ logL,
+                                                             const unsigned int* maxL, const ReweightScalars* rs) {
+    const double factor = rs->factor;
+    if (!(factor > 0.0)) return;
+    const int n = min(*count_ptr, cap);
+    const double mx = (double)ord2f(*maxL);
+    const size_t total = (size_t)n * K;
+    for (size_t q = (size_t)blockIdx.x * NT + threadIdx.x; q < total; q += (size_t)gridDim.x * NT) {
+        const int s = (int)(q / K), k = (int)(q % K);
+        const size_t at = (size_t)k * hw + samples[s];
+        // the new values sum to the set's old mass, so each is finite and at most that mass
+        const double b = (double)Store<T>::ld(B + at);
+        logL[q] = b > 0.0 ? (float)(factor * exp((double)logL[q] + log(b) - mx)) : 0.0f;
+    }
+}
+
+// Stores the new values (one thread per sampled cell, its bins in order: the BF16 rounding
+// residual runs along theta); the last CTA updates Z by the change of the set's sum.
 template <typename T>
 __global__ void __launch_bounds__(NT) reweight_apply_kernel(T* __restrict__ B, size_t hw, int K,
                                                             const int32_t* __restrict__ samples, const int* count_ptr,
-                                                            int cap, const float* __restrict__ logL,
-                                                            const unsigned int* maxL, ReweightScalars* rs,
-                                                            double* partials, SessionDev* sd) {
+                                                            int cap, const float* __restrict__ vals,
+                                                            ReweightScalars* rs, double* partials, SessionDev* sd) {
     __shared__ double red[NT / 32];
     const double factor = rs->factor;
     const int n = min(*count_ptr, cap);
-    const double mx = (double)ord2f(*maxL);
     KahanF acc;
     if (factor > 0.0) {
-        // one thread per sampled cell, its bins in order: the BF16 rounding residual runs along theta
         for (int s = blockIdx.x * NT + threadIdx.x; s < n; s += gridDim.x * NT) {
             const size_t cell = (size_t)samples[s];
+            const float* v = vals + (size_t)s * K;
             float res = 0.0f;
-            for (int k = 0; k < K; ++k) {
-                const size_t at = (size_t)k * hw + cell;
-                // the new values sum to the set's old mass, so each is finite and at most that mass
-                const double b = (double)Store<T>::ld(B + at);
-                const double v = b > 0.0 ? factor * exp((double)logL[(size_t)s * K + k] + log(b) - mx) : 0.0;
-                acc.add(store_diffused<T>(B + at, (float)v, res));
-            }
+#pragma unroll 4
+            for (int k = 0; k < K; ++k) acc.add(store_diffused<T>(B + (size_t)k * hw + cell, v[k], res));
         }
     }
     const double bt = block_sum<NT>(acc.value(), red);
@@ -680,9 +695,11 @@ cudaError_t launch_score_reweight(void* B, int storage, const uint8_t* trav, con
                                                                        maxL)));
     LOC_DISPATCH(storage, (reweight_sums_kernel<T><<<nb, NT, 0, st>>>((const T*)B, hw, K, samples, count, cap, logL,
                                                                         maxL, partials, r)));
+    LOC_DISPATCH(storage, (reweight_values_kernel<T><<<nb, NT, 0, st>>>((const T*)B, hw, K, samples, count, cap, logL,
+                                                                          maxL, r)));
     const unsigned int nb_cells = grid_for((size_t)cap, half > 0 ? half : 1);
     LOC_DISPATCH(storage, (reweight_apply_kernel<T><<<nb_cells, NT, 0, st>>>((T*)B, hw, K, samples, count, cap, logL,
-                                                                               maxL, r, partials, sd)));
+                                                                               r, partials, sd)));
     return cudaGetLastError();
 }
 
