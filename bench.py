@@ -215,6 +215,28 @@ def profiled_traffic(wl, args):
     return int(val.group(1))
 
 
+def served_traffic(alg_bytes_per_launch):
+    """DRAM bytes per batched launch of the served workload: the ratio of DRAM to algorithmic
+    bytes that the committed ncu summary measured on a batched launch (batch64: the same kernel
+    source, a smaller workload that ncu can capture in full), times this run's algorithmic bytes
+    per launch, only while the batched kernel's source is the one that was profiled (else None).
+    The kernel reads each input plane once and writes each output once, so its traffic grows in
+    proportion to the cell-updates of the launch."""
+    import hashlib
+    import re
+    try:
+        text = open(os.path.join(ROOT, "profiles", "batch_kernel_batch64_bf16.md")).read()
+        csrc = os.path.join(ROOT, "paper_1910_00572_gb300", "csrc")
+        src = b"".join(open(os.path.join(csrc, f), "rb").read() for f in ("tiled_common.cuh", "batch.cu"))
+    except OSError:
+        return None
+    sha = re.search(r"source_sha256:\s*([0-9a-f]+)", text)
+    ratio = re.search(r"dram_per_algorithmic_byte:\s*([0-9.]+)", text)
+    if not sha or not ratio or sha.group(1) != hashlib.sha256(src).hexdigest() or not alg_bytes_per_launch:
+        return None
+    return float(ratio.group(1)) * alg_bytes_per_launch
+
+
 # ----------------------------------------------------------------------------- arms
 
 def run_reference(args, wl, occ, walk, ws, rank):
@@ -875,7 +897,12 @@ def run_headline(args, wl, ws, rank, local):
                       "its propagation",
         "runs": res,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak if achieved else None, "traffic": None,
+                     "frac": achieved / peak if achieved else None,
+                     "traffic": served_traffic(cap["device_bytes"]["batch"] / max(bd["n_batches"], 1)),
+                     "traffic_is": "DRAM bytes per launch: the DRAM / algorithmic byte ratio of a batched "
+                                   "launch captured by ncu (batch64, same kernel source: "
+                                   "profiles/batch_kernel_batch64_bf16.md) times this run's algorithmic bytes "
+                                   "per launch",
                      "kernel": "batch (persistent propagation of every session the tick propagates)",
                      "algorithmic_bytes_per_launch": cap["device_bytes"]["batch"] / max(bd["n_batches"], 1),
                      "launches": bd["n_batches"], "peak_source": src,
@@ -886,7 +913,9 @@ def run_headline(args, wl, ws, rank, local):
                 "path": "loc_server_odometry / loc_server_scan from host arrays (every timed message at once), "
                         "loc_server_drain, then every admitted session's pose read back (loc_argmax); "
                         "host wall clock"},
-        "gpu_launches": bd["n_batches"] + 5 * bd["n_scans"],
+        # a batched launch per tick; per scan update: restart check, belief map, dithering, row
+        # scan, compaction, scoring and the three reweighting kernels
+        "gpu_launches": bd["n_batches"] + 9 * bd["n_scans"],
         "clocks": cap["clocks"],
         "office512_f32": single,
         "office2048_bf16_scans": scans2,

@@ -27,3 +27,12 @@ def test_traffic_is_not_reported_for_other_kernels():
     assert bench.profiled_traffic(wl, SimpleNamespace(tile=3, kernel=0)) is None
     assert bench.profiled_traffic(wl, SimpleNamespace(tile=0, kernel=1)) is None
     assert bench.profiled_traffic(workloads.get("office2048"), SimpleNamespace(tile=0, kernel=0)) is None
+
+
+def test_served_traffic_scales_the_profiled_ratio():
+    """The default line's roofline traffic: the batched kernel's profiled DRAM / algorithmic byte
+    ratio times the run's algorithmic bytes per launch, tied to the profiled source."""
+    t = bench.served_traffic(4.0e10)
+    assert t is not None
+    assert 0.5 * 4.0e10 < t < 1.5 * 4.0e10
+    assert bench.served_traffic(0.0) is None
