@@ -914,8 +914,8 @@ def run_headline(args, wl, ws, rank, local):
                         "loc_server_drain, then every admitted session's pose read back (loc_argmax); "
                         "host wall clock"},
         # a batched launch per tick; per scan update: restart check, belief map, dithering, row
-        # scan, compaction, scoring and the three reweighting kernels
-        "gpu_launches": bd["n_batches"] + 9 * bd["n_scans"],
+        # scan, compaction, scoring and the four reweighting kernels
+        "gpu_launches": bd["n_batches"] + 10 * bd["n_scans"],
         "clocks": cap["clocks"],
         "office512_f32": single,
         "office2048_bf16_scans": scans2,
