@@ -185,3 +185,62 @@ def test_server_rejects_bad_requests():
         assert loc.loc_server_stats(srv)["n_active"] == 1
     finally:
         loc.loc_server_destroy(srv)
+
+
+@pytest.mark.slow
+def test_serve256_sessions_one_served_tick_sampled_against_oracle():
+    """Sessions of the served workload at full size -- the largest (1984 x 1984 x 72, 283 M states),
+    a mid-sized and the smallest -- served together in BF16 the way the benchmark serves them
+    (batched launch, autotuned tile, the 1-cell gate), one odometry message each.  From a belief
+    with sharp peaks set through the session handle, sampled states of each session's propagated
+    tensor are recomputed one by one from the definitions by the oracle (Alg. 1's propagation
+    from the same stored input): each within one BF16 rounding step of its own exact value
+    plus the FP32 error (tests/bounds.py), and the tensor sums to 1."""
+    import bounds
+    from oracle import filter as F
+    from oracle.odometry import Odometry
+    from synth import fields
+    wl = workloads.get("serve256")
+    mix = workloads.make_sessions(wl, 2)
+    order = sorted(range(len(mix)), key=lambda q: -mix[q]["H"] * mix[q]["W"] * mix[q]["K"])
+    picks = [mix[order[0]], mix[order[len(order) // 2]], mix[order[-1]]]
+    u, v, w = 0.043, -0.029, 0.004                    # 1.04 cells: opens the 1-cell gate
+    srv = loc.loc_server_create(loc.loc_server_params_default(hbm_budget_bytes=wl["hbm_budget_gb"] * 1e9,
+                                                              storage="bf16", batching=1, tile=0))
+    try:
+        ids = [loc.loc_server_open(srv, s["occ"], loc.loc_params_default(
+            H=s["H"], W=s["W"], K=s["K"], cell_m=s["cell"], storage="bf16",
+            min_shift_cells=wl["min_shift_cells"], n_samples=wl["n_samples"])) for s in picks]
+        loc.loc_server_drain(srv, 300.0)
+        befores = []
+        for q, (s, sid) in enumerate(zip(picks, ids)):
+            state, h = loc.loc_server_session(srv, sid)
+            assert state == loc.LOC_SESSION_ACTIVE
+            loc.loc_set_belief(h, fields.belief_like(s["occ"], s["K"], seed=31 + q, dtype=np.float32))
+            befores.append(loc.loc_belief(h))          # the stored BF16 input, normalised
+        loc.loc_server_odometry(srv, ids, [u] * len(ids), [v] * len(ids), [w] * len(ids))
+        loc.loc_server_drain(srv, 300.0)
+        assert loc.loc_server_stats(srv)["n_propagations"] == len(ids)
+        rng = np.random.default_rng(12)
+        for s, sid, before in zip(picks, ids, befores):
+            _, h = loc.loc_server_session(srv, sid)
+            got = loc.loc_belief(h)
+            Z = loc.loc_stats(h)["last_Z"]
+            K, H, W = s["K"], s["H"], s["W"]
+            odo = Odometry(K, s["cell"])
+            odo.add(u, v, w)
+            M = F.traversability(s["occ"])
+            g = F.motion_kernel(wl["sigma_xy_cells"], wl["sigma_theta_bins"])
+            idx = [(int(rng.integers(K)), int(rng.integers(H)), int(rng.integers(W))) for _ in range(1500)]
+            for qq in np.argpartition(before.reshape(-1), -4)[-4:]:
+                k, rem = divmod(int(qq), H * W)
+                j, i = rem // W, rem % W
+                idx += [(k, jj, ii) for jj in range(max(0, j - 2), min(H, j + 3))
+                        for ii in range(max(0, i - 2), min(W, i + 3))]
+            T = F.propagate_at(before.astype(np.float64), M, odo.shifts(), g, idx)
+            gotT = np.array([got[k, j, i] for (k, j, i) in idx], np.float64) * Z
+            bad = np.flatnonzero(np.abs(gotT - T) > bounds.bf16_step_bound(T))
+            assert bad.size == 0, (H, K, [(idx[b], gotT[b], T[b]) for b in bad[:5]])
+            assert abs(got.astype(np.float64).sum() - 1.0) < 1e-4
+    finally:
+        loc.loc_server_destroy(srv)
