@@ -90,16 +90,19 @@ typedef struct {
                                   cannot join a batch. */
 } loc_params;
 
-#define LOC_TILE_CONFIGS 16    /* tile rows x 64 columns, threads: 1: 32 (256), 2: 16 (256),
+#define LOC_TILE_CONFIGS 18    /* tile rows x 64 columns, threads: 1: 32 (256), 2: 16 (256),
                                   3: 16 (128), 4: 16 (512), 5: 32 (512); warp-specialised
                                   producer/consumer pipelines: 6: 16 (256), 7: 8 (256),
                                   13: 14 (256); with cells paired 32 columns apart on the
                                   packed FP32 pipe: 8: 16 (128), 9: 16 (256), 10: 32 (256),
                                   11: 8 (128), 12: 16 (128, 2 raw stages); warp-specialised
                                   with the producers split into S-pass and X-pass warps:
-                                  14: 16 (320), 15: 14 (288), 16: 28 (512, one CTA per SM).
+                                  14: 16 (320), 15: 14 (288), 16: 28 (512, one CTA per SM);
+                                  3 and 2 as a software pipeline over the planes (one CTA
+                                  barrier per plane): 17: 16 (128), 18: 16 (256).
                                   With tile = 0 a grid of at least 8 sixteen-row tiles per SM
-                                  takes 3; smaller grids take whichever of 6, 15 and 16 gives
+                                  takes 17 (FP32) or 3 (16-bit storage); smaller grids take
+                                  whichever of 6, 15 and 16 gives
                                   the busiest SM the fewest rows to blur (tile rows + 4 per
                                   tile it runs). */
 

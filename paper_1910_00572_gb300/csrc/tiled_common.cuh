@@ -25,11 +25,12 @@ constexpr int NWRAP = 2 * RT;          // 6 planes kept for the circular wrap
 constexpr unsigned long long kWaitNs = 200ull * 1000 * 1000;   // bounded mbarrier wait
 
 // TH tile rows, MR rows per P-pass thread (2 columns each), SR S-pass rows per item, XW
-// X-pass columns per item, NSTAGE raw stages, MINB CTAs per SM asked of the compiler.
-template <int TH_, int MR_, int SR_, int XW_, int NSTAGE_, int MINB_>
+// X-pass columns per item, NSTAGE raw stages, MINB CTAs per SM asked of the compiler.  PIPE
+// runs the passes as a software pipeline over the planes (run_tile_pipe).
+template <int TH_, int MR_, int SR_, int XW_, int NSTAGE_, int MINB_, bool PIPE_ = false>
 struct Cfg {
     static constexpr int TH = TH_, MR = MR_, SR = SR_, XW = XW_, NSTAGE = NSTAGE_, MINB = MINB_;
-    static constexpr bool PAIRS = false;
+    static constexpr bool PAIRS = false, PIPE = PIPE_;
     static constexpr int CR = TH;                  // rows the P-pass threads cover
     static constexpr int NT = (TH / MR) * 32;
     static constexpr int XR = TH + 2 * R;          // rows of S and X
@@ -73,6 +74,19 @@ struct Smem {
     float X[C::XR][XW_PITCH];
     float wrap[NWRAP][C::CR][TW];
     float mk[C::XR][MW];                     // 1 free, 0 occupied / off-grid
+    unsigned long long bar[C::NSTAGE];
+    double red[C::NT / 32];
+};
+
+// The pipelined tile body's shared memory: S and X double-buffered (the S-pass of plane p, the
+// X-pass of plane p - 1 and the P-pass of plane p - 2 share one iteration).
+template <typename T, typename C>
+struct SmemPipe {
+    T raw[C::NSTAGE][raw_stride<T, C>()];
+    float S[2][C::XR][SW];
+    float X[2][C::XR][XW_PITCH];
+    float wrap[NWRAP][C::CR][TW];
+    float mk[C::XR][MW];
     unsigned long long bar[C::NSTAGE];
     double red[C::NT / 32];
 };
@@ -708,6 +722,133 @@ __device__ __forceinline__ bool run_tile(Smem<T, C>& sm, const TileJob& j, unsig
     }
     p_stop = p;
     // the wrap planes and the X plane are read again by the next tile's first passes
+    __syncthreads();
+    return !failed;
+}
+
+// run_tile as a software pipeline over the planes: iteration it runs the S-pass of plane it,
+// the X-pass of plane it - 1 and the P-pass of plane it - 2 (each from the buffers the previous
+// iteration wrote) and ends with one CTA barrier, where run_tile has two per plane.  The passes
+// and their operation order are run_tile's, so the results are bit-identical to the
+// synchronous configuration with the same tile.  Same contract as run_tile.
+template <typename T, typename C>
+__device__ __forceinline__ bool run_tile_pipe(SmemPipe<T, C>& sm, const TileJob& j, unsigned int gp0, KahanF2& acc,
+                                              int& p_stop, int& next_issue) {
+    constexpr int NT = C::NT, MR = C::MR, NSTAGE = C::NSTAGE, XR = C::XR;
+    constexpr uint32_t kBoxBytes = C::RAW_H * BW * sizeof(T);
+    const int tid = threadIdx.x;
+    const int H = j.o.H, W = j.o.W, K = j.o.K;
+    const int ty0 = j.ty0, tx0 = j.tx0;
+    const int reinit = j.reinit;
+
+    for (int q = tid; q < XR * MW; q += NT) {
+        const int y = q / MW, c = q % MW;
+        const int gy = ty0 - R + y, gx = tx0 - R + c;
+        sm.mk[y][c] = (gy >= 0 && gy < H && gx >= 0 && gx < W && j.trav[(size_t)gy * W + gx]) ? 1.0f : 0.0f;
+    }
+    __syncthreads();
+    auto issue = [&](int q) {       // TMA of plane q (thread 0 only)
+        const Shift s = j.sh[q];
+        int x_al, xo;
+        box_x<T>(tx0, s, x_al, xo);
+        const unsigned int g = gp0 + (unsigned int)q;
+        unsigned long long* b = &sm.bar[g % NSTAGE];
+        bar_expect(b, kBoxBytes);
+        tma_load(&sm.raw[g % NSTAGE][0], j.tmap, b, x_al, ty0 - R + s.oy, q);
+    };
+    next_issue = 0;
+    if (!reinit) {
+        next_issue = NSTAGE < K ? NSTAGE : K;
+        if (tid == 0) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            for (int q = 0; q < next_issue; ++q) issue(q);
+        }
+    }
+    const int cp = tid % 32, rg = tid / 32;
+    const int r0 = MR * rg, gxp = tx0 + 2 * cp;
+    f2 cs[MR];
+#pragma unroll
+    for (int rr = 0; rr < MR; ++rr) {
+        const int gy = ty0 + r0 + rr;
+        float c0 = 0.0f, c1 = 0.0f;
+        if (gy < H && gxp < W) {
+            c0 = j.corr[(size_t)gy * W + gxp] * j.in_scale;
+            c1 = j.corr[(size_t)gy * W + gxp + 1] * j.in_scale;
+        }
+        cs[rr] = pk(c0, c1);
+    }
+    Taps2 tp;
+    tp.g0 = pk(j.g0, j.g0);
+    tp.g1 = pk(j.g1, j.g1);
+    tp.g2 = pk(j.g2, j.g2);
+#pragma unroll
+    for (int d = 0; d < RING; ++d) tp.gt[d] = pk(j.gt[d], j.gt[d]);
+    f2 ring[RING][MR], res[MR];
+#pragma unroll
+    for (int d = 0; d < RING; ++d)
+#pragma unroll
+        for (int k = 0; k < MR; ++k) ring[d][k] = 0ull;
+#pragma unroll
+    for (int k = 0; k < MR; ++k) res[k] = 0ull;
+    const PCtx<T> pc = p_ctx<T, C>(j.o, r0, ty0, gxp);
+    const SItem si = s_item<C>(tid);
+    const XItem xi = x_item<C>(tid);
+    int failed = 0;
+    int ph = 0;                                         // (it - 2) mod RING: the P-pass's ring slot
+    int it = 0;
+    for (; it < K + NWRAP + 2; ++it) {
+        const int ps = it, px = it - 1, pp = it - 2;
+        if (ps < K) {
+            const unsigned int g = gp0 + (unsigned int)ps;
+            const int stage = g % NSTAGE;
+            const Shift s = j.sh[ps];
+            int x_al, xo;
+            box_x<T>(tx0, s, x_al, xo);
+            if (reinit) {
+                // the uniform input, written where TMA would have put the tile (M as 0/1); every
+                // thread takes this branch (the flag is per launch)
+                const int y0 = ty0 - R + s.oy;
+                for (int q = tid; q < C::RAW_H * BW; q += NT) {
+                    const int y = q / BW, c = q % BW;
+                    const int gy = y0 + y, gx = x_al + c;
+                    float v = 0.0f;
+                    if (gy >= 0 && gy < H && gx >= 0 && gx < W) v = (float)j.trav[(size_t)gy * W + gx];
+                    sm.raw[stage][y * BW + c] = T(v);
+                }
+                __syncthreads();
+            } else if (!bar_wait(&sm.bar[stage], (g / NSTAGE) & 1u)) {
+                failed = 1;
+            }
+            if (!failed) s_pass_any<T, C>(sm.raw[stage], &sm.mk[0][0], &sm.S[ps & 1][0][0], si, xo, s.fx, s.fy);
+        }
+        if (px >= 0 && px < K && !failed) x_pass<C>(&sm.S[px & 1][0][0], &sm.X[px & 1][0][0], xi, j.g0, j.g1, j.g2);
+        if (pp >= 0 && !failed) {
+            const float (*X)[XW_PITCH] = sm.X[pp & 1];
+            switch (ph) {
+                case 0: p_pass<T, C, 0>(X, sm.wrap, pc, K, tp, ring, cs, res, pp, r0, cp, acc); break;
+                case 1: p_pass<T, C, 1>(X, sm.wrap, pc, K, tp, ring, cs, res, pp, r0, cp, acc); break;
+                case 2: p_pass<T, C, 2>(X, sm.wrap, pc, K, tp, ring, cs, res, pp, r0, cp, acc); break;
+                case 3: p_pass<T, C, 3>(X, sm.wrap, pc, K, tp, ring, cs, res, pp, r0, cp, acc); break;
+                case 4: p_pass<T, C, 4>(X, sm.wrap, pc, K, tp, ring, cs, res, pp, r0, cp, acc); break;
+                case 5: p_pass<T, C, 5>(X, sm.wrap, pc, K, tp, ring, cs, res, pp, r0, cp, acc); break;
+                default: p_pass<T, C, 6>(X, sm.wrap, pc, K, tp, ring, cs, res, pp, r0, cp, acc); break;
+            }
+            ph = ph == RING - 1 ? 0 : ph + 1;
+        }
+        // S of plane ps, X of plane px and the P-pass's reads of X are done everywhere
+        if (__syncthreads_or(failed)) {
+            failed = 1;
+            break;
+        }
+        if (!reinit && ps < K && ps + NSTAGE < K) {   // the stage of plane ps takes plane ps + NSTAGE
+            if (tid == 0) {
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                issue(ps + NSTAGE);
+            }
+            next_issue = ps + NSTAGE + 1;
+        }
+    }
+    p_stop = it < K ? it : K;
     __syncthreads();
     return !failed;
 }

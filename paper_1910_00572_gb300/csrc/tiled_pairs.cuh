@@ -36,7 +36,7 @@ constexpr int XPW = 68;                // X row pitch in floats (34 pairs; 4 mod
 template <int TH_, int MR_, int SR_, int XP_, int NSTAGE_, int MINB_>
 struct PCfg {
     static constexpr int TH = TH_, MR = MR_, SR = SR_, XP = XP_, NSTAGE = NSTAGE_, MINB = MINB_;
-    static constexpr bool PAIRS = true;
+    static constexpr bool PAIRS = true, PIPE = false;
     static constexpr int NT = (TH / MR) * 32;
     static constexpr int XR = TH + 2 * R;
     static constexpr int RAW_H = XR + 1;

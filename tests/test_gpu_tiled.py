@@ -45,7 +45,7 @@ SHAPES = [
 ]
 
 
-@pytest.mark.parametrize("tile", list(range(1, 17)))
+@pytest.mark.parametrize("tile", list(range(1, 19)))
 @pytest.mark.parametrize("H,W,K,mot", SHAPES, ids=[f"{s[0]}x{s[1]}x{s[2]}" for s in SHAPES])
 def test_tiled_matches_oracle_and_generic(H, W, K, mot, tile):
     rng = np.random.default_rng(H * 7 + W * 3 + K)
@@ -76,7 +76,7 @@ def test_tiled_matches_oracle_and_generic(H, W, K, mot, tile):
         loc.loc_destroy(hg)
 
 
-@pytest.mark.parametrize("tile", [1, 3, 6, 8, 13, 14, 15, 16])
+@pytest.mark.parametrize("tile", [1, 3, 6, 8, 13, 14, 15, 16, 17])
 def test_largest_theta_count(tile):
     """K = LOC_MAX_K (256 bins): the theta ring and the wrap planes at the largest size."""
     H, W, K = 20, 72, 256
@@ -139,7 +139,7 @@ def test_tiled_is_refused_where_it_does_not_apply():
     with pytest.raises(loc.LocError):
         make(np.zeros((32, 32), np.uint8), 16, 0.1, sigma_xy_cells=1.0)
     with pytest.raises(loc.LocError):
-        make(np.zeros((32, 32), np.uint8), 16, 0.1, tile=17)   # beyond LOC_TILE_CONFIGS
+        make(np.zeros((32, 32), np.uint8), 16, 0.1, tile=19)   # beyond LOC_TILE_CONFIGS
 
 
 @pytest.mark.parametrize("storage", ["bf16", "f16"])
@@ -184,6 +184,36 @@ def test_split_producers_are_bit_identical(packed, scalar, storage):
     hp = make(occ, K, 0.05, tile=packed, storage=storage)
     hs = make(occ, K, 0.05, tile=scalar, storage=storage)
     try:
+        loc.loc_set_belief(hp, b)
+        loc.loc_set_belief(hs, b)
+        for (u, v, w) in [(0.013, -0.041, 0.05), (0.07, 0.02, -0.1), (-0.11, 0.09, 0.0)]:
+            loc.loc_step(hp, u, v, w)
+            loc.loc_step(hs, u, v, w)
+            assert np.array_equal(loc.loc_belief(hp), loc.loc_belief(hs))
+            assert loc.loc_stats(hp)["last_Z"] == loc.loc_stats(hs)["last_Z"]
+    finally:
+        loc.loc_destroy(hp)
+        loc.loc_destroy(hs)
+
+
+@pytest.mark.parametrize("storage", ["f32", "bf16", "f16"])
+@pytest.mark.parametrize("piped,plain", [(17, 3), (18, 2)])
+def test_pipelined_tiles_are_bit_identical(piped, plain, storage):
+    """The software-pipelined configurations (the S-pass of plane p, the X-pass of p - 1 and the
+    P-pass of p - 2 between one barrier) run the same passes on the same cells as the synchronous
+    configuration with the same tile: bit-identical tensors and normalisers, step after step,
+    including a restart read from the map."""
+    H, W, K = 75, 200, 20
+    rng = np.random.default_rng(piped)
+    occ = (rng.random((H, W)) < 0.15).astype(np.uint8)
+    b = fields.belief_like(occ, K, seed=piped, dtype=np.float32)
+    hp = make(occ, K, 0.05, tile=piped, storage=storage)
+    hs = make(occ, K, 0.05, tile=plain, storage=storage)
+    try:
+        for (u, v, w) in [(0.02, 0.01, 0.0)]:          # the first step reads the uniform start
+            loc.loc_step(hp, u, v, w)
+            loc.loc_step(hs, u, v, w)
+            assert np.array_equal(loc.loc_belief(hp), loc.loc_belief(hs))
         loc.loc_set_belief(hp, b)
         loc.loc_set_belief(hs, b)
         for (u, v, w) in [(0.013, -0.041, 0.05), (0.07, 0.02, -0.1), (-0.11, 0.09, 0.0)]:
