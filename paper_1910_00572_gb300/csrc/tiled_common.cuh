@@ -604,49 +604,48 @@ struct TileJob {
     int ty0, tx0;
 };
 
-// gp0: planes this CTA has already loaded through the mbarriers (their phases continue).
-// Returns false when a bounded wait gave up; p_stop / next_issue then bound the copies that
-// may still be in flight.
-template <typename T, typename C>
-__device__ __forceinline__ bool run_tile(Smem<T, C>& sm, const TileJob& j, unsigned int gp0, KahanF2& acc,
-                                         int& p_stop, int& next_issue) {
-    constexpr int NT = C::NT, MR = C::MR, NSTAGE = C::NSTAGE, XR = C::XR;
+// TMA of plane q of the tile into its raw stage (thread 0 only); gp0 as for run_tile.
+template <typename T, typename C, typename SM>
+__device__ __forceinline__ void issue_plane(SM& sm, const TileJob& j, unsigned int gp0, int q) {
     constexpr uint32_t kBoxBytes = C::RAW_H * BW * sizeof(T);
-    const int tid = threadIdx.x;
-    const int H = j.o.H, W = j.o.W, K = j.o.K;
-    const int ty0 = j.ty0, tx0 = j.tx0;
-    const int reinit = j.reinit;
+    const Shift s = j.sh[q];
+    int x_al, xo;
+    box_x<T>(j.tx0, s, x_al, xo);
+    const unsigned int g = gp0 + (unsigned int)q;
+    unsigned long long* b = &sm.bar[g % C::NSTAGE];
+    bar_expect(b, kBoxBytes);
+    tma_load(&sm.raw[g % C::NSTAGE][0], j.tmap, b, x_al, j.ty0 - R + s.oy, q);
+}
 
-    // map mask over the halo region: rows ty0-2 .., cols tx0-2 ..
-    for (int q = tid; q < XR * MW; q += NT) {
+// The start of a synchronous tile: the map mask over the halo region (rows ty0-2 .., cols
+// tx0-2 ..) into shared memory, and the first planes requested by TMA (none for a restart,
+// which reads M).  Returns the number of planes requested.
+template <typename T, typename C, typename SM>
+__device__ __forceinline__ int tile_start(SM& sm, const TileJob& j, unsigned int gp0) {
+    const int H = j.o.H, W = j.o.W, K = j.o.K;
+    for (int q = threadIdx.x; q < C::XR * MW; q += C::NT) {
         const int y = q / MW, c = q % MW;
-        const int gy = ty0 - R + y, gx = tx0 - R + c;
+        const int gy = j.ty0 - R + y, gx = j.tx0 - R + c;
         sm.mk[y][c] = (gy >= 0 && gy < H && gx >= 0 && gx < W && j.trav[(size_t)gy * W + gx]) ? 1.0f : 0.0f;
     }
     __syncthreads();                // the S-passes read the whole mask
-    auto issue = [&](int q) {       // TMA of plane q (thread 0 only)
-        const Shift s = j.sh[q];
-        int x_al, xo;
-        box_x<T>(tx0, s, x_al, xo);
-        const unsigned int g = gp0 + (unsigned int)q;
-        unsigned long long* b = &sm.bar[g % NSTAGE];
-        bar_expect(b, kBoxBytes);
-        tma_load(&sm.raw[g % NSTAGE][0], j.tmap, b, x_al, ty0 - R + s.oy, q);
-    };
-    next_issue = 0;
-    if (!reinit) {
-        next_issue = NSTAGE < K ? NSTAGE : K;
-        if (tid == 0) {
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            for (int q = 0; q < next_issue; ++q) issue(q);
-        }
+    if (j.reinit) return 0;
+    const int n = C::NSTAGE < K ? C::NSTAGE : K;
+    if (threadIdx.x == 0) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        for (int q = 0; q < n; ++q) issue_plane<T, C>(sm, j, gp0, q);
     }
-    const int cp = tid % 32, rg = tid / 32;
-    const int r0 = MR * rg, gxp = tx0 + 2 * cp;
-    f2 cs[MR];
+    return n;
+}
+
+// A P-pass thread's correction times the input scale, for its rows r0 .. r0+MR-1 and columns
+// gxp, gxp+1 (0 outside the grid).
+template <typename C>
+__device__ __forceinline__ void tile_corr(f2 (&cs)[C::MR], const TileJob& j, int r0, int gxp) {
+    const int H = j.o.H, W = j.o.W;
 #pragma unroll
-    for (int rr = 0; rr < MR; ++rr) {
-        const int gy = ty0 + r0 + rr;
+    for (int rr = 0; rr < C::MR; ++rr) {
+        const int gy = j.ty0 + r0 + rr;
         float c0 = 0.0f, c1 = 0.0f;
         if (gy < H && gxp < W) {
             c0 = j.corr[(size_t)gy * W + gxp] * j.in_scale;
@@ -654,12 +653,35 @@ __device__ __forceinline__ bool run_tile(Smem<T, C>& sm, const TileJob& j, unsig
         }
         cs[rr] = pk(c0, c1);
     }
+}
+
+__device__ __forceinline__ Taps2 tile_taps(const TileJob& j) {
     Taps2 tp;
     tp.g0 = pk(j.g0, j.g0);
     tp.g1 = pk(j.g1, j.g1);
     tp.g2 = pk(j.g2, j.g2);
 #pragma unroll
     for (int d = 0; d < RING; ++d) tp.gt[d] = pk(j.gt[d], j.gt[d]);
+    return tp;
+}
+
+// gp0: planes this CTA has already loaded through the mbarriers (their phases continue).
+// Returns false when a bounded wait gave up; p_stop / next_issue then bound the copies that
+// may still be in flight.
+template <typename T, typename C>
+__device__ __forceinline__ bool run_tile(Smem<T, C>& sm, const TileJob& j, unsigned int gp0, KahanF2& acc,
+                                         int& p_stop, int& next_issue) {
+    constexpr int NT = C::NT, MR = C::MR, NSTAGE = C::NSTAGE;
+    const int tid = threadIdx.x;
+    const int H = j.o.H, W = j.o.W, K = j.o.K;
+    const int ty0 = j.ty0, tx0 = j.tx0;
+    const int reinit = j.reinit;
+    next_issue = tile_start<T, C>(sm, j, gp0);
+    const int cp = tid % 32, rg = tid / 32;
+    const int r0 = MR * rg, gxp = tx0 + 2 * cp;
+    f2 cs[MR];
+    tile_corr<C>(cs, j, r0, gxp);
+    const Taps2 tp = tile_taps(j);
     f2 ring[RING][MR], res[MR];
 #pragma unroll
     for (int d = 0; d < RING; ++d)
@@ -703,7 +725,7 @@ __device__ __forceinline__ bool run_tile(Smem<T, C>& sm, const TileJob& j, unsig
             if (!reinit && p + NSTAGE < K) {
                 if (tid == 0) {
                     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                    issue(p + NSTAGE);
+                    issue_plane<T, C>(sm, j, gp0, p + NSTAGE);
                 }
                 next_issue = p + NSTAGE + 1;
             }
@@ -734,55 +756,17 @@ __device__ __forceinline__ bool run_tile(Smem<T, C>& sm, const TileJob& j, unsig
 template <typename T, typename C>
 __device__ __forceinline__ bool run_tile_pipe(SmemPipe<T, C>& sm, const TileJob& j, unsigned int gp0, KahanF2& acc,
                                               int& p_stop, int& next_issue) {
-    constexpr int NT = C::NT, MR = C::MR, NSTAGE = C::NSTAGE, XR = C::XR;
-    constexpr uint32_t kBoxBytes = C::RAW_H * BW * sizeof(T);
+    constexpr int NT = C::NT, MR = C::MR, NSTAGE = C::NSTAGE;
     const int tid = threadIdx.x;
     const int H = j.o.H, W = j.o.W, K = j.o.K;
     const int ty0 = j.ty0, tx0 = j.tx0;
     const int reinit = j.reinit;
-
-    for (int q = tid; q < XR * MW; q += NT) {
-        const int y = q / MW, c = q % MW;
-        const int gy = ty0 - R + y, gx = tx0 - R + c;
-        sm.mk[y][c] = (gy >= 0 && gy < H && gx >= 0 && gx < W && j.trav[(size_t)gy * W + gx]) ? 1.0f : 0.0f;
-    }
-    __syncthreads();
-    auto issue = [&](int q) {       // TMA of plane q (thread 0 only)
-        const Shift s = j.sh[q];
-        int x_al, xo;
-        box_x<T>(tx0, s, x_al, xo);
-        const unsigned int g = gp0 + (unsigned int)q;
-        unsigned long long* b = &sm.bar[g % NSTAGE];
-        bar_expect(b, kBoxBytes);
-        tma_load(&sm.raw[g % NSTAGE][0], j.tmap, b, x_al, ty0 - R + s.oy, q);
-    };
-    next_issue = 0;
-    if (!reinit) {
-        next_issue = NSTAGE < K ? NSTAGE : K;
-        if (tid == 0) {
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            for (int q = 0; q < next_issue; ++q) issue(q);
-        }
-    }
+    next_issue = tile_start<T, C>(sm, j, gp0);
     const int cp = tid % 32, rg = tid / 32;
     const int r0 = MR * rg, gxp = tx0 + 2 * cp;
     f2 cs[MR];
-#pragma unroll
-    for (int rr = 0; rr < MR; ++rr) {
-        const int gy = ty0 + r0 + rr;
-        float c0 = 0.0f, c1 = 0.0f;
-        if (gy < H && gxp < W) {
-            c0 = j.corr[(size_t)gy * W + gxp] * j.in_scale;
-            c1 = j.corr[(size_t)gy * W + gxp + 1] * j.in_scale;
-        }
-        cs[rr] = pk(c0, c1);
-    }
-    Taps2 tp;
-    tp.g0 = pk(j.g0, j.g0);
-    tp.g1 = pk(j.g1, j.g1);
-    tp.g2 = pk(j.g2, j.g2);
-#pragma unroll
-    for (int d = 0; d < RING; ++d) tp.gt[d] = pk(j.gt[d], j.gt[d]);
+    tile_corr<C>(cs, j, r0, gxp);
+    const Taps2 tp = tile_taps(j);
     f2 ring[RING][MR], res[MR];
 #pragma unroll
     for (int d = 0; d < RING; ++d)
@@ -843,7 +827,7 @@ __device__ __forceinline__ bool run_tile_pipe(SmemPipe<T, C>& sm, const TileJob&
         if (!reinit && ps < K && ps + NSTAGE < K) {   // the stage of plane ps takes plane ps + NSTAGE
             if (tid == 0) {
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                issue(ps + NSTAGE);
+                issue_plane<T, C>(sm, j, gp0, ps + NSTAGE);
             }
             next_issue = ps + NSTAGE + 1;
         }
