@@ -60,7 +60,12 @@ typedef enum {
     LOC_ERR_STATE = -5         /* handle is sticky-failed or destroyed */
 } loc_status;
 
-enum { LOC_F32 = 0, LOC_BF16 = 1, LOC_F16 = 2 };   /* belief storage type */
+/* Belief storage type.  Arithmetic is FP32 in every case.  BF16 stores round by error diffusion
+ * along theta: each stored value is one of the two BF16 neighbours of its FP32 value, and the
+ * rounding residual of a cell is carried to its next bin, so a cell's mass over its bins is kept
+ * to within half a unit in the last place.  FP16 stores the belief times 2^14, rounded to
+ * nearest. */
+enum { LOC_F32 = 0, LOC_BF16 = 1, LOC_F16 = 2 };
 enum { LOC_MAP_SUM = 0, LOC_MAP_MAX = 1 };         /* loc_marginal modes */
 
 #define LOC_MAX_K 256          /* orientation bins per session */
