@@ -31,6 +31,7 @@
 
 #include "dda.cuh"
 #include "kernels.h"
+#include "tiled_common.cuh"
 
 namespace loc {
 namespace {
@@ -119,8 +120,33 @@ __global__ void __launch_bounds__(DC) dense_score_kernel(const uint8_t* __restri
         float acc[KC];
 #pragma unroll
         for (int kk = 0; kk < KC; ++kk) acc[kk] = 0.0f;
-        // bins k0 .. k0+KC-1 of every used beam; a chunk past K is guarded (rows stay below r RB + RB)
-        auto beams = [&](auto full) {
+        // bins k0 .. k0+KC-1 of every used beam (rows stay below r RB + RB).  A full chunk runs
+        // bin pairs on the packed FP32 pipe: each lane of a pair is the scalar code's operations
+        // on its own bin in the same order, so the sums are the same bit for bit.
+        if (k0 + KC <= K) {
+            using tiled::f2;
+            f2 acc2[KC / 2];
+#pragma unroll
+            for (int kk = 0; kk < KC / 2; ++kk) acc2[kk] = 0ull;
+            const f2 bias = tiled::pk(-8388608.0f, -8388608.0f);
+            for (int u = 0; u < nu; ++u) {
+                int k1 = sm_q[u] + k0;
+                if (k1 >= K) k1 -= K;
+                const uint8_t* col = Us + sm_r[u] + k1 * DC + t;
+                const f2 zu = tiled::pk(sm_z[u], sm_z[u]);
+#pragma unroll
+                for (int kk = 0; kk < KC; kk += 2) {
+                    const uint32_t q0 = col[kk * DC], q1 = col[(kk + 1) * DC];
+                    // the codes as floats (2^23 + q, exact, minus 2^23)
+                    const f2 qf = tiled::fadd2(tiled::pk(__uint_as_float(0x4B000000u | q0),
+                                                         __uint_as_float(0x4B000000u | q1)), bias);
+                    const f2 d = tiled::fsub2(zu, qf);
+                    acc2[kk / 2] = tiled::ffma2(d, d, acc2[kk / 2]);
+                }
+            }
+#pragma unroll
+            for (int kk = 0; kk < KC; kk += 2) tiled::upk(acc2[kk / 2], acc[kk], acc[kk + 1]);
+        } else {
             for (int u = 0; u < nu; ++u) {
                 int k1 = sm_q[u] + k0;
                 if (k1 >= K) k1 -= K;
@@ -128,7 +154,7 @@ __global__ void __launch_bounds__(DC) dense_score_kernel(const uint8_t* __restri
                 const float zu = sm_z[u];
 #pragma unroll
                 for (int kk = 0; kk < KC; ++kk) {
-                    if (decltype(full)::value || k0 + kk < K) {
+                    if (k0 + kk < K) {
                         const uint32_t q = col[kk * DC];
                         const float qf = __uint_as_float(0x4B000000u | q) - 8388608.0f;
                         const float d = zu - qf;
@@ -136,9 +162,7 @@ __global__ void __launch_bounds__(DC) dense_score_kernel(const uint8_t* __restri
                     }
                 }
             }
-        };
-        if (k0 + KC <= K) beams(std::true_type{});
-        else beams(std::false_type{});
+        }
 #pragma unroll
         for (int kk = 0; kk < KC; ++kk) {
             if (k0 + kk < K && in) {
